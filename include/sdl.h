@@ -1,0 +1,164 @@
+/*
+ * sdl.h - C ABI of the GB300 separable dictionary learning library.
+ *
+ * The library learns a pair dictionary (D1, D2) for 2D signals,
+ * Y_k ~= D1 X_k D2^T with s-sparse X_k, by the Tensor-MOD alternation of
+ * Rusu & Irofti, "Efficient and Parallel Separable Dictionary Learning"
+ * (arXiv 2007.03800): 2D-OMP sparse coding (Sec. III step 1) followed by the
+ * closed-form least-squares dictionary updates of Corollary 1 (D1) and
+ * Result 1 (D2), one iteration being the main loop of Algorithm 1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Y   : float32, p1 x p2 x N, each signal column-major and signals back to
+ *          back: element (a, b, k) at Y[a + p1*b + p1*p2*k].
+ *  - D1  : float32 p1 x n1 column-major (D1[a + p1*i]); D2 likewise p2 x n2.
+ *          Dictionaries passed in are expected to have unit-norm columns
+ *          (the constraint of Eq. (1)); outputs always do.
+ *  - Sparse codes X_k are stored per signal as s_max slots in pick order:
+ *          support[k*s_max + l]  int32 pair index q = i + n1*j  (the column of
+ *                                D2 (x) D1 under column-order vec, Sec. I),
+ *                                -1 in unused slots;
+ *          coef[k*s_max + l]     float32 value of X_k[i, j] (0 in unused slots);
+ *          nnz[k]                int32 number of used slots.
+ *  - Every pointer argument is a DEVICE pointer owned by the caller, unless
+ *    stated otherwise; the library never frees or retains caller memory.
+ *    Buffers must not overlap unless an argument is documented in/out.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream: they return after
+ *    enqueueing.  A negative return value is an argument or launch error
+ *    detected on the host, and then nothing was enqueued.  Errors found on
+ *    the device (non-finite data, a singular normal matrix) are recorded in
+ *    the context and reported by sdl_status().
+ *  - Supported shapes: 1 <= p1, p2 <= 64, p1*p2 <= 1024; n1, n2 >= 1 with
+ *    (n1, n2) inside one of the compiled tile shapes (see
+ *    sdl_shape_supported); 1 <= s_max <= min(p1*p2, n1*n2, 32).
+ *  - Precision: FP32 arithmetic throughout.  Tie rule of the greedy step:
+ *    the largest |correlation|, ties to the smallest q.  A pick whose new
+ *    Cholesky pivot^2 <= 1e-6 * A_tt, or whose best score is exactly 0,
+ *    stops that signal early (nnz < s_max).
+ *  - A context is not thread-safe: calls sharing one context must be issued
+ *    from one host thread and on streams ordered with each other.
+ */
+#ifndef SDL_GB300_H
+#define SDL_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdl_ctx sdl_ctx;
+
+enum sdl_error {
+    SDL_OK = 0,
+    SDL_ERR_ARG = -1,          /* invalid argument (null pointer, bad size)   */
+    SDL_ERR_CUDA = -2,         /* a CUDA runtime call failed                  */
+    SDL_ERR_NONFINITE = -3,    /* NaN/Inf in Y or in a normal matrix          */
+    SDL_ERR_SINGULAR = -4,     /* normal matrix P or M not positive definite  */
+    SDL_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up          */
+    SDL_ERR_WORKSPACE = -6,    /* workspace allocation failed                 */
+    SDL_ERR_UNSUPPORTED = -7   /* shape outside the compiled tile shapes      */
+};
+
+/* Create a context on CUDA device `device` (the device is made current).
+ * The context owns only its workspace (partial sums, Gram matrices, scale
+ * factors, the device error word), grown on demand.  Returns SDL_OK and sets
+ * *ctx, or a negative code and sets *ctx = NULL. */
+int sdl_create(sdl_ctx** ctx, int device);
+
+/* Free the context and its workspace (synchronises the device first).
+ * NULL is accepted and ignored. */
+int sdl_destroy(sdl_ctx* ctx);
+
+/* Human-readable name of an error code (static string). */
+const char* sdl_strerror(int code);
+
+/* Synchronise `stream`, then return the first device-side error recorded by
+ * work enqueued through `ctx` since the previous sdl_status call (SDL_OK if
+ * none) and clear it.  Also reports pending CUDA errors as SDL_ERR_CUDA. */
+int sdl_status(sdl_ctx* ctx, void* stream);
+
+/* 1 if (p1, p2, n1, n2, s_max) is handled by a compiled kernel shape, else 0. */
+int sdl_shape_supported(int p1, int p2, int n1, int n2, int s_max);
+
+/* Pre-size the context workspace for problems up to these sizes, so that
+ * later calls allocate nothing (needed before capturing calls into a CUDA
+ * graph).  Synchronous. */
+int sdl_reserve(sdl_ctx* ctx, int p1, int p2, int n1, int n2, int s_max);
+
+/*
+ * sdl_sparse_code - 2D-OMP of all N signals (Sec. III step 1; the greedy
+ * pursuit over atom pairs d1_i d2_j^T that is equivalent to 1D OMP on
+ * D2 (x) D1, Sec. II), with a full least-squares re-fit after every pick.
+ *
+ *   eps <= 0 : exactly s_max picks per signal (fewer only at a degenerate
+ *              pick, see above);
+ *   eps >  0 : error-driven mode of the denoising experiments (Sec. IV):
+ *              before every pick, stop once ||R_k||_F <= eps; at most s_max.
+ *
+ * Outputs support/coef (N*s_max), nnz (N) and, if res_energy != NULL,
+ * res_energy[k] = ||Y_k - D1 X_k D2^T||_F^2 (FP32, from the least-squares
+ * energy identity).  N = 0 enqueues nothing.  Signals containing NaN/Inf get
+ * nnz = 0 and raise SDL_ERR_NONFINITE in sdl_status.
+ */
+int sdl_sparse_code(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
+                    const float* D1, int n1, const float* D2, int n2,
+                    int s_max, float eps,
+                    int32_t* support, float* coef, int32_t* nnz,
+                    float* res_energy, void* stream);
+
+/*
+ * sdl_update_D1 - optimal left dictionary for fixed codes (Corollary 1):
+ *   T_k = X_k D2^T,  P = sum_k T_k T_k^T (n1 x n1),  B1 = sum_k Y_k T_k^T,
+ *   D1* = B1 P^{-1},  W1 = diag(1/||d1*_i||),  D1 <- D1* W1,  X_k <- W1^{-1} X_k.
+ * P is accumulated through the Gram shortcut of Sec. III,
+ * T_k T_k^T = X_k (D2^T D2) X_k^T.
+ *
+ *   D1   in/out: replaced by the normalised optimum on success; left
+ *        unchanged if the update fails on the device (see sdl_status).
+ *   coef in/out: rescaled by W1^{-1} (slot l times ||d1*_{i_l}||).
+ *   objective_out: NULL or device float[2] = {objective of Eq. (1) before,
+ *        after} the update, FP32.
+ * Atoms used by no signal (zero row/column of P) are kept unchanged and the
+ * normal equations are solved on the used atoms.
+ */
+int sdl_update_D1(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
+                  float* D1, int n1, const float* D2, int n2, int s_max,
+                  const int32_t* support, float* coef,
+                  float* objective_out, void* stream);
+
+/*
+ * sdl_update_D2 - optimal right dictionary for fixed codes (Result 1):
+ *   Z_k = D1 X_k,  M = sum_k Z_k^T Z_k (n2 x n2),  B2 = sum_k Y_k^T Z_k,
+ *   D2* = B2 M^{-1} (the transpose of the printed (D2*)^T = M^{-1} sum Z^T Y),
+ *   W2 = diag(1/||d2*_j||),  D2 <- D2* W2,  X_k <- X_k W2^{-1}.
+ * Same argument rules as sdl_update_D1, mirrored.
+ */
+int sdl_update_D2(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
+                  const float* D1, int n1, float* D2, int n2, int s_max,
+                  const int32_t* support, float* coef,
+                  float* objective_out, void* stream);
+
+/*
+ * sdl_iterate - one iteration of Algorithm 1 on one GPU:
+ *   1. 2D-OMP of all signals with (D1, D2), accumulating P and B1 on the fly;
+ *   2. D1 update (Corollary 1);
+ *   3. 2D-OMP again with the new D1, accumulating M and B2;
+ *   4. D2 update (Result 1), and X_k <- X_k W2^{-1}.
+ * D1, D2 in/out.  support/coef/nnz receive the codes of step 3 rescaled as
+ * in step 4, consistent with the returned dictionaries.  rmse_out: NULL or
+ * device float[2] = RMSE ||Y - D1 X D2^T||_F / sqrt(p1 p2 N) right after step
+ * 2 and right after step 4.  eps as in sdl_sparse_code.
+ */
+int sdl_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
+                float* D1, int n1, float* D2, int n2, int s_max, float eps,
+                int32_t* support, float* coef, int32_t* nnz,
+                float* rmse_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDL_GB300_H */

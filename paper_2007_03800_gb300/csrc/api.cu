@@ -1,0 +1,304 @@
+// C ABI of the library (declared in include/sdl.h): argument checks, the
+// context workspace, and the launch sequences of the entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "sdl_internal.cuh"
+
+using namespace sdl;
+
+struct sdl_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int* err = nullptr;          // device error word
+    float* G1 = nullptr;         // Gram matrices of the current dictionaries
+    float* G2 = nullptr;
+    float* part_f = nullptr;     // partial-sum slots
+    double* part_d = nullptr;
+    float* red_f = nullptr;      // reduced sums
+    double* red_d = nullptr;
+    float* norms = nullptr;      // column norms of the last solve
+    size_t cap_g1 = 0, cap_g2 = 0, cap_part = 0, cap_slots = 0, cap_red = 0, cap_redd = 0,
+           cap_norms = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+int grow(T*& ptr, size_t& cap, size_t need) {
+    if (need <= cap && ptr) return SDL_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    const size_t n = std::max<size_t>(need, 1);
+    if (cudaMalloc(&ptr, n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return SDL_ERR_WORKSPACE;
+    }
+    cap = n;
+    return SDL_OK;
+}
+
+int ensure_workspace(sdl_ctx* c, int p1, int p2, int n1, int n2) {
+    const size_t nmax = (size_t)std::max(n1, n2);
+    const size_t nf = std::max<size_t>((size_t)n1 * n1 + (size_t)p1 * n1,
+                                       (size_t)n2 * n2 + (size_t)p2 * n2);
+    const size_t slots = (size_t)max_partial_slots(c->num_sms);
+    int rc;
+    if ((rc = grow(c->G1, c->cap_g1, nmax * nmax)) != SDL_OK) return rc;
+    if ((rc = grow(c->G2, c->cap_g2, nmax * nmax)) != SDL_OK) return rc;
+    if ((rc = grow(c->part_f, c->cap_part, slots * nf)) != SDL_OK) return rc;
+    if ((rc = grow(c->part_d, c->cap_slots, slots * 2)) != SDL_OK) return rc;
+    if ((rc = grow(c->red_f, c->cap_red, nf)) != SDL_OK) return rc;
+    if ((rc = grow(c->red_d, c->cap_redd, (size_t)2)) != SDL_OK) return rc;
+    if ((rc = grow(c->norms, c->cap_norms, nmax)) != SDL_OK) return rc;
+    return SDL_OK;
+}
+
+bool valid_common(const sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, int n1, int n2,
+                  int s) {
+    if (!c || p1 < 1 || p2 < 1 || n1 < 1 || n2 < 1 || N < 0 || s < 1) return false;
+    if (N > 0 && !Y) return false;
+    return true;
+}
+
+int check_shape(int p1, int p2, int n1, int n2, int s) {
+    if (s > kMaxS || s > p1 * p2 || s > n1 * n2) return SDL_ERR_ARG;
+    if (!code_shape_supported(p1, p2, n1, n2, s)) return SDL_ERR_UNSUPPORTED;
+    return SDL_OK;
+}
+
+PassArgs base_args(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const float* D1, int n1,
+                   const float* D2, int n2, int s) {
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.Y = Y;
+    a.p1 = p1;
+    a.p2 = p2;
+    a.N = N;
+    a.D1 = D1;
+    a.D2 = D2;
+    a.G1 = c->G1;
+    a.G2 = c->G2;
+    a.n1 = n1;
+    a.n2 = n2;
+    a.s = s;
+    a.part_f = c->part_f;
+    a.part_d = c->part_d;
+    a.n_slots = 1;
+    a.err = c->err;
+    return a;
+}
+
+// reduce -> solve for one dictionary side, using the partial sums in slots.
+int finish_update(sdl_ctx* c, int slots, int side, float* D, int p1, int p2, int64_t N, int n1,
+                  int n2, float* objective_out, float* rmse_out, cudaStream_t st) {
+    const int p = side == kSideD1 ? p1 : p2;
+    const int n = side == kSideD1 ? n1 : n2;
+    const int nf = n * n + p * n;
+    launch_reduce_partials(c->part_f, c->part_d, slots, nf, c->red_f, c->red_d, st);
+    const double inv_count = N > 0 ? 1.0 / ((double)p1 * p2 * (double)N) : 0.0;
+    return launch_solve(c->red_f, c->red_d, D, p, n, c->norms, inv_count, objective_out, rmse_out,
+                        c->err, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sdl_strerror(int code) {
+    switch (code) {
+        case SDL_OK: return "ok";
+        case SDL_ERR_ARG: return "invalid argument";
+        case SDL_ERR_CUDA: return "CUDA runtime error";
+        case SDL_ERR_NONFINITE: return "non-finite value in the data or a normal matrix";
+        case SDL_ERR_SINGULAR: return "normal matrix not positive definite";
+        case SDL_ERR_TIMEOUT: return "device-side wait timed out";
+        case SDL_ERR_WORKSPACE: return "workspace allocation failed";
+        case SDL_ERR_UNSUPPORTED: return "shape not supported by the compiled kernels";
+        default: return "unknown error";
+    }
+}
+
+int sdl_create(sdl_ctx** out, int device) {
+    if (!out) return SDL_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return SDL_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return SDL_ERR_CUDA;
+    sdl_ctx* c = new (std::nothrow) sdl_ctx();
+    if (!c) return SDL_ERR_WORKSPACE;
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return SDL_ERR_CUDA;
+    }
+    if (cudaMalloc(&c->err, sizeof(int)) != cudaSuccess || cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SDL_ERR_WORKSPACE;
+    }
+    *out = c;
+    return SDL_OK;
+}
+
+int sdl_destroy(sdl_ctx* c) {
+    if (!c) return SDL_OK;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    cudaFree(c->err);
+    cudaFree(c->G1);
+    cudaFree(c->G2);
+    cudaFree(c->part_f);
+    cudaFree(c->part_d);
+    cudaFree(c->red_f);
+    cudaFree(c->red_d);
+    cudaFree(c->norms);
+    delete c;
+    return SDL_OK;
+}
+
+int sdl_status(sdl_ctx* c, void* stream) {
+    if (!c) return SDL_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SDL_ERR_CUDA;
+    }
+    int h = 0;
+    if (cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return SDL_ERR_CUDA;
+    }
+    return h;
+}
+
+int sdl_shape_supported(int p1, int p2, int n1, int n2, int s) {
+    return check_shape(p1, p2, n1, n2, s) == SDL_OK && p1 >= 1 && p2 >= 1 ? 1 : 0;
+}
+
+int sdl_reserve(sdl_ctx* c, int p1, int p2, int n1, int n2, int s) {
+    if (!c || p1 < 1 || p2 < 1 || n1 < 1 || n2 < 1 || s < 1) return SDL_ERR_ARG;
+    int rc = check_shape(p1, p2, n1, n2, s);
+    if (rc != SDL_OK) return rc;
+    DeviceGuard g(c->device);
+    return ensure_workspace(c, p1, p2, n1, n2);
+}
+
+int sdl_sparse_code(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const float* D1, int n1,
+                    const float* D2, int n2, int s, float eps, int32_t* support, float* coef,
+                    int32_t* nnz, float* res_energy, void* stream) {
+    if (!valid_common(c, Y, p1, p2, N, n1, n2, s) || !D1 || !D2) return SDL_ERR_ARG;
+    if (N > 0 && (!support || !coef || !nnz)) return SDL_ERR_ARG;
+    int rc = check_shape(p1, p2, n1, n2, s);
+    if (rc != SDL_OK) return rc;
+    if (N == 0) return SDL_OK;
+    DeviceGuard g(c->device);
+    if ((rc = ensure_workspace(c, p1, p2, n1, n2)) != SDL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_gram(D1, p1, n1, c->G1, st);
+    launch_gram(D2, p2, n2, c->G2, st);
+    PassArgs a = base_args(c, Y, p1, p2, N, D1, n1, D2, n2, s);
+    a.eps2 = eps > 0.f ? eps * eps : 0.f;
+    a.support = support;
+    a.coef = coef;
+    a.nnz = nnz;
+    a.res_energy = res_energy;
+    rc = launch_code_pass(a, kCodeOnly, st, c->num_sms);
+    return rc < 0 ? rc : SDL_OK;
+}
+
+static int update_common(sdl_ctx* c, int side, const float* Y, int p1, int p2, int64_t N,
+                         const float* D1, float* D1w, int n1, const float* D2, float* D2w, int n2,
+                         int s, const int32_t* support, float* coef, float* objective_out,
+                         void* stream) {
+    if (!valid_common(c, Y, p1, p2, N, n1, n2, s) || !D1 || !D2) return SDL_ERR_ARG;
+    if (N > 0 && (!support || !coef)) return SDL_ERR_ARG;
+    int rc = check_shape(p1, p2, n1, n2, s);
+    if (rc != SDL_OK) return rc;
+    DeviceGuard g(c->device);
+    if ((rc = ensure_workspace(c, p1, p2, n1, n2)) != SDL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_gram(D1, p1, n1, c->G1, st);
+    launch_gram(D2, p2, n2, c->G2, st);
+    PassArgs a = base_args(c, Y, p1, p2, N, D1, n1, D2, n2, s);
+    a.in_support = support;
+    a.in_coef = coef;
+    const int slots = launch_accumulate_pass(a, side, st, c->num_sms);
+    if (slots < 0) return slots;
+    float* D = side == kSideD1 ? D1w : D2w;
+    rc = finish_update(c, slots, side, D, p1, p2, N, n1, n2, objective_out, nullptr, st);
+    if (rc != SDL_OK) return rc;
+    launch_rescale(support, coef, N * (long long)s, n1, n2, side, c->norms, st);
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+int sdl_update_D1(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1, int n1,
+                  const float* D2, int n2, int s, const int32_t* support, float* coef,
+                  float* objective_out, void* stream) {
+    return update_common(c, kSideD1, Y, p1, p2, N, D1, D1, n1, D2, nullptr, n2, s, support, coef,
+                         objective_out, stream);
+}
+
+int sdl_update_D2(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const float* D1, int n1,
+                  float* D2, int n2, int s, const int32_t* support, float* coef,
+                  float* objective_out, void* stream) {
+    return update_common(c, kSideD2, Y, p1, p2, N, D1, nullptr, n1, D2, D2, n2, s, support, coef,
+                         objective_out, stream);
+}
+
+int sdl_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1, int n1, float* D2,
+                int n2, int s, float eps, int32_t* support, float* coef, int32_t* nnz,
+                float* rmse_out, void* stream) {
+    if (!valid_common(c, Y, p1, p2, N, n1, n2, s) || !D1 || !D2) return SDL_ERR_ARG;
+    if (N > 0 && (!support || !coef || !nnz)) return SDL_ERR_ARG;
+    int rc = check_shape(p1, p2, n1, n2, s);
+    if (rc != SDL_OK) return rc;
+    DeviceGuard g(c->device);
+    if ((rc = ensure_workspace(c, p1, p2, n1, n2)) != SDL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float eps2 = eps > 0.f ? eps * eps : 0.f;
+
+    // steps 1-2: code with (D1, D2) accumulating P, B1; solve for D1
+    launch_gram(D1, p1, n1, c->G1, st);
+    launch_gram(D2, p2, n2, c->G2, st);
+    PassArgs a = base_args(c, Y, p1, p2, N, D1, n1, D2, n2, s);
+    a.eps2 = eps2;
+    int slots = launch_code_pass(a, kSideD1, st, c->num_sms);
+    if (slots < 0) return slots;
+    rc = finish_update(c, slots, kSideD1, D1, p1, p2, N, n1, n2, nullptr, rmse_out, st);
+    if (rc != SDL_OK) return rc;
+    // steps 3-4: code with the new D1 accumulating M, B2; solve for D2
+    launch_gram(D1, p1, n1, c->G1, st);
+    a.support = support;
+    a.coef = coef;
+    a.nnz = nnz;
+    slots = launch_code_pass(a, kSideD2, st, c->num_sms);
+    if (slots < 0) return slots;
+    rc = finish_update(c, slots, kSideD2, D2, p1, p2, N, n1, n2, nullptr,
+                       rmse_out ? rmse_out + 1 : nullptr, st);
+    if (rc != SDL_OK) return rc;
+    launch_rescale(support, coef, N * (long long)s, n1, n2, kSideD2, c->norms, st);
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+}  // extern "C"

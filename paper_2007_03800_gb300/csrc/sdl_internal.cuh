@@ -1,0 +1,77 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sdl.h"
+
+namespace sdl {
+
+// Degenerate-pick rule of the greedy step: the new Cholesky pivot^2 must
+// exceed this fraction of the new pair's Gram diagonal.
+constexpr float kPivotRel = 1e-6f;
+// Singular-normal-matrix rule of the dictionary solves (relative pivot).
+constexpr float kSolvePivotRel = 1e-7f;
+// Hard limit of the per-signal register Cholesky (one lane per row).
+constexpr int kMaxS = 32;
+// Largest dictionary dimension handled by the update solve.
+constexpr int kMaxN = 128;
+constexpr int kMaxP = 64;
+
+// Which partial sums a coding pass accumulates next to the codes.
+enum Side : int {
+    kCodeOnly = 0,   // sparse coding only
+    kSideD1 = 1,     // P = sum X G2 X^T, B1 = sum (Y D2) X^T  (Corollary 1)
+    kSideD2 = 2      // M = sum X^T G1 X, B2 = sum (Y^T D1) X  (Result 1)
+};
+
+// Arguments of a coding / accumulation pass (device pointers).
+struct PassArgs {
+    const float* Y;
+    int p1, p2;
+    long long N;
+    const float* D1;      // p1 x n1 column-major
+    const float* D2;      // p2 x n2 column-major
+    const float* G1;      // n1 x n1 (symmetric)
+    const float* G2;      // n2 x n2
+    int n1, n2;
+    int s;                // slots per signal (s_max)
+    float eps2;           // > 0: error-driven stop at ||R||^2 <= eps2
+    int32_t* support;     // may be null (codes not stored)
+    float* coef;
+    int32_t* nnz;
+    float* res_energy;    // may be null
+    const int32_t* in_support;   // accumulation-only pass: given codes
+    const float* in_coef;
+    float* part_f;        // partial sums: [slot][n*n + p*n]
+    double* part_d;       // [slot][2]: residual energy, ||Y||^2
+    int acc_in_smem;      // 1: CTA-private shared accumulators, slot = CTA
+    int n_slots;          // global-accumulator mode: slots (CTA % n_slots)
+    int* err;
+};
+
+// Host launchers (omp_pass.cu).  They return the number of partial-sum
+// slots written (to be reduced), or a negative sdl_error.
+int launch_code_pass(const PassArgs& a, int side, cudaStream_t st, int num_sms);
+int launch_accumulate_pass(const PassArgs& a, int side, cudaStream_t st, int num_sms);
+bool code_shape_supported(int p1, int p2, int n1, int n2, int s);
+// Upper bound of the partial-sum slots any pass may use for these sizes.
+int max_partial_slots(int num_sms);
+
+// tmod.cu
+void launch_gram(const float* D, int p, int n, float* G, cudaStream_t st);
+void launch_reduce_partials(const float* part_f, const double* part_d, int n_slots,
+                            int nf, float* red_f, double* red_d, cudaStream_t st);
+int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n,
+                 float* norms, double inv_count, float* objective_out, float* rmse_out,
+                 int* err, cudaStream_t st);
+void launch_rescale(const int32_t* support, float* coef, long long count, int n1, int n2,
+                    int side, const float* norms, cudaStream_t st);
+
+// Record the first device-side error (first writer wins).
+__device__ __forceinline__ void record_error(int* err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+}  // namespace sdl

@@ -1,0 +1,224 @@
+"""Thin Python binding of the C ABI in ``include/sdl.h`` (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are PyTorch CUDA tensors; PyTorch provides device memory
+and streams.  There is no CPU fallback: if the library has not been built,
+``lib()`` raises.
+
+Layout helpers: signals are (N, p1, p2) tensors whose memory is column-major
+per signal (strides (p1*p2, 1, p1)); dictionaries are (p, n) column-major
+tensors (strides (1, p)).  ``signals()`` and ``dictionary()`` produce them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsdl_gb300.so")
+_lib = None
+
+SDL_OK = 0
+ERRORS = {
+    -1: "SDL_ERR_ARG", -2: "SDL_ERR_CUDA", -3: "SDL_ERR_NONFINITE", -4: "SDL_ERR_SINGULAR",
+    -5: "SDL_ERR_TIMEOUT", -6: "SDL_ERR_WORKSPACE", -7: "SDL_ERR_UNSUPPORTED",
+}
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_int64
+_F = ctypes.c_float
+
+# name -> argtypes (every entry point returns int)
+SIGNATURES = {
+    "sdl_create": [ctypes.POINTER(_P), _I],
+    "sdl_destroy": [_P],
+    "sdl_status": [_P, _P],
+    "sdl_shape_supported": [_I, _I, _I, _I, _I],
+    "sdl_reserve": [_P, _I, _I, _I, _I, _I],
+    "sdl_sparse_code": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
+    "sdl_update_D1": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _P, _P, _P],
+    "sdl_update_D2": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _P, _P, _P],
+    "sdl_iterate": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
+}
+
+
+class SDLError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)}")
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, argtypes in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = argtypes
+            fn.restype = _I
+        L.sdl_strerror.argtypes = [_I]
+        L.sdl_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != SDL_OK:
+        raise SDLError(rc, where)
+
+
+def signals(Y: torch.Tensor) -> torch.Tensor:
+    """(N, p1, p2) tensor -> same values, memory column-major per signal."""
+    return Y.transpose(1, 2).contiguous().transpose(1, 2)
+
+
+def dictionary(D: torch.Tensor) -> torch.Tensor:
+    """(p, n) tensor -> same values, column-major memory."""
+    return D.t().contiguous().t()
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, shape, strides, name: str):
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if strides is not None and t.numel() > 1 and tuple(t.stride()) != tuple(strides):
+        raise ValueError(f"{name} has strides {t.stride()}, expected {strides}")
+
+
+def _check_Y(Y):
+    if Y.dim() != 3:
+        raise ValueError("Y must be (N, p1, p2)")
+    N, p1, p2 = Y.shape
+    _need(Y, torch.float32, (N, p1, p2), (p1 * p2, 1, p1), "Y")
+    return N, p1, p2
+
+
+def _check_D(D, p, name):
+    if D.dim() != 2 or D.shape[0] != p:
+        raise ValueError(f"{name} must be ({p}, n)")
+    _need(D, torch.float32, D.shape, (1, p), name)
+    return D.shape[1]
+
+
+def shape_supported(p1, p2, n1, n2, s) -> bool:
+    return bool(lib().sdl_shape_supported(p1, p2, n1, n2, s))
+
+
+class Codes:
+    """Sparse codes of N signals: support (N, s) int32 pair indices q = i + n1*j
+    (-1 unused), coef (N, s) float32, nnz (N,) int32."""
+
+    def __init__(self, support, coef, nnz, res_energy=None):
+        self.support, self.coef, self.nnz, self.res_energy = support, coef, nnz, res_energy
+
+    @staticmethod
+    def empty(N, s, device, with_energy=False):
+        return Codes(torch.empty((N, s), dtype=torch.int32, device=device),
+                     torch.empty((N, s), dtype=torch.float32, device=device),
+                     torch.empty((N,), dtype=torch.int32, device=device),
+                     torch.empty((N,), dtype=torch.float32, device=device) if with_energy else None)
+
+
+class Context:
+    """One library context (``sdl_create``) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        _check(self._lib.sdl_create(ctypes.byref(h), int(device)), "sdl_create")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sdl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None) -> int:
+        """Synchronise and return (and clear) the recorded device-side error."""
+        return self._lib.sdl_status(self._h, _stream(stream))
+
+    def check(self, stream=None) -> None:
+        _check(self.status(stream), "device")
+
+    def reserve(self, p1, p2, n1, n2, s) -> None:
+        _check(self._lib.sdl_reserve(self._h, p1, p2, n1, n2, s), "sdl_reserve")
+
+    def sparse_code(self, Y, D1, D2, s, eps=0.0, out: Codes | None = None, stream=None) -> Codes:
+        N, p1, p2 = _check_Y(Y)
+        n1, n2 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2")
+        if out is None:
+            out = Codes.empty(N, s, Y.device, with_energy=True)
+        _need(out.support, torch.int32, (N, s), None, "support")
+        _need(out.coef, torch.float32, (N, s), None, "coef")
+        _need(out.nnz, torch.int32, (N,), None, "nnz")
+        rc = self._lib.sdl_sparse_code(self._h, _ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2,
+                                       s, float(eps), _ptr(out.support), _ptr(out.coef),
+                                       _ptr(out.nnz), _ptr(out.res_energy), _stream(stream))
+        _check(rc, "sdl_sparse_code")
+        return out
+
+    def _update(self, fn, Y, D1, D2, codes: Codes, objective_out, stream):
+        N, p1, p2 = _check_Y(Y)
+        n1, n2 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2")
+        s = codes.support.shape[1]
+        _need(codes.support, torch.int32, (N, s), None, "support")
+        _need(codes.coef, torch.float32, (N, s), None, "coef")
+        if objective_out is not None:
+            _need(objective_out, torch.float32, (2,), None, "objective_out")
+        rc = fn(self._h, _ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2, s,
+                _ptr(codes.support), _ptr(codes.coef), _ptr(objective_out), _stream(stream))
+        return rc
+
+    def update_D1(self, Y, D1, D2, codes: Codes, objective_out=None, stream=None):
+        """Corollary 1: D1 and codes.coef updated in place."""
+        _check(self._update(self._lib.sdl_update_D1, Y, D1, D2, codes, objective_out, stream),
+               "sdl_update_D1")
+
+    def update_D2(self, Y, D1, D2, codes: Codes, objective_out=None, stream=None):
+        """Result 1: D2 and codes.coef updated in place."""
+        _check(self._update(self._lib.sdl_update_D2, Y, D1, D2, codes, objective_out, stream),
+               "sdl_update_D2")
+
+    def iterate(self, Y, D1, D2, s, eps=0.0, out: Codes | None = None, rmse_out=None,
+                stream=None) -> Codes:
+        """One iteration of Algorithm 1; D1, D2 updated in place."""
+        N, p1, p2 = _check_Y(Y)
+        n1, n2 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2")
+        if out is None:
+            out = Codes.empty(N, s, Y.device)
+        _need(out.support, torch.int32, (N, s), None, "support")
+        _need(out.coef, torch.float32, (N, s), None, "coef")
+        _need(out.nnz, torch.int32, (N,), None, "nnz")
+        if rmse_out is not None:
+            _need(rmse_out, torch.float32, (2,), None, "rmse_out")
+        rc = self._lib.sdl_iterate(self._h, _ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2, s,
+                                   float(eps), _ptr(out.support), _ptr(out.coef), _ptr(out.nnz),
+                                   _ptr(rmse_out), _stream(stream))
+        _check(rc, "sdl_iterate")
+        return out

@@ -1,0 +1,75 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+entry point the header declares, and rejects bad arguments on the host
+without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sdl.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\*?(sdl_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2007_03800_gb300 import _build, sdl
+    if not os.path.exists(sdl.LIB_PATH):
+        _build.build()
+    return sdl.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("sdl_sparse_code", "sdl_update_D1", "sdl_update_D2", "sdl_iterate",
+                 "sdl_create", "sdl_destroy", "sdl_status"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in sdl.h but not exported"
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2007_03800_gb300 import sdl
+    for name in declared_functions():
+        assert name in sdl.SIGNATURES or name == "sdl_strerror", name
+
+
+def test_shape_support_rules(lib):
+    assert lib.sdl_shape_supported(8, 8, 16, 16, 4) == 1
+    assert lib.sdl_shape_supported(12, 12, 24, 24, 6) == 1
+    assert lib.sdl_shape_supported(16, 64, 32, 128, 10) == 1
+    assert lib.sdl_shape_supported(16, 16, 32, 32, 8) == 1
+    assert lib.sdl_shape_supported(8, 8, 16, 16, 33) == 0      # s above the register Cholesky
+    assert lib.sdl_shape_supported(2, 2, 16, 16, 5) == 0       # s > p1*p2
+    assert lib.sdl_shape_supported(8, 8, 256, 16, 4) == 0      # no tile shape
+    assert lib.sdl_shape_supported(65, 8, 16, 16, 4) == 0
+
+
+def test_host_argument_errors_without_gpu(lib):
+    from paper_2007_03800_gb300 import sdl
+    assert lib.sdl_sparse_code(None, None, 8, 8, 10, None, 16, None, 16, 4, 0.0,
+                               None, None, None, None, None) == -1
+    assert lib.sdl_iterate(None, None, 8, 8, 10, None, 16, None, 16, 4, 0.0,
+                           None, None, None, None, None) == -1
+    assert lib.sdl_create(None, 0) == -1
+    assert lib.sdl_destroy(None) == 0
+    assert lib.sdl_strerror(-4) == b"normal matrix not positive definite"
+    assert sdl.ERRORS[-7] == "SDL_ERR_UNSUPPORTED"
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.sdl_create(ctypes.byref(h), 0) == -2
+    assert h.value is None

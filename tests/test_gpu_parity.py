@@ -1,0 +1,261 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs come from the seeded generators only; expected values come from the
+oracle only.  Supports must match pick for pick except at argmax ties the
+oracle itself shows (counted); coefficients, dictionaries and RMSE must match
+within 1e-4 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2007_03800_gb300 import sdl, synth
+from parity import (COEF_RTOL, DICT_RTOL, RMSE_RTOL, codes_from_oracle, coef_rel_error,
+                    compare_supports, to_gpu_problem)
+
+pytestmark = pytest.mark.gpu
+
+
+def run_code(ctx, Y, D1, D2, s, eps=0.0):
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    out = ctx.sparse_code(Yg, D1g, D2g, s, eps=eps)
+    assert ctx.status() == 0
+    return (out.support.cpu().numpy(), out.coef.cpu().numpy(), out.nnz.cpu().numpy(),
+            out.res_energy.cpu().numpy())
+
+
+def check_code(ctx, Y, D1, D2, s, eps=None, max_tie_frac=2e-3):
+    ref = oracle.omp2d(Y, D1, D2, s, eps=eps)
+    sup, coef, nnz, energy = run_code(ctx, Y, D1, D2, s, eps=eps or 0.0)
+    rep, exact = compare_supports(sup, nnz, ref, eps=eps)
+    assert rep.bad == 0, rep
+    assert rep.ties <= max(2, max_tie_frac * rep.n), rep
+    err = coef_rel_error(coef, ref.coef, exact)
+    assert err.max(initial=0.0) < COEF_RTOL, (err.max(), rep)
+    ynorm = np.sum(np.asarray(Y) ** 2, axis=(1, 2))
+    e_err = np.abs(energy[exact] - ref.res_energy[exact]) / (ref.res_energy[exact] + 1e-5 * ynorm[exact])
+    assert e_err.max(initial=0.0) < 1e-3
+    return rep
+
+
+# ----------------------------------------------------------------- sparse coding
+@pytest.mark.parametrize("p1,p2,n1,n2,s,N", [
+    (8, 8, 16, 16, 4, 4096),      # 8x8 Kronecker workload, 256 atom pairs
+    (12, 12, 24, 24, 6, 3001),    # 12x12 patches, ragged count
+    (16, 16, 32, 32, 8, 1003),
+    (16, 64, 32, 128, 10, 257),   # hyperspectral shape: 4-warp team
+    (6, 10, 12, 20, 5, 999),      # p1 != p2, n1 != n2
+    (8, 8, 6, 6, 3, 500),         # undercomplete
+    (8, 8, 16, 16, 1, 777),       # s = 1
+    (4, 4, 8, 8, 8, 640),         # s = p1 p2 / 2
+    (20, 20, 50, 50, 6, 300),     # 64 x 64 tile
+    (40, 8, 100, 16, 4, 300),     # 128 x 32 tile
+])
+def test_sparse_code_matches_oracle(gpu_ctx, p1, p2, n1, n2, s, N):
+    rng = np.random.default_rng(1000 + p1 * 7 + n2)
+    Y = rng.standard_normal((N, p1, p2))
+    D1, D2 = synth.init_dictionaries(p1, p2, n1, n2, seed=1)
+    check_code(gpu_ctx, Y, D1, D2, s)
+
+
+def test_sparse_code_kronecker_model_recovery(gpu_ctx):
+    """Noisy planted codes (20 dB): GPU and oracle agree on every pick, so the
+    recovery rate of the planted supports is identical."""
+    Y, D1t, D2t, sup_true, _ = synth.kron_model(4096, 8, 8, 16, 16, 4, 20.0, seed=11)
+    rep = check_code(gpu_ctx, Y, D1t, D2t, 4)
+    ref = oracle.omp2d(Y, D1t, D2t, 4)
+    sup, _, _, _ = run_code(gpu_ctx, Y, D1t, D2t, 4)
+    rec_ref = np.mean([set(ref.support[k]) == set(sup_true[k]) for k in range(4096)])
+    rec_gpu = np.mean([set(sup[k]) == set(sup_true[k]) for k in range(4096)])
+    assert abs(rec_ref - rec_gpu) <= rep.ties / 4096
+
+
+def test_sparse_code_noiseless_orthonormal_exact(gpu_ctx):
+    rng = np.random.default_rng(5)
+    p = 8
+    Q1, _ = np.linalg.qr(rng.standard_normal((p, p)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((p, p)))
+    N, s = 1000, 6
+    sup = np.stack([rng.choice(p * p, s, replace=False) for _ in range(N)])
+    coef = np.sign(rng.standard_normal((N, s))) * (0.5 + rng.random((N, s)))
+    Y = oracle.reconstruct(Q1, Q2, sup, coef)
+    gs, gc, gn, _ = run_code(gpu_ctx, Y, Q1, Q2, s)
+    assert np.all(gn == s)
+    for k in range(N):
+        m = dict(zip(sup[k], coef[k]))
+        assert set(gs[k]) == set(sup[k])
+        assert np.allclose([m[q] for q in gs[k]], gc[k], rtol=1e-5, atol=1e-5)
+
+
+def test_error_driven_mode(gpu_ctx):
+    """Denoising-style error-bounded coding (Sec. IV): stop at ||R|| <= eps."""
+    img = synth.synthetic_image(7, size=128)
+    noisy = img + np.random.default_rng(8).normal(0, 20.0, img.shape)
+    Y, _ = synth.all_patches(noisy, 8)
+    Y = Y[::5][:3000]
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    eps = 1.15 * 20.0 * 8
+    rep = check_code(gpu_ctx, Y, D1, D2, 4, eps=eps)
+    assert rep.exact >= 0.99 * rep.n
+
+
+# ------------------------------------------------------------ dictionary updates
+@pytest.mark.parametrize("p1,p2,n1,n2,s,N", [
+    (8, 8, 16, 16, 4, 4096),
+    (12, 12, 24, 24, 6, 2000),
+    (16, 64, 32, 128, 10, 600),
+    (6, 10, 12, 20, 5, 999),
+])
+@pytest.mark.parametrize("side", [1, 2])
+def test_update_matches_oracle(gpu_ctx, p1, p2, n1, n2, s, N, side):
+    Y, _, _, _, _ = synth.kron_model(N, p1, p2, n1, n2, s, 20.0, seed=21 + side)
+    D1, D2 = synth.init_dictionaries(p1, p2, n1, n2, seed=1)
+    ref_code = oracle.omp2d(Y, D1, D2, s)
+    upd = (oracle.update_D1 if side == 1 else oracle.update_D2)(Y, D1, D2, ref_code.support,
+                                                                ref_code.coef)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    codes = codes_from_oracle(ref_code.support, ref_code.coef)
+    obj = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    (gpu_ctx.update_D1 if side == 1 else gpu_ctx.update_D2)(Yg, D1g, D2g, codes, objective_out=obj)
+    assert gpu_ctx.status() == 0
+    D = (D1g if side == 1 else D2g).cpu().numpy()
+    assert np.abs(D - upd.D).max() < DICT_RTOL
+    err = coef_rel_error(codes.coef.cpu().numpy(), upd.coef, np.ones(N, bool))
+    assert err.max() < COEF_RTOL
+    o = obj.cpu().numpy()
+    assert abs(o[0] - upd.obj_before) / upd.obj_before < 1e-4
+    assert abs(o[1] - upd.obj_after) / upd.obj_after < 1e-4
+    # the untouched dictionary really is untouched
+    other = (D2g if side == 1 else D1g).cpu().numpy()
+    assert np.array_equal(other, np.asarray(D2 if side == 1 else D1, dtype=np.float32))
+
+
+def test_update_keeps_unused_atom(gpu_ctx):
+    Y, _, _, _, _ = synth.kron_model(1500, 8, 8, 16, 16, 4, 20.0, seed=31)
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    ref_code = oracle.omp2d(Y, D1, D2, 4)
+    sup, coef = ref_code.support.copy(), ref_code.coef.copy()
+    coef[sup % 16 == 5] = 0.0                     # atom i = 5 of D1 carries no weight
+    upd = oracle.update_D1(Y, D1, D2, sup, coef)
+    assert not upd.used[5]
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    codes = codes_from_oracle(sup, coef)
+    gpu_ctx.update_D1(Yg, D1g, D2g, codes)
+    assert gpu_ctx.status() == 0
+    got = D1g.cpu().numpy()
+    assert np.array_equal(got[:, 5], np.asarray(D1[:, 5], dtype=np.float32))
+    assert np.abs(got - upd.D).max() < DICT_RTOL
+
+
+# ------------------------------------------------------------------ Algorithm 1
+def test_iterate_one_step(gpu_ctx):
+    Y, _, _, _, _ = synth.kron_model(4096, 8, 8, 16, 16, 4, 20.0, seed=11)
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    ref = oracle.iterate(Y, D1, D2, 4)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    out = gpu_ctx.iterate(Yg, D1g, D2g, 4, rmse_out=rmse)
+    assert gpu_ctx.status() == 0
+    r = rmse.cpu().numpy()
+    assert abs(r[0] - ref.rmse_after_D1) / ref.rmse_after_D1 < RMSE_RTOL
+    assert abs(r[1] - ref.rmse_after_D2) / ref.rmse_after_D2 < RMSE_RTOL
+    assert np.abs(D1g.cpu().numpy() - ref.D1).max() < DICT_RTOL
+    assert np.abs(D2g.cpu().numpy() - ref.D2).max() < DICT_RTOL
+    rep, exact = compare_supports(out.support.cpu().numpy(), out.nnz.cpu().numpy(), ref.omp_b)
+    assert rep.bad == 0 and rep.ties <= 4, rep
+    err = coef_rel_error(out.coef.cpu().numpy(), ref.coef, exact)
+    assert err.max() < COEF_RTOL
+
+
+def test_iterate_ten_steps_rmse_trajectory(gpu_ctx):
+    """10 iterations on the 8x8 Kronecker workload: the RMSE after every
+    dictionary update follows the oracle's within 1e-4 relative."""
+    Y, _, _, _, _ = synth.kron_model(4096, 8, 8, 16, 16, 4, 20.0, seed=11)
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    out = None
+    for it in range(10):
+        ref = oracle.iterate(Y, D1, D2, 4)
+        D1, D2 = ref.D1, ref.D2
+        out = gpu_ctx.iterate(Yg, D1g, D2g, 4, out=out, rmse_out=rmse)
+        r = rmse.cpu().numpy()
+        assert abs(r[0] - ref.rmse_after_D1) / ref.rmse_after_D1 < RMSE_RTOL, (it, r, ref.rmse_after_D1)
+        assert abs(r[1] - ref.rmse_after_D2) / ref.rmse_after_D2 < RMSE_RTOL, (it, r, ref.rmse_after_D2)
+    assert gpu_ctx.status() == 0
+
+
+def test_iterate_full_size_properties(gpu_ctx):
+    """200k mean-removed 12x12 image patches, 12x24 dictionaries, s = 6 (the
+    benchmark workload, same launch configuration): sampled signals match the
+    oracle, and the closed-form RMSE equals the explicit residual of the
+    returned (D1, D2, X)."""
+    imgs = np.stack([synth.synthetic_image(100 + i) for i in range(8)])
+    Y = synth.random_patches(imgs, 200_000, 12, seed=5)
+    D1, D2 = synth.init_dictionaries(12, 12, 24, 24, seed=1)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    codes = gpu_ctx.sparse_code(Yg, D1g, D2g, 6)
+    rows = np.random.default_rng(0).choice(200_000, 1500, replace=False)
+    ref = oracle.omp2d(Y[rows], D1, D2, 6)
+    rep, exact = compare_supports(codes.support.cpu().numpy()[rows], codes.nnz.cpu().numpy()[rows], ref)
+    assert rep.bad == 0 and rep.ties <= 3, rep
+    assert coef_rel_error(codes.coef.cpu().numpy()[rows], ref.coef, exact).max() < COEF_RTOL
+
+    rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    out = gpu_ctx.iterate(Yg, D1g, D2g, 6, rmse_out=rmse)
+    assert gpu_ctx.status() == 0
+    D1n, D2n = D1g.cpu().numpy().astype(np.float64), D2g.cpu().numpy().astype(np.float64)
+    assert np.allclose(np.linalg.norm(D1n, axis=0), 1.0, atol=1e-5)
+    assert np.allclose(np.linalg.norm(D2n, axis=0), 1.0, atol=1e-5)
+    sup = out.support.cpu().numpy().astype(np.int64)
+    cf = out.coef.cpu().numpy().astype(np.float64)
+    explicit = oracle.rmse(Y, D1n, D2n, sup, cf)
+    assert abs(rmse.cpu().numpy()[1] - explicit) / explicit < 2e-4
+
+
+# ------------------------------------------------------------------ edge cases
+def test_empty_and_single_signal(gpu_ctx):
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    Y = np.zeros((0, 8, 8))
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    out = gpu_ctx.sparse_code(Yg, D1g, D2g, 4)
+    assert out.support.shape == (0, 4)
+    Y1 = np.random.default_rng(3).standard_normal((1, 8, 8))
+    check_code(gpu_ctx, Y1, D1, D2, 4)
+
+
+def test_nonfinite_signal_flagged(gpu_ctx):
+    rng = np.random.default_rng(4)
+    Y = rng.standard_normal((100, 8, 8))
+    Y[17, 3, 2] = np.nan
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    out = gpu_ctx.sparse_code(Yg, D1g, D2g, 4)
+    assert gpu_ctx.status() == -3          # SDL_ERR_NONFINITE, then cleared
+    assert gpu_ctx.status() == 0
+    nnz = out.nnz.cpu().numpy()
+    assert nnz[17] == 0 and np.all(nnz[np.arange(100) != 17] == 4)
+
+
+def test_zero_signal_gets_empty_code(gpu_ctx):
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    Y = np.zeros((3, 8, 8))
+    Y[1] = np.random.default_rng(2).standard_normal((8, 8))
+    _, _, nnz, _ = run_code(gpu_ctx, Y, D1, D2, 4)
+    assert list(nnz) == [0, 4, 0]
+
+
+def test_host_argument_errors(gpu_ctx):
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    Y = np.random.default_rng(1).standard_normal((10, 8, 8))
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    with pytest.raises(sdl.SDLError) as e:
+        gpu_ctx.sparse_code(Yg, D1g, D2g, 65)
+    assert e.value.code in (-1, -7)
+    Dbig = sdl.dictionary(torch.randn(8, 300, device="cuda:0"))
+    with pytest.raises(sdl.SDLError) as e:
+        gpu_ctx.sparse_code(Yg, Dbig, D2g, 4)
+    assert e.value.code == -7
+    with pytest.raises(ValueError):
+        gpu_ctx.sparse_code(Yg.contiguous(), D1g, D2g, 4)   # wrong memory layout
