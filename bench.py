@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Throughput of one separable-dictionary-learning iteration on GB300.
+
+One step = one iteration of Algorithm 1 (two 2D-OMP coding passes with the
+fused partial sums, the D1 and D2 least-squares updates and the code
+rescale) over the whole training set, through the library's C ABI.
+
+Workload: image-patch learning, N = 200000 mean-removed 12x12 FP32 patches
+cut at seeded positions from 64 seeded synthetic 512x512 images, D1, D2
+12x24 (576 atom pairs), s = 6.  Metric: signals/s per iteration.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With --gpus N > 1 (torchrun) every rank runs
+an independent replica of the workload on its own GPU ("replicas only": the
+one-GPU method has no data-path exchange between GPUs); value aggregates all
+ranks.  --impl reference times the FP64 CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "signals/sec per 2D-OMP+TMOD iteration"
+UNIT = "signals/s"
+W = dict(N=200_000, p1=12, p2=12, n1=24, n2=24, s=6, n_images=64, image_seed=100,
+         patch_seed=5, dict_seed=1)
+WORKLOAD = ("image-patch learning: N=200000 mean-removed 12x12 FP32 patches from 64 seeded "
+            "synthetic 512x512 images, D1,D2 12x24, s=6, one Algorithm-1 iteration per step")
+CPU_SAMPLE = 32768          # signals in the timed oracle sample (cpu_baseline)
+REF_SAMPLE = 4096           # signals per step of the reference arm
+FLUSH_BYTES = 256 << 20     # > 129 MB L2
+
+
+def make_inputs():
+    from paper_2007_03800_gb300 import synth
+    imgs = np.stack([synth.synthetic_image(W["image_seed"] + i) for i in range(W["n_images"])])
+    Y = synth.random_patches(imgs, W["N"], W["p1"], seed=W["patch_seed"])
+    D1, D2 = synth.init_dictionaries(W["p1"], W["p2"], W["n1"], W["n2"], seed=W["dict_seed"])
+    return Y, D1, D2
+
+
+# ------------------------------------------------------------- algorithmic work
+def flops_per_signal_pass(p1, p2, n1, n2, s, side):
+    """Algorithmic FLOPs of one 2D-OMP coding pass of one signal (with the
+    fused partial sums of `side`): correlation C0 = D1^T (Y D2) in the cheaper
+    association, the Gram-domain correlation updates sum_t 2 t n1 n2, the
+    incremental Cholesky/solves ~2 t^2 per step, and the epilogue sums."""
+    c0 = 2 * min(p1 * p2 * n2 + n1 * p1 * n2, n1 * p1 * p2 + n1 * p2 * n2)
+    upd = sum(2 * t * n1 * n2 for t in range(s))
+    chol = sum(2 * t * t + 4 * t + 4 for t in range(s))
+    if side == 1:
+        epi = 2 * p1 * s + 3 * s * s
+    else:
+        epi = 2 * p1 * p2 * s + 2 * p2 * s + 3 * s * s
+    return c0 + upd + chol + epi
+
+
+def bytes_per_signal_pass(p1, p2, s, side):
+    """Algorithmic HBM bytes: Y read once per pass; codes written by pass 2."""
+    return 4 * p1 * p2 + (8 * s + 4 if side == 2 else 0)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2007_03800_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- CPU oracle
+_ORACLE_SNIPPET = r"""
+import sys, time, json
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+d = np.load(sys.argv[2])
+Y, D1, D2, s, reps = d["Y"], d["D1"], d["D2"], int(d["s"]), int(d["reps"])
+times = []
+for _ in range(reps):
+    t = time.perf_counter()
+    oracle.iterate(Y, D1, D2, s)
+    times.append(time.perf_counter() - t)
+print(json.dumps(times))
+"""
+
+
+def time_oracle(Y, D1, D2, s, reps):
+    """Run the FP64 oracle (unmodified) on one host core in a child process;
+    returns the per-iteration wall times."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "sample.npz")
+        np.savez(path, Y=Y, D1=D1, D2=D2, s=s, reps=reps)
+        out = subprocess.run([sys.executable, "-c", _ORACLE_SNIPPET, ROOT, path], env=env,
+                             capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ arms
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    Y, D1, D2 = make_inputs()
+    sample = Y[:REF_SAMPLE]
+    times = time_oracle(sample, D1, D2, W["s"], args.warmup + args.steps)[args.warmup:]
+    per_step = sum(times) / len(times)
+    value = REF_SAMPLE / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_signals_per_step": REF_SAMPLE},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {REF_SAMPLE} of the 200000 patches, one full "
+                                   "Algorithm-1 iteration per step, FP64 numpy, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2007_03800_gb300 import sdl
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    else:
+        dist = None
+        torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    p1, p2, n1, n2, s, N = W["p1"], W["p2"], W["n1"], W["n2"], W["s"], W["N"]
+
+    Y, D1, D2 = make_inputs()
+    Y32 = np.asarray(Y, dtype=np.float32)
+    ctx = sdl.Context(local)
+    ctx.reserve(p1, p2, n1, n2, s)
+    Yg = sdl.signals(torch.from_numpy(Y32).to(dev))
+    D1_0 = sdl.dictionary(torch.tensor(D1, dtype=torch.float32, device=dev))
+    D2_0 = sdl.dictionary(torch.tensor(D2, dtype=torch.float32, device=dev))
+    D1g, D2g = sdl.dictionary(D1_0.clone()), sdl.dictionary(D2_0.clone())
+    codes = sdl.Codes.empty(N, s, dev)
+    rmse = torch.zeros(2, dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctx.iterate(Yg, D1g, D2g, s, out=codes, rmse_out=rmse)
+    ctx.check()
+    ctx.profile_collect()                      # reset counters
+
+    # ---- timed region: K iterations, L2 flushed between them (untimed)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ctx.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            ctx.iterate(Yg, D1g, D2g, s, out=codes, rmse_out=rmse)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ctx.profile(False)
+    ctx.check()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    prof = ctx.profile_collect()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * N / (ms_per_step / 1e3)
+    final_rmse = rmse.cpu().tolist()
+
+    # ---- end to end: host inputs in, results out, every step
+    if args.quick:
+        print(json.dumps({"quick": True, "ms_per_step": ms_per_step, "kernels": prof}), flush=True)
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    Yh = torch.from_numpy(np.ascontiguousarray(Y32.transpose(0, 2, 1))).pin_memory()  # (N, p2, p1)
+    D1h = torch.tensor(D1, dtype=torch.float32).t().contiguous().pin_memory()   # column-major
+    D2h = torch.tensor(D2, dtype=torch.float32).t().contiguous().pin_memory()
+    out_h = {"D1": torch.empty_like(D1h).pin_memory(), "D2": torch.empty_like(D2h).pin_memory(),
+             "support": torch.empty((N, s), dtype=torch.int32).pin_memory(),
+             "coef": torch.empty((N, s), dtype=torch.float32).pin_memory(),
+             "nnz": torch.empty((N,), dtype=torch.int32).pin_memory(),
+             "rmse": torch.empty(2, dtype=torch.float32).pin_memory()}
+    Ybuf = torch.empty((N, p2, p1), dtype=torch.float32, device=dev)
+    D1buf = torch.empty((n1, p1), dtype=torch.float32, device=dev)
+    D2buf = torch.empty((n2, p2), dtype=torch.float32, device=dev)
+    h2d = Yh.numel() * 4 + D1h.numel() * 4 + D2h.numel() * 4
+    d2h = sum(t.numel() * t.element_size() for t in out_h.values())
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Ybuf.view(-1).copy_(Yh.view(-1), non_blocking=True)
+        D1buf.copy_(D1h, non_blocking=True)
+        D2buf.copy_(D2h, non_blocking=True)
+        Yv = Ybuf.transpose(1, 2)
+        D1v, D2v = D1buf.t(), D2buf.t()
+        ctx.iterate(Yv, D1v, D2v, s, out=codes, rmse_out=rmse)
+        out_h["D1"].copy_(D1buf, non_blocking=True)
+        out_h["D2"].copy_(D2buf, non_blocking=True)
+        out_h["support"].copy_(codes.support, non_blocking=True)
+        out_h["coef"].copy_(codes.coef, non_blocking=True)
+        out_h["nnz"].copy_(codes.nnz, non_blocking=True)
+        out_h["rmse"].copy_(rmse, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    ctx.check()
+    e2e_total = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * N / (e2e_total / args.steps / 1e3)
+
+    line = None
+    if rank == 0:
+        peaks = measured_peaks()
+        props = torch.cuda.get_device_properties(dev)
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+        kinds = {k: v for k, v in prof.items() if v[1] > 0}
+        dom = max(kinds, key=lambda k: kinds[k][0])
+        dom_ms, dom_n = kinds[dom]
+        side = {"code_D1": 1, "code_D2": 2}.get(dom, 2)
+        flops = N * flops_per_signal_pass(p1, p2, n1, n2, s, side)
+        achieved = flops / (dom_ms / dom_n / 1e3) / 1e12
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tpath):
+            t = json.load(open(tpath))
+            ent = t.get(dom)
+            if ent and ent.get("source_hash") == source_hash() and ent.get("N") == N:
+                traffic = ent["dram_bytes_per_launch"]
+        cpu_times = time_oracle(Y[:CPU_SAMPLE], D1, D2, s, 1)
+        clk = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "p1": p1, "p2": p2, "n1": n1, "n2": n2,
+                       "s": s, "l2": "256 MiB buffer written between timed steps (untimed)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "final_rmse": final_rmse},
+            "gpu_launches": int(sum(v[1] for v in prof.values())),
+            "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in kinds.items()},
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                         "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes "
+                                       f"x 2 x {sm_max:.0f} MHz",
+                         "algorithmic_flops_per_launch": flops,
+                         "hbm_gbs": N * bytes_per_signal_pass(p1, p2, s, side) /
+                                    (dom_ms / dom_n / 1e3) / 1e9},
+            "cpu_baseline": {"value": CPU_SAMPLE / cpu_times[0], "unit": UNIT, "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"first {CPU_SAMPLE} of the 200000 patches, one full "
+                                       "Algorithm-1 iteration, FP64 numpy, 1 thread"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "clocks": clk,
+        }
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed region only: no e2e loop, CPU baseline or clock sampling "
+                         "(for profiler runs; its numbers are not bench values)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

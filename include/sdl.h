@@ -157,6 +157,37 @@ int sdl_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
                 int32_t* support, float* coef, int32_t* nnz,
                 float* rmse_out, void* stream);
 
+/*
+ * Tracing: per-kernel device time and launch counts.  The paper reports only
+ * wall-clock times (Tables I, II, IV); this hook gives the per-kernel split.
+ *
+ * Kernel kinds (index into the arrays of sdl_profile_collect):
+ *   0 gram          G = D^T D of a dictionary
+ *   1 code          2D-OMP pass without partial sums (sdl_sparse_code)
+ *   2 code_D1       2D-OMP pass fused with the P, B1 partial sums
+ *   3 code_D2       2D-OMP pass fused with the M, B2 partial sums
+ *   4 accum_D1      partial sums of given codes, D1 side
+ *   5 accum_D2      partial sums of given codes, D2 side
+ *   6 reduce        fixed-order reduction of the partial-sum slots
+ *   7 solve         normal-equation solve + atom normalisation
+ *   8 rescale       X <- W^{-1} X
+ *   9 memset        zeroing of global accumulation slots
+ */
+#define SDL_NUM_KERNEL_KINDS 10
+
+/* Enable (1) or disable (0) event timing of every kernel this context
+ * enqueues.  Launch counts are kept either way.  Host-side, synchronous. */
+int sdl_profile_enable(sdl_ctx* ctx, int enable);
+
+/* Synchronise the device, then write for each kind k < max_kinds the total
+ * device milliseconds (total_ms[k], 0 when timing is off) and the number of
+ * launches (launches[k]) since the previous call, and reset both.  Host
+ * arrays; either may be NULL.  Returns SDL_NUM_KERNEL_KINDS or an error. */
+int sdl_profile_collect(sdl_ctx* ctx, double* total_ms, int64_t* launches, int max_kinds);
+
+/* Name of a kernel kind (static string), "?" when out of range. */
+const char* sdl_kernel_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "sdl_internal.cuh"
 
@@ -23,9 +24,46 @@ struct sdl_ctx {
     float* norms = nullptr;      // column norms of the last solve
     size_t cap_g1 = 0, cap_g2 = 0, cap_part = 0, cap_slots = 0, cap_red = 0, cap_redd = 0,
            cap_norms = 0;
+    // tracing: launch counters and (optionally) one event pair per launch
+    struct Rec {
+        int kind;
+        cudaEvent_t beg, end;
+    };
+    bool timing = false;
+    std::vector<Rec> recs;           // event pool, reused
+    size_t n_recs = 0;               // records in use
+    int64_t launches[SDL_NUM_KERNEL_KINDS] = {};
 };
 
 namespace {
+
+enum Kind { kGram = 0, kCode, kCodeD1, kCodeD2, kAccD1, kAccD2, kReduce, kSolve, kRescale, kMemset };
+constexpr size_t kMaxRecs = 1 << 16;
+
+// Bracket one launch of `kind` on `st` with timing events (when enabled).
+struct Trace {
+    sdl_ctx* c;
+    cudaStream_t st;
+    sdl_ctx::Rec* rec = nullptr;
+    Trace(sdl_ctx* c_, int kind, cudaStream_t st_) : c(c_), st(st_) {
+        c->launches[kind] += 1;
+        if (!c->timing || c->n_recs >= kMaxRecs) return;
+        if (c->n_recs == c->recs.size()) {
+            sdl_ctx::Rec r{kind, nullptr, nullptr};
+            if (cudaEventCreate(&r.beg) != cudaSuccess || cudaEventCreate(&r.end) != cudaSuccess) {
+                cudaGetLastError();
+                return;
+            }
+            c->recs.push_back(r);
+        }
+        rec = &c->recs[c->n_recs++];
+        rec->kind = kind;
+        cudaEventRecord(rec->beg, st);
+    }
+    ~Trace() {
+        if (rec) cudaEventRecord(rec->end, st);
+    }
+};
 
 struct DeviceGuard {
     int prev = -1;
@@ -105,14 +143,28 @@ PassArgs base_args(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const 
     return a;
 }
 
+void grams(sdl_ctx* c, const float* D1, int p1, int n1, const float* D2, int p2, int n2,
+           cudaStream_t st) {
+    {
+        Trace tr(c, kGram, st);
+        launch_gram(D1, p1, n1, c->G1, st);
+    }
+    Trace tr(c, kGram, st);
+    launch_gram(D2, p2, n2, c->G2, st);
+}
+
 // reduce -> solve for one dictionary side, using the partial sums in slots.
 int finish_update(sdl_ctx* c, int slots, int side, float* D, int p1, int p2, int64_t N, int n1,
                   int n2, float* objective_out, float* rmse_out, cudaStream_t st) {
     const int p = side == kSideD1 ? p1 : p2;
     const int n = side == kSideD1 ? n1 : n2;
     const int nf = n * n + p * n;
-    launch_reduce_partials(c->part_f, c->part_d, slots, nf, c->red_f, c->red_d, st);
+    {
+        Trace tr(c, kReduce, st);
+        launch_reduce_partials(c->part_f, c->part_d, slots, nf, c->red_f, c->red_d, st);
+    }
     const double inv_count = N > 0 ? 1.0 / ((double)p1 * p2 * (double)N) : 0.0;
+    Trace tr(c, kSolve, st);
     return launch_solve(c->red_f, c->red_d, D, p, n, c->norms, inv_count, objective_out, rmse_out,
                         c->err, st);
 }
@@ -172,6 +224,10 @@ int sdl_destroy(sdl_ctx* c) {
     cudaFree(c->red_f);
     cudaFree(c->red_d);
     cudaFree(c->norms);
+    for (auto& r : c->recs) {
+        cudaEventDestroy(r.beg);
+        cudaEventDestroy(r.end);
+    }
     delete c;
     return SDL_OK;
 }
@@ -215,15 +271,17 @@ int sdl_sparse_code(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const
     DeviceGuard g(c->device);
     if ((rc = ensure_workspace(c, p1, p2, n1, n2)) != SDL_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    launch_gram(D1, p1, n1, c->G1, st);
-    launch_gram(D2, p2, n2, c->G2, st);
+    grams(c, D1, p1, n1, D2, p2, n2, st);
     PassArgs a = base_args(c, Y, p1, p2, N, D1, n1, D2, n2, s);
     a.eps2 = eps > 0.f ? eps * eps : 0.f;
     a.support = support;
     a.coef = coef;
     a.nnz = nnz;
     a.res_energy = res_energy;
-    rc = launch_code_pass(a, kCodeOnly, st, c->num_sms);
+    {
+        Trace tr(c, kCode, st);
+        rc = launch_code_pass(a, kCodeOnly, st, c->num_sms);
+    }
     return rc < 0 ? rc : SDL_OK;
 }
 
@@ -238,17 +296,23 @@ static int update_common(sdl_ctx* c, int side, const float* Y, int p1, int p2, i
     DeviceGuard g(c->device);
     if ((rc = ensure_workspace(c, p1, p2, n1, n2)) != SDL_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    launch_gram(D1, p1, n1, c->G1, st);
-    launch_gram(D2, p2, n2, c->G2, st);
+    grams(c, D1, p1, n1, D2, p2, n2, st);
     PassArgs a = base_args(c, Y, p1, p2, N, D1, n1, D2, n2, s);
     a.in_support = support;
     a.in_coef = coef;
-    const int slots = launch_accumulate_pass(a, side, st, c->num_sms);
+    int slots;
+    {
+        Trace tr(c, side == kSideD1 ? kAccD1 : kAccD2, st);
+        slots = launch_accumulate_pass(a, side, st, c->num_sms);
+    }
     if (slots < 0) return slots;
     float* D = side == kSideD1 ? D1w : D2w;
     rc = finish_update(c, slots, side, D, p1, p2, N, n1, n2, objective_out, nullptr, st);
     if (rc != SDL_OK) return rc;
-    launch_rescale(support, coef, N * (long long)s, n1, n2, side, c->norms, st);
+    if (N > 0) {
+        Trace tr(c, kRescale, st);
+        launch_rescale(support, coef, N * (long long)s, n1, n2, side, c->norms, st);
+    }
     return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
 }
 
@@ -279,26 +343,76 @@ int sdl_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1
     const float eps2 = eps > 0.f ? eps * eps : 0.f;
 
     // steps 1-2: code with (D1, D2) accumulating P, B1; solve for D1
-    launch_gram(D1, p1, n1, c->G1, st);
-    launch_gram(D2, p2, n2, c->G2, st);
+    grams(c, D1, p1, n1, D2, p2, n2, st);
     PassArgs a = base_args(c, Y, p1, p2, N, D1, n1, D2, n2, s);
     a.eps2 = eps2;
-    int slots = launch_code_pass(a, kSideD1, st, c->num_sms);
+    int slots;
+    {
+        Trace tr(c, kCodeD1, st);
+        slots = launch_code_pass(a, kSideD1, st, c->num_sms);
+    }
     if (slots < 0) return slots;
     rc = finish_update(c, slots, kSideD1, D1, p1, p2, N, n1, n2, nullptr, rmse_out, st);
     if (rc != SDL_OK) return rc;
     // steps 3-4: code with the new D1 accumulating M, B2; solve for D2
-    launch_gram(D1, p1, n1, c->G1, st);
+    {
+        Trace tr(c, kGram, st);
+        launch_gram(D1, p1, n1, c->G1, st);
+    }
     a.support = support;
     a.coef = coef;
     a.nnz = nnz;
-    slots = launch_code_pass(a, kSideD2, st, c->num_sms);
+    {
+        Trace tr(c, kCodeD2, st);
+        slots = launch_code_pass(a, kSideD2, st, c->num_sms);
+    }
     if (slots < 0) return slots;
     rc = finish_update(c, slots, kSideD2, D2, p1, p2, N, n1, n2, nullptr,
                        rmse_out ? rmse_out + 1 : nullptr, st);
     if (rc != SDL_OK) return rc;
-    launch_rescale(support, coef, N * (long long)s, n1, n2, kSideD2, c->norms, st);
+    if (N > 0) {
+        Trace tr(c, kRescale, st);
+        launch_rescale(support, coef, N * (long long)s, n1, n2, kSideD2, c->norms, st);
+    }
     return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+int sdl_profile_enable(sdl_ctx* c, int enable) {
+    if (!c) return SDL_ERR_ARG;
+    c->timing = enable != 0;
+    return SDL_OK;
+}
+
+int sdl_profile_collect(sdl_ctx* c, double* total_ms, int64_t* launches, int max_kinds) {
+    if (!c || max_kinds < 0) return SDL_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return SDL_ERR_CUDA;
+    }
+    double tot[SDL_NUM_KERNEL_KINDS] = {};
+    for (size_t r = 0; r < c->n_recs; ++r) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->recs[r].beg, c->recs[r].end) == cudaSuccess)
+            tot[c->recs[r].kind] += ms;
+        else
+            cudaGetLastError();
+    }
+    c->n_recs = 0;
+    const int m = std::min(max_kinds, (int)SDL_NUM_KERNEL_KINDS);
+    for (int k = 0; k < m; ++k) {
+        if (total_ms) total_ms[k] = tot[k];
+        if (launches) launches[k] = c->launches[k];
+    }
+    for (int k = 0; k < SDL_NUM_KERNEL_KINDS; ++k) c->launches[k] = 0;
+    return SDL_NUM_KERNEL_KINDS;
+}
+
+const char* sdl_kernel_name(int kind) {
+    static const char* names[SDL_NUM_KERNEL_KINDS] = {
+        "gram", "code", "code_D1", "code_D2", "accum_D1", "accum_D2",
+        "reduce", "solve", "rescale", "memset"};
+    return (kind >= 0 && kind < SDL_NUM_KERNEL_KINDS) ? names[kind] : "?";
 }
 
 }  // extern "C"

@@ -42,6 +42,8 @@ SIGNATURES = {
     "sdl_update_D1": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _P, _P, _P],
     "sdl_update_D2": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _P, _P, _P],
     "sdl_iterate": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
+    "sdl_profile_enable": [_P, _I],
+    "sdl_profile_collect": [_P, _P, _P, _I],
 }
 
 
@@ -63,8 +65,9 @@ def lib() -> ctypes.CDLL:
             fn = getattr(L, name)
             fn.argtypes = argtypes
             fn.restype = _I
-        L.sdl_strerror.argtypes = [_I]
-        L.sdl_strerror.restype = ctypes.c_char_p
+        for name in ("sdl_strerror", "sdl_kernel_name"):
+            getattr(L, name).argtypes = [_I]
+            getattr(L, name).restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -165,6 +168,20 @@ class Context:
 
     def check(self, stream=None) -> None:
         _check(self.status(stream), "device")
+
+    def profile(self, enable: bool = True) -> None:
+        """Turn per-kernel event timing on or off (launch counts are always kept)."""
+        _check(self._lib.sdl_profile_enable(self._h, int(bool(enable))), "sdl_profile_enable")
+
+    def profile_collect(self) -> dict:
+        """{kernel name: (total device ms, launches)} since the last collect."""
+        n = 16
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        k = self._lib.sdl_profile_collect(self._h, ms, cnt, n)
+        if k < 0:
+            raise SDLError(k, "sdl_profile_collect")
+        return {self._lib.sdl_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(k)}
 
     def reserve(self, p1, p2, n1, n2, s) -> None:
         _check(self._lib.sdl_reserve(self._h, p1, p2, n1, n2, s), "sdl_reserve")
