@@ -59,7 +59,8 @@ enum sdl_error {
     SDL_ERR_SINGULAR = -4,     /* normal matrix P or M not positive definite  */
     SDL_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up          */
     SDL_ERR_WORKSPACE = -6,    /* workspace allocation failed                 */
-    SDL_ERR_UNSUPPORTED = -7   /* shape outside the compiled tile shapes      */
+    SDL_ERR_UNSUPPORTED = -7,  /* shape outside the compiled tile shapes      */
+    SDL_ERR_CAPACITY = -8      /* problem too large for the static scratch    */
 };
 
 /* Create a context on CUDA device `device` (the device is made current).
@@ -156,6 +157,36 @@ int sdl_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
                 float* D1, int n1, float* D2, int n2, int s_max, float eps,
                 int32_t* support, float* coef, int32_t* nnz,
                 float* rmse_out, void* stream);
+
+/*
+ * sdl_sparse_code_static - the sparse coder of sdl_sparse_code with no
+ * context and no device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory once running
+ * (an application that serves all GPU memory from its own pre-sized pool, or
+ * a latency-critical loop that cannot afford cudaMalloc's implicit device
+ * synchronisation and its possible failure under memory pressure) and for
+ * callers that cannot keep a library context.
+ *
+ * Arguments, layouts and results are those of sdl_sparse_code (the caller
+ * still provides Y, D1, D2 and the output buffers).  The only scratch, the
+ * Gram matrices D1^T D1 and D2^T D2, lives in one file-scope device array of
+ * 8192 floats (32 KiB) that every GPU which loads the library holds until
+ * the process exits; hence n1*n1 + n2*n2 <= 8192, else SDL_ERR_CAPACITY and
+ * nothing is enqueued.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call on a device shares the one array, which keeps the contents
+ *    of the last call (each call rewrites both Gram matrices before reading
+ *    them).  Calls whose work overlaps on the GPU (different streams, no
+ *    ordering between them) race on the array and give wrong codes.
+ *  - Device-side errors are not recorded (no context): a signal with NaN/Inf
+ *    gets nnz = 0.
+ */
+int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
+                           const float* D1, int n1, const float* D2, int n2,
+                           int s_max, float eps,
+                           int32_t* support, float* coef, int32_t* nnz,
+                           float* res_energy, void* stream);
 
 /*
  * Tracing: per-kernel device time and launch counts.  The paper reports only

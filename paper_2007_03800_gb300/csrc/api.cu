@@ -183,6 +183,7 @@ const char* sdl_strerror(int code) {
         case SDL_ERR_TIMEOUT: return "device-side wait timed out";
         case SDL_ERR_WORKSPACE: return "workspace allocation failed";
         case SDL_ERR_UNSUPPORTED: return "shape not supported by the compiled kernels";
+        case SDL_ERR_CAPACITY: return "problem exceeds the static scratch capacity";
         default: return "unknown error";
     }
 }

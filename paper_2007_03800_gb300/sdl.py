@@ -24,6 +24,7 @@ SDL_OK = 0
 ERRORS = {
     -1: "SDL_ERR_ARG", -2: "SDL_ERR_CUDA", -3: "SDL_ERR_NONFINITE", -4: "SDL_ERR_SINGULAR",
     -5: "SDL_ERR_TIMEOUT", -6: "SDL_ERR_WORKSPACE", -7: "SDL_ERR_UNSUPPORTED",
+    -8: "SDL_ERR_CAPACITY",
 }
 
 _P = ctypes.c_void_p
@@ -42,6 +43,7 @@ SIGNATURES = {
     "sdl_update_D1": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _P, _P, _P],
     "sdl_update_D2": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _P, _P, _P],
     "sdl_iterate": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
+    "sdl_sparse_code_static": [_P, _I, _I, _L, _P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
     "sdl_profile_enable": [_P, _I],
     "sdl_profile_collect": [_P, _P, _P, _I],
 }
@@ -124,6 +126,24 @@ def _check_D(D, p, name):
 
 def shape_supported(p1, p2, n1, n2, s) -> bool:
     return bool(lib().sdl_shape_supported(p1, p2, n1, n2, s))
+
+
+def sparse_code_static(Y, D1, D2, s, eps=0.0, out: "Codes | None" = None, stream=None) -> "Codes":
+    """``sdl_sparse_code_static``: the sparse coder without a context and
+    without device allocation (scratch in a static device array; see the
+    header for its limits)."""
+    N, p1, p2 = _check_Y(Y)
+    n1, n2 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2")
+    if out is None:
+        out = Codes.empty(N, s, Y.device, with_energy=True)
+    _need(out.support, torch.int32, (N, s), None, "support")
+    _need(out.coef, torch.float32, (N, s), None, "coef")
+    _need(out.nnz, torch.int32, (N,), None, "nnz")
+    rc = lib().sdl_sparse_code_static(_ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2, s,
+                                      float(eps), _ptr(out.support), _ptr(out.coef),
+                                      _ptr(out.nnz), _ptr(out.res_energy), _stream(stream))
+    _check(rc, "sdl_sparse_code_static")
+    return out
 
 
 class Codes:
