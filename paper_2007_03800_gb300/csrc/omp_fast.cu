@@ -1,0 +1,565 @@
+// 2D-OMP coding pass specialised at compile time for the common pair shapes
+// (one warp per signal), with the TMOD partial sums fused into its epilogue.
+//
+// Same method and results as code_pass_kernel (omp_pass.cu); what changes is
+// the schedule:
+//   * every shape (p1, p2, n1, n2) and the step count s are template
+//     constants, so the s greedy steps are fully unrolled and the selected
+//     pairs, the coefficients, the Cholesky factor and y live in registers;
+//   * lane l keeps row l of L (forward solve) and column l of L (back solve),
+//     so both triangular solves are one shuffle + one FMA per row;
+//   * the argmax is one compare/select pass per entry plus two redux.sync;
+//   * the next signal of each warp is fetched by a TMA bulk copy
+//     (cp.async.bulk, mbarrier completion) while the current one is coded;
+//   * shared-memory rows of D1, G1, G2 and Z are padded so that each lane's
+//     block of the n1 x n2 correlation matrix loads with 64/128-bit accesses.
+// Correlation C0 = D1^T (Y D2): Z = Y D2 is formed cooperatively (a ZA x ZB
+// block per lane) into shared memory, then each lane contracts its RI x RJ
+// block.  Scores are recomputed from C0 every step (Gram domain):
+//   C = C0 - sum_l x_l G1[:, i_l] G2[j_l, :].
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+#include "sdl_internal.cuh"
+
+namespace sdl {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr long long kWaitLimit = 1ll << 26;   // bounded mbarrier wait (polls)
+
+__host__ __device__ constexpr int pad_vec(int r) { return r <= 2 ? r : ((r + 3) & ~3); }
+__host__ __device__ constexpr int al4(int x) { return (x + 3) & ~3; }
+
+template <int P1_, int P2_, int N1_, int N2_, int S_, int LI_, int RI_, int RJ_, int ZA_, int ZB_,
+          int MINB_>
+struct Shape {
+    static constexpr int P1 = P1_, P2 = P2_, N1 = N1_, N2 = N2_, S = S_;
+    static constexpr int MINB = MINB_;   // CTAs of 256 threads per SM the registers must allow
+    static constexpr int LI = LI_, LJ = 32 / LI_, RI = RI_, RJ = RJ_, E = RI_ * RJ_;
+    static constexpr int RIP = pad_vec(RI_), RJP = pad_vec(RJ_);
+    static constexpr int LD1 = LI * RIP, LD2 = LJ * RJP;     // padded row strides
+    static constexpr int ZA = ZA_, ZB = ZB_;
+    static constexpr int ZLA = P1_ / ZA_, ZLB = N2_ / ZB_;   // Z-stage lane grid
+    static constexpr int PP = P1_ * P2_;
+    // lane stride of the C0 blocks in shared memory: a multiple of 4 floats
+    // that is not a multiple of 32 (8 lanes of a 128-bit phase hit distinct banks)
+    static constexpr int EP = (al4(E) % 32 == 0) ? al4(E) + 4 : al4(E);
+    static_assert(LI * RI == N1 && LJ * RJ == N2, "lane grid must tile n1 x n2 exactly");
+    static_assert(ZLA * ZA == P1 && ZLB * ZB == N2 && ZLA * ZLB <= 32, "Z tiling");
+    static_assert(S <= 32 && S <= P1 * P2 && S <= N1 * N2, "s");
+    static_assert((PP * 4) % 16 == 0, "TMA bulk copies need 16-byte multiples");
+};
+
+// padded position of correlation row i / column j inside the SMEM row layouts
+template <class Sh> __device__ __forceinline__ int pos1(int i) {
+    return (i / Sh::RI) * Sh::RIP + i % Sh::RI;
+}
+template <class Sh> __device__ __forceinline__ int pos2(int j) {
+    return (j / Sh::RJ) * Sh::RJP + j % Sh::RJ;
+}
+
+template <int R>
+__device__ __forceinline__ void vload(float (&v)[R], const float* p) {
+    if constexpr (R % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < R; k += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(p + k);
+            v[k] = t.x; v[k + 1] = t.y; v[k + 2] = t.z; v[k + 3] = t.w;
+        }
+    } else if constexpr (R == 2) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else if constexpr (R == 3) {
+        const float4 t = *reinterpret_cast<const float4*>(p);   // 4th lane is padding
+        v[0] = t.x; v[1] = t.y; v[2] = t.z;
+    } else if constexpr (R == 6) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        const float2 u = *reinterpret_cast<const float2*>(p + 4);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; v[4] = u.x; v[5] = u.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = p[k];
+    }
+}
+
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// ---------------------------------------------------------------- mbarrier / TMA
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// arrive (this thread) and expect `bytes` of asynchronous transactions
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy completing on `bar`
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// bounded wait for phase `parity` of `bar`; false on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned a = smem_addr(bar);
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ layout
+template <class Sh>
+struct FastLayout {
+    // floats; every region starts 16-byte aligned
+    static constexpr int d1r = 0;                                   // P1 x LD1
+    static constexpr int d1c = d1r + al4(Sh::P1 * Sh::LD1);         // N1 x P1 (D1 columns)
+    static constexpr int d2r = d1c + al4(Sh::N1 * Sh::P1);          // P2 x N2
+    static constexpr int g1 = d2r + al4(Sh::P2 * Sh::N2);           // N1 x LD1
+    static constexpr int g2 = g1 + al4(Sh::N1 * Sh::LD1);           // N2 x LD2
+    static constexpr int acc = g2 + al4(Sh::N2 * Sh::LD2);
+    __host__ __device__ static constexpr int nf(int side) {
+        return side == kSideD1 ? Sh::N1 * Sh::N1 + Sh::P1 * Sh::N1
+               : side == kSideD2 ? Sh::N2 * Sh::N2 + Sh::P2 * Sh::N2 : 0;
+    }
+    __host__ __device__ static constexpr int accd(int side) { return acc + al4(nf(side)); }     // 2 doubles
+    __host__ __device__ static constexpr int warp0(int side) { return accd(side) + 4; }
+    // per warp: mbarriers (4 floats), Y double buffer, Z, the C0 blocks of
+    // the 32 lanes (lane-major, stride EP: conflict-free 128-bit loads)
+    static constexpr int EP = Sh::EP;
+    static constexpr int w_bar = 0;
+    static constexpr int w_y = 4;
+    static constexpr int w_z = w_y + 2 * al4(Sh::PP);
+    static constexpr int w_c0 = w_z + al4(Sh::P1 * Sh::LD2);
+    static constexpr int w_stride = w_c0 + 32 * EP;
+    __host__ __device__ static constexpr int total(int side, int wpc) { return warp0(side) + wpc * w_stride; }
+};
+
+template <class Sh, int SIDE>
+__global__ void __launch_bounds__(256, Sh::MINB) code_fast_kernel(PassArgs a) {
+    using L = FastLayout<Sh>;
+    constexpr int P1 = Sh::P1, P2 = Sh::P2, N1 = Sh::N1, N2 = Sh::N2, S = Sh::S;
+    constexpr int RI = Sh::RI, RJ = Sh::RJ, E = Sh::E, LI = Sh::LI;
+    constexpr int LD1 = Sh::LD1, LD2 = Sh::LD2, RIP = Sh::RIP, RJP = Sh::RJP;
+    constexpr int PP = Sh::PP;
+    constexpr unsigned kBytes = PP * 4;
+    extern __shared__ __align__(16) float smem[];
+
+    const int wpc = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li = lane % LI, lj = lane / LI;
+    float* D1r = smem + L::d1r;
+    float* D1c = smem + L::d1c;
+    float* D2r = smem + L::d2r;
+    float* G1s = smem + L::g1;
+    float* G2s = smem + L::g2;
+    float* acc = smem + L::acc;
+    double* accd = reinterpret_cast<double*>(smem + L::accd(SIDE));
+    float* wb = smem + L::warp0(SIDE) + w * L::w_stride;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(wb + L::w_bar);
+    float* Ybuf = wb + L::w_y;
+    float* Zs = wb + L::w_z;
+    float* C0s = wb + L::w_c0;
+    float* myc0 = C0s + lane * L::EP;
+    constexpr int nf = L::nf(SIDE);
+
+    // ---- CTA set-up: padded copies of D1, D2, G1, G2; zero accumulators
+    for (int e = threadIdx.x; e < P1 * LD1; e += blockDim.x) {
+        const int r = e / LD1, pp = e % LD1;
+        const int blk = pp / RIP, off = pp % RIP;
+        D1r[e] = (off < RI) ? a.D1[r + P1 * (blk * RI + off)] : 0.f;
+    }
+    for (int e = threadIdx.x; e < N1 * P1; e += blockDim.x) D1c[e] = a.D1[e];
+    for (int e = threadIdx.x; e < P2 * N2; e += blockDim.x) {
+        const int r = e / N2, j = e % N2;
+        D2r[e] = a.D2[r + P2 * j];
+    }
+    for (int e = threadIdx.x; e < N1 * LD1; e += blockDim.x) {
+        const int c = e / LD1, pp = e % LD1;
+        const int blk = pp / RIP, off = pp % RIP;
+        G1s[e] = (off < RI) ? a.G1[c * N1 + blk * RI + off] : 0.f;
+    }
+    for (int e = threadIdx.x; e < N2 * LD2; e += blockDim.x) {
+        const int c = e / LD2, pp = e % LD2;
+        const int blk = pp / RJP, off = pp % RJP;
+        G2s[e] = (off < RJ) ? a.G2[c * N2 + blk * RJ + off] : 0.f;
+    }
+    if constexpr (SIDE != kCodeOnly) {
+        for (int e = threadIdx.x; e < nf; e += blockDim.x) acc[e] = 0.f;
+        if (threadIdx.x < 2) accd[threadIdx.x] = 0.0;
+    }
+    for (int e = threadIdx.x; e < wpc * L::w_stride; e += blockDim.x)
+        smem[L::warp0(SIDE) + e] = 0.f;   // Z padding columns stay 0
+    __syncthreads();
+
+    const long long stride = (long long)gridDim.x * wpc;
+    long long k = (long long)blockIdx.x * wpc + w;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    if (lane == 0 && k < a.N) {
+        mbar_arrive_tx(&bar[0], kBytes);
+        tma_load_1d(Ybuf, a.Y + (size_t)k * PP, kBytes, &bar[0]);
+    }
+    unsigned phase0 = 0, phase1 = 0;
+    double w_energy = 0.0, w_ynorm = 0.0;
+    bool alive = true;
+    int pending = 0;
+
+    for (int it = 0; k < a.N && alive; ++it, k += stride) {
+        const int buf = it & 1;
+        float* Ys = Ybuf + buf * al4(PP);
+        const bool got = mbar_wait(&bar[buf], buf ? phase1 : phase0);
+        if (!__all_sync(kFull, got)) {
+            if (lane == 0) record_error(a.err, SDL_ERR_TIMEOUT);
+            alive = false;
+            pending = buf;
+            break;
+        }
+        if (buf) phase1 ^= 1u; else phase0 ^= 1u;
+        // prefetch this warp's next signal into the other buffer
+        const long long kn = k + stride;
+        if (lane == 0 && kn < a.N) {
+            fence_proxy_async();
+            mbar_arrive_tx(&bar[buf ^ 1], kBytes);
+            tma_load_1d(Ybuf + (buf ^ 1) * al4(PP), a.Y + (size_t)kn * PP, kBytes, &bar[buf ^ 1]);
+        }
+
+        // ---- ||Y||^2
+        float ss = 0.f;
+#pragma unroll
+        for (int e = lane; e < PP; e += 32) ss = fmaf(Ys[e], Ys[e], ss);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+        const bool finite = isfinite(ss);
+
+        int cnt = 0;
+        float E2 = ss;
+        int myi = 0, myj = 0;
+        float myx = 0.f;
+        if (finite) {
+            // ---- Z = Y D2 (ZA x ZB block per lane)
+            if (lane < Sh::ZLA * Sh::ZLB) {
+                const int za = lane % Sh::ZLA, zb = lane / Sh::ZLA;
+                const int a0 = za * Sh::ZA, j0 = zb * Sh::ZB;
+                float z[Sh::ZA][Sh::ZB];
+#pragma unroll
+                for (int r = 0; r < Sh::ZA; ++r)
+#pragma unroll
+                    for (int c = 0; c < Sh::ZB; ++c) z[r][c] = 0.f;
+#pragma unroll
+                for (int b = 0; b < P2; ++b) {
+                    float yv[Sh::ZA], dv[Sh::ZB];
+#pragma unroll
+                    for (int r = 0; r < Sh::ZA; ++r) yv[r] = Ys[b * P1 + a0 + r];
+#pragma unroll
+                    for (int c = 0; c < Sh::ZB; ++c) dv[c] = D2r[b * N2 + j0 + c];
+#pragma unroll
+                    for (int r = 0; r < Sh::ZA; ++r)
+#pragma unroll
+                        for (int c = 0; c < Sh::ZB; ++c) z[r][c] = fmaf(yv[r], dv[c], z[r][c]);
+                }
+#pragma unroll
+                for (int r = 0; r < Sh::ZA; ++r)
+#pragma unroll
+                    for (int c = 0; c < Sh::ZB; ++c) Zs[(a0 + r) * LD2 + pos2<Sh>(j0 + c)] = z[r][c];
+            }
+            __syncwarp();
+            // ---- C0 = D1^T Z on the lane's RI x RJ block (flat index e = c*RI + r)
+            float c0[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) c0[e] = 0.f;
+#pragma unroll
+            for (int aa = 0; aa < P1; ++aa) {
+                float u[RI], v[RJ];
+                vload<RI>(u, D1r + aa * LD1 + li * RIP);
+                vload<RJ>(v, Zs + aa * LD2 + lj * RJP);
+#pragma unroll
+                for (int c = 0; c < RJ; ++c)
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) c0[c * RI + r] = fmaf(u[r], v[c], c0[c * RI + r]);
+            }
+
+            // keep C0 in shared memory: re-read once per step, masked by one store
+#pragma unroll
+            for (int e = 0; e < E; e += 4) {
+                if (e + 4 <= E) {
+                    *reinterpret_cast<float4*>(myc0 + e) = make_float4(c0[e], c0[e + 1], c0[e + 2], c0[e + 3]);
+                } else {
+#pragma unroll
+                    for (int k2 = e; k2 < E; ++k2) myc0[k2] = c0[k2];
+                }
+            }
+            __syncwarp();
+
+            // ---- greedy steps, fully unrolled
+            int si[S], sj[S];
+            float xs[S], Lrow[S], Lcol[S];
+#pragma unroll
+            for (int m = 0; m < S; ++m) {
+                si[m] = 0; sj[m] = 0; xs[m] = 0.f; Lrow[m] = 0.f; Lcol[m] = 0.f;
+            }
+            float myinvd = 0.f, myy = 0.f;
+            bool go = true;
+            const int qbase = li * RI + N1 * (lj * RJ);
+            static_for<0, S>([&](auto tc) {
+                constexpr int t = decltype(tc)::value;
+                if (!go) return;
+                if (a.eps2 > 0.f && E2 <= a.eps2) { go = false; return; }
+                float sc[E];
+                if constexpr (t == 0) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) sc[e] = c0[e];
+                } else {
+                    vload<E>(sc, myc0);
+                }
+#pragma unroll
+                for (int l = 0; l < t; ++l) {
+                    float u[RI], v[RJ];
+                    vload<RI>(u, G1s + si[l] * LD1 + li * RIP);
+                    vload<RJ>(v, G2s + sj[l] * LD2 + lj * RJP);
+#pragma unroll
+                    for (int c = 0; c < RJ; ++c) {
+                        const float vx = v[c] * xs[l];
+#pragma unroll
+                        for (int r = 0; r < RI; ++r) sc[c * RI + r] = fmaf(-u[r], vx, sc[c * RI + r]);
+                    }
+                }
+                // argmax |sc|, ties to the smallest q: entries visited in increasing q
+                float best = 0.f;
+                int bq = 0x7fffffff;
+#pragma unroll
+                for (int c = 0; c < RJ; ++c)
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) {
+                        const float v = fabsf(sc[c * RI + r]);
+                        if (v > best) { best = v; bq = qbase + r + N1 * c; }
+                    }
+                const unsigned M = __reduce_max_sync(kFull, __float_as_uint(best));
+                if (M == 0u) { go = false; return; }
+                const unsigned cand = (__float_as_uint(best) == M) ? (unsigned)bq : 0xffffffffu;
+                const int q = (int)__reduce_min_sync(kFull, cand);
+                const int it_ = q % N1, jt = q / N1;
+                const int owner = it_ / RI + LI * (jt / RJ);
+                float* cq = C0s + owner * L::EP + (jt % RJ) * RI + it_ % RI;
+                const float b = *cq;
+                __syncwarp();
+                if (lane == 0) *cq = __int_as_float(0x7fc00000);   // mask the pick
+                // ---- Cholesky row t:  w = L^{-1} a,  L_tt = sqrt(A_tt - w.w)
+                const int p1t = pos1<Sh>(it_), p2t = pos2<Sh>(jt);
+                float r = 0.f;
+                if (lane < t) r = G1s[it_ * LD1 + pos1<Sh>(myi)] * G2s[jt * LD2 + pos2<Sh>(myj)];
+                const float Att = G1s[it_ * LD1 + p1t] * G2s[jt * LD2 + p2t];
+                float ww = 0.f, wy = 0.f;
+#pragma unroll
+                for (int m = 0; m < t; ++m) {
+                    const float wm = __shfl_sync(kFull, r * myinvd, m);
+                    const float ym = __shfl_sync(kFull, myy, m);
+                    r = fmaf(-Lrow[m], wm, r);
+                    ww = fmaf(wm, wm, ww);
+                    wy = fmaf(wm, ym, wy);
+                    if (lane == t) Lrow[m] = wm;
+                    if (lane == m) Lcol[t] = wm;
+                }
+                const float d = Att - ww;
+                if (!(d > kPivotRel * Att)) { go = false; return; }
+                const float inv = rsqrtf(d);
+                const float yt = (b - wy) * inv;
+                si[t] = it_;
+                sj[t] = jt;
+                if (lane == t) {
+                    Lrow[t] = d * inv;
+                    myinvd = inv;
+                    myy = yt;
+                    myi = it_;
+                    myj = jt;
+                }
+                // ---- x = L^{-T} y (rows 0..t)
+                float rb = myy;
+#pragma unroll
+                for (int kk = t; kk >= 0; --kk) {
+                    const float xk = __shfl_sync(kFull, rb * myinvd, kk);
+                    rb = fmaf(-Lcol[kk], xk, rb);
+                    xs[kk] = xk;
+                }
+                E2 = fmaf(-yt, yt, E2);
+                cnt = t + 1;
+                __syncwarp();   // the masked C0 entry is visible to the next step
+            });
+#pragma unroll
+            for (int m = 0; m < S; ++m)
+                if (lane == m) myx = xs[m];
+        }
+
+        // ---- emit the code (lane l holds pick l)
+        if (a.support && lane < S) {
+            a.support[(size_t)k * S + lane] = (lane < cnt) ? myi + N1 * myj : -1;
+            a.coef[(size_t)k * S + lane] = (lane < cnt) ? myx : 0.f;
+        }
+        if (lane == 0) {
+            if (a.nnz) a.nnz[k] = cnt;
+            if (a.res_energy) a.res_energy[k] = finite ? fmaxf(E2, 0.f) : __int_as_float(0x7fc00000);
+            if (!finite) record_error(a.err, SDL_ERR_NONFINITE);
+        }
+
+        // ---- fused partial sums
+        if constexpr (SIDE == kSideD1) {
+            float* accP = acc;
+            float* accB = acc + N1 * N1;
+#pragma unroll
+            for (int e0 = 0; e0 < P1 * S; e0 += 32) {
+                const int e = e0 + lane;
+                const int l = e / P1, r = e % P1;
+                const int il = __shfl_sync(kFull, myi, l & 31), jl = __shfl_sync(kFull, myj, l & 31);
+                const float xl = __shfl_sync(kFull, myx, l & 31);
+                if (l < cnt) atomicAdd(&accB[r * N1 + il], xl * Zs[r * LD2 + pos2<Sh>(jl)]);
+            }
+#pragma unroll
+            for (int e0 = 0; e0 < S * S; e0 += 32) {
+                const int e = e0 + lane;
+                const int l = e / S, m = e % S;
+                const int il = __shfl_sync(kFull, myi, l & 31), im = __shfl_sync(kFull, myi, m);
+                const int jl = __shfl_sync(kFull, myj, l & 31), jm = __shfl_sync(kFull, myj, m);
+                const float xl = __shfl_sync(kFull, myx, l & 31), xm = __shfl_sync(kFull, myx, m);
+                if (l < cnt && m < cnt)
+                    atomicAdd(&accP[il * N1 + im], xl * xm * G2s[jl * LD2 + pos2<Sh>(jm)]);
+            }
+        } else if constexpr (SIDE == kSideD2) {
+            float* accM = acc;
+            float* accB = acc + N2 * N2;
+#pragma unroll
+            for (int e0 = 0; e0 < P2 * S; e0 += 32) {
+                const int e = e0 + lane;
+                const int l = e / P2, bb = e % P2;
+                const int il = __shfl_sync(kFull, myi, l & 31), jl = __shfl_sync(kFull, myj, l & 31);
+                const float xl = __shfl_sync(kFull, myx, l & 31);
+                if (l < cnt) {
+                    float wsum = 0.f;
+                    const float* yc = Ys + bb * P1;
+                    const float* dc = D1c + il * P1;
+#pragma unroll
+                    for (int r = 0; r < P1; ++r) wsum = fmaf(yc[r], dc[r], wsum);
+                    atomicAdd(&accB[bb * N2 + jl], xl * wsum);
+                }
+            }
+#pragma unroll
+            for (int e0 = 0; e0 < S * S; e0 += 32) {
+                const int e = e0 + lane;
+                const int l = e / S, m = e % S;
+                const int il = __shfl_sync(kFull, myi, l & 31), im = __shfl_sync(kFull, myi, m);
+                const int jl = __shfl_sync(kFull, myj, l & 31), jm = __shfl_sync(kFull, myj, m);
+                const float xl = __shfl_sync(kFull, myx, l & 31), xm = __shfl_sync(kFull, myx, m);
+                if (l < cnt && m < cnt)
+                    atomicAdd(&accM[jl * N2 + jm], xl * xm * G1s[il * LD1 + pos1<Sh>(im)]);
+            }
+        }
+        if (lane == 0 && finite) {
+            w_energy += (double)fmaxf(E2, 0.f);
+            w_ynorm += (double)ss;
+        }
+        __syncwarp();
+    }
+    if (!alive && lane == 0) {
+        // give the copy that timed out a last bounded chance to land before the
+        // CTA's shared memory is released
+        mbar_wait(&bar[pending], pending ? phase1 : phase0);
+    }
+
+    if constexpr (SIDE != kCodeOnly) {
+        if (lane == 0) {
+            atomicAdd(&accd[0], w_energy);
+            atomicAdd(&accd[1], w_ynorm);
+        }
+        __syncthreads();
+        float* dst = a.part_f + (size_t)blockIdx.x * nf;
+        for (int e = threadIdx.x; e < nf; e += blockDim.x) dst[e] = acc[e];
+        if (threadIdx.x < 2) a.part_d[(size_t)blockIdx.x * 2 + threadIdx.x] = accd[threadIdx.x];
+    }
+}
+
+constexpr int kWarpsPerCta = 8;
+constexpr int kMaxCtasPerSm = 8;
+
+template <class Sh, int SIDE>
+int launch_fast_impl(const PassArgs& a, cudaStream_t st, int num_sms) {
+    using L = FastLayout<Sh>;
+    const size_t bytes = sizeof(float) * (size_t)L::total(SIDE, kWarpsPerCta);
+    auto kern = code_fast_kernel<Sh, SIDE>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return SDL_ERR_CUDA;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kWarpsPerCta * 32, bytes) !=
+        cudaSuccess)
+        return SDL_ERR_CUDA;
+    bps = std::max(1, std::min(bps, kMaxCtasPerSm));
+    const long long need = (a.N + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms * bps));
+    kern<<<grid, kWarpsPerCta * 32, bytes, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
+    return SIDE == kCodeOnly ? 0 : grid;
+}
+
+template <class Sh>
+int launch_fast_side(const PassArgs& a, int side, cudaStream_t st, int num_sms) {
+    switch (side) {
+        case kCodeOnly: return launch_fast_impl<Sh, kCodeOnly>(a, st, num_sms);
+        case kSideD1: return launch_fast_impl<Sh, kSideD1>(a, st, num_sms);
+        case kSideD2: return launch_fast_impl<Sh, kSideD2>(a, st, num_sms);
+        default: return SDL_ERR_ARG;
+    }
+}
+
+// Compiled shapes: <p1, p2, n1, n2, s, LI, RI, RJ, ZA, ZB, min CTAs/SM>
+using F8x16s4 = Shape<8, 8, 16, 16, 4, 4, 4, 2, 2, 2, 3>;
+using F12x24s6 = Shape<12, 12, 24, 24, 6, 4, 6, 3, 3, 3, 2>;
+using F16x32s8 = Shape<16, 16, 32, 32, 8, 4, 8, 4, 4, 4, 2>;
+
+}  // namespace
+
+int launch_code_pass_fast(const PassArgs& a, int side, cudaStream_t st, int num_sms) {
+    // the fast kernels keep the pass's accumulators in shared memory and
+    // write one partial-sum slot per CTA, like the generic kernel
+    const int key[5] = {a.p1, a.p2, a.n1, a.n2, a.s};
+    auto is = [&](int p1, int p2, int n1, int n2, int s) {
+        return key[0] == p1 && key[1] == p2 && key[2] == n1 && key[3] == n2 && key[4] == s;
+    };
+    if (is(8, 8, 16, 16, 4)) return launch_fast_side<F8x16s4>(a, side, st, num_sms);
+    if (is(12, 12, 24, 24, 6)) return launch_fast_side<F12x24s6>(a, side, st, num_sms);
+    if (is(16, 16, 32, 32, 8)) return launch_fast_side<F16x32s8>(a, side, st, num_sms);
+    return SDL_ERR_UNSUPPORTED;
+}
+
+}  // namespace sdl

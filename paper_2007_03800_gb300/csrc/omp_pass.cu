@@ -692,6 +692,11 @@ bool code_shape_supported(int p1, int p2, int n1, int n2, int s) {
 int max_partial_slots(int num_sms) { return std::max(num_sms * kCtaSlotsPerSm, kGlobalSlots); }
 
 int launch_code_pass(const PassArgs& a, int side, cudaStream_t st, int num_sms) {
+    // the specialised kernels fetch signals with 16-byte TMA bulk copies
+    if ((reinterpret_cast<uintptr_t>(a.Y) & 15u) == 0) {
+        const int r = launch_code_pass_fast(a, side, st, num_sms);
+        if (r != SDL_ERR_UNSUPPORTED) return r;
+    }
     switch (side) {
         case kCodeOnly: return dispatch_code<kCodeOnly>(a, st, num_sms);
         case kSideD1: return dispatch_code<kSideD1>(a, st, num_sms);

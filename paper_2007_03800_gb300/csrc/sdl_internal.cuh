@@ -55,6 +55,9 @@ struct PassArgs {
 // slots written (to be reduced), or a negative sdl_error.
 int launch_code_pass(const PassArgs& a, int side, cudaStream_t st, int num_sms);
 int launch_accumulate_pass(const PassArgs& a, int side, cudaStream_t st, int num_sms);
+// omp_fast.cu: compile-time-shape kernels; SDL_ERR_UNSUPPORTED when no
+// specialisation matches (the caller then uses the generic kernel).
+int launch_code_pass_fast(const PassArgs& a, int side, cudaStream_t st, int num_sms);
 bool code_shape_supported(int p1, int p2, int n1, int n2, int s);
 // Upper bound of the partial-sum slots any pass may use for these sizes.
 int max_partial_slots(int num_sms);
