@@ -145,17 +145,14 @@ PassArgs base_args(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const 
 
 void grams(sdl_ctx* c, const float* D1, int p1, int n1, const float* D2, int p2, int n2,
            cudaStream_t st) {
-    {
-        Trace tr(c, kGram, st);
-        launch_gram(D1, p1, n1, c->G1, st);
-    }
     Trace tr(c, kGram, st);
-    launch_gram(D2, p2, n2, c->G2, st);
+    launch_gram2(D1, p1, n1, c->G1, D2, p2, n2, c->G2, st);
 }
 
 // reduce -> solve for one dictionary side, using the partial sums in slots.
 int finish_update(sdl_ctx* c, int slots, int side, float* D, int p1, int p2, int64_t N, int n1,
-                  int n2, float* objective_out, float* rmse_out, cudaStream_t st) {
+                  int n2, float* objective_out, float* rmse_out, cudaStream_t st,
+                  float* G_out = nullptr) {
     const int p = side == kSideD1 ? p1 : p2;
     const int n = side == kSideD1 ? n1 : n2;
     const int nf = n * n + p * n;
@@ -166,7 +163,7 @@ int finish_update(sdl_ctx* c, int slots, int side, float* D, int p1, int p2, int
     const double inv_count = N > 0 ? 1.0 / ((double)p1 * p2 * (double)N) : 0.0;
     Trace tr(c, kSolve, st);
     return launch_solve(c->red_f, c->red_d, D, p, n, c->norms, inv_count, objective_out, rmse_out,
-                        c->err, st);
+                        c->err, st, G_out);
 }
 
 }  // namespace
@@ -353,13 +350,10 @@ int sdl_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1
         slots = launch_code_pass(a, kSideD1, st, c->num_sms);
     }
     if (slots < 0) return slots;
-    rc = finish_update(c, slots, kSideD1, D1, p1, p2, N, n1, n2, nullptr, rmse_out, st);
+    // the solve also refreshes G1 for the new D1
+    rc = finish_update(c, slots, kSideD1, D1, p1, p2, N, n1, n2, nullptr, rmse_out, st, c->G1);
     if (rc != SDL_OK) return rc;
     // steps 3-4: code with the new D1 accumulating M, B2; solve for D2
-    {
-        Trace tr(c, kGram, st);
-        launch_gram(D1, p1, n1, c->G1, st);
-    }
     a.support = support;
     a.coef = coef;
     a.nnz = nnz;

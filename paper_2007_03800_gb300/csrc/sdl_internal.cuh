@@ -66,9 +66,12 @@ int max_partial_slots(int num_sms);
 void launch_gram(const float* D, int p, int n, float* G, cudaStream_t st);
 void launch_reduce_partials(const float* part_f, const double* part_d, int n_slots,
                             int nf, float* red_f, double* red_d, cudaStream_t st);
+void launch_gram2(const float* D1, int p1, int n1, float* G1, const float* D2, int p2, int n2,
+                  float* G2, cudaStream_t st);
+// G_out (may be NULL): receives the Gram matrix of D after the update.
 int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n,
                  float* norms, double inv_count, float* objective_out, float* rmse_out,
-                 int* err, cudaStream_t st);
+                 int* err, cudaStream_t st, float* G_out = nullptr);
 void launch_rescale(const int32_t* support, float* coef, long long count, int n1, int n2,
                     int side, const float* norms, cudaStream_t st);
 
