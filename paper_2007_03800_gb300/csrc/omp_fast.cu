@@ -33,10 +33,11 @@ __host__ __device__ constexpr int pad_vec(int r) { return r <= 2 ? r : ((r + 3) 
 __host__ __device__ constexpr int al4(int x) { return (x + 3) & ~3; }
 
 template <int P1_, int P2_, int N1_, int N2_, int S_, int LI_, int RI_, int RJ_, int ZA_, int ZB_,
-          int MINB_>
+          int WPC_, int MINB_>
 struct Shape {
     static constexpr int P1 = P1_, P2 = P2_, N1 = N1_, N2 = N2_, S = S_;
-    static constexpr int MINB = MINB_;   // CTAs of 256 threads per SM the registers must allow
+    static constexpr int WPC = WPC_;     // warps (= signals in flight) per CTA
+    static constexpr int MINB = MINB_;   // CTAs per SM the register budget must allow
     static constexpr int LI = LI_, LJ = 32 / LI_, RI = RI_, RJ = RJ_, E = RI_ * RJ_;
     static constexpr int RIP = pad_vec(RI_), RJP = pad_vec(RJ_);
     static constexpr int LD1 = LI * RIP, LD2 = LJ * RJP;     // padded row strides
@@ -79,8 +80,18 @@ __device__ __forceinline__ void vload(float (&v)[R], const float* p) {
         const float2 u = *reinterpret_cast<const float2*>(p + 4);
         v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; v[4] = u.x; v[5] = u.y;
     } else {
+        // 16-byte-aligned p: float4 chunks, then a float2 / float tail
 #pragma unroll
-        for (int k = 0; k < R; ++k) v[k] = p[k];
+        for (int k = 0; k + 4 <= R; k += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(p + k);
+            v[k] = t.x; v[k + 1] = t.y; v[k + 2] = t.z; v[k + 3] = t.w;
+        }
+        constexpr int k0 = R & ~3;
+        if constexpr (R - k0 >= 2) {
+            const float2 t = *reinterpret_cast<const float2*>(p + k0);
+            v[k0] = t.x; v[k0 + 1] = t.y;
+        }
+        if constexpr ((R - k0) & 1) v[R - 1] = p[R - 1];
     }
 }
 
@@ -165,7 +176,7 @@ struct FastLayout {
 };
 
 template <class Sh, int SIDE>
-__global__ void __launch_bounds__(256, Sh::MINB) code_fast_kernel(PassArgs a) {
+__global__ void __launch_bounds__(Sh::WPC * 32, Sh::MINB) code_fast_kernel(PassArgs a) {
     using L = FastLayout<Sh>;
     constexpr int P1 = Sh::P1, P2 = Sh::P2, N1 = Sh::N1, N2 = Sh::N2, S = Sh::S;
     constexpr int RI = Sh::RI, RJ = Sh::RJ, E = Sh::E, LI = Sh::LI;
@@ -234,7 +245,9 @@ __global__ void __launch_bounds__(256, Sh::MINB) code_fast_kernel(PassArgs a) {
         tma_load_1d(Ybuf, a.Y + (size_t)k * PP, kBytes, &bar[0]);
     }
     unsigned phase0 = 0, phase1 = 0;
-    double w_energy = 0.0, w_ynorm = 0.0;
+    // per-warp residual-energy and ||Y||^2 sums: compensated FP32 (the FP64
+    // pipe is slow on this part), widened to FP64 once per warp
+    float w_energy = 0.f, w_energy_c = 0.f, w_ynorm = 0.f, w_ynorm_c = 0.f;
     bool alive = true;
     int pending = 0;
 
@@ -326,10 +339,10 @@ __global__ void __launch_bounds__(256, Sh::MINB) code_fast_kernel(PassArgs a) {
 
             // ---- greedy steps, fully unrolled
             int si[S], sj[S];
-            float xs[S], Lrow[S], Lcol[S];
+            float xs[S], yv[S], Lrow[S], Lcol[S];
 #pragma unroll
             for (int m = 0; m < S; ++m) {
-                si[m] = 0; sj[m] = 0; xs[m] = 0.f; Lrow[m] = 0.f; Lcol[m] = 0.f;
+                si[m] = 0; sj[m] = 0; xs[m] = 0.f; yv[m] = 0.f; Lrow[m] = 0.f; Lcol[m] = 0.f;
             }
             float myinvd = 0.f, myy = 0.f;
             bool go = true;
@@ -386,10 +399,9 @@ __global__ void __launch_bounds__(256, Sh::MINB) code_fast_kernel(PassArgs a) {
 #pragma unroll
                 for (int m = 0; m < t; ++m) {
                     const float wm = __shfl_sync(kFull, r * myinvd, m);
-                    const float ym = __shfl_sync(kFull, myy, m);
                     r = fmaf(-Lrow[m], wm, r);
                     ww = fmaf(wm, wm, ww);
-                    wy = fmaf(wm, ym, wy);
+                    wy = fmaf(wm, yv[m], wy);
                     if (lane == t) Lrow[m] = wm;
                     if (lane == m) Lcol[t] = wm;
                 }
@@ -397,6 +409,7 @@ __global__ void __launch_bounds__(256, Sh::MINB) code_fast_kernel(PassArgs a) {
                 if (!(d > kPivotRel * Att)) { go = false; return; }
                 const float inv = rsqrtf(d);
                 const float yt = (b - wy) * inv;
+                yv[t] = yt;
                 si[t] = it_;
                 sj[t] = jt;
                 if (lane == t) {
@@ -486,8 +499,14 @@ __global__ void __launch_bounds__(256, Sh::MINB) code_fast_kernel(PassArgs a) {
             }
         }
         if (lane == 0 && finite) {
-            w_energy += (double)fmaxf(E2, 0.f);
-            w_ynorm += (double)ss;
+            const float ye = fmaxf(E2, 0.f) - w_energy_c;
+            const float te = w_energy + ye;
+            w_energy_c = (te - w_energy) - ye;
+            w_energy = te;
+            const float yy = ss - w_ynorm_c;
+            const float ty = w_ynorm + yy;
+            w_ynorm_c = (ty - w_ynorm) - yy;
+            w_ynorm = ty;
         }
         __syncwarp();
     }
@@ -499,8 +518,8 @@ __global__ void __launch_bounds__(256, Sh::MINB) code_fast_kernel(PassArgs a) {
 
     if constexpr (SIDE != kCodeOnly) {
         if (lane == 0) {
-            atomicAdd(&accd[0], w_energy);
-            atomicAdd(&accd[1], w_ynorm);
+            atomicAdd(&accd[0], (double)w_energy - (double)w_energy_c);
+            atomicAdd(&accd[1], (double)w_ynorm - (double)w_ynorm_c);
         }
         __syncthreads();
         float* dst = a.part_f + (size_t)blockIdx.x * nf;
@@ -509,12 +528,12 @@ __global__ void __launch_bounds__(256, Sh::MINB) code_fast_kernel(PassArgs a) {
     }
 }
 
-constexpr int kWarpsPerCta = 8;
 constexpr int kMaxCtasPerSm = 8;
 
 template <class Sh, int SIDE>
 int launch_fast_impl(const PassArgs& a, cudaStream_t st, int num_sms) {
     using L = FastLayout<Sh>;
+    constexpr int kWarpsPerCta = Sh::WPC;
     const size_t bytes = sizeof(float) * (size_t)L::total(SIDE, kWarpsPerCta);
     auto kern = code_fast_kernel<Sh, SIDE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
@@ -542,10 +561,10 @@ int launch_fast_side(const PassArgs& a, int side, cudaStream_t st, int num_sms) 
     }
 }
 
-// Compiled shapes: <p1, p2, n1, n2, s, LI, RI, RJ, ZA, ZB, min CTAs/SM>
-using F8x16s4 = Shape<8, 8, 16, 16, 4, 4, 4, 2, 2, 2, 3>;
-using F12x24s6 = Shape<12, 12, 24, 24, 6, 4, 6, 3, 3, 3, 2>;
-using F16x32s8 = Shape<16, 16, 32, 32, 8, 4, 8, 4, 4, 4, 2>;
+// Compiled shapes: <p1, p2, n1, n2, s, LI, RI, RJ, ZA, ZB, warps/CTA, min CTAs/SM>
+using F8x16s4 = Shape<8, 8, 16, 16, 4, 4, 4, 2, 2, 2, 8, 3>;
+using F12x24s6 = Shape<12, 12, 24, 24, 6, 4, 6, 3, 3, 3, 8, 2>;
+using F16x32s8 = Shape<16, 16, 32, 32, 8, 4, 8, 4, 4, 4, 8, 2>;
 
 }  // namespace
 
