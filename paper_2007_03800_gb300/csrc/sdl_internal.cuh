@@ -72,6 +72,7 @@ void launch_gram2(const float* D1, int p1, int n1, float* G1, const float* D2, i
 int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n,
                  float* norms, double inv_count, float* objective_out, float* rmse_out,
                  int* err, cudaStream_t st, float* G_out = nullptr);
+
 void launch_rescale(const int32_t* support, float* coef, long long count, int n1, int n2,
                     int side, const float* norms, cudaStream_t st);
 

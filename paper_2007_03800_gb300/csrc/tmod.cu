@@ -52,16 +52,30 @@ __global__ void __launch_bounds__(kReduceWarps * 32)
     __shared__ float ws[kReduceWarps][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int e = blockIdx.x * 32 + lane;
-    float sum = 0.f, comp = 0.f;
+    // four interleaved compensated sums keep four loads in flight
+    float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
     if (e < nf) {
-        for (int c = warp; c < n_slots; c += kReduceWarps) {
-            const float y = part_f[(size_t)c * nf + e] - comp;
-            const float t = sum + y;
-            comp = (t - sum) - y;
-            sum = t;
+        int c = warp;
+        for (; c + 3 * kReduceWarps < n_slots; c += 4 * kReduceWarps) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = part_f[(size_t)(c + u * kReduceWarps) * nf + e];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float y = v[u] - comp[u];
+                const float t = sum[u] + y;
+                comp[u] = (t - sum[u]) - y;
+                sum[u] = t;
+            }
+        }
+        for (; c < n_slots; c += kReduceWarps) {
+            const float y = part_f[(size_t)c * nf + e] - comp[0];
+            const float t = sum[0] + y;
+            comp[0] = (t - sum[0]) - y;
+            sum[0] = t;
         }
     }
-    ws[warp][lane] = sum - comp;
+    ws[warp][lane] = ((sum[0] - comp[0]) + (sum[1] - comp[1])) + ((sum[2] - comp[2]) + (sum[3] - comp[3]));
     __syncthreads();
     if (warp == 0 && e < nf) {
         float tot = 0.f, c2 = 0.f;
@@ -81,283 +95,168 @@ __global__ void __launch_bounds__(kReduceWarps * 32)
     }
 }
 
-// Single-warp version of solve_kernel (below) for n <= 32: lane i owns row i
-// of the Cholesky factor, lane a owns right-hand side a; only __syncwarp.
-// Also writes G = D_new^T D_new (row-major) when G_out != NULL.
-__global__ void __launch_bounds__(32)
-    solve_small_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D,
-                       int p, int n, float* __restrict__ norms, double inv_count,
-                       float* objective_out, float* rmse_out, int* err, float* G_out) {
-    extern __shared__ __align__(16) float sm[];
-    const int ldb = n | 1;                   // odd strides: lanes hit distinct banks
-    float* A = sm;                           // nu x nu (row stride n), becomes L
-    float* Bc = A + n * n;                   // p rows of stride ldb: RHS -> D* rows
-    float* Dn = Bc + p * ldb;                // p rows of stride ldb: old, then new D
-    float* invL = Dn + p * ldb;              // n
-    float* nrm = invL + n;                   // n
-    int* idx = reinterpret_cast<int*>(nrm + n);   // n
-    const int lane = threadIdx.x;
-    const float* P = red_f;
-    const float* B = red_f + n * n;
-
-    bool bad = false;
-    float dl = 0.f;
-    if (lane < n) {
-        dl = P[lane * n + lane];
-        bad = !isfinite(dl);
-    }
-    const unsigned um = __ballot_sync(kFull, lane < n && dl > 0.f);
-    const int nu = __popc(um);
-    if (lane < n && dl > 0.f) idx[__popc(um & ((1u << lane) - 1u))] = lane;
-    __syncwarp();
-    for (int e = lane; e < nu * nu; e += 32) {
-        const int r = e / nu, c = e - r * nu;
-        const float v = P[idx[r] * n + idx[c]];
-        A[r * n + c] = v;
-        bad |= !isfinite(v);
-    }
-    for (int e = lane; e < p * nu; e += 32) {
-        const int r = e / nu, c = e - r * nu;
-        const float v = B[r * n + idx[c]];
-        Bc[r * ldb + c] = v;
-        bad |= !isfinite(v);
-    }
-    for (int e = lane; e < p * n; e += 32) {
-        const int r = e % p, c = e / p;
-        Dn[r * ldb + c] = D[r + p * c];
-    }
-    int fail = __any_sync(kFull, bad) ? SDL_ERR_NONFINITE : 0;
-    __syncwarp();
-    // Cholesky, lane i updates row i
-    for (int k = 0; k < nu && !fail; ++k) {
-        const float akk = A[k * n + k];
-        const float d0 = P[idx[k] * n + idx[k]];
-        if (!(akk > kSolvePivotRel * d0)) {
-            fail = SDL_ERR_SINGULAR;
-            break;
-        }
-        const float Lkk = sqrtf(akk), inv = 1.f / Lkk;
-        __syncwarp();
-        if (lane == k) {
-            A[k * n + k] = Lkk;
-            invL[k] = inv;
-        }
-        if (lane > k && lane < nu) A[lane * n + k] *= inv;
-        __syncwarp();
-        if (lane > k && lane < nu) {
-            const float lik = A[lane * n + k];
-            for (int j = k + 1; j <= lane; ++j) A[lane * n + j] = fmaf(-lik, A[j * n + k], A[lane * n + j]);
-        }
-        __syncwarp();
-    }
-    double trace = 0.0;
-    if (!fail) {
-        float acc = 0.f;
-        for (int a = lane; a < p; a += 32) {
-            float* row = Bc + a * ldb;
-            for (int k = 0; k < nu; ++k) {          // L z = b
-                float z = row[k];
-                for (int j = 0; j < k; ++j) z = fmaf(-A[k * n + j], row[j], z);
-                row[k] = z * invL[k];
-            }
-            for (int k = nu - 1; k >= 0; --k) {     // L^T x = z
-                float x = row[k];
-                for (int j = k + 1; j < nu; ++j) x = fmaf(-A[j * n + k], row[j], x);
-                row[k] = x * invL[k];
-            }
-            for (int i = 0; i < nu; ++i) {          // ||L^T delta||^2
-                float v = 0.f;
-                for (int k = i; k < nu; ++k) v = fmaf(A[k * n + i], Dn[a * ldb + idx[k]] - row[k], v);
-                acc = fmaf(v, v, acc);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        trace = (double)acc;
-        __syncwarp();
-        bool zero = false;
-        for (int c = lane; c < nu; c += 32) {
-            float ss = 0.f;
-            for (int a = 0; a < p; ++a) ss = fmaf(Bc[a * ldb + c], Bc[a * ldb + c], ss);
-            nrm[c] = sqrtf(ss);
-            zero |= !(nrm[c] > 0.f) || !isfinite(nrm[c]);
-        }
-        if (__any_sync(kFull, zero)) fail = SDL_ERR_SINGULAR;
-        __syncwarp();
-    }
-    for (int i = lane; i < n; i += 32) norms[i] = 1.f;
-    __syncwarp();
-    if (!fail) {
-        for (int c = lane; c < nu; c += 32) norms[idx[c]] = nrm[c];
-        for (int e = lane; e < p * nu; e += 32) {
-            const int a = e / nu, c = e - a * nu;
-            const float v = Bc[a * ldb + c] / nrm[c];
-            Dn[a * ldb + idx[c]] = v;
-            D[a + p * idx[c]] = v;
-        }
-        __syncwarp();
-        if (G_out) {
-            for (int e = lane; e < n * n; e += 32) {
-                const int i = e / n, j = e - i * n;
-                float g = 0.f;
-                for (int a = 0; a < p; ++a) g = fmaf(Dn[a * ldb + i], Dn[a * ldb + j], g);
-                G_out[e] = g;
-            }
-        }
-    }
-    if (lane == 0) {
-        if (fail) record_error(err, fail);
-        const double before = red_d[0];
-        const double after = fail ? before : before - trace;
-        if (objective_out) {
-            objective_out[0] = (float)before;
-            objective_out[1] = (float)after;
-        }
-        if (rmse_out) rmse_out[0] = (float)sqrt(fmax(after, 0.0) * inv_count);
-    }
-}
-
-// One CTA: D* = B P^{-1} on the used atoms (diag(P) > 0), unit-norm columns,
-// the objective after the update, and the column norms for the code rescale.
+// One CTA: the normal-equation solve of a dictionary update with atom
+// normalisation (Corollary 1 for D1, Result 1 for D2).
 //   red_f = [P (n x n, row-major) | B (p x n, row-major)], red_d[0] = objective
 //   before the update (sum of residual energies with the old dictionary).
-// Objective after = before - tr(Delta P Delta^T), Delta = D_old - D*, which
-// is ||L^T delta_a||^2 summed over the rows a (P = L L^T).  On any failure the
-// dictionary is left untouched and the norms are set to 1.
+// Only the used atoms (diag(P) > 0) take part; unused atoms keep their column.
+//   1. P_u^{-1} by in-place Gauss-Jordan elimination without pivoting: for an
+//      SPD matrix the k-th pivot is the k-th Cholesky pivot squared, so the
+//      same relative-pivot test flags a singular P;
+//   2. D* = B_u P_u^{-1} (rows of the right-hand side times the inverse);
+//   3. objective after = before - tr(Delta P Delta^T), Delta = D_old - D*
+//      (the exact decrease of the least-squares objective, Result 1);
+//   4. norms of the columns of D*, D <- D* diag(1/norm), optional G = D^T D.
+// Every step is a data-parallel sweep with two barriers per pivot.  On any
+// failure D is left untouched and the norms are set to 1.
 constexpr int kSolveThreads = 512;
 
 __global__ void __launch_bounds__(kSolveThreads)
     solve_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D, int p,
                  int n, float* __restrict__ norms, double inv_count, float* objective_out,
-                 float* rmse_out, int* err) {
+                 float* rmse_out, int* err, float* G_out) {
     extern __shared__ __align__(16) float sm[];
-    float* A = sm;                       // nu x nu, becomes L (lower)
-    float* Bc = A + n * n;               // p x nu right-hand sides, become D* rows
-    float* Dold = Bc + p * n;            // p x n row-major
-    float* diag0 = Dold + p * n;         // n
-    float* invL = diag0 + n;             // n
-    int* idx = reinterpret_cast<int*>(invL + n);   // n
+    const int lda = n | 1;                          // odd row strides: fewer bank conflicts
+    float* A = sm;                                  // nu x nu (stride lda), becomes P_u^{-1}
+    float* Bc = A + n * lda;                        // p x nu right-hand sides (stride lda)
+    float* X = Bc + p * lda;                        // p x nu, D* rows (stride lda)
+    float* Dn = X + p * lda;                        // p x n, old then new D (stride lda)
+    float* nrm = Dn + p * lda;                      // n
+    float* d0 = nrm + n;                            // n
+    int* idx = reinterpret_cast<int*>(d0 + n);      // n
     __shared__ int s_nu, s_fail;
-    __shared__ double s_trace;
+    __shared__ float s_red[kSolveThreads / 32];
 
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
     const float* P = red_f;
     const float* B = red_f + n * n;
 
-    if (tid == 0) {
-        int nu = 0, fail = 0;
-        for (int i = 0; i < n; ++i) {
-            const float d = P[i * n + i];
-            if (!isfinite(d)) fail = SDL_ERR_NONFINITE;
-            if (d > 0.f) idx[nu++] = i;
+    if (tid < 32) {
+        int base = 0, fail = 0;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const float dl = (i < n) ? P[i * n + i] : 0.f;
+            if (i < n && !isfinite(dl)) fail = SDL_ERR_NONFINITE;
+            const unsigned um = __ballot_sync(0xffffffffu, i < n && dl > 0.f);
+            if (i < n && dl > 0.f) {
+                const int pos = base + __popc(um & ((1u << lane) - 1u));
+                idx[pos] = i;
+                d0[pos] = dl;
+            }
+            base += __popc(um);
         }
-        s_nu = nu;
-        s_fail = fail;
-        s_trace = 0.0;
+        fail = __reduce_or_sync(0xffffffffu, fail);
+        if (lane == 0) {
+            s_nu = base;
+            s_fail = fail;
+        }
     }
     __syncthreads();
     const int nu = s_nu;
     for (int e = tid; e < nu * nu; e += nth) {
         const int r = e / nu, c = e - r * nu;
         const float v = P[idx[r] * n + idx[c]];
-        A[e] = v;
+        A[r * lda + c] = v;
         if (!isfinite(v)) s_fail = SDL_ERR_NONFINITE;
     }
     for (int e = tid; e < p * nu; e += nth) {
         const int r = e / nu, c = e - r * nu;
         const float v = B[r * n + idx[c]];
-        Bc[e] = v;
+        Bc[r * lda + c] = v;
         if (!isfinite(v)) s_fail = SDL_ERR_NONFINITE;
     }
     for (int e = tid; e < p * n; e += nth) {
-        const int r = e / n, c = e - r * n;
-        Dold[e] = D[r + p * c];
+        const int r = e % p, c = e / p;
+        Dn[r * lda + c] = D[r + p * c];
     }
-    for (int c = tid; c < nu; c += nth) diag0[c] = P[idx[c] * n + idx[c]];
     __syncthreads();
 
-    // right-looking Cholesky of the used block
-    if (s_fail == 0) {
-        for (int k = 0; k < nu; ++k) {
-            if (tid == 0) {
-                const float piv = A[k * nu + k];
-                if (!(piv > kSolvePivotRel * diag0[k])) s_fail = SDL_ERR_SINGULAR;
-                const float Lkk = sqrtf(fmaxf(piv, 1e-30f));
-                A[k * nu + k] = Lkk;
-                invL[k] = 1.f / Lkk;
-            }
+    // 1. Gauss-Jordan inverse of the used block
+    for (int k = 0; k < nu && s_fail == 0; ++k) {
+        const float piv = A[k * lda + k];
+        if (!(piv > kSolvePivotRel * d0[k])) {
             __syncthreads();
-            const float il = invL[k];
-            for (int i = k + 1 + tid; i < nu; i += nth) A[i * nu + k] *= il;
+            if (tid == 0) s_fail = SDL_ERR_SINGULAR;
             __syncthreads();
-            const int m = nu - k - 1;
-            for (int e = tid; e < m * m; e += nth) {
-                const int i = k + 1 + e / m, j = k + 1 + e % m;
-                if (j <= i) A[i * nu + j] = fmaf(-A[i * nu + k], A[j * nu + k], A[i * nu + j]);
-            }
-            __syncthreads();
+            break;
         }
-    }
-    const bool ok_chol = (s_fail == 0);
-    // solve L L^T x = b for every right-hand-side row (one warp per row)
-    if (ok_chol) {
-        for (int a = warp; a < p; a += nwarps) {
-            float* row = Bc + a * nu;
-            for (int k = 0; k < nu; ++k) {
-                __syncwarp();
-                const float zk = row[k] * invL[k];
-                __syncwarp();
-                if (lane == 0) row[k] = zk;
-                for (int i = k + 1 + lane; i < nu; i += 32) row[i] = fmaf(-A[i * nu + k], zk, row[i]);
-            }
-            for (int k = nu - 1; k >= 0; --k) {
-                __syncwarp();
-                const float xk = row[k] * invL[k];
-                __syncwarp();
-                if (lane == 0) row[k] = xk;
-                for (int i = lane; i < k; i += 32) row[i] = fmaf(-A[k * nu + i], xk, row[i]);
-            }
-            __syncwarp();
-            // ||L^T delta||^2 with delta = D_old[a, used] - D*[a, :]
-            float acc = 0.f;
-            for (int i = lane; i < nu; i += 32) {
-                float v = 0.f;
-                for (int k = i; k < nu; ++k)
-                    v = fmaf(A[k * nu + i], Dold[a * n + idx[k]] - row[k], v);
-                acc = fmaf(v, v, acc);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-            if (lane == 0) atomicAdd(&s_trace, (double)acc);
+        const float inv = 1.f / piv;
+        for (int e = tid; e < nu * nu; e += nth) {
+            const int i = e / nu, j = e - i * nu;
+            if (i != k && j != k) A[i * lda + j] = fmaf(-A[i * lda + k] * inv, A[k * lda + j], A[i * lda + j]);
         }
+        __syncthreads();
+        for (int e = tid; e < 2 * nu; e += nth) {
+            if (e < nu) {
+                if (e != k) A[k * lda + e] *= inv;          // row k
+            } else {
+                const int i = e - nu;
+                if (i != k) A[i * lda + k] *= -inv;         // column k
+            }
+        }
+        if (tid == 0) A[k * lda + k] = inv;
+        __syncthreads();
     }
-    __syncthreads();
-    // column norms of D*; a zero or non-finite norm fails the update
-    if (ok_chol) {
+    const bool ok_inv = (s_fail == 0);
+    float part = 0.f;
+    if (ok_inv) {
+        // 2. D* rows
+        for (int e = tid; e < p * nu; e += nth) {
+            const int a = e / nu, c = e - a * nu;
+            float x = 0.f;
+            for (int k = 0; k < nu; ++k) x = fmaf(Bc[a * lda + k], A[k * lda + c], x);
+            X[a * lda + c] = x;
+        }
+        __syncthreads();
+        // 3. delta^T P delta per row a, with P (used block) read back from red_f
+        for (int e = tid; e < p * nu; e += nth) {
+            const int a = e / nu, c = e - a * nu;
+            float w = 0.f;
+            const float* prow = P + (size_t)idx[c] * n;
+            for (int k = 0; k < nu; ++k) w = fmaf(prow[idx[k]], Dn[a * lda + idx[k]] - X[a * lda + k], w);
+            part = fmaf(w, Dn[a * lda + idx[c]] - X[a * lda + c], part);
+        }
+        // 4. column norms of D*
         for (int c = tid; c < nu; c += nth) {
             float ss = 0.f;
-            for (int a = 0; a < p; ++a) ss = fmaf(Bc[a * nu + c], Bc[a * nu + c], ss);
+            for (int a = 0; a < p; ++a) ss = fmaf(X[a * lda + c], X[a * lda + c], ss);
             const float nr = sqrtf(ss);
-            diag0[c] = nr;
+            nrm[c] = nr;
             if (!(nr > 0.f) || !isfinite(nr)) s_fail = SDL_ERR_SINGULAR;
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) s_red[warp] = part;
     __syncthreads();
     const bool ok = (s_fail == 0);
     for (int i = tid; i < n; i += nth) norms[i] = 1.f;
     __syncthreads();
     if (ok) {
-        for (int c = tid; c < nu; c += nth) norms[idx[c]] = diag0[c];
+        for (int c = tid; c < nu; c += nth) norms[idx[c]] = nrm[c];
         for (int e = tid; e < p * nu; e += nth) {
             const int a = e / nu, c = e - a * nu;
-            D[a + p * idx[c]] = Bc[e] / diag0[c];
+            const float v = X[a * lda + c] / nrm[c];
+            Dn[a * lda + idx[c]] = v;
+            D[a + p * idx[c]] = v;
+        }
+        __syncthreads();
+        if (G_out) {
+            for (int e = tid; e < n * n; e += nth) {
+                const int i = e / n, j = e - i * n;
+                float g = 0.f;
+                for (int a = 0; a < p; ++a) g = fmaf(Dn[a * lda + i], Dn[a * lda + j], g);
+                G_out[e] = g;
+            }
         }
     }
     if (tid == 0) {
+        double trace = 0.0;
+        for (int w = 0; w < nth / 32; ++w) trace += (double)s_red[w];
         if (!ok) record_error(err, s_fail);
         const double before = red_d[0];
-        const double after = ok ? before - s_trace : before;
+        const double after = ok ? before - trace : before;
         if (objective_out) {
             objective_out[0] = (float)before;
             objective_out[1] = (float)after;
@@ -404,25 +303,15 @@ void launch_reduce_partials(const float* part_f, const double* part_d, int n_slo
 int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n, float* norms,
                  double inv_count, float* objective_out, float* rmse_out, int* err,
                  cudaStream_t st, float* G_out) {
-    if (n <= 32) {
-        const int ldb = n | 1;
-        const size_t bytes = sizeof(float) * ((size_t)n * n + 2 * (size_t)p * ldb + 3 * (size_t)n);
-        if (cudaFuncSetAttribute(solve_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes) != cudaSuccess)
-            return SDL_ERR_CUDA;
-        solve_small_kernel<<<1, 32, bytes, st>>>(red_f, red_d, D, p, n, norms, inv_count,
-                                                 objective_out, rmse_out, err, G_out);
-        return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
-    }
-    const size_t bytes = sizeof(float) * ((size_t)n * n + 2 * (size_t)p * n + 3 * (size_t)n);
+    const size_t lda = (size_t)(n | 1);
+    const size_t bytes = sizeof(float) * ((size_t)n * lda + 3 * (size_t)p * lda + 3 * (size_t)n);
     if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) != cudaSuccess)
         return SDL_ERR_CUDA;
-    solve_kernel<<<1, kSolveThreads, bytes, st>>>(red_f, red_d, D, p, n, norms, inv_count,
-                                                  objective_out, rmse_out, err);
-    if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
-    if (G_out) launch_gram(D, p, n, G_out, st);   // Gram of the (possibly unchanged) D
-    return SDL_OK;
+    const int threads = n <= 32 ? 256 : kSolveThreads;
+    solve_kernel<<<1, threads, bytes, st>>>(red_f, red_d, D, p, n, norms, inv_count, objective_out,
+                                            rmse_out, err, G_out);
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
 }
 
 void launch_rescale(const int32_t* support, float* coef, long long count, int n1, int n2,
