@@ -88,10 +88,13 @@ __global__ void __launch_bounds__(kReduceWarps * 32)
         }
         red_f[e] = tot;
     }
-    if (blockIdx.x == 0 && threadIdx.x < 2) {
+    if (blockIdx.x == 0 && warp < 2) {
+        // the two FP64 sums: lanes stride over the slots, then a fixed shuffle tree
         double d = 0.0;
-        for (int c = 0; c < n_slots; ++c) d += part_d[(size_t)c * 2 + threadIdx.x];
-        red_d[threadIdx.x] = d;
+        for (int c = lane; c < n_slots; c += 32) d += part_d[(size_t)c * 2 + warp];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) red_d[warp] = d;
     }
 }
 
@@ -114,14 +117,15 @@ constexpr int kSolveThreads = 512;
 __global__ void __launch_bounds__(kSolveThreads)
     solve_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D, int p,
                  int n, float* __restrict__ norms, double inv_count, float* objective_out,
-                 float* rmse_out, int* err, float* G_out) {
+                 float* rmse_out, int* err, float* G_out, int keep_p) {
     extern __shared__ __align__(16) float sm[];
     const int lda = n | 1;                          // odd row strides: fewer bank conflicts
     float* A = sm;                                  // nu x nu (stride lda), becomes P_u^{-1}
     float* Bc = A + n * lda;                        // p x nu right-hand sides (stride lda)
     float* X = Bc + p * lda;                        // p x nu, D* rows (stride lda)
     float* Dn = X + p * lda;                        // p x n, old then new D (stride lda)
-    float* nrm = Dn + p * lda;                      // n
+    float* P0 = Dn + p * lda;                       // nu x nu copy of P_u (stride lda), if kept
+    float* nrm = P0 + (keep_p ? n * lda : 0);       // n
     float* d0 = nrm + n;                            // n
     int* idx = reinterpret_cast<int*>(d0 + n);      // n
     __shared__ int s_nu, s_fail;
@@ -158,6 +162,7 @@ __global__ void __launch_bounds__(kSolveThreads)
         const int r = e / nu, c = e - r * nu;
         const float v = P[idx[r] * n + idx[c]];
         A[r * lda + c] = v;
+        if (keep_p) P0[r * lda + c] = v;
         if (!isfinite(v)) s_fail = SDL_ERR_NONFINITE;
     }
     for (int e = tid; e < p * nu; e += nth) {
@@ -213,8 +218,13 @@ __global__ void __launch_bounds__(kSolveThreads)
         for (int e = tid; e < p * nu; e += nth) {
             const int a = e / nu, c = e - a * nu;
             float w = 0.f;
-            const float* prow = P + (size_t)idx[c] * n;
-            for (int k = 0; k < nu; ++k) w = fmaf(prow[idx[k]], Dn[a * lda + idx[k]] - X[a * lda + k], w);
+            if (keep_p) {
+                const float* prow = P0 + c * lda;
+                for (int k = 0; k < nu; ++k) w = fmaf(prow[k], Dn[a * lda + idx[k]] - X[a * lda + k], w);
+            } else {
+                const float* prow = P + (size_t)idx[c] * n;
+                for (int k = 0; k < nu; ++k) w = fmaf(prow[idx[k]], Dn[a * lda + idx[k]] - X[a * lda + k], w);
+            }
             part = fmaf(w, Dn[a * lda + idx[c]] - X[a * lda + c], part);
         }
         // 4. column norms of D*
@@ -304,13 +314,16 @@ int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n
                  double inv_count, float* objective_out, float* rmse_out, int* err,
                  cudaStream_t st, float* G_out) {
     const size_t lda = (size_t)(n | 1);
-    const size_t bytes = sizeof(float) * ((size_t)n * lda + 3 * (size_t)p * lda + 3 * (size_t)n);
+    const size_t base = (size_t)n * lda + 3 * (size_t)p * lda + 3 * (size_t)n;
+    // keep a copy of P in shared memory for the objective term when it fits
+    const int keep_p = sizeof(float) * (base + (size_t)n * lda) <= 200 * 1024 ? 1 : 0;
+    const size_t bytes = sizeof(float) * (base + (keep_p ? (size_t)n * lda : 0));
     if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) != cudaSuccess)
         return SDL_ERR_CUDA;
     const int threads = n <= 32 ? 256 : kSolveThreads;
     solve_kernel<<<1, threads, bytes, st>>>(red_f, red_d, D, p, n, norms, inv_count, objective_out,
-                                            rmse_out, err, G_out);
+                                            rmse_out, err, G_out, keep_p);
     return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
 }
 
