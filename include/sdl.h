@@ -159,6 +159,66 @@ int sdl_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
                 float* rmse_out, void* stream);
 
 /*
+ * Batching: several independent dictionary-learning problems ("groups") that
+ * differ in signal size, dictionary size, sparsity and stopping rule, run
+ * together.  This is the GB300 counterpart of the paper's many-worker setting
+ * (Algorithm 1 with its data split over nodes): each coding pass of all groups
+ * is ONE persistent launch, each update stage (Gram, reduction, solve,
+ * rescale) is one launch for all groups, and with SDL_BATCH_GRAPH the whole
+ * iteration is captured once into a CUDA graph and replayed.
+ *
+ * A group is described like the arguments of sdl_iterate (all device
+ * pointers, owned by the caller, which must keep them valid and unmoved for
+ * the batch's lifetime; Y 16-byte aligned).  Each group must have a compiled
+ * specialised shape: (p1, p2, n1, n2, s_max) in {(8,8,16,16,4),
+ * (12,12,24,24,6), (16,16,32,32,8)}, else SDL_ERR_UNSUPPORTED.  eps > 0 gives
+ * the group an error-driven stop (Sec. IV), per group.
+ */
+typedef struct sdl_group {
+    const float* Y;      /* p1 x p2 x N signals (layout as in sdl_iterate)   */
+    int p1, p2;
+    int64_t N;           /* >= 1                                              */
+    float* D1;           /* p1 x n1, in/out                                   */
+    int n1;
+    float* D2;           /* p2 x n2, in/out                                   */
+    int n2;
+    int s_max;
+    float eps;
+    int32_t* support;    /* N x s_max outputs of the codes                    */
+    float* coef;
+    int32_t* nnz;
+    float* res_energy;   /* N, may be NULL                                    */
+} sdl_group;
+
+#define SDL_BATCH_AUTOTUNE 1  /* time each group's compiled lane tilings and
+                                 split the CTAs between groups by measured cost */
+#define SDL_BATCH_GRAPH 2     /* capture one iteration into a CUDA graph       */
+
+typedef struct sdl_batch sdl_batch;
+
+/* Validate the groups, allocate the batch workspace, autotune (if asked) by
+ * timing coding passes on the groups' own data (writes only workspace), build
+ * the launch descriptors and capture the graph.  Synchronous on `stream`. */
+int sdl_batch_create(sdl_ctx* ctx, const sdl_group* groups, int n_groups, int flags,
+                     void* stream, sdl_batch** out);
+
+/* 2D-OMP of every group's signals in one persistent launch (codes only). */
+int sdl_batch_sparse_code(sdl_batch* batch, void* stream);
+
+/* One Algorithm-1 iteration of every group (graph replay when captured).
+ * rmse_out: NULL or device float[2 * n_groups], for group g the RMSE after
+ * its D1 update (2g) and after its D2 update (2g + 1). */
+int sdl_batch_iterate(sdl_batch* batch, float* rmse_out, void* stream);
+
+/* Host arrays of n_groups (each may be NULL): chosen tiling id, CTAs given to
+ * the group, and the measured (autotune) or modelled cost of one of its
+ * coding passes in microseconds.  Returns n_groups. */
+int sdl_batch_tuning(const sdl_batch* batch, int* shape_id, int* ctas, float* cost_us);
+
+/* Synchronise the device and free the batch (NULL accepted). */
+int sdl_batch_destroy(sdl_batch* batch);
+
+/*
  * sdl_sparse_code_static - the sparse coder of sdl_sparse_code with no
  * context and no device allocation.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory once running
@@ -203,8 +263,10 @@ int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
  *   7 solve         normal-equation solve + atom normalisation
  *   8 rescale       X <- W^{-1} X
  *   9 memset        zeroing of global accumulation slots
+ *  10 batch_graph   one replay of a batch's captured iteration graph
+ *                   (its kernels are counted under their own kinds too)
  */
-#define SDL_NUM_KERNEL_KINDS 10
+#define SDL_NUM_KERNEL_KINDS 11
 
 /* Enable (1) or disable (0) event timing of every kernel this context
  * enqueues.  Launch counts are kept either way.  Host-side, synchronous. */

@@ -7,75 +7,11 @@
 #include <new>
 #include <vector>
 
-#include "sdl_internal.cuh"
+#include "ctx.cuh"
 
 using namespace sdl;
 
-struct sdl_ctx {
-    int device = 0;
-    int num_sms = 0;
-    int* err = nullptr;          // device error word
-    float* G1 = nullptr;         // Gram matrices of the current dictionaries
-    float* G2 = nullptr;
-    float* part_f = nullptr;     // partial-sum slots
-    double* part_d = nullptr;
-    float* red_f = nullptr;      // reduced sums
-    double* red_d = nullptr;
-    float* norms = nullptr;      // column norms of the last solve
-    size_t cap_g1 = 0, cap_g2 = 0, cap_part = 0, cap_slots = 0, cap_red = 0, cap_redd = 0,
-           cap_norms = 0;
-    // tracing: launch counters and (optionally) one event pair per launch
-    struct Rec {
-        int kind;
-        cudaEvent_t beg, end;
-    };
-    bool timing = false;
-    std::vector<Rec> recs;           // event pool, reused
-    size_t n_recs = 0;               // records in use
-    int64_t launches[SDL_NUM_KERNEL_KINDS] = {};
-};
-
 namespace {
-
-enum Kind { kGram = 0, kCode, kCodeD1, kCodeD2, kAccD1, kAccD2, kReduce, kSolve, kRescale, kMemset };
-constexpr size_t kMaxRecs = 1 << 16;
-
-// Bracket one launch of `kind` on `st` with timing events (when enabled).
-struct Trace {
-    sdl_ctx* c;
-    cudaStream_t st;
-    sdl_ctx::Rec* rec = nullptr;
-    Trace(sdl_ctx* c_, int kind, cudaStream_t st_) : c(c_), st(st_) {
-        c->launches[kind] += 1;
-        if (!c->timing || c->n_recs >= kMaxRecs) return;
-        if (c->n_recs == c->recs.size()) {
-            sdl_ctx::Rec r{kind, nullptr, nullptr};
-            if (cudaEventCreate(&r.beg) != cudaSuccess || cudaEventCreate(&r.end) != cudaSuccess) {
-                cudaGetLastError();
-                return;
-            }
-            c->recs.push_back(r);
-        }
-        rec = &c->recs[c->n_recs++];
-        rec->kind = kind;
-        cudaEventRecord(rec->beg, st);
-    }
-    ~Trace() {
-        if (rec) cudaEventRecord(rec->end, st);
-    }
-};
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 template <class T>
 int grow(T*& ptr, size_t& cap, size_t need) {
@@ -406,7 +342,7 @@ int sdl_profile_collect(sdl_ctx* c, double* total_ms, int64_t* launches, int max
 const char* sdl_kernel_name(int kind) {
     static const char* names[SDL_NUM_KERNEL_KINDS] = {
         "gram", "code", "code_D1", "code_D2", "accum_D1", "accum_D2",
-        "reduce", "solve", "rescale", "memset"};
+        "reduce", "solve", "rescale", "memset", "batch_graph"};
     return (kind >= 0 && kind < SDL_NUM_KERNEL_KINDS) ? names[kind] : "?";
 }
 

@@ -44,9 +44,9 @@ struct Shape {
     static constexpr int ZA = ZA_, ZB = ZB_;
     static constexpr int ZLA = P1_ / ZA_, ZLB = N2_ / ZB_;   // Z-stage lane grid
     static constexpr int PP = P1_ * P2_;
-    // lane stride of the C0 blocks in shared memory: a multiple of 4 floats
-    // that is not a multiple of 32 (8 lanes of a 128-bit phase hit distinct banks)
-    static constexpr int EP = (al4(E) % 32 == 0) ? al4(E) + 4 : al4(E);
+    // lane stride of the C0 blocks in shared memory: an odd multiple of 4
+    // floats, so the 8 lanes of a 128-bit load phase hit distinct banks
+    static constexpr int EP = ((al4(E) / 4) % 2 == 0) ? al4(E) + 4 : al4(E);
     static_assert(LI * RI == N1 && LJ * RJ == N2, "lane grid must tile n1 x n2 exactly");
     static_assert(ZLA * ZA == P1 && ZLB * ZB == N2 && ZLA * ZLB <= 32, "Z tiling");
     static_assert(S <= 32 && S <= P1 * P2 && S <= N1 * N2, "s");
@@ -175,8 +175,10 @@ struct FastLayout {
     __host__ __device__ static constexpr int total(int side, int wpc) { return warp0(side) + wpc * w_stride; }
 };
 
+// Body of the coding pass for one CTA: `cta` of `n_ctas` CTAs working on the
+// signals of problem `a` (grid-stride over warps), partial sums to `slot`.
 template <class Sh, int SIDE>
-__global__ void __launch_bounds__(Sh::WPC * 32, Sh::MINB) code_fast_kernel(PassArgs a) {
+__device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n_ctas, int slot) {
     using L = FastLayout<Sh>;
     constexpr int P1 = Sh::P1, P2 = Sh::P2, N1 = Sh::N1, N2 = Sh::N2, S = Sh::S;
     constexpr int RI = Sh::RI, RJ = Sh::RJ, E = Sh::E, LI = Sh::LI;
@@ -232,8 +234,8 @@ __global__ void __launch_bounds__(Sh::WPC * 32, Sh::MINB) code_fast_kernel(PassA
         smem[L::warp0(SIDE) + e] = 0.f;   // Z padding columns stay 0
     __syncthreads();
 
-    const long long stride = (long long)gridDim.x * wpc;
-    long long k = (long long)blockIdx.x * wpc + w;
+    const long long stride = (long long)n_ctas * wpc;
+    long long k = (long long)cta * wpc + w;
     if (lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -522,16 +524,21 @@ __global__ void __launch_bounds__(Sh::WPC * 32, Sh::MINB) code_fast_kernel(PassA
             atomicAdd(&accd[1], (double)w_ynorm - (double)w_ynorm_c);
         }
         __syncthreads();
-        float* dst = a.part_f + (size_t)blockIdx.x * nf;
+        float* dst = a.part_f + (size_t)slot * nf;
         for (int e = threadIdx.x; e < nf; e += blockDim.x) dst[e] = acc[e];
-        if (threadIdx.x < 2) a.part_d[(size_t)blockIdx.x * 2 + threadIdx.x] = accd[threadIdx.x];
+        if (threadIdx.x < 2) a.part_d[(size_t)slot * 2 + threadIdx.x] = accd[threadIdx.x];
     }
+}
+
+template <class Sh, int SIDE>
+__global__ void __launch_bounds__(Sh::WPC * 32, Sh::MINB) code_fast_kernel(PassArgs a) {
+    code_fast_body<Sh, SIDE>(a, blockIdx.x, gridDim.x, blockIdx.x);
 }
 
 constexpr int kMaxCtasPerSm = 8;
 
 template <class Sh, int SIDE>
-int launch_fast_impl(const PassArgs& a, cudaStream_t st, int num_sms) {
+int launch_fast_impl(const PassArgs& a, cudaStream_t st, int num_sms, int ctas_per_sm) {
     using L = FastLayout<Sh>;
     constexpr int kWarpsPerCta = Sh::WPC;
     const size_t bytes = sizeof(float) * (size_t)L::total(SIDE, kWarpsPerCta);
@@ -544,6 +551,7 @@ int launch_fast_impl(const PassArgs& a, cudaStream_t st, int num_sms) {
         cudaSuccess)
         return SDL_ERR_CUDA;
     bps = std::max(1, std::min(bps, kMaxCtasPerSm));
+    if (ctas_per_sm > 0) bps = std::min(bps, ctas_per_sm);
     const long long need = (a.N + kWarpsPerCta - 1) / kWarpsPerCta;
     const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms * bps));
     kern<<<grid, kWarpsPerCta * 32, bytes, st>>>(a);
@@ -552,33 +560,142 @@ int launch_fast_impl(const PassArgs& a, cudaStream_t st, int num_sms) {
 }
 
 template <class Sh>
-int launch_fast_side(const PassArgs& a, int side, cudaStream_t st, int num_sms) {
+int launch_fast_side(const PassArgs& a, int side, cudaStream_t st, int num_sms, int ctas_per_sm) {
     switch (side) {
-        case kCodeOnly: return launch_fast_impl<Sh, kCodeOnly>(a, st, num_sms);
-        case kSideD1: return launch_fast_impl<Sh, kSideD1>(a, st, num_sms);
-        case kSideD2: return launch_fast_impl<Sh, kSideD2>(a, st, num_sms);
+        case kCodeOnly: return launch_fast_impl<Sh, kCodeOnly>(a, st, num_sms, ctas_per_sm);
+        case kSideD1: return launch_fast_impl<Sh, kSideD1>(a, st, num_sms, ctas_per_sm);
+        case kSideD2: return launch_fast_impl<Sh, kSideD2>(a, st, num_sms, ctas_per_sm);
         default: return SDL_ERR_ARG;
     }
 }
 
-// Compiled shapes: <p1, p2, n1, n2, s, LI, RI, RJ, ZA, ZB, warps/CTA, min CTAs/SM>
+// Compiled shapes: <p1, p2, n1, n2, s, LI, RI, RJ, ZA, ZB, warps/CTA, min CTAs/SM>.
+// Two lane tilings of the n1 x n2 correlation block per problem shape; the
+// batch autotuner times both.
 using F8x16s4 = Shape<8, 8, 16, 16, 4, 4, 4, 2, 2, 2, 8, 3>;
+using F8x16s4b = Shape<8, 8, 16, 16, 4, 8, 2, 4, 2, 2, 8, 2>;
 using F12x24s6 = Shape<12, 12, 24, 24, 6, 4, 6, 3, 3, 3, 8, 2>;
+using F12x24s6b = Shape<12, 12, 24, 24, 6, 8, 3, 6, 3, 3, 8, 2>;
 using F16x32s8 = Shape<16, 16, 32, 32, 8, 4, 8, 4, 4, 4, 8, 2>;
+using F16x32s8b = Shape<16, 16, 32, 32, 8, 8, 4, 8, 4, 4, 8, 2>;
+
+enum FastId { k8x16a = 0, k8x16b, k12x24a, k12x24b, k16x32a, k16x32b, kNumFast };
+
+struct FastKey {
+    int p1, p2, n1, n2, s;
+};
+constexpr FastKey kFastKeys[kNumFast] = {{8, 8, 16, 16, 4},  {8, 8, 16, 16, 4},
+                                         {12, 12, 24, 24, 6}, {12, 12, 24, 24, 6},
+                                         {16, 16, 32, 32, 8}, {16, 16, 32, 32, 8}};
+
+template <class F>
+int with_shape(int id, F&& f) {
+    switch (id) {
+        case k8x16a: return f(F8x16s4{});
+        case k8x16b: return f(F8x16s4b{});
+        case k12x24a: return f(F12x24s6{});
+        case k12x24b: return f(F12x24s6b{});
+        case k16x32a: return f(F16x32s8{});
+        case k16x32b: return f(F16x32s8b{});
+        default: return SDL_ERR_UNSUPPORTED;
+    }
+}
+
+// Persistent multi-problem pass: CTAs [cta_begin[g], cta_begin[g+1]) code the
+// signals of problem g with its compiled shape; each problem writes one
+// partial-sum slot per CTA into its own buffers.
+template <int SIDE>
+__global__ void __launch_bounds__(256, 2)
+    code_multi_kernel(const PassArgs* __restrict__ groups, const int* __restrict__ cta_begin,
+                      const int* __restrict__ shape, int G) {
+    int g = 0;
+    while (g + 1 < G && (int)blockIdx.x >= cta_begin[g + 1]) ++g;
+    const int cta = blockIdx.x - cta_begin[g];
+    const int n = cta_begin[g + 1] - cta_begin[g];
+    const PassArgs a = groups[g];
+    switch (shape[g]) {
+        case k8x16a: code_fast_body<F8x16s4, SIDE>(a, cta, n, cta); break;
+        case k8x16b: code_fast_body<F8x16s4b, SIDE>(a, cta, n, cta); break;
+        case k12x24a: code_fast_body<F12x24s6, SIDE>(a, cta, n, cta); break;
+        case k12x24b: code_fast_body<F12x24s6b, SIDE>(a, cta, n, cta); break;
+        case k16x32a: code_fast_body<F16x32s8, SIDE>(a, cta, n, cta); break;
+        case k16x32b: code_fast_body<F16x32s8b, SIDE>(a, cta, n, cta); break;
+        default: break;
+    }
+}
+
+template <int SIDE>
+int launch_multi_impl(const PassArgs* d_groups, const int* d_cta_begin, const int* d_shape, int G,
+                      int total_ctas, size_t smem, cudaStream_t st) {
+    auto kern = code_multi_kernel<SIDE>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return SDL_ERR_CUDA;
+    kern<<<total_ctas, 256, smem, st>>>(d_groups, d_cta_begin, d_shape, G);
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
 
 }  // namespace
 
-int launch_code_pass_fast(const PassArgs& a, int side, cudaStream_t st, int num_sms) {
-    // the fast kernels keep the pass's accumulators in shared memory and
-    // write one partial-sum slot per CTA, like the generic kernel
-    const int key[5] = {a.p1, a.p2, a.n1, a.n2, a.s};
-    auto is = [&](int p1, int p2, int n1, int n2, int s) {
-        return key[0] == p1 && key[1] == p2 && key[2] == n1 && key[3] == n2 && key[4] == s;
+int fast_shape_variants(int p1, int p2, int n1, int n2, int s, int* ids, int max_ids) {
+    int k = 0;
+    for (int id = 0; id < kNumFast; ++id) {
+        const FastKey& f = kFastKeys[id];
+        if (f.p1 == p1 && f.p2 == p2 && f.n1 == n1 && f.n2 == n2 && f.s == s && k < max_ids)
+            ids[k++] = id;
+    }
+    return k;
+}
+
+size_t fast_smem_bytes(int shape_id, int side) {
+    const int r = with_shape(shape_id, [&](auto sh) {
+        using Sh = decltype(sh);
+        return (int)(sizeof(float) * (size_t)FastLayout<Sh>::total(side, Sh::WPC));
+    });
+    return r < 0 ? 0 : (size_t)r;
+}
+
+int launch_code_pass_variant(const PassArgs& a, int side, int shape_id, int ctas_per_sm,
+                             cudaStream_t st, int num_sms) {
+    return with_shape(shape_id, [&](auto sh) {
+        return launch_fast_side<decltype(sh)>(a, side, st, num_sms, ctas_per_sm);
+    });
+}
+
+int launch_code_multi(const PassArgs* d_groups, const int* d_cta_begin, const int* d_shape, int G,
+                      int total_ctas, size_t smem, int side, cudaStream_t st) {
+    switch (side) {
+        case kCodeOnly: return launch_multi_impl<kCodeOnly>(d_groups, d_cta_begin, d_shape, G, total_ctas, smem, st);
+        case kSideD1: return launch_multi_impl<kSideD1>(d_groups, d_cta_begin, d_shape, G, total_ctas, smem, st);
+        case kSideD2: return launch_multi_impl<kSideD2>(d_groups, d_cta_begin, d_shape, G, total_ctas, smem, st);
+        default: return SDL_ERR_ARG;
+    }
+}
+
+int multi_ctas_per_sm(size_t smem, int side) {
+    int bps = 0;
+    cudaError_t e = cudaSuccess;
+    auto occ = [&](auto kern) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, smem);
     };
-    if (is(8, 8, 16, 16, 4)) return launch_fast_side<F8x16s4>(a, side, st, num_sms);
-    if (is(12, 12, 24, 24, 6)) return launch_fast_side<F12x24s6>(a, side, st, num_sms);
-    if (is(16, 16, 32, 32, 8)) return launch_fast_side<F16x32s8>(a, side, st, num_sms);
-    return SDL_ERR_UNSUPPORTED;
+    if (side == kCodeOnly) occ(code_multi_kernel<kCodeOnly>);
+    else if (side == kSideD1) occ(code_multi_kernel<kSideD1>);
+    else occ(code_multi_kernel<kSideD2>);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return bps;
+}
+
+int launch_code_pass_fast(const PassArgs& a, int side, cudaStream_t st, int num_sms) {
+    // default tiling: the first compiled variant of the shape
+    int ids[2];
+    if (fast_shape_variants(a.p1, a.p2, a.n1, a.n2, a.s, ids, 2) == 0) return SDL_ERR_UNSUPPORTED;
+    return launch_code_pass_variant(a, side, ids[0], 0, st, num_sms);
 }
 
 }  // namespace sdl

@@ -58,6 +58,17 @@ int launch_accumulate_pass(const PassArgs& a, int side, cudaStream_t st, int num
 // omp_fast.cu: compile-time-shape kernels; SDL_ERR_UNSUPPORTED when no
 // specialisation matches (the caller then uses the generic kernel).
 int launch_code_pass_fast(const PassArgs& a, int side, cudaStream_t st, int num_sms);
+// Compiled tilings ("shape ids") for a problem shape; returns how many.
+int fast_shape_variants(int p1, int p2, int n1, int n2, int s, int* ids, int max_ids);
+size_t fast_smem_bytes(int shape_id, int side);
+// One problem with a given tiling; ctas_per_sm > 0 caps the resident CTAs per SM.
+int launch_code_pass_variant(const PassArgs& a, int side, int shape_id, int ctas_per_sm,
+                             cudaStream_t st, int num_sms);
+// Several problems in one persistent launch (device arrays of G entries,
+// cta_begin has G+1); smem = the largest per-problem requirement.
+int launch_code_multi(const PassArgs* d_groups, const int* d_cta_begin, const int* d_shape, int G,
+                      int total_ctas, size_t smem, int side, cudaStream_t st);
+int multi_ctas_per_sm(size_t smem, int side);
 bool code_shape_supported(int p1, int p2, int n1, int n2, int s);
 // Upper bound of the partial-sum slots any pass may use for these sizes.
 int max_partial_slots(int num_sms);
@@ -75,6 +86,45 @@ int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n
 
 void launch_rescale(const int32_t* support, float* coef, long long count, int n1, int n2,
                     int side, const float* norms, cudaStream_t st);
+
+// Descriptors of the batched (several problems per launch) update kernels.
+struct GramDesc {
+    const float* D;
+    int p, n;
+    float* G;
+    int block_begin;
+};
+struct ReduceDesc {
+    const float* part_f;
+    const double* part_d;
+    int n_slots, nf;
+    float* red_f;
+    double* red_d;
+    int block_begin;
+};
+struct SolveDesc {
+    const float* red_f;
+    const double* red_d;
+    float* D;
+    int p, n;
+    float* norms;
+    double inv_count;
+    float* objective_out;
+    float* rmse_out;
+    float* G_out;
+    int keep_p;
+};
+struct RescaleDesc {
+    const int32_t* support;
+    float* coef;
+    long long count;
+    int n1, n2, side;
+    const float* norms;
+};
+// which: 0 gram, 1 reduce, 2 solve (one CTA per problem), 3 rescale.
+int launch_multi_update_kernels(int which, const void* d_desc, int G, int blocks, size_t smem,
+                                int* err, cudaStream_t st);
+size_t solve_smem_bytes(int p, int n, int* keep_p);
 
 // Record the first device-side error (first writer wins).
 __device__ __forceinline__ void record_error(int* err, int code) {

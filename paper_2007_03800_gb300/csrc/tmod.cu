@@ -9,7 +9,6 @@
 namespace sdl {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 
 // G = D^T D (row-major n x n) for a column-major p x n dictionary.
 __global__ void gram_kernel(const float* __restrict__ D, int p, int n, float* __restrict__ G) {
@@ -21,6 +20,19 @@ __global__ void gram_kernel(const float* __restrict__ D, int p, int n, float* __
     float g = 0.f;
     for (int a = 0; a < p; ++a) g = fmaf(di[a], dj[a], g);
     G[e] = g;
+}
+
+// Gram matrices of several dictionaries in one launch (block ranges per entry).
+__global__ void gram_multi_kernel(const GramDesc* __restrict__ d, int G) {
+    int g = 0;
+    while (g + 1 < G && (int)blockIdx.x >= d[g + 1].block_begin) ++g;
+    const GramDesc q = d[g];
+    const int e = (blockIdx.x - q.block_begin) * blockDim.x + threadIdx.x;
+    if (e >= q.n * q.n) return;
+    const int i = e / q.n, j = e - i * q.n;
+    float acc = 0.f;
+    for (int a = 0; a < q.p; ++a) acc = fmaf(q.D[(size_t)q.p * i + a], q.D[(size_t)q.p * j + a], acc);
+    q.G[e] = acc;
 }
 
 // Both Gram matrices in one launch: blocks [0, b1) for D1, the rest for D2.
@@ -45,13 +57,13 @@ __global__ void gram2_kernel(const float* __restrict__ D1, int p1, int n1, float
 // adds the 8 warp sums in order.
 constexpr int kReduceWarps = 8;
 
-__global__ void __launch_bounds__(kReduceWarps * 32)
-    reduce_partials_kernel(const float* __restrict__ part_f, const double* __restrict__ part_d,
-                           int n_slots, int nf, float* __restrict__ red_f,
-                           double* __restrict__ red_d) {
+__device__ __forceinline__ void reduce_body(const float* __restrict__ part_f,
+                                            const double* __restrict__ part_d, int n_slots,
+                                            int nf, float* __restrict__ red_f,
+                                            double* __restrict__ red_d, int blk) {
     __shared__ float ws[kReduceWarps][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int e = blockIdx.x * 32 + lane;
+    const int e = blk * 32 + lane;
     // four interleaved compensated sums keep four loads in flight
     float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
     if (e < nf) {
@@ -88,7 +100,7 @@ __global__ void __launch_bounds__(kReduceWarps * 32)
         }
         red_f[e] = tot;
     }
-    if (blockIdx.x == 0 && warp < 2) {
+    if (blk == 0 && warp < 2) {
         // the two FP64 sums: lanes stride over the slots, then a fixed shuffle tree
         double d = 0.0;
         for (int c = lane; c < n_slots; c += 32) d += part_d[(size_t)c * 2 + warp];
@@ -96,6 +108,23 @@ __global__ void __launch_bounds__(kReduceWarps * 32)
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         if (lane == 0) red_d[warp] = d;
     }
+}
+
+__global__ void __launch_bounds__(kReduceWarps * 32)
+    reduce_partials_kernel(const float* __restrict__ part_f, const double* __restrict__ part_d,
+                           int n_slots, int nf, float* __restrict__ red_f,
+                           double* __restrict__ red_d) {
+    reduce_body(part_f, part_d, n_slots, nf, red_f, red_d, blockIdx.x);
+}
+
+// Reductions of several problems in one launch; d[g].block_begin is the first
+// block of problem g (ascending), blocks of a problem cover its nf entries.
+__global__ void __launch_bounds__(kReduceWarps * 32)
+    reduce_multi_kernel(const ReduceDesc* __restrict__ d, int G) {
+    int g = 0;
+    while (g + 1 < G && (int)blockIdx.x >= d[g + 1].block_begin) ++g;
+    const ReduceDesc r = d[g];
+    reduce_body(r.part_f, r.part_d, r.n_slots, r.nf, r.red_f, r.red_d, blockIdx.x - r.block_begin);
 }
 
 // One CTA: the normal-equation solve of a dictionary update with atom
@@ -114,10 +143,11 @@ __global__ void __launch_bounds__(kReduceWarps * 32)
 // failure D is left untouched and the norms are set to 1.
 constexpr int kSolveThreads = 512;
 
-__global__ void __launch_bounds__(kSolveThreads)
-    solve_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D, int p,
-                 int n, float* __restrict__ norms, double inv_count, float* objective_out,
-                 float* rmse_out, int* err, float* G_out, int keep_p) {
+__device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
+                                           const double* __restrict__ red_d, float* D, int p,
+                                           int n, float* __restrict__ norms, double inv_count,
+                                           float* objective_out, float* rmse_out, int* err,
+                                           float* G_out, int keep_p) {
     extern __shared__ __align__(16) float sm[];
     const int lda = n | 1;                          // odd row strides: fewer bank conflicts
     float* A = sm;                                  // nu x nu (stride lda), becomes P_u^{-1}
@@ -275,6 +305,22 @@ __global__ void __launch_bounds__(kSolveThreads)
     }
 }
 
+__global__ void __launch_bounds__(kSolveThreads)
+    solve_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D, int p,
+                 int n, float* __restrict__ norms, double inv_count, float* objective_out,
+                 float* rmse_out, int* err, float* G_out, int keep_p) {
+    solve_body(red_f, red_d, D, p, n, norms, inv_count, objective_out, rmse_out, err, G_out,
+               keep_p);
+}
+
+// One CTA per problem.
+__global__ void __launch_bounds__(kSolveThreads) solve_multi_kernel(const SolveDesc* __restrict__ d,
+                                                                    int* err) {
+    const SolveDesc q = d[blockIdx.x];
+    solve_body(q.red_f, q.red_d, q.D, q.p, q.n, q.norms, q.inv_count, q.objective_out, q.rmse_out,
+               err, q.G_out, q.keep_p);
+}
+
 // X <- W^{-1} X: slot l of every code times the norm of its D1 atom (side 1,
 // Corollary 1) or D2 atom (side 2, Result 1).
 __global__ void rescale_kernel(const int32_t* __restrict__ support, float* __restrict__ coef,
@@ -289,7 +335,53 @@ __global__ void rescale_kernel(const int32_t* __restrict__ support, float* __res
     }
 }
 
+// Code rescale of several problems: blockIdx.y = problem.
+__global__ void rescale_multi_kernel(const RescaleDesc* __restrict__ d) {
+    const RescaleDesc q = d[blockIdx.y];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < q.count;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int v = q.support[e];
+        if (v < 0 || v >= q.n1 * q.n2) continue;
+        const int atom = (q.side == kSideD1) ? v % q.n1 : v / q.n1;
+        q.coef[e] *= q.norms[atom];
+    }
+}
+
 }  // namespace
+
+size_t solve_smem_bytes(int p, int n, int* keep_p) {
+    const size_t lda = (size_t)(n | 1);
+    const size_t base = (size_t)n * lda + 3 * (size_t)p * lda + 3 * (size_t)n;
+    const int keep = sizeof(float) * (base + (size_t)n * lda) <= 200 * 1024 ? 1 : 0;
+    if (keep_p) *keep_p = keep;
+    return sizeof(float) * (base + (keep ? (size_t)n * lda : 0));
+}
+
+int launch_multi_update_kernels(int which, const void* d_desc, int G, int blocks, size_t smem,
+                                int* err, cudaStream_t st) {
+    switch (which) {
+        case 0:
+            gram_multi_kernel<<<blocks, 256, 0, st>>>(static_cast<const GramDesc*>(d_desc), G);
+            break;
+        case 1:
+            reduce_multi_kernel<<<blocks, kReduceWarps * 32, 0, st>>>(
+                static_cast<const ReduceDesc*>(d_desc), G);
+            break;
+        case 2:
+            if (cudaFuncSetAttribute(solve_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return SDL_ERR_CUDA;
+            solve_multi_kernel<<<G, kSolveThreads, smem, st>>>(static_cast<const SolveDesc*>(d_desc),
+                                                               err);
+            break;
+        case 3:
+            rescale_multi_kernel<<<dim3(std::max(1, blocks), G), 256, 0, st>>>(
+                static_cast<const RescaleDesc*>(d_desc));
+            break;
+        default: return SDL_ERR_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
 
 void launch_gram(const float* D, int p, int n, float* G, cudaStream_t st) {
     const int threads = 256;
@@ -313,11 +405,9 @@ void launch_reduce_partials(const float* part_f, const double* part_d, int n_slo
 int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n, float* norms,
                  double inv_count, float* objective_out, float* rmse_out, int* err,
                  cudaStream_t st, float* G_out) {
-    const size_t lda = (size_t)(n | 1);
-    const size_t base = (size_t)n * lda + 3 * (size_t)p * lda + 3 * (size_t)n;
     // keep a copy of P in shared memory for the objective term when it fits
-    const int keep_p = sizeof(float) * (base + (size_t)n * lda) <= 200 * 1024 ? 1 : 0;
-    const size_t bytes = sizeof(float) * (base + (keep_p ? (size_t)n * lda : 0));
+    int keep_p = 0;
+    const size_t bytes = solve_smem_bytes(p, n, &keep_p);
     if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) != cudaSuccess)
         return SDL_ERR_CUDA;

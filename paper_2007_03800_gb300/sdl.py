@@ -44,6 +44,11 @@ SIGNATURES = {
     "sdl_update_D2": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _P, _P, _P],
     "sdl_iterate": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
     "sdl_sparse_code_static": [_P, _I, _I, _L, _P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
+    "sdl_batch_create": [_P, _P, _I, _I, _P, ctypes.POINTER(_P)],
+    "sdl_batch_sparse_code": [_P, _P],
+    "sdl_batch_iterate": [_P, _P, _P],
+    "sdl_batch_tuning": [_P, _P, _P, _P],
+    "sdl_batch_destroy": [_P],
     "sdl_profile_enable": [_P, _I],
     "sdl_profile_collect": [_P, _P, _P, _I],
 }
@@ -259,3 +264,72 @@ class Context:
                                    _ptr(rmse_out), _stream(stream))
         _check(rc, "sdl_iterate")
         return out
+
+
+class _Group(ctypes.Structure):
+    """Mirror of ``sdl_group`` in include/sdl.h."""
+    _fields_ = [("Y", _P), ("p1", _I), ("p2", _I), ("N", _L), ("D1", _P), ("n1", _I),
+                ("D2", _P), ("n2", _I), ("s_max", _I), ("eps", _F), ("support", _P),
+                ("coef", _P), ("nnz", _P), ("res_energy", _P)]
+
+
+BATCH_AUTOTUNE = 1
+BATCH_GRAPH = 2
+
+
+class Batch:
+    """Several dictionary-learning problems run together (``sdl_batch_*``).
+
+    groups: list of dicts with keys Y, D1, D2, s, eps (optional) and codes
+    (optional :class:`Codes`; allocated when absent).  The tensors must stay
+    alive and in place for the batch's lifetime (the batch keeps references).
+    """
+
+    def __init__(self, ctx: Context, groups, autotune: bool = True, graph: bool = True,
+                 stream=None):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        self.groups = []
+        arr = (_Group * len(groups))()
+        for g, spec in enumerate(groups):
+            Y, D1, D2, s = spec["Y"], spec["D1"], spec["D2"], int(spec["s"])
+            N, p1, p2 = _check_Y(Y)
+            n1, n2 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2")
+            codes = spec.get("codes") or Codes.empty(N, s, Y.device, with_energy=True)
+            self.groups.append(dict(Y=Y, D1=D1, D2=D2, s=s, eps=float(spec.get("eps", 0.0)),
+                                    codes=codes))
+            arr[g] = _Group(Y.data_ptr(), p1, p2, N, D1.data_ptr(), n1, D2.data_ptr(), n2, s,
+                            float(spec.get("eps", 0.0)), codes.support.data_ptr(),
+                            codes.coef.data_ptr(), codes.nnz.data_ptr(),
+                            codes.res_energy.data_ptr() if codes.res_energy is not None else None)
+        flags = (BATCH_AUTOTUNE if autotune else 0) | (BATCH_GRAPH if graph else 0)
+        h = ctypes.c_void_p()
+        _check(self._lib.sdl_batch_create(ctx._h, arr, len(groups), flags, _stream(stream),
+                                          ctypes.byref(h)), "sdl_batch_create")
+        self._h = h
+
+    def sparse_code(self, stream=None):
+        _check(self._lib.sdl_batch_sparse_code(self._h, _stream(stream)), "sdl_batch_sparse_code")
+
+    def iterate(self, rmse_out=None, stream=None):
+        if rmse_out is not None:
+            _need(rmse_out, torch.float32, (2 * len(self.groups),), None, "rmse_out")
+        _check(self._lib.sdl_batch_iterate(self._h, _ptr(rmse_out), _stream(stream)),
+               "sdl_batch_iterate")
+
+    def tuning(self):
+        G = len(self.groups)
+        sid, ctas, cost = (_I * G)(), (_I * G)(), (_F * G)()
+        self._lib.sdl_batch_tuning(self._h, sid, ctas, cost)
+        return [dict(shape_id=sid[g], ctas=ctas[g], cost_us=cost[g]) for g in range(G)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sdl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

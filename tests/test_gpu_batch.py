@@ -1,0 +1,113 @@
+"""Batched problems (sdl_batch_*): groups of different shapes, sparsities and
+stopping rules in one persistent launch per pass, with an autotuner and a
+captured CUDA graph per iteration.  Each group must match the FP64 oracle
+exactly as a stand-alone problem would."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2007_03800_gb300 import sdl, synth
+from parity import (COEF_RTOL, DICT_RTOL, RMSE_RTOL, coef_rel_error, compare_supports,
+                    to_gpu_problem)
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [  # p, n, s, eps
+    (8, 16, 4, 1.15 * 20.0 * 8),
+    (12, 24, 6, 0.0),
+    (16, 32, 8, 1.15 * 20.0 * 16),
+]
+
+
+def make_groups(seed=0, N=(3000, 2500, 1200)):
+    img = synth.synthetic_image(300 + seed, size=160)
+    noisy = img + np.random.default_rng(seed).normal(0, 20.0, img.shape)
+    out = []
+    for (p, n, s, eps), n_sig in zip(SHAPES, N):
+        Y, _ = synth.all_patches(noisy, p)
+        Y = Y[np.random.default_rng(seed + p).choice(Y.shape[0], n_sig, replace=False)]
+        D1, D2 = synth.init_dictionaries(p, p, n, n, seed=1)
+        out.append(dict(Y=Y, D1=D1, D2=D2, s=s, eps=eps))
+    return out
+
+
+def to_specs(groups):
+    specs = []
+    for g in groups:
+        Yg, D1g, D2g = to_gpu_problem(g["Y"], g["D1"], g["D2"])
+        specs.append(dict(Y=Yg, D1=D1g, D2=D2g, s=g["s"], eps=g["eps"]))
+    return specs
+
+
+def test_batch_sparse_code_matches_oracle_and_single_calls(gpu_ctx):
+    groups = make_groups()
+    specs = to_specs(groups)
+    batch = sdl.Batch(gpu_ctx, specs, autotune=True, graph=False)
+    batch.sparse_code()
+    assert gpu_ctx.status() == 0
+    for g, spec in zip(groups, batch.groups):
+        eps = g["eps"] or None
+        ref = oracle.omp2d(g["Y"], g["D1"], g["D2"], g["s"], eps=eps)
+        codes = spec["codes"]
+        rep, exact = compare_supports(codes.support.cpu().numpy(), codes.nnz.cpu().numpy(), ref,
+                                      eps=eps)
+        assert rep.bad == 0 and rep.ties <= max(2, 2e-3 * rep.n), rep
+        assert coef_rel_error(codes.coef.cpu().numpy(), ref.coef, exact).max(initial=0) < COEF_RTOL
+        # every lane tiling performs the same per-entry arithmetic: identical codes
+        single = gpu_ctx.sparse_code(spec["Y"], spec["D1"], spec["D2"], spec["s"], eps=spec["eps"])
+        assert torch.equal(single.support, codes.support)
+        assert torch.equal(single.coef, codes.coef)
+    tun = batch.tuning()
+    assert len(tun) == 3 and all(t["ctas"] >= 1 and t["cost_us"] > 0 for t in tun)
+    batch.close()
+
+
+def test_batch_iterate_matches_oracle(gpu_ctx):
+    groups = make_groups(seed=1)
+    specs = to_specs(groups)
+    batch = sdl.Batch(gpu_ctx, specs, autotune=True, graph=True)
+    rmse = torch.zeros(6, dtype=torch.float32, device="cuda:0")
+    batch.iterate(rmse_out=rmse)
+    assert gpu_ctx.status() == 0
+    r = rmse.cpu().numpy()
+    for g, (grp, spec) in enumerate(zip(groups, batch.groups)):
+        ref = oracle.iterate(grp["Y"], grp["D1"], grp["D2"], grp["s"], eps=grp["eps"] or None)
+        assert abs(r[2 * g] - ref.rmse_after_D1) / ref.rmse_after_D1 < RMSE_RTOL, (g, r, ref.rmse_after_D1)
+        assert abs(r[2 * g + 1] - ref.rmse_after_D2) / ref.rmse_after_D2 < RMSE_RTOL
+        assert np.abs(spec["D1"].cpu().numpy() - ref.D1).max() < DICT_RTOL
+        assert np.abs(spec["D2"].cpu().numpy() - ref.D2).max() < DICT_RTOL
+        codes = spec["codes"]
+        rep, exact = compare_supports(codes.support.cpu().numpy(), codes.nnz.cpu().numpy(),
+                                      ref.omp_b, eps=grp["eps"] or None)
+        assert rep.bad == 0, rep
+        assert coef_rel_error(codes.coef.cpu().numpy(), ref.coef, exact).max(initial=0) < COEF_RTOL
+    batch.close()
+
+
+def test_graph_replay_equals_direct_launches(gpu_ctx):
+    """The captured graph runs exactly the direct launch sequence: three
+    iterations give bit-identical dictionaries, codes and RMSE."""
+    groups = make_groups(seed=2, N=(1500, 1300, 700))
+    results = []
+    for graph in (False, True):
+        specs = to_specs(groups)
+        batch = sdl.Batch(gpu_ctx, specs, autotune=False, graph=graph)
+        rmse = torch.zeros(6, dtype=torch.float32, device="cuda:0")
+        for _ in range(3):
+            batch.iterate(rmse_out=rmse)
+        assert gpu_ctx.status() == 0
+        results.append([(s["D1"].clone(), s["D2"].clone(), s["codes"].support.clone(),
+                         s["codes"].coef.clone()) for s in batch.groups] + [rmse.clone()])
+        batch.close()
+    for a, b in zip(results[0][:-1], results[1][:-1]):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    assert torch.equal(results[0][-1], results[1][-1])
+
+
+def test_batch_rejects_shapes_without_specialisation(gpu_ctx):
+    Yg, D1g, D2g = to_gpu_problem(np.zeros((64, 16, 64)), *synth.init_dictionaries(16, 64, 32, 128))
+    with pytest.raises(sdl.SDLError) as e:
+        sdl.Batch(gpu_ctx, [dict(Y=Yg, D1=D1g, D2=D2g, s=10)])
+    assert e.value.code == -7
