@@ -162,8 +162,11 @@ struct FastLayout {
         return side == kSideD1 ? Sh::N1 * Sh::N1 + Sh::P1 * Sh::N1
                : side == kSideD2 ? Sh::N2 * Sh::N2 + Sh::P2 * Sh::N2 : 0;
     }
-    __host__ __device__ static constexpr int accd(int side) { return acc + al4(nf(side)); }     // 2 doubles
-    __host__ __device__ static constexpr int warp0(int side) { return accd(side) + 4; }
+    // warp-private accumulators: WPC x nf floats (summed in warp order at the end)
+    __host__ __device__ static constexpr int accw(int side) { return al4(nf(side)) * Sh::WPC; }
+    // per-warp energy sums: WPC x 2 floats
+    __host__ __device__ static constexpr int acce(int side) { return acc + accw(side); }
+    __host__ __device__ static constexpr int warp0(int side) { return acce(side) + al4(2 * Sh::WPC); }
     // per warp: mbarriers (4 floats), Y double buffer, Z, the C0 blocks of
     // the 32 lanes (lane-major, stride EP: conflict-free 128-bit loads)
     static constexpr int EP = Sh::EP;
@@ -171,7 +174,8 @@ struct FastLayout {
     static constexpr int w_y = 4;
     static constexpr int w_z = w_y + 2 * al4(Sh::PP);
     static constexpr int w_c0 = w_z + al4(Sh::P1 * Sh::LD2);
-    static constexpr int w_stride = w_c0 + 32 * EP;
+    static constexpr int w_pick = w_c0 + 32 * EP;             // (i, j, x) of the picks
+    static constexpr int w_stride = w_pick + al4(3 * Sh::S);
     __host__ __device__ static constexpr int total(int side, int wpc) { return warp0(side) + wpc * w_stride; }
 };
 
@@ -196,14 +200,19 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
     float* G1s = smem + L::g1;
     float* G2s = smem + L::g2;
     float* acc = smem + L::acc;
-    double* accd = reinterpret_cast<double*>(smem + L::accd(SIDE));
+    float* acce = smem + L::acce(SIDE);
     float* wb = smem + L::warp0(SIDE) + w * L::w_stride;
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(wb + L::w_bar);
     float* Ybuf = wb + L::w_y;
     float* Zs = wb + L::w_z;
     float* C0s = wb + L::w_c0;
     float* myc0 = C0s + lane * L::EP;
+    int* pick_i = reinterpret_cast<int*>(wb + L::w_pick);
+    int* pick_j = pick_i + S;
+    float* pick_x = reinterpret_cast<float*>(pick_j + S);
     constexpr int nf = L::nf(SIDE);
+    constexpr int nfa = al4(nf);
+    float* wacc = acc + w * nfa;     // this warp's private accumulators
 
     // ---- CTA set-up: padded copies of D1, D2, G1, G2; zero accumulators
     for (int e = threadIdx.x; e < P1 * LD1; e += blockDim.x) {
@@ -227,8 +236,7 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
         G2s[e] = (off < RJ) ? a.G2[c * N2 + blk * RJ + off] : 0.f;
     }
     if constexpr (SIDE != kCodeOnly) {
-        for (int e = threadIdx.x; e < nf; e += blockDim.x) acc[e] = 0.f;
-        if (threadIdx.x < 2) accd[threadIdx.x] = 0.0;
+        for (int e = threadIdx.x; e < L::accw(SIDE) + al4(2 * Sh::WPC); e += blockDim.x) acc[e] = 0.f;
     }
     for (int e = threadIdx.x; e < wpc * L::w_stride; e += blockDim.x)
         smem[L::warp0(SIDE) + e] = 0.f;   // Z padding columns stay 0
@@ -449,55 +457,78 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
             if (!finite) record_error(a.err, SDL_ERR_NONFINITE);
         }
 
-        // ---- fused partial sums
-        if constexpr (SIDE == kSideD1) {
-            float* accP = acc;
-            float* accB = acc + N1 * N1;
+        // ---- fused partial sums, deterministic: every address of the warp's
+        // private accumulators is owned by one lane, which adds its terms in
+        // a fixed order (no atomics)
+        if constexpr (SIDE != kCodeOnly) {
+            constexpr int NA = SIDE == kSideD1 ? N1 : N2;    // P (or M) is NA x NA
+            constexpr int PB = SIDE == kSideD1 ? P1 : P2;    // B has PB rows
+            float* wP = wacc;
+            float* wB = wacc + NA * NA;
+            // B: lane r owns row r, picks in order
+            for (int l = 0; l < cnt; ++l) {
+                const int il = __shfl_sync(kFull, myi, l), jl = __shfl_sync(kFull, myj, l);
+                const float xl = __shfl_sync(kFull, myx, l);
+                if (lane < PB) {
+                    if constexpr (SIDE == kSideD1) {
+                        // B1[r, i_l] += x_l (Y D2)[r, j_l]
+                        wB[lane * N1 + il] = fmaf(xl, Zs[lane * LD2 + pos2<Sh>(jl)], wB[lane * N1 + il]);
+                    } else {
+                        // B2[b, j_l] += x_l (Y^T d1_{i_l})[b]
+                        float wsum = 0.f;
+                        const float* yc = Ys + lane * P1;
+                        const float* dc = D1c + il * P1;
 #pragma unroll
-            for (int e0 = 0; e0 < P1 * S; e0 += 32) {
-                const int e = e0 + lane;
-                const int l = e / P1, r = e % P1;
-                const int il = __shfl_sync(kFull, myi, l & 31), jl = __shfl_sync(kFull, myj, l & 31);
-                const float xl = __shfl_sync(kFull, myx, l & 31);
-                if (l < cnt) atomicAdd(&accB[r * N1 + il], xl * Zs[r * LD2 + pos2<Sh>(jl)]);
-            }
-#pragma unroll
-            for (int e0 = 0; e0 < S * S; e0 += 32) {
-                const int e = e0 + lane;
-                const int l = e / S, m = e % S;
-                const int il = __shfl_sync(kFull, myi, l & 31), im = __shfl_sync(kFull, myi, m);
-                const int jl = __shfl_sync(kFull, myj, l & 31), jm = __shfl_sync(kFull, myj, m);
-                const float xl = __shfl_sync(kFull, myx, l & 31), xm = __shfl_sync(kFull, myx, m);
-                if (l < cnt && m < cnt)
-                    atomicAdd(&accP[il * N1 + im], xl * xm * G2s[jl * LD2 + pos2<Sh>(jm)]);
-            }
-        } else if constexpr (SIDE == kSideD2) {
-            float* accM = acc;
-            float* accB = acc + N2 * N2;
-#pragma unroll
-            for (int e0 = 0; e0 < P2 * S; e0 += 32) {
-                const int e = e0 + lane;
-                const int l = e / P2, bb = e % P2;
-                const int il = __shfl_sync(kFull, myi, l & 31), jl = __shfl_sync(kFull, myj, l & 31);
-                const float xl = __shfl_sync(kFull, myx, l & 31);
-                if (l < cnt) {
-                    float wsum = 0.f;
-                    const float* yc = Ys + bb * P1;
-                    const float* dc = D1c + il * P1;
-#pragma unroll
-                    for (int r = 0; r < P1; ++r) wsum = fmaf(yc[r], dc[r], wsum);
-                    atomicAdd(&accB[bb * N2 + jl], xl * wsum);
+                        for (int r = 0; r < P1; ++r) wsum = fmaf(yc[r], dc[r], wsum);
+                        wB[lane * N2 + jl] = fmaf(xl, wsum, wB[lane * N2 + jl]);
+                    }
                 }
             }
-#pragma unroll
-            for (int e0 = 0; e0 < S * S; e0 += 32) {
-                const int e = e0 + lane;
-                const int l = e / S, m = e % S;
-                const int il = __shfl_sync(kFull, myi, l & 31), im = __shfl_sync(kFull, myi, m);
-                const int jl = __shfl_sync(kFull, myj, l & 31), jm = __shfl_sync(kFull, myj, m);
-                const float xl = __shfl_sync(kFull, myx, l & 31), xm = __shfl_sync(kFull, myx, m);
-                if (l < cnt && m < cnt)
-                    atomicAdd(&accM[jl * N2 + jm], xl * xm * G1s[il * LD1 + pos1<Sh>(im)]);
+            // P[i_l, i_m] += x_l x_m G2[j_l, j_m]  (D1 side) or
+            // M[j_l, j_m] += x_l x_m G1[i_l, i_m]  (D2 side): lane l owns row
+            // i_l (j_l) when the picks' row atoms are distinct
+            const int rowkey = SIDE == kSideD1 ? myi : myj;
+            const unsigned peers = __match_any_sync(kFull, lane < cnt ? rowkey : -1 - lane);
+            if (__all_sync(kFull, lane >= cnt || peers == (1u << lane))) {
+                for (int m = 0; m < cnt; ++m) {
+                    const int im = __shfl_sync(kFull, myi, m), jm = __shfl_sync(kFull, myj, m);
+                    const float xm = __shfl_sync(kFull, myx, m);
+                    if (lane < cnt) {
+                        float g;
+                        int addr;
+                        if constexpr (SIDE == kSideD1) {
+                            g = G2s[myj * LD2 + pos2<Sh>(jm)];
+                            addr = myi * N1 + im;
+                        } else {
+                            g = G1s[myi * LD1 + pos1<Sh>(im)];
+                            addr = myj * N2 + jm;
+                        }
+                        wP[addr] = fmaf(myx * xm, g, wP[addr]);
+                    }
+                }
+            } else {
+                // a row atom picked twice: one lane adds all pairs in order
+                if (lane < cnt) {
+                    pick_i[lane] = myi;
+                    pick_j[lane] = myj;
+                    pick_x[lane] = myx;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    for (int l = 0; l < cnt; ++l)
+                        for (int m = 0; m < cnt; ++m) {
+                            float g;
+                            int addr;
+                            if constexpr (SIDE == kSideD1) {
+                                g = G2s[pick_j[l] * LD2 + pos2<Sh>(pick_j[m])];
+                                addr = pick_i[l] * N1 + pick_i[m];
+                            } else {
+                                g = G1s[pick_i[l] * LD1 + pos1<Sh>(pick_i[m])];
+                                addr = pick_j[l] * N2 + pick_j[m];
+                            }
+                            wP[addr] = fmaf(pick_x[l] * pick_x[m], g, wP[addr]);
+                        }
+                }
             }
         }
         if (lane == 0 && finite) {
@@ -520,13 +551,23 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
 
     if constexpr (SIDE != kCodeOnly) {
         if (lane == 0) {
-            atomicAdd(&accd[0], (double)w_energy - (double)w_energy_c);
-            atomicAdd(&accd[1], (double)w_ynorm - (double)w_ynorm_c);
+            acce[2 * w] = w_energy - w_energy_c;
+            acce[2 * w + 1] = w_ynorm - w_ynorm_c;
         }
         __syncthreads();
+        // combine the warps' accumulators in warp order
+        const int wpc_all = blockDim.x >> 5;
         float* dst = a.part_f + (size_t)slot * nf;
-        for (int e = threadIdx.x; e < nf; e += blockDim.x) dst[e] = acc[e];
-        if (threadIdx.x < 2) a.part_d[(size_t)slot * 2 + threadIdx.x] = accd[threadIdx.x];
+        for (int e = threadIdx.x; e < nf; e += blockDim.x) {
+            float v = 0.f;
+            for (int ww = 0; ww < wpc_all; ++ww) v += acc[ww * nfa + e];
+            dst[e] = v;
+        }
+        if (threadIdx.x < 2) {
+            double d = 0.0;
+            for (int ww = 0; ww < wpc_all; ++ww) d += (double)acce[2 * ww + threadIdx.x];
+            a.part_d[(size_t)slot * 2 + threadIdx.x] = d;
+        }
     }
 }
 
