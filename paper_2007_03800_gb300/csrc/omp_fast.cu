@@ -459,7 +459,8 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
 
         // ---- fused partial sums, deterministic: every address of the warp's
         // private accumulators is owned by one lane, which adds its terms in
-        // a fixed order (no atomics)
+        // a fixed order; the adds are shared-memory reductions (no return
+        // value, so no wait), never contended by another lane
         if constexpr (SIDE != kCodeOnly) {
             constexpr int NA = SIDE == kSideD1 ? N1 : N2;    // P (or M) is NA x NA
             constexpr int PB = SIDE == kSideD1 ? P1 : P2;    // B has PB rows
@@ -472,7 +473,7 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                 if (lane < PB) {
                     if constexpr (SIDE == kSideD1) {
                         // B1[r, i_l] += x_l (Y D2)[r, j_l]
-                        wB[lane * N1 + il] = fmaf(xl, Zs[lane * LD2 + pos2<Sh>(jl)], wB[lane * N1 + il]);
+                        atomicAdd(&wB[lane * N1 + il], xl * Zs[lane * LD2 + pos2<Sh>(jl)]);
                     } else {
                         // B2[b, j_l] += x_l (Y^T d1_{i_l})[b]
                         float wsum = 0.f;
@@ -480,7 +481,7 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                         const float* dc = D1c + il * P1;
 #pragma unroll
                         for (int r = 0; r < P1; ++r) wsum = fmaf(yc[r], dc[r], wsum);
-                        wB[lane * N2 + jl] = fmaf(xl, wsum, wB[lane * N2 + jl]);
+                        atomicAdd(&wB[lane * N2 + jl], xl * wsum);
                     }
                 }
             }
@@ -503,7 +504,7 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                             g = G1s[myi * LD1 + pos1<Sh>(im)];
                             addr = myj * N2 + jm;
                         }
-                        wP[addr] = fmaf(myx * xm, g, wP[addr]);
+                        atomicAdd(&wP[addr], myx * xm * g);
                     }
                 }
             } else {
@@ -526,7 +527,7 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                                 g = G1s[pick_i[l] * LD1 + pos1<Sh>(pick_i[m])];
                                 addr = pick_j[l] * N2 + pick_j[m];
                             }
-                            wP[addr] = fmaf(pick_x[l] * pick_x[m], g, wP[addr]);
+                            atomicAdd(&wP[addr], pick_x[l] * pick_x[m] * g);
                         }
                 }
             }
