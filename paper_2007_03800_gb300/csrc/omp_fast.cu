@@ -174,8 +174,7 @@ struct FastLayout {
     static constexpr int w_y = 4;
     static constexpr int w_z = w_y + 2 * al4(Sh::PP);
     static constexpr int w_c0 = w_z + al4(Sh::P1 * Sh::LD2);
-    static constexpr int w_pick = w_c0 + 32 * EP;             // (i, j, x) of the picks
-    static constexpr int w_stride = w_pick + al4(3 * Sh::S);
+    static constexpr int w_stride = w_c0 + 32 * EP;
     __host__ __device__ static constexpr int total(int side, int wpc) { return warp0(side) + wpc * w_stride; }
 };
 
@@ -207,9 +206,6 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
     float* Zs = wb + L::w_z;
     float* C0s = wb + L::w_c0;
     float* myc0 = C0s + lane * L::EP;
-    int* pick_i = reinterpret_cast<int*>(wb + L::w_pick);
-    int* pick_j = pick_i + S;
-    float* pick_x = reinterpret_cast<float*>(pick_j + S);
     constexpr int nf = L::nf(SIDE);
     constexpr int nfa = al4(nf);
     float* wacc = acc + w * nfa;     // this warp's private accumulators
@@ -457,79 +453,58 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
             if (!finite) record_error(a.err, SDL_ERR_NONFINITE);
         }
 
-        // ---- fused partial sums, deterministic: every address of the warp's
-        // private accumulators is owned by one lane, which adds its terms in
-        // a fixed order; the adds are shared-memory reductions (no return
-        // value, so no wait), never contended by another lane
-        if constexpr (SIDE != kCodeOnly) {
-            constexpr int NA = SIDE == kSideD1 ? N1 : N2;    // P (or M) is NA x NA
-            constexpr int PB = SIDE == kSideD1 ? P1 : P2;    // B has PB rows
+        // ---- fused partial sums into this warp's private accumulators (no
+        // other warp touches them, and the warps are combined in a fixed
+        // order at the end); terms are spread over the lanes as (pick, row)
+        // and (pick, pick) pairs
+        if constexpr (SIDE == kSideD1) {
             float* wP = wacc;
-            float* wB = wacc + NA * NA;
-            // B: lane r owns row r, picks in order
-            for (int l = 0; l < cnt; ++l) {
-                const int il = __shfl_sync(kFull, myi, l), jl = __shfl_sync(kFull, myj, l);
-                const float xl = __shfl_sync(kFull, myx, l);
-                if (lane < PB) {
-                    if constexpr (SIDE == kSideD1) {
-                        // B1[r, i_l] += x_l (Y D2)[r, j_l]
-                        atomicAdd(&wB[lane * N1 + il], xl * Zs[lane * LD2 + pos2<Sh>(jl)]);
-                    } else {
-                        // B2[b, j_l] += x_l (Y^T d1_{i_l})[b]
-                        float wsum = 0.f;
-                        const float* yc = Ys + lane * P1;
-                        const float* dc = D1c + il * P1;
+            float* wB = wacc + N1 * N1;
 #pragma unroll
-                        for (int r = 0; r < P1; ++r) wsum = fmaf(yc[r], dc[r], wsum);
-                        atomicAdd(&wB[lane * N2 + jl], xl * wsum);
-                    }
+            for (int e0 = 0; e0 < P1 * S; e0 += 32) {
+                const int e = e0 + lane;
+                const int l = e / P1, r = e % P1;
+                const int il = __shfl_sync(kFull, myi, l & 31), jl = __shfl_sync(kFull, myj, l & 31);
+                const float xl = __shfl_sync(kFull, myx, l & 31);
+                if (l < cnt) atomicAdd(&wB[r * N1 + il], xl * Zs[r * LD2 + pos2<Sh>(jl)]);
+            }
+#pragma unroll
+            for (int e0 = 0; e0 < S * S; e0 += 32) {
+                const int e = e0 + lane;
+                const int l = e / S, m = e % S;
+                const int il = __shfl_sync(kFull, myi, l & 31), im = __shfl_sync(kFull, myi, m);
+                const int jl = __shfl_sync(kFull, myj, l & 31), jm = __shfl_sync(kFull, myj, m);
+                const float xl = __shfl_sync(kFull, myx, l & 31), xm = __shfl_sync(kFull, myx, m);
+                if (l < cnt && m < cnt)
+                    atomicAdd(&wP[il * N1 + im], xl * xm * G2s[jl * LD2 + pos2<Sh>(jm)]);
+            }
+        } else if constexpr (SIDE == kSideD2) {
+            float* wM = wacc;
+            float* wB = wacc + N2 * N2;
+#pragma unroll
+            for (int e0 = 0; e0 < P2 * S; e0 += 32) {
+                const int e = e0 + lane;
+                const int l = e / P2, bb = e % P2;
+                const int il = __shfl_sync(kFull, myi, l & 31), jl = __shfl_sync(kFull, myj, l & 31);
+                const float xl = __shfl_sync(kFull, myx, l & 31);
+                if (l < cnt) {
+                    float wsum = 0.f;
+                    const float* yc = Ys + bb * P1;
+                    const float* dc = D1c + il * P1;
+#pragma unroll
+                    for (int r = 0; r < P1; ++r) wsum = fmaf(yc[r], dc[r], wsum);
+                    atomicAdd(&wB[bb * N2 + jl], xl * wsum);
                 }
             }
-            // P[i_l, i_m] += x_l x_m G2[j_l, j_m]  (D1 side) or
-            // M[j_l, j_m] += x_l x_m G1[i_l, i_m]  (D2 side): lane l owns row
-            // i_l (j_l) when the picks' row atoms are distinct
-            const int rowkey = SIDE == kSideD1 ? myi : myj;
-            const unsigned peers = __match_any_sync(kFull, lane < cnt ? rowkey : -1 - lane);
-            if (__all_sync(kFull, lane >= cnt || peers == (1u << lane))) {
-                for (int m = 0; m < cnt; ++m) {
-                    const int im = __shfl_sync(kFull, myi, m), jm = __shfl_sync(kFull, myj, m);
-                    const float xm = __shfl_sync(kFull, myx, m);
-                    if (lane < cnt) {
-                        float g;
-                        int addr;
-                        if constexpr (SIDE == kSideD1) {
-                            g = G2s[myj * LD2 + pos2<Sh>(jm)];
-                            addr = myi * N1 + im;
-                        } else {
-                            g = G1s[myi * LD1 + pos1<Sh>(im)];
-                            addr = myj * N2 + jm;
-                        }
-                        atomicAdd(&wP[addr], myx * xm * g);
-                    }
-                }
-            } else {
-                // a row atom picked twice: one lane adds all pairs in order
-                if (lane < cnt) {
-                    pick_i[lane] = myi;
-                    pick_j[lane] = myj;
-                    pick_x[lane] = myx;
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    for (int l = 0; l < cnt; ++l)
-                        for (int m = 0; m < cnt; ++m) {
-                            float g;
-                            int addr;
-                            if constexpr (SIDE == kSideD1) {
-                                g = G2s[pick_j[l] * LD2 + pos2<Sh>(pick_j[m])];
-                                addr = pick_i[l] * N1 + pick_i[m];
-                            } else {
-                                g = G1s[pick_i[l] * LD1 + pos1<Sh>(pick_i[m])];
-                                addr = pick_j[l] * N2 + pick_j[m];
-                            }
-                            atomicAdd(&wP[addr], pick_x[l] * pick_x[m] * g);
-                        }
-                }
+#pragma unroll
+            for (int e0 = 0; e0 < S * S; e0 += 32) {
+                const int e = e0 + lane;
+                const int l = e / S, m = e % S;
+                const int il = __shfl_sync(kFull, myi, l & 31), im = __shfl_sync(kFull, myi, m);
+                const int jl = __shfl_sync(kFull, myj, l & 31), jm = __shfl_sync(kFull, myj, m);
+                const float xl = __shfl_sync(kFull, myx, l & 31), xm = __shfl_sync(kFull, myx, m);
+                if (l < cnt && m < cnt)
+                    atomicAdd(&wM[jl * N2 + jm], xl * xm * G1s[il * LD1 + pos1<Sh>(im)]);
             }
         }
         if (lane == 0 && finite) {
