@@ -219,6 +219,36 @@ int sdl_batch_tuning(const sdl_batch* batch, int* shape_id, int* ctas, float* co
 int sdl_batch_destroy(sdl_batch* batch);
 
 /*
+ * Patch-based denoising (Sec. IV): the sparse coder applied to every
+ * overlapping patch of a noisy image, the image rebuilt by averaging.
+ *
+ * sdl_extract_patches - every stride-1 p x p patch of an H x W row-major FP32
+ *   image, raster order of the top-left corner (k = r*(W-p+1) + c), each with
+ *   its mean removed: patches[k*p*p + a + p*b] = img[(r+a)*W + c+b] - means[k].
+ *   N = (H-p+1)(W-p+1) patches; patches holds N*p*p floats, means N.
+ */
+int sdl_extract_patches(const float* image, int H, int W, int p, float* patches,
+                        float* means, void* stream);
+
+/*
+ * sdl_patch_average - rebuild the image from coded patches: pixel (y, x) is
+ *   the plain average, over every patch k covering it, of
+ *   means[k] + (D1 X_k D2^T)[y - r, x - c]   (D1 p x n1, D2 p x n2).
+ *   Codes as written by the coders (N x s_max slots).  The reconstructed
+ *   patches go through a context-owned workspace of N*p*p floats.  Output
+ *   image_out: H*W floats, row-major.  Deterministic (fixed summation order).
+ */
+int sdl_patch_average(sdl_ctx* ctx, const int32_t* support, const float* coef,
+                      const float* means, int s_max, const float* D1, int n1,
+                      const float* D2, int n2, int p, int H, int W, float* image_out,
+                      void* stream);
+
+/* sdl_psnr - 10 log10(peak^2 / MSE(x, ref)) over `count` floats, written to
+ * device float out[0]. */
+int sdl_psnr(const float* x, const float* ref, int64_t count, float peak, float* out,
+             void* stream);
+
+/*
  * sdl_sparse_code_static - the sparse coder of sdl_sparse_code with no
  * context and no device allocation.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory once running

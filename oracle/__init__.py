@@ -9,4 +9,4 @@ generators in ``paper_2007_03800_gb300.synth`` (data only, no method
 arithmetic).
 """
 from .sdl_oracle import *  # noqa: F401,F403
-from .sdl_oracle import __all__  # noqa: F401
+from . import denoise  # noqa: F401

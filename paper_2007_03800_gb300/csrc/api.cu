@@ -158,6 +158,7 @@ int sdl_destroy(sdl_ctx* c) {
     cudaFree(c->red_f);
     cudaFree(c->red_d);
     cudaFree(c->norms);
+    cudaFree(c->rec);
     for (auto& r : c->recs) {
         cudaEventDestroy(r.beg);
         cudaEventDestroy(r.end);

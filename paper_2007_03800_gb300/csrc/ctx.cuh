@@ -17,6 +17,8 @@ struct sdl_ctx {
     float* red_f = nullptr;      // reduced sums
     double* red_d = nullptr;
     float* norms = nullptr;      // column norms of the last solve
+    float* rec = nullptr;        // reconstructed patches (patch averaging)
+    size_t cap_rec = 0;
     size_t cap_g1 = 0, cap_g2 = 0, cap_part = 0, cap_slots = 0, cap_red = 0, cap_redd = 0,
            cap_norms = 0;
     // tracing: launch counters and (optionally) one event pair per launch

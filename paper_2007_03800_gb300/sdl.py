@@ -49,6 +49,9 @@ SIGNATURES = {
     "sdl_batch_iterate": [_P, _P, _P],
     "sdl_batch_tuning": [_P, _P, _P, _P],
     "sdl_batch_destroy": [_P],
+    "sdl_extract_patches": [_P, _I, _I, _I, _P, _P, _P],
+    "sdl_patch_average": [_P, _P, _P, _P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _P],
+    "sdl_psnr": [_P, _P, _L, _F, _P, _P],
     "sdl_profile_enable": [_P, _I],
     "sdl_profile_collect": [_P, _P, _P, _I],
 }
@@ -333,3 +336,40 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def extract_patches(image: torch.Tensor, p: int, stream=None):
+    """Every stride-1 p x p patch of a (H, W) FP32 CUDA image, mean removed.
+    Returns (patches as an (N, p, p) signals tensor, means (N,))."""
+    if image.dim() != 2:
+        raise ValueError("image must be (H, W)")
+    H, W = image.shape
+    _need(image, torch.float32, (H, W), (W, 1), "image")
+    N = (H - p + 1) * (W - p + 1)
+    buf = torch.empty((N, p, p), dtype=torch.float32, device=image.device)   # (k, b, a)
+    means = torch.empty((N,), dtype=torch.float32, device=image.device)
+    _check(lib().sdl_extract_patches(_ptr(image), H, W, p, _ptr(buf), _ptr(means),
+                                     _stream(stream)), "sdl_extract_patches")
+    return buf.transpose(1, 2), means
+
+
+def psnr(x: torch.Tensor, ref: torch.Tensor, peak: float = 255.0, stream=None) -> torch.Tensor:
+    """Device scalar PSNR in dB (``sdl_psnr``)."""
+    if x.shape != ref.shape or not x.is_contiguous() or not ref.is_contiguous():
+        raise ValueError("x and ref must be contiguous and of one shape")
+    out = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib().sdl_psnr(_ptr(x), _ptr(ref), x.numel(), float(peak), _ptr(out), _stream(stream)),
+           "sdl_psnr")
+    return out
+
+
+def patch_average(ctx: Context, codes: Codes, means, D1, D2, p: int, H: int, W: int,
+                  stream=None) -> torch.Tensor:
+    """Rebuild an (H, W) image from coded patches (``sdl_patch_average``)."""
+    n1, n2 = _check_D(D1, p, "D1"), _check_D(D2, p, "D2")
+    s = codes.support.shape[1]
+    out = torch.empty((H, W), dtype=torch.float32, device=means.device)
+    _check(ctx._lib.sdl_patch_average(ctx._h, _ptr(codes.support), _ptr(codes.coef), _ptr(means),
+                                      s, _ptr(D1), n1, _ptr(D2), n2, p, H, W, _ptr(out),
+                                      _stream(stream)), "sdl_patch_average")
+    return out

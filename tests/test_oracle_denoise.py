@@ -1,0 +1,57 @@
+"""Pins of the oracle's denoising pipeline (Sec. IV) against brute force and
+closed forms."""
+import numpy as np
+
+import oracle
+from oracle import denoise as dn
+from paper_2007_03800_gb300 import synth
+
+
+def test_patches_are_windows_minus_mean():
+    img = np.arange(7 * 9, dtype=float).reshape(7, 9) ** 1.5
+    Y, means = dn.extract_patches(img, 3)
+    assert Y.shape == (5 * 7, 3, 3)
+    k = 2 * 7 + 4                                   # corner (2, 4)
+    win = img[2:5, 4:7]
+    assert np.allclose(Y[k], win - win.mean()) and np.isclose(means[k], win.mean())
+    assert np.allclose(Y.mean(axis=(1, 2)), 0.0, atol=1e-12)
+
+
+def test_average_of_exact_patches_is_the_image():
+    img = synth.synthetic_image(3, size=40)
+    Y, means = dn.extract_patches(img, 6)
+    back = dn.patch_average(Y + means[:, None, None], 40, 40)
+    assert np.allclose(back, img, atol=1e-12)
+
+
+def test_average_weights_by_brute_force():
+    """Replace patch k by the constant k: each pixel is the mean index of the
+    patches that cover it, computed here pixel by pixel."""
+    H, W, p = 9, 11, 4
+    N = (H - p + 1) * (W - p + 1)
+    pat = np.arange(N, dtype=float)[:, None, None] * np.ones((1, p, p))
+    out = dn.patch_average(pat, H, W)
+    for y in range(H):
+        for x in range(W):
+            ks = [r * (W - p + 1) + c for r in range(H - p + 1) for c in range(W - p + 1)
+                  if r <= y < r + p and c <= x < c + p]
+            assert np.isclose(out[y, x], np.mean(ks))
+
+
+def test_psnr_closed_form():
+    ref = np.full((8, 8), 100.0)
+    assert np.isclose(dn.psnr(ref + 1.0, ref), 20 * np.log10(255.0))
+    assert np.isclose(dn.psnr(ref + 2.0, ref, peak=1.0), 10 * np.log10(1 / 4.0))
+
+
+def test_denoise_with_orthonormal_dictionary_is_thresholding():
+    """Orthonormal D1 = D2 = I: error-driven OMP keeps the largest pixels of
+    each mean-removed patch until the residual drops below eps (Remark 1's
+    T_s with a data-driven s); with eps = 0 and s = p^2 the image comes back."""
+    img = synth.synthetic_image(5, size=24)
+    I = np.eye(4)
+    back, code = dn.denoise(img, I, I, 16, eps=1e-9)
+    assert np.allclose(back, img, atol=1e-9)
+    Y, _ = dn.extract_patches(img, 4)
+    r = oracle.residual(Y, I, I, code.support, code.coef)
+    assert np.all(np.sqrt(np.sum(r * r, axis=(1, 2))) <= 1e-9 + 1e-12)
