@@ -249,6 +249,22 @@ int sdl_psnr(const float* x, const float* ref, int64_t count, float peak, float*
              void* stream);
 
 /*
+ * sdl_gemm_bf16 - the library's tensor-core GEMM (used by the support-
+ * proposal network and the BF16 correlation path):
+ *   out = act(alpha * A B^T + bias),   A: M x K, B: N x K, both BF16 row-major
+ *   with K contiguous (leading dimensions lda, ldb in elements, multiples of
+ *   8, pointers 16-byte aligned), FP32 accumulation on tcgen05 tensor cores.
+ *   act: 0 none, 1 GELU (0.5 x (1 + erf(x / sqrt 2))); bias: NULL or FP32 [N].
+ * Outputs (each optional, NULL to skip): C FP32 (C += out when accumulate),
+ * Cb BF16 copy, Ct BF16 transposed copy (Ct[n*ldct + m]), pre FP32 values
+ * before the activation.  A device-side timeout is reported by sdl_status.
+ */
+int sdl_gemm_bf16(sdl_ctx* ctx, const void* A, int lda, const void* B, int ldb, int M, int N,
+                  int K, float alpha, const float* bias, int act, float* C, int ldc,
+                  int accumulate, void* Cb, int ldcb, void* Ct, int ldct, float* pre,
+                  int ldpre, void* stream);
+
+/*
  * sdl_sparse_code_static - the sparse coder of sdl_sparse_code with no
  * context and no device allocation.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory once running

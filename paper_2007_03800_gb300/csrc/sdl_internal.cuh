@@ -126,6 +126,12 @@ int launch_multi_update_kernels(int which, const void* d_desc, int G, int blocks
                                 int* err, cudaStream_t st);
 size_t solve_smem_bytes(int p, int n, int* keep_p);
 
+// tc_gemm.cu: C = alpha A B^T (+bias, GELU) on tcgen05 tensor cores, BF16 in,
+// FP32 accumulate; optional FP32 / BF16 / transposed-BF16 / pre-activation outputs.
+int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float alpha,
+            const float* bias, int act, float* C, int ldc, int accumulate, void* Cb, int ldcb,
+            void* Ct, int ldct, float* pre, int ldpre, int* err, cudaStream_t st);
+
 // Record the first device-side error (first writer wins).
 __device__ __forceinline__ void record_error(int* err, int code) {
     if (err) atomicCAS(err, 0, code);

@@ -1,0 +1,314 @@
+// BF16 tensor-core GEMM for sm_103a: C = alpha * A B^T (+ bias, activation),
+// A (M x K) and B (N x K) row-major with K contiguous, FP32 accumulation.
+//
+// Blackwell path: operand tiles arrive by TMA (cp.async.bulk.tensor, 128-byte
+// swizzle) into a 4-stage shared-memory ring guarded by mbarriers; one
+// thread issues tcgen05.mma (128 x 128 x 16 per instruction) into a 128 x 128
+// FP32 accumulator in tensor memory; tcgen05.commit releases ring stages back
+// to the producer; the four warps then read the accumulator with tcgen05.ld
+// (warp w owns TMEM lanes 32w..32w+31 = output rows) and apply the epilogue.
+// Every wait is bounded: on a timeout the CTA records SDL_ERR_TIMEOUT, lets
+// its in-flight copies land and frees its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "ctx.cuh"
+
+using namespace sdl;
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, UMMA_K = 16;
+constexpr int TILE_A = BM * BK * 2;   // bytes
+constexpr int TILE_B = BN * BK * 2;
+constexpr long long kSpin = 1ll << 26;
+
+struct Epi {
+    float alpha;
+    const float* bias;   // [N] or null
+    int act;             // 0 none, 1 GELU (erf form)
+    float* C;            // FP32 output or null
+    int ldc;
+    int accumulate;      // C += result
+    __nv_bfloat16* Cb;   // BF16 copy or null
+    int ldcb;
+    __nv_bfloat16* Ct;   // BF16 transposed copy (Ct[n * ldct + m]) or null
+    int ldct;
+    float* pre;          // FP32 pre-activation (alpha*acc + bias) or null
+    int ldpre;
+};
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    const uint32_t a = saddr(b);
+    for (long long i = 0; i < kSpin; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// K-major operand tile, 128-byte swizzle: rows of 128 B, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    const uint64_t a = (saddr(p) & 0x3FFFFu) >> 4;
+    return a | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
+}
+// kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t instr_desc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   int M, int N, int K, Epi epi, int* err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~uintptr_t(1023));
+    uint8_t* sA = base;
+    uint8_t* sB = base + STAGES * TILE_A;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * TILE_B);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accb = empty + STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk = (K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tslot)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        int issued = 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            mbar_arrive_tx(&full[s], TILE_A + TILE_B);
+            tma_load_2d(sA + s * TILE_A, &tmA, kb * BK, m0, &full[s]);
+            tma_load_2d(sB + s * TILE_B, &tmB, kb * BK, n0, &full[s]);
+            ++issued;
+        }
+        if (s_fail) {
+            // let the copies already issued land before shared memory is released
+            for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; ++kb)
+                mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        const uint32_t idesc = instr_desc();
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                const uint64_t ad = smem_desc(sA + s * TILE_A + kk * UMMA_K * 2);
+                const uint64_t bd = smem_desc(sB + s * TILE_B + kk * UMMA_K * 2);
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    saddr(&empty[s]))
+                : "memory");
+        }
+        if (!s_fail)
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    saddr(accb))
+                : "memory");
+    }
+    __syncwarp();
+    __syncthreads();   // s_fail is final here (the MMAs themselves may still run)
+
+    // ---- epilogue: thread = output row, 32 accumulator columns per load
+    const bool got = !s_fail && mbar_wait(accb, 0);
+    tc_fence_after();
+    const int r = warp * 32 + lane;
+    const int m = m0 + r;
+    if (__all_sync(0xffffffffu, got)) {
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+                "%26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+                  "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                  "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                  "=r"(v[30]), "=r"(v[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m < M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n >= N) break;
+                    float x = epi.alpha * __uint_as_float(v[j]);
+                    if (epi.bias) x += epi.bias[n];
+                    if (epi.pre) epi.pre[(size_t)m * epi.ldpre + n] = x;
+                    if (epi.act == 1) x = 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
+                    if (epi.C) {
+                        float* c = epi.C + (size_t)m * epi.ldc + n;
+                        *c = epi.accumulate ? *c + x : x;
+                    }
+                    if (epi.Cb) epi.Cb[(size_t)m * epi.ldcb + n] = __float2bfloat16_rn(x);
+                    if (epi.Ct) epi.Ct[(size_t)n * epi.ldct + m] = __float2bfloat16_rn(x);
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        record_error(err, SDL_ERR_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// rows x cols bf16 matrix, row stride ld (elements), box 128 rows x 64 cols
+int make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
+    auto fn = encode_fn();
+    if (!fn) return SDL_ERR_CUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, 128u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SDL_OK : SDL_ERR_ARG;
+}
+
+constexpr size_t kSmemBytes = 1024 + STAGES * (TILE_A + TILE_B) + 256;
+
+}  // namespace
+
+namespace sdl {
+int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float alpha,
+            const float* bias, int act, float* C, int ldc, int accumulate, void* Cb, int ldcb,
+            void* Ct, int ldct, float* pre, int ldpre, int* err, cudaStream_t st) {
+    if (!A || !B || M < 1 || N < 1 || K < 1) return SDL_ERR_ARG;
+    if ((lda % 8) || (ldb % 8) || lda < K || ldb < K) return SDL_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u))
+        return SDL_ERR_ARG;
+    CUtensorMap ma, mb;
+    int rc;
+    if ((rc = make_map(&ma, A, M, K, lda)) != SDL_OK) return rc;
+    if ((rc = make_map(&mb, B, N, K, ldb)) != SDL_OK) return rc;
+    Epi e;
+    e.alpha = alpha;
+    e.bias = bias;
+    e.act = act;
+    e.C = C;
+    e.ldc = ldc;
+    e.accumulate = accumulate;
+    e.Cb = static_cast<__nv_bfloat16*>(Cb);
+    e.ldcb = ldcb;
+    e.Ct = static_cast<__nv_bfloat16*>(Ct);
+    e.ldct = ldct;
+    e.pre = pre;
+    e.ldpre = ldpre;
+    if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes) != cudaSuccess)
+        return SDL_ERR_CUDA;
+    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    tc_gemm_kernel<<<grid, 128, kSmemBytes, st>>>(ma, mb, M, N, K, e, err);
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+}  // namespace sdl
+
+extern "C" int sdl_gemm_bf16(sdl_ctx* c, const void* A, int lda, const void* B, int ldb, int M,
+                             int N, int K, float alpha, const float* bias, int act, float* C,
+                             int ldc, int accumulate, void* Cb, int ldcb, void* Ct, int ldct,
+                             float* pre, int ldpre, void* stream) {
+    if (!c) return SDL_ERR_ARG;
+    DeviceGuard guard(c->device);
+    return tc_gemm(A, lda, B, ldb, M, N, K, alpha, bias, act, C, ldc, accumulate, Cb, ldcb, Ct,
+                   ldct, pre, ldpre, c->err, (cudaStream_t)stream);
+}

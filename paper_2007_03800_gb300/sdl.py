@@ -52,6 +52,8 @@ SIGNATURES = {
     "sdl_extract_patches": [_P, _I, _I, _I, _P, _P, _P],
     "sdl_patch_average": [_P, _P, _P, _P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _P],
     "sdl_psnr": [_P, _P, _L, _F, _P, _P],
+    "sdl_gemm_bf16": [_P, _P, _I, _P, _I, _I, _I, _I, _F, _P, _I, _P, _I, _I, _P, _I, _P, _I,
+                      _P, _I, _P],
     "sdl_profile_enable": [_P, _I],
     "sdl_profile_collect": [_P, _P, _P, _I],
 }
@@ -373,3 +375,27 @@ def patch_average(ctx: Context, codes: Codes, means, D1, D2, p: int, H: int, W: 
                                       s, _ptr(D1), n1, _ptr(D2), n2, p, H, W, _ptr(out),
                                       _stream(stream)), "sdl_patch_average")
     return out
+
+
+def gemm_bf16(ctx: Context, A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0, bias=None,
+              act: int = 0, C=None, accumulate: bool = False, Cb=None, Ct=None, pre=None,
+              stream=None):
+    """``sdl_gemm_bf16``: act(alpha A B^T + bias) with A (M, K), B (N, K) BF16
+    (row stride = shape[1] padded to a multiple of 8).  Returns C (allocated
+    as FP32 (M, N) when not given and no other output is requested)."""
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A and B must share K")
+    for t, name in ((A, "A"), (B, "B")):
+        if t.dtype != torch.bfloat16 or t.stride(1) != 1:
+            raise ValueError(f"{name} must be BF16 with contiguous rows")
+    if C is None and Cb is None and Ct is None and pre is None:
+        C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    rc = ctx._lib.sdl_gemm_bf16(
+        ctx._h, _ptr(A), A.stride(0), _ptr(B), B.stride(0), M, N, K, float(alpha), _ptr(bias),
+        int(act), _ptr(C), C.stride(0) if C is not None else 0, int(bool(accumulate)), _ptr(Cb),
+        Cb.stride(0) if Cb is not None else 0, _ptr(Ct), Ct.stride(0) if Ct is not None else 0,
+        _ptr(pre), pre.stride(0) if pre is not None else 0, _stream(stream))
+    _check(rc, "sdl_gemm_bf16")
+    return C
