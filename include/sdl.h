@@ -265,6 +265,66 @@ int sdl_gemm_bf16(sdl_ctx* ctx, const void* A, int lda, const void* B, int ldb, 
                   int ldpre, void* stream);
 
 /*
+ * Learned support proposal (an extension beyond the paper).  A two-layer
+ * network scores every atom pair of a signal,
+ *   x = vec(Y)/||Y||_F,  h = GELU(W1 x + b1),  z = W2 h + b2  (z: n1*n2 scores),
+ * with BF16 weights/activations and FP32 accumulation on tcgen05 tensor cores.
+ * It is trained on (signal, 2D-OMP support) pairs with the mean over the
+ * batch of the summed binary cross-entropy with logits and Adam (FP32 master
+ * weights; beta1 0.9, beta2 0.999, eps 1e-8).
+ */
+typedef struct sdl_mlp sdl_mlp;
+
+/* Network for p1 x p2 signals and n1 x n2 pairs (n1*n2 <= 1024, a multiple
+ * of 8), `hidden` units (multiple of 8), batches of up to max_batch (multiple
+ * of 8) signals.  Weights start at zero: set them with sdl_mlp_set_weights. */
+int sdl_mlp_create(sdl_ctx* ctx, int p1, int p2, int n1, int n2, int hidden, int max_batch,
+                   sdl_mlp** out);
+int sdl_mlp_destroy(sdl_mlp* mlp);
+
+/* HOST FP32 arrays: W1 [hidden x p1p2] (row-major, input index = column-order
+ * vec of Y), b1 [hidden], W2 [n1n2 x hidden], b2 [n1n2].  Synchronous.
+ * set resets the Adam moments and step count. */
+int sdl_mlp_set_weights(sdl_mlp* mlp, const float* W1, const float* b1, const float* W2,
+                        const float* b2);
+int sdl_mlp_get_weights(sdl_mlp* mlp, float* W1, float* b1, float* W2, float* b2);
+
+/* One Adam step on a batch: Y (device, B signals laid out as for
+ * sdl_iterate), support (device, B x s pair indices, -1 = none) = the labels,
+ * B a multiple of 8 <= max_batch.  loss_out: NULL or device float[1]. */
+int sdl_mlp_train_step(sdl_mlp* mlp, const float* Y, const int32_t* support, int s, int B,
+                       float lr, float* loss_out, void* stream);
+
+/* Loss and gradients of a batch without updating (gradient check): HOST
+ * FP32 outputs shaped like the weights (each may be NULL).  Synchronous. */
+int sdl_mlp_gradients(sdl_mlp* mlp, const float* Y, const int32_t* support, int s, int B,
+                      float* loss_out, float* gW1, float* gb1, float* gW2, float* gb2,
+                      void* stream);
+
+/* Scores of N signals: device FP32 N x n1n2. */
+int sdl_mlp_forward(sdl_mlp* mlp, const float* Y, int64_t N, float* scores, void* stream);
+
+/*
+ * sdl_sparse_code_learned - 2D-OMP on learned shortlists, with the full coder
+ * as the fallback:
+ *   1. the network scores all pairs; the k best (1 <= k <= 32) form the
+ *      shortlist, the next k the check set;
+ *   2. 2D-OMP (same greedy rule, re-fit and stopping as sdl_sparse_code,
+ *      fixed s_max) searches only the shortlist;
+ *   3. a signal is flagged when some check-set pair correlates with the final
+ *      residual more strongly than the weakest pick did when chosen, or its
+ *      data is not finite; flagged signals are coded again by the full coder.
+ * Outputs as sdl_sparse_code plus fallback[N] (1 = re-coded) and device
+ * int n_fallback[1].  Compiled for (p1,p2,n1,n2,s_max) = (12,12,24,24,6) and
+ * (8,8,16,16,4); the network must match the shape.
+ */
+int sdl_sparse_code_learned(sdl_ctx* ctx, sdl_mlp* mlp, const float* Y, int p1, int p2,
+                            int64_t N, const float* D1, int n1, const float* D2, int n2,
+                            int s_max, int k, int32_t* support, float* coef, int32_t* nnz,
+                            float* res_energy, int32_t* fallback, int32_t* n_fallback,
+                            void* stream);
+
+/*
  * sdl_sparse_code_static - the sparse coder of sdl_sparse_code with no
  * context and no device allocation.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory once running
@@ -311,8 +371,12 @@ int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
  *   9 memset        zeroing of global accumulation slots
  *  10 batch_graph   one replay of a batch's captured iteration graph
  *                   (its kernels are counted under their own kinds too)
+ *  11 mlp           support-network forward / backward (GEMMs + element-wise)
+ *  12 adam          support-network parameter update
+ *  13 topk          shortlist selection from the network's scores
+ *  14 shortlist     2D-OMP restricted to the shortlists, with the fallback test
  */
-#define SDL_NUM_KERNEL_KINDS 11
+#define SDL_NUM_KERNEL_KINDS 15
 
 /* Enable (1) or disable (0) event timing of every kernel this context
  * enqueues.  Launch counts are kept either way.  Host-side, synchronous. */

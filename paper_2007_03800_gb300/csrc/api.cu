@@ -159,6 +159,7 @@ int sdl_destroy(sdl_ctx* c) {
     cudaFree(c->red_d);
     cudaFree(c->norms);
     cudaFree(c->rec);
+    cudaFree(c->learn);
     for (auto& r : c->recs) {
         cudaEventDestroy(r.beg);
         cudaEventDestroy(r.end);
@@ -343,7 +344,8 @@ int sdl_profile_collect(sdl_ctx* c, double* total_ms, int64_t* launches, int max
 const char* sdl_kernel_name(int kind) {
     static const char* names[SDL_NUM_KERNEL_KINDS] = {
         "gram", "code", "code_D1", "code_D2", "accum_D1", "accum_D2",
-        "reduce", "solve", "rescale", "memset", "batch_graph"};
+        "reduce", "solve", "rescale", "memset", "batch_graph", "mlp", "adam", "topk",
+        "shortlist"};
     return (kind >= 0 && kind < SDL_NUM_KERNEL_KINDS) ? names[kind] : "?";
 }
 

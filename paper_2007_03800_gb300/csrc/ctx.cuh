@@ -19,6 +19,8 @@ struct sdl_ctx {
     float* norms = nullptr;      // column norms of the last solve
     float* rec = nullptr;        // reconstructed patches (patch averaging)
     size_t cap_rec = 0;
+    char* learn = nullptr;       // learned-coder workspace
+    size_t cap_learn = 0;
     size_t cap_g1 = 0, cap_g2 = 0, cap_part = 0, cap_slots = 0, cap_red = 0, cap_redd = 0,
            cap_norms = 0;
     // tracing: launch counters and (optionally) one event pair per launch
@@ -36,7 +38,7 @@ namespace sdl {
 
 enum Kind {
     kGram = 0, kCode, kCodeD1, kCodeD2, kAccD1, kAccD2, kReduce, kSolve, kRescale, kMemset,
-    kBatchGraph
+    kBatchGraph, kMlp, kAdam, kTopk, kShortlist
 };
 constexpr size_t kMaxRecs = 1 << 16;
 

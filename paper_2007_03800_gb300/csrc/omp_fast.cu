@@ -239,14 +239,17 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
     __syncthreads();
 
     const long long stride = (long long)n_ctas * wpc;
-    long long k = (long long)cta * wpc + w;
+    // positions j index either the signals themselves or a list of signals
+    const long long count = a.idx ? (long long)*a.idx_count : a.N;
+    long long j = (long long)cta * wpc + w;
+    long long k = (a.idx && j < count) ? (long long)a.idx[j] : j;
     if (lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
     }
     __syncwarp();
-    if (lane == 0 && k < a.N) {
+    if (lane == 0 && j < count) {
         mbar_arrive_tx(&bar[0], kBytes);
         tma_load_1d(Ybuf, a.Y + (size_t)k * PP, kBytes, &bar[0]);
     }
@@ -257,7 +260,8 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
     bool alive = true;
     int pending = 0;
 
-    for (int it = 0; k < a.N && alive; ++it, k += stride) {
+    for (int it = 0; j < count && alive; ++it, j += stride) {
+        k = a.idx ? (long long)a.idx[j] : j;
         const int buf = it & 1;
         float* Ys = Ybuf + buf * al4(PP);
         const bool got = mbar_wait(&bar[buf], buf ? phase1 : phase0);
@@ -269,8 +273,9 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
         }
         if (buf) phase1 ^= 1u; else phase0 ^= 1u;
         // prefetch this warp's next signal into the other buffer
-        const long long kn = k + stride;
-        if (lane == 0 && kn < a.N) {
+        const long long jn = j + stride;
+        if (lane == 0 && jn < count) {
+            const long long kn = a.idx ? (long long)a.idx[jn] : jn;
             fence_proxy_async();
             mbar_arrive_tx(&bar[buf ^ 1], kBytes);
             tma_load_1d(Ybuf + (buf ^ 1) * al4(PP), a.Y + (size_t)kn * PP, kBytes, &bar[buf ^ 1]);

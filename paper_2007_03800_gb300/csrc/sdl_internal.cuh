@@ -49,6 +49,8 @@ struct PassArgs {
     int acc_in_smem;      // 1: CTA-private shared accumulators, slot = CTA
     int n_slots;          // global-accumulator mode: slots (CTA % n_slots)
     int* err;
+    const int32_t* idx;   // optional: code only the signals idx[0 .. *idx_count)
+    const int* idx_count; //   (specialised kernels only; device count)
 };
 
 // Host launchers (omp_pass.cu).  They return the number of partial-sum
@@ -130,7 +132,8 @@ size_t solve_smem_bytes(int p, int n, int* keep_p);
 // FP32 accumulate; optional FP32 / BF16 / transposed-BF16 / pre-activation outputs.
 int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float alpha,
             const float* bias, int act, float* C, int ldc, int accumulate, void* Cb, int ldcb,
-            void* Ct, int ldct, float* pre, int ldpre, int* err, cudaStream_t st);
+            void* Ct, int ldct, float* pre, int ldpre, int* err, cudaStream_t st,
+            const float* gin = nullptr, int ldgin = 0);
 
 // Record the first device-side error (first writer wins).
 __device__ __forceinline__ void record_error(int* err, int code) {

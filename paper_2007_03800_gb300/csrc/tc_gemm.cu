@@ -40,6 +40,8 @@ struct Epi {
     int ldct;
     float* pre;          // FP32 pre-activation (alpha*acc + bias) or null
     int ldpre;
+    const float* gin;    // act 2: multiply by GELU'(gin[m, n])
+    int ldgin;
 };
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -213,7 +215,15 @@ __global__ void __launch_bounds__(128, 1)
                     float x = epi.alpha * __uint_as_float(v[j]);
                     if (epi.bias) x += epi.bias[n];
                     if (epi.pre) epi.pre[(size_t)m * epi.ldpre + n] = x;
-                    if (epi.act == 1) x = 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
+                    if (epi.act == 1) {
+                        x = 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
+                    } else if (epi.act == 2) {
+                        // chain rule through GELU: d/du [u Phi(u)] = Phi(u) + u phi(u)
+                        const float u = epi.gin[(size_t)m * epi.ldgin + n];
+                        const float Phi = 0.5f * (1.f + erff(u * 0.70710678118654752f));
+                        const float phi = 0.3989422804014327f * expf(-0.5f * u * u);
+                        x *= Phi + u * phi;
+                    }
                     if (epi.C) {
                         float* c = epi.C + (size_t)m * epi.ldc + n;
                         *c = epi.accumulate ? *c + x : x;
@@ -272,8 +282,10 @@ constexpr size_t kSmemBytes = 1024 + STAGES * (TILE_A + TILE_B) + 256;
 namespace sdl {
 int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float alpha,
             const float* bias, int act, float* C, int ldc, int accumulate, void* Cb, int ldcb,
-            void* Ct, int ldct, float* pre, int ldpre, int* err, cudaStream_t st) {
+            void* Ct, int ldct, float* pre, int ldpre, int* err, cudaStream_t st,
+            const float* gin, int ldgin) {
     if (!A || !B || M < 1 || N < 1 || K < 1) return SDL_ERR_ARG;
+    if (act == 2 && !gin) return SDL_ERR_ARG;
     if ((lda % 8) || (ldb % 8) || lda < K || ldb < K) return SDL_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u))
         return SDL_ERR_ARG;
@@ -294,6 +306,8 @@ int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
     e.ldct = ldct;
     e.pre = pre;
     e.ldpre = ldpre;
+    e.gin = gin;
+    e.ldgin = ldgin;
     if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSmemBytes) != cudaSuccess)
         return SDL_ERR_CUDA;
@@ -309,6 +323,7 @@ extern "C" int sdl_gemm_bf16(sdl_ctx* c, const void* A, int lda, const void* B, 
                              float* pre, int ldpre, void* stream) {
     if (!c) return SDL_ERR_ARG;
     DeviceGuard guard(c->device);
+    if (act == 2) return SDL_ERR_ARG;   // the GELU-derivative mode is internal
     return tc_gemm(A, lda, B, ldb, M, N, K, alpha, bias, act, C, ldc, accumulate, Cb, ldcb, Ct,
-                   ldct, pre, ldpre, c->err, (cudaStream_t)stream);
+                   ldct, pre, ldpre, c->err, (cudaStream_t)stream, nullptr, 0);
 }

@@ -54,6 +54,15 @@ SIGNATURES = {
     "sdl_psnr": [_P, _P, _L, _F, _P, _P],
     "sdl_gemm_bf16": [_P, _P, _I, _P, _I, _I, _I, _I, _F, _P, _I, _P, _I, _I, _P, _I, _P, _I,
                       _P, _I, _P],
+    "sdl_mlp_create": [_P, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_P)],
+    "sdl_mlp_destroy": [_P],
+    "sdl_mlp_set_weights": [_P, _P, _P, _P, _P],
+    "sdl_mlp_get_weights": [_P, _P, _P, _P, _P],
+    "sdl_mlp_train_step": [_P, _P, _P, _I, _I, _F, _P, _P],
+    "sdl_mlp_gradients": [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P, _P],
+    "sdl_mlp_forward": [_P, _P, _L, _P, _P],
+    "sdl_sparse_code_learned": [_P, _P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P,
+                                _P, _P, _P],
     "sdl_profile_enable": [_P, _I],
     "sdl_profile_collect": [_P, _P, _P, _I],
 }
@@ -399,3 +408,95 @@ def gemm_bf16(ctx: Context, A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0
         _ptr(pre), pre.stride(0) if pre is not None else 0, _stream(stream))
     _check(rc, "sdl_gemm_bf16")
     return C
+
+
+def _host_f32(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+class MLP:
+    """The support-proposal network (``sdl_mlp_*``): p1*p2 -> hidden (GELU) ->
+    n1*n2 scores, trained on the GPU by the library's own kernels."""
+
+    def __init__(self, ctx: Context, p1, p2, n1, n2, hidden=512, max_batch=4096):
+        self.ctx, self._lib = ctx, ctx._lib
+        self.shape = (p1, p2, n1, n2, hidden)
+        h = ctypes.c_void_p()
+        _check(self._lib.sdl_mlp_create(ctx._h, p1, p2, n1, n2, hidden, max_batch,
+                                        ctypes.byref(h)), "sdl_mlp_create")
+        self._h = h
+        self.max_batch = max_batch
+
+    def init(self, seed=0):
+        """He-style random initial weights from a seeded generator."""
+        import numpy as np
+        p1, p2, n1, n2, H = self.shape
+        rng = np.random.default_rng(seed)
+        P, Q = p1 * p2, n1 * n2
+        self.set_weights(rng.standard_normal((H, P)) * np.sqrt(2.0 / P), np.zeros(H),
+                         rng.standard_normal((Q, H)) * np.sqrt(1.0 / H), np.full(Q, -3.0))
+
+    def set_weights(self, W1, b1, W2, b2):
+        arrs = [_host_f32(a) for a in (W1, b1, W2, b2)]
+        _check(self._lib.sdl_mlp_set_weights(self._h, *[p for _, p in arrs]), "sdl_mlp_set_weights")
+
+    def get_weights(self):
+        import numpy as np
+        p1, p2, n1, n2, H = self.shape
+        out = [np.empty((H, p1 * p2), np.float32), np.empty(H, np.float32),
+               np.empty((n1 * n2, H), np.float32), np.empty(n1 * n2, np.float32)]
+        _check(self._lib.sdl_mlp_get_weights(self._h, *[o.ctypes.data_as(ctypes.c_void_p) for o in out]),
+               "sdl_mlp_get_weights")
+        return out
+
+    def train_step(self, Y, support, lr, loss_out=None, stream=None):
+        N, p1, p2 = _check_Y(Y)
+        _check(self._lib.sdl_mlp_train_step(self._h, _ptr(Y), _ptr(support), support.shape[1], N,
+                                            float(lr), _ptr(loss_out), _stream(stream)),
+               "sdl_mlp_train_step")
+
+    def gradients(self, Y, support, stream=None):
+        import numpy as np
+        N, p1, p2 = _check_Y(Y)
+        _, _, n1, n2, H = self.shape
+        g = [np.empty((H, p1 * p2), np.float32), np.empty(H, np.float32),
+             np.empty((n1 * n2, H), np.float32), np.empty(n1 * n2, np.float32)]
+        loss = torch.zeros(1, dtype=torch.float32, device=Y.device)
+        _check(self._lib.sdl_mlp_gradients(self._h, _ptr(Y), _ptr(support), support.shape[1], N,
+                                           _ptr(loss), *[a.ctypes.data_as(ctypes.c_void_p) for a in g],
+                                           _stream(stream)), "sdl_mlp_gradients")
+        return loss.item(), dict(W1=g[0], b1=g[1], W2=g[2], b2=g[3])
+
+    def forward(self, Y, stream=None):
+        N, p1, p2 = _check_Y(Y)
+        out = torch.empty((N, self.shape[2] * self.shape[3]), dtype=torch.float32, device=Y.device)
+        _check(self._lib.sdl_mlp_forward(self._h, _ptr(Y), N, _ptr(out), _stream(stream)),
+               "sdl_mlp_forward")
+        return out
+
+    def sparse_code(self, Y, D1, D2, s, k=32, out: Codes | None = None, stream=None):
+        """``sdl_sparse_code_learned``: returns (codes, fallback flags, n_fallback)."""
+        N, p1, p2 = _check_Y(Y)
+        n1, n2 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2")
+        if out is None:
+            out = Codes.empty(N, s, Y.device, with_energy=True)
+        flags = torch.empty(N, dtype=torch.int32, device=Y.device)
+        nfb = torch.zeros(1, dtype=torch.int32, device=Y.device)
+        _check(self._lib.sdl_sparse_code_learned(
+            self.ctx._h, self._h, _ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2, s, k,
+            _ptr(out.support), _ptr(out.coef), _ptr(out.nnz), _ptr(out.res_energy), _ptr(flags),
+            _ptr(nfb), _stream(stream)), "sdl_sparse_code_learned")
+        return out, flags, nfb
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sdl_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

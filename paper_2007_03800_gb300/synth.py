@@ -63,14 +63,19 @@ def kron_model(N: int, p1: int, p2: int, n1: int, n2: int, s: int,
     D2t = random_dictionary(p2, n2, np.random.default_rng(dict_seeds[1]))
     rng = np.random.default_rng(seed + 1000)
     nq = n1 * n2
-    # s distinct pairs per signal: argsort of uniform keys picks a random subset.
-    keys = rng.random((N, nq))
-    support = np.argsort(keys, axis=1)[:, :s].astype(np.int64)
+    # s distinct pairs per signal: the s smallest of nq uniform keys pick a
+    # uniformly random subset (in key order)
+    keys = rng.random((N, nq), dtype=np.float32)
+    part = np.argpartition(keys, s - 1, axis=1)[:, :s]
+    order = np.argsort(np.take_along_axis(keys, part, axis=1), axis=1)
+    support = np.take_along_axis(part, order, axis=1).astype(np.int64)
     coef = rng.standard_normal((N, s))
-    X = np.zeros((N, n1 * n2))
-    np.put_along_axis(X, support, coef, axis=1)
-    X = X.reshape(N, n2, n1).transpose(0, 2, 1)          # q = i + n1*j
-    clean = np.einsum("ai,kij,bj->kab", D1t, X, D2t, optimize=True)
+    ii, jj = support % n1, support // n1                  # q = i + n1*j
+    clean = np.empty((N, p1, p2))
+    for a in range(0, N, 65536):                          # memory only
+        b = slice(a, a + 65536)
+        clean[b] = np.einsum("kl,akl,bkl->kab", coef[b], D1t[:, ii[b]], D2t[:, jj[b]],
+                             optimize=True)
     Y = clean
     if snr_db is not None:
         energy = np.einsum("kab,kab->k", clean, clean)
