@@ -308,12 +308,13 @@ int sdl_mlp_forward(sdl_mlp* mlp, const float* Y, int64_t N, float* scores, void
  * sdl_sparse_code_learned - 2D-OMP on learned shortlists, with the full coder
  * as the fallback:
  *   1. the network scores all pairs; the k best (1 <= k <= 32) form the
- *      shortlist, the next k the check set;
+ *      shortlist, the next 2k the check set;
  *   2. 2D-OMP (same greedy rule, re-fit and stopping as sdl_sparse_code,
  *      fixed s_max) searches only the shortlist;
  *   3. a signal is flagged when some check-set pair correlates with the final
- *      residual more strongly than the weakest pick did when chosen, or its
- *      data is not finite; flagged signals are coded again by the full coder.
+ *      residual more strongly than 0.7 x the weakest greedy score of its picks,
+ *      or its data is not finite; flagged signals are coded again by the full
+ *      coder.
  * Outputs as sdl_sparse_code plus fallback[N] (1 = re-coded) and device
  * int n_fallback[1].  Compiled for (p1,p2,n1,n2,s_max) = (12,12,24,24,6) and
  * (8,8,16,16,4); the network must match the shape.

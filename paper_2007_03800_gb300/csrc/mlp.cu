@@ -218,6 +218,11 @@ __global__ void topk_kernel(const float* __restrict__ Z, int ldz, long long N, i
 }
 
 // ---------------------------------------------------------------- shortlist OMP
+// check set = the 2k pairs ranked after the shortlist (2 per lane at k = 32);
+// a check pair whose residual correlation exceeds this fraction of the
+// weakest greedy score flags the signal
+constexpr int kCheck = 2;
+constexpr float kCheckMargin = 0.7f;
 template <int B, int E, class F>
 __device__ __forceinline__ void sfor(F&& f) {
     if constexpr (B < E) {
@@ -275,19 +280,27 @@ __global__ void __launch_bounds__(256) shortlist_omp_kernel(
             Zs[e] = z;
         }
         __syncwarp();
-        // lane's shortlist candidate and check candidate
+        // lane's shortlist candidate and its kCheck check candidates
         const int q = lane < k1 ? cand[(size_t)k * k2 + lane] : -1;
-        const int qe = lane < k2 - k1 ? cand[(size_t)k * k2 + k1 + lane] : -1;
         const int ci = q >= 0 ? q % N1 : 0, cj = q >= 0 ? q / N1 : 0;
-        const int ei = qe >= 0 ? qe % N1 : 0, ej = qe >= 0 ? qe / N1 : 0;
-        float c0 = 0.f, c0e = 0.f;
+        int qe[kCheck], ei[kCheck], ej[kCheck];
+        float c0e[kCheck];
+#pragma unroll
+        for (int u = 0; u < kCheck; ++u) {
+            const int pos = k1 + u * 32 + lane;
+            qe[u] = pos < k2 ? cand[(size_t)k * k2 + pos] : -1;
+            ei[u] = qe[u] >= 0 ? qe[u] % N1 : 0;
+            ej[u] = qe[u] >= 0 ? qe[u] / N1 : 0;
+            c0e[u] = 0.f;
+        }
+        float c0 = 0.f;
 #pragma unroll
         for (int a = 0; a < P1; ++a) {
             c0 = fmaf(D1c[ci * P1 + a], Zs[a * N2 + cj], c0);
-            c0e = fmaf(D1c[ei * P1 + a], Zs[a * N2 + ej], c0e);
+#pragma unroll
+            for (int u = 0; u < kCheck; ++u) c0e[u] = fmaf(D1c[ei[u] * P1 + a], Zs[a * N2 + ej[u]], c0e[u]);
         }
         if (q < 0) c0 = __int_as_float(0x7fc00000);
-        if (qe < 0) c0e = 0.f;
         int si[S], sj[S];
         float xs[S], yv[S], Lrow[S], Lcol[S];
 #pragma unroll
@@ -357,13 +370,17 @@ __global__ void __launch_bounds__(256) shortlist_omp_kernel(
         for (int m = 0; m < S; ++m)
             if (lane == m) myx = xs[m];
         // fallback test on the check set
-        float sce = c0e;
+        float ve = 0.f;
 #pragma unroll
-        for (int l = 0; l < S; ++l)
-            if (l < cnt) sce = fmaf(-xs[l] * G1s[ei * N1 + si[l]], G2s[sj[l] * N2 + ej], sce);
-        const float ve = qe >= 0 ? fabsf(sce) : 0.f;
-        const float maxe = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(ve == ve ? ve : 0.f)));
-        const bool fb = !isfinite(ss) || (cnt == S && maxe > weakest);
+        for (int u = 0; u < kCheck; ++u) {
+            float sce = c0e[u];
+#pragma unroll
+            for (int l = 0; l < S; ++l)
+                if (l < cnt) sce = fmaf(-xs[l] * G1s[ei[u] * N1 + si[l]], G2s[sj[l] * N2 + ej[u]], sce);
+            if (qe[u] >= 0 && fabsf(sce) == fabsf(sce)) ve = fmaxf(ve, fabsf(sce));
+        }
+        const float maxe = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(ve)));
+        const bool fb = !isfinite(ss) || (cnt == S && maxe > kCheckMargin * weakest);
         if (lane < S) {
             support[(size_t)k * S + lane] = lane < cnt ? myi + N1 * myj : -1;
             coef[(size_t)k * S + lane] = lane < cnt ? myx : 0.f;
@@ -679,7 +696,7 @@ extern "C" int sdl_sparse_code_learned(sdl_ctx* c, sdl_mlp* m, const float* Y, i
     if (!shape_a && !shape_b) return SDL_ERR_UNSUPPORTED;
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const int k2 = 2 * k, Q = m->Q;
+    const int k2 = k + 32 * kCheck < 3 * k ? k + 32 * kCheck : 3 * k, Q = m->Q;
     // workspace: scores of one chunk, candidates, Grams, scan buffers, index list
     const long long chunk = m->Bmax;
     const int nblk = (int)((N + kScanBlock - 1) / kScanBlock);
