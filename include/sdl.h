@@ -265,6 +265,31 @@ int sdl_gemm_bf16(sdl_ctx* ctx, const void* A, int lda, const void* B, int ldb, 
                   int ldpre, void* stream);
 
 /*
+ * Precision modes (an extension beyond the paper; default SDL_PREC_FP32).
+ *  SDL_PREC_BF16_CORR: the correlations C0 = D1^T Y_k D2 of a coding pass come
+ *    from ONE BF16 tensor-core GEMM of the vectorised signals with the
+ *    Kronecker dictionary D2 (x) D1 (Sec. I), FP32 accumulation.  Every entry
+ *    is within 2^-7 (1.03) ||Y_k||_F of its FP32 value; at every greedy step
+ *    each entry that close to the running maximum is re-scored in FP32
+ *    (d1_i^T Y_k d2_j), so the picks are FP32 picks.  The Gram-domain updates,
+ *    the Cholesky factor and the partial sums stay FP32.  Needs p1*p2 a
+ *    multiple of 8; uses N x n1n2 FP32 of workspace.
+ *  SDL_PREC_NO_RESCORE: with BF16_CORR, skip the re-scoring (pure BF16 picks;
+ *    for precision studies).
+ *  SDL_PREC_FP64_SOLVE: the normal-equation solves, the objective decrease and
+ *    the atom renormalisation in FP64 (partial sums stay FP32).
+ */
+#define SDL_PREC_FP32 0
+#define SDL_PREC_BF16_CORR 1
+#define SDL_PREC_NO_RESCORE 2
+#define SDL_PREC_FP64_SOLVE 4
+int sdl_set_precision(sdl_ctx* ctx, int flags);
+
+/* Number of correlation entries re-scored in FP32 since the previous call
+ * (synchronises the device). */
+int sdl_precision_stats(sdl_ctx* ctx, uint64_t* rescored_entries);
+
+/*
  * Learned support proposal (an extension beyond the paper).  A two-layer
  * network scores every atom pair of a signal,
  *   x = vec(Y)/||Y||_F,  h = GELU(W1 x + b1),  z = W2 h + b2  (z: n1*n2 scores),
@@ -376,8 +401,9 @@ int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
  *  12 adam          support-network parameter update
  *  13 topk          shortlist selection from the network's scores
  *  14 shortlist     2D-OMP restricted to the shortlists, with the fallback test
+ *  15 tc_corr       tensor-core correlations (precision extension)
  */
-#define SDL_NUM_KERNEL_KINDS 15
+#define SDL_NUM_KERNEL_KINDS 16
 
 /* Enable (1) or disable (0) event timing of every kernel this context
  * enqueues.  Launch counts are kept either way.  Host-side, synchronous. */

@@ -85,6 +85,35 @@ void grams(sdl_ctx* c, const float* D1, int p1, int n1, const float* D2, int p2,
     launch_gram2(D1, p1, n1, c->G1, D2, p2, n2, c->G2, st);
 }
 
+// Tensor-core correlations for a coding pass (precision extension): fills
+// ctx->C0 and points the pass at it.
+constexpr float kC0ErrRel = 0.0081f;   // 2^-7 (1 + 3%): BF16 operands, FP32 accumulation
+
+int prepare_tc_pass(sdl_ctx* c, PassArgs& a, bool fill_y, cudaStream_t st) {
+    const long long N = a.N;
+    const int Kp = (a.p1 * a.p2 + 7) & ~7, Q = a.n1 * a.n2;
+    int rc;
+    if ((rc = grow(reinterpret_cast<char*&>(c->Yb), c->cap_yb, (size_t)N * Kp * 2)) != SDL_OK) return rc;
+    if ((rc = grow(reinterpret_cast<char*&>(c->KT), c->cap_kt, (size_t)Q * Kp * 2)) != SDL_OK) return rc;
+    if ((rc = grow(c->C0, c->cap_c0, (size_t)N * Q)) != SDL_OK) return rc;
+    if (!c->rescored) {
+        if (cudaMalloc(&c->rescored, sizeof(unsigned long long)) != cudaSuccess) return SDL_ERR_WORKSPACE;
+        cudaMemset(c->rescored, 0, sizeof(unsigned long long));
+    }
+    {
+        Trace tr(c, kTcCorr, st);
+        rc = tc_correlations(a.Y, N, a.p1, a.p2, a.D1, a.n1, a.D2, a.n2,
+                             static_cast<__nv_bfloat16*>(c->Yb), fill_y,
+                             static_cast<__nv_bfloat16*>(c->KT), c->C0, c->err, st);
+    }
+    if (rc) return rc;
+    a.c0ext = c->C0;
+    a.ldc0 = Q;
+    a.c0_err_rel = (c->prec & SDL_PREC_NO_RESCORE) ? 0.f : kC0ErrRel;
+    a.rescored = c->rescored;
+    return SDL_OK;
+}
+
 // reduce -> solve for one dictionary side, using the partial sums in slots.
 int finish_update(sdl_ctx* c, int slots, int side, float* D, int p1, int p2, int64_t N, int n1,
                   int n2, float* objective_out, float* rmse_out, cudaStream_t st,
@@ -98,6 +127,9 @@ int finish_update(sdl_ctx* c, int slots, int side, float* D, int p1, int p2, int
     }
     const double inv_count = N > 0 ? 1.0 / ((double)p1 * p2 * (double)N) : 0.0;
     Trace tr(c, kSolve, st);
+    if (c->prec & SDL_PREC_FP64_SOLVE)
+        return launch_solve64(c->red_f, c->red_d, D, p, n, c->norms, inv_count, objective_out,
+                              rmse_out, c->err, st, G_out);
     return launch_solve(c->red_f, c->red_d, D, p, n, c->norms, inv_count, objective_out, rmse_out,
                         c->err, st, G_out);
 }
@@ -160,6 +192,10 @@ int sdl_destroy(sdl_ctx* c) {
     cudaFree(c->norms);
     cudaFree(c->rec);
     cudaFree(c->learn);
+    cudaFree(c->Yb);
+    cudaFree(c->KT);
+    cudaFree(c->C0);
+    cudaFree(c->rescored);
     for (auto& r : c->recs) {
         cudaEventDestroy(r.beg);
         cudaEventDestroy(r.end);
@@ -214,6 +250,7 @@ int sdl_sparse_code(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const
     a.coef = coef;
     a.nnz = nnz;
     a.res_energy = res_energy;
+    if ((c->prec & SDL_PREC_BF16_CORR) && (rc = prepare_tc_pass(c, a, true, st)) != SDL_OK) return rc;
     {
         Trace tr(c, kCode, st);
         rc = launch_code_pass(a, kCodeOnly, st, c->num_sms);
@@ -282,6 +319,8 @@ int sdl_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1
     grams(c, D1, p1, n1, D2, p2, n2, st);
     PassArgs a = base_args(c, Y, p1, p2, N, D1, n1, D2, n2, s);
     a.eps2 = eps2;
+    const bool tc = (c->prec & SDL_PREC_BF16_CORR) != 0;
+    if (tc && (rc = prepare_tc_pass(c, a, true, st)) != SDL_OK) return rc;
     int slots;
     {
         Trace tr(c, kCodeD1, st);
@@ -295,6 +334,7 @@ int sdl_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1
     a.support = support;
     a.coef = coef;
     a.nnz = nnz;
+    if (tc && (rc = prepare_tc_pass(c, a, false, st)) != SDL_OK) return rc;   // new D1
     {
         Trace tr(c, kCodeD2, st);
         slots = launch_code_pass(a, kSideD2, st, c->num_sms);
@@ -308,6 +348,28 @@ int sdl_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1
         launch_rescale(support, coef, N * (long long)s, n1, n2, kSideD2, c->norms, st);
     }
     return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+int sdl_set_precision(sdl_ctx* c, int flags) {
+    if (!c || (flags & ~(SDL_PREC_BF16_CORR | SDL_PREC_NO_RESCORE | SDL_PREC_FP64_SOLVE))) return SDL_ERR_ARG;
+    c->prec = flags;
+    return SDL_OK;
+}
+
+int sdl_precision_stats(sdl_ctx* c, uint64_t* rescored) {
+    if (!c || !rescored) return SDL_ERR_ARG;
+    DeviceGuard g(c->device);
+    *rescored = 0;
+    if (!c->rescored) return SDL_OK;
+    unsigned long long h = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&h, c->rescored, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(c->rescored, 0, sizeof(h)) != cudaSuccess) {
+        cudaGetLastError();
+        return SDL_ERR_CUDA;
+    }
+    *rescored = (uint64_t)h;
+    return SDL_OK;
 }
 
 int sdl_profile_enable(sdl_ctx* c, int enable) {
@@ -345,7 +407,7 @@ const char* sdl_kernel_name(int kind) {
     static const char* names[SDL_NUM_KERNEL_KINDS] = {
         "gram", "code", "code_D1", "code_D2", "accum_D1", "accum_D2",
         "reduce", "solve", "rescale", "memset", "batch_graph", "mlp", "adam", "topk",
-        "shortlist"};
+        "shortlist", "tc_corr"};
     return (kind >= 0 && kind < SDL_NUM_KERNEL_KINDS) ? names[kind] : "?";
 }
 

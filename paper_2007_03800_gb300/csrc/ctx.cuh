@@ -21,6 +21,13 @@ struct sdl_ctx {
     size_t cap_rec = 0;
     char* learn = nullptr;       // learned-coder workspace
     size_t cap_learn = 0;
+    // precision extension
+    int prec = 0;                // SDL_PREC_* flags
+    void* Yb = nullptr;          // BF16 signals (N x Kp)
+    void* KT = nullptr;          // BF16 Kronecker dictionary rows (n1n2 x Kp)
+    float* C0 = nullptr;         // tensor-core correlations (N x n1n2)
+    size_t cap_yb = 0, cap_kt = 0, cap_c0 = 0;
+    unsigned long long* rescored = nullptr;
     size_t cap_g1 = 0, cap_g2 = 0, cap_part = 0, cap_slots = 0, cap_red = 0, cap_redd = 0,
            cap_norms = 0;
     // tracing: launch counters and (optionally) one event pair per launch
@@ -38,7 +45,7 @@ namespace sdl {
 
 enum Kind {
     kGram = 0, kCode, kCodeD1, kCodeD2, kAccD1, kAccD2, kReduce, kSolve, kRescale, kMemset,
-    kBatchGraph, kMlp, kAdam, kTopk, kShortlist
+    kBatchGraph, kMlp, kAdam, kTopk, kShortlist, kTcCorr
 };
 constexpr size_t kMaxRecs = 1 << 16;
 

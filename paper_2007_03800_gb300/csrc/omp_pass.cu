@@ -222,30 +222,43 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
         int cnt = 0;
         float E = ss;
         if (finite) {
-            // ---- Z = Y D2 (p1 x N2P, row-major)
-            for (int e = tau; e < p1 * N2P; e += T) {
-                int r = e / N2P, j = e - r * N2P;
-                float z = 0.f;
-                for (int b = 0; b < p2; ++b) z = fmaf(Ys[r + p1 * b], D2r[b * N2P + j], z);
-                Zs[e] = z;
-            }
-            team_sync<TW>(team);
-            // ---- C0 = D1^T Z on this thread's (RI x RJ) block
             float c0[RI][RJ];
-#pragma unroll
-            for (int r = 0; r < RI; ++r)
-#pragma unroll
-                for (int c = 0; c < RJ; ++c) c0[r][c] = 0.f;
-            for (int aa = 0; aa < p1; ++aa) {
-                float u[RI], v[RJ];
-#pragma unroll
-                for (int r = 0; r < RI; ++r) u[r] = D1r[aa * N1P + i0 + r];
-#pragma unroll
-                for (int c = 0; c < RJ; ++c) v[c] = Zs[aa * N2P + j0 + c];
+            unsigned exact = 0xffffffffu;      // bit r*RJ+c: c0 entry is an FP32 value
+            const float bound = a.c0ext ? a.c0_err_rel * sqrtf(ss) : 0.f;
+            if (!a.c0ext) {
+                // ---- Z = Y D2 (p1 x N2P, row-major)
+                for (int e = tau; e < p1 * N2P; e += T) {
+                    int r = e / N2P, j = e - r * N2P;
+                    float z = 0.f;
+                    for (int b = 0; b < p2; ++b) z = fmaf(Ys[r + p1 * b], D2r[b * N2P + j], z);
+                    Zs[e] = z;
+                }
+                team_sync<TW>(team);
+                // ---- C0 = D1^T Z on this thread's (RI x RJ) block
 #pragma unroll
                 for (int r = 0; r < RI; ++r)
 #pragma unroll
-                    for (int c = 0; c < RJ; ++c) c0[r][c] = fmaf(u[r], v[c], c0[r][c]);
+                    for (int c = 0; c < RJ; ++c) c0[r][c] = 0.f;
+                for (int aa = 0; aa < p1; ++aa) {
+                    float u[RI], v[RJ];
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) u[r] = D1r[aa * N1P + i0 + r];
+#pragma unroll
+                    for (int c = 0; c < RJ; ++c) v[c] = Zs[aa * N2P + j0 + c];
+#pragma unroll
+                    for (int r = 0; r < RI; ++r)
+#pragma unroll
+                        for (int c = 0; c < RJ; ++c) c0[r][c] = fmaf(u[r], v[c], c0[r][c]);
+                }
+            } else {
+                // ---- C0 from the tensor-core correlations (approximate)
+                const float* cg = a.c0ext + (size_t)k * a.ldc0;
+#pragma unroll
+                for (int r = 0; r < RI; ++r)
+#pragma unroll
+                    for (int c = 0; c < RJ; ++c)
+                        c0[r][c] = (i0 + r < n1 && j0 + c < n2) ? cg[(i0 + r) + n1 * (j0 + c)] : 0.f;
+                if (bound > 0.f) exact = 0u;
             }
 #pragma unroll
             for (int r = 0; r < RI; ++r)
@@ -279,8 +292,45 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                 for (int r = 0; r < RI; ++r)
 #pragma unroll
                     for (int c = 0; c < RJ; ++c) m = fmaxf(m, fabsf(sc[r][c]));
-                const unsigned Mu =
-                    team_max_u32<TW>(__float_as_uint(m), misc + kMiscMax, wit, lane, team);
+                unsigned Mu = team_max_u32<TW>(__float_as_uint(m), misc + kMiscMax, wit, lane, team);
+                if (bound > 0.f) {
+                    // FP32 re-scoring: every approximate entry within 2*bound of
+                    // the running maximum gets its FP32 correlation
+                    // d1_i^T Y d2_j; repeat until the maximum and every entry
+                    // that could reach it are FP32 values
+                    for (;;) {
+                        const float thr = __uint_as_float(Mu) - 2.f * bound;
+                        unsigned did = 0;
+#pragma unroll
+                        for (int r = 0; r < RI; ++r)
+#pragma unroll
+                            for (int c = 0; c < RJ; ++c) {
+                                const int e = r * RJ + c;
+                                if (!((exact >> e) & 1u) && fabsf(sc[r][c]) >= thr) {
+                                    const int i = i0 + r, j = j0 + c;
+                                    float ex = 0.f;
+                                    for (int aa = 0; aa < p1; ++aa) {
+                                        float z = 0.f;
+                                        for (int b = 0; b < p2; ++b)
+                                            z = fmaf(Ys[aa + p1 * b], D2r[b * N2P + j], z);
+                                        ex = fmaf(D1r[aa * N1P + i], z, ex);
+                                    }
+                                    sc[r][c] = ex - (c0[r][c] - sc[r][c]);
+                                    c0[r][c] = ex;
+                                    exact |= 1u << e;
+                                    ++did;
+                                }
+                            }
+                        if (a.rescored && did) atomicAdd(a.rescored, (unsigned long long)did);
+                        if (team_max_u32<TW>(did, misc + kMiscSum, wit, lane, team) == 0u) break;
+                        m = 0.f;
+#pragma unroll
+                        for (int r = 0; r < RI; ++r)
+#pragma unroll
+                            for (int c = 0; c < RJ; ++c) m = fmaxf(m, fabsf(sc[r][c]));
+                        Mu = team_max_u32<TW>(__float_as_uint(m), misc + kMiscMax, wit, lane, team);
+                    }
+                }
                 if (Mu == 0u) break;  // every remaining score is exactly 0
                 const float Mf = __uint_as_float(Mu);
                 unsigned cand = 0xffffffffu;
@@ -376,7 +426,14 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
             float* accB = acc + n1 * n1;
             for (int e = tau; e < p1 * cnt; e += T) {
                 const int l = e / p1, r = e - l * p1;
-                atomicAdd(&accB[r * n1 + si[l]], xv[l] * Zs[r * N2P + sj[l]]);
+                float z;
+                if (a.c0ext) {   // no Z stage ran: (Y D2)[r, j_l] here
+                    z = 0.f;
+                    for (int b = 0; b < p2; ++b) z = fmaf(Ys[r + p1 * b], D2r[b * N2P + sj[l]], z);
+                } else {
+                    z = Zs[r * N2P + sj[l]];
+                }
+                atomicAdd(&accB[r * n1 + si[l]], xv[l] * z);
             }
             for (int e = tau; e < cnt * cnt; e += T) {
                 const int l = e / cnt, m2 = e - l * cnt;
@@ -692,8 +749,9 @@ bool code_shape_supported(int p1, int p2, int n1, int n2, int s) {
 int max_partial_slots(int num_sms) { return std::max(num_sms * kCtaSlotsPerSm, kGlobalSlots); }
 
 int launch_code_pass(const PassArgs& a, int side, cudaStream_t st, int num_sms) {
-    // the specialised kernels fetch signals with 16-byte TMA bulk copies
-    if ((reinterpret_cast<uintptr_t>(a.Y) & 15u) == 0) {
+    // the specialised kernels fetch signals with 16-byte TMA bulk copies; the
+    // tensor-core correlation path runs on the generic kernel
+    if (!a.c0ext && (reinterpret_cast<uintptr_t>(a.Y) & 15u) == 0) {
         const int r = launch_code_pass_fast(a, side, st, num_sms);
         if (r != SDL_ERR_UNSUPPORTED) return r;
     }

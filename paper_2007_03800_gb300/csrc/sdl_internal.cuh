@@ -51,6 +51,14 @@ struct PassArgs {
     int* err;
     const int32_t* idx;   // optional: code only the signals idx[0 .. *idx_count)
     const int* idx_count; //   (specialised kernels only; device count)
+    // optional correlations C0 from outside (BF16 tensor-core path), N x ldc0
+    // FP32 with entry q = i + n1*j, each within c0_err_rel * ||Y_k|| of the
+    // FP32 value; entries near the running maximum are re-scored in FP32
+    // (generic kernel only; c0_err_rel = 0: no re-scoring)
+    const float* c0ext;
+    int ldc0;
+    float c0_err_rel;
+    unsigned long long* rescored;   // optional counter of re-scored entries
 };
 
 // Host launchers (omp_pass.cu).  They return the number of partial-sum
@@ -127,6 +135,16 @@ struct RescaleDesc {
 int launch_multi_update_kernels(int which, const void* d_desc, int G, int blocks, size_t smem,
                                 int* err, cudaStream_t st);
 size_t solve_smem_bytes(int p, int n, int* keep_p);
+int launch_solve64(const float* red_f, const double* red_d, float* D, int p, int n, float* norms,
+                   double inv_count, float* objective_out, float* rmse_out, int* err,
+                   cudaStream_t st, float* G_out);
+}  // namespace sdl
+#include <cuda_bf16.h>
+namespace sdl {
+// precision.cu: C0 of N signals by one BF16 tensor-core GEMM (FP32 out, N x n1n2)
+int tc_correlations(const float* Y, long long N, int p1, int p2, const float* D1, int n1,
+                    const float* D2, int n2, __nv_bfloat16* Yb, bool fill_y, __nv_bfloat16* KT,
+                    float* C0, int* err, cudaStream_t st);
 
 // tc_gemm.cu: C = alpha A B^T (+bias, GELU) on tcgen05 tensor cores, BF16 in,
 // FP32 accumulate; optional FP32 / BF16 / transposed-BF16 / pre-activation outputs.

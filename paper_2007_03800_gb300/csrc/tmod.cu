@@ -321,6 +321,153 @@ __global__ void __launch_bounds__(kSolveThreads) solve_multi_kernel(const SolveD
                err, q.G_out, q.keep_p);
 }
 
+// FP64 version of solve_kernel (precision extension): the same steps with
+// the normal matrix, its inverse, D*, the objective decrease and the column
+// norms in double precision (inputs are the FP32 partial sums).
+constexpr int kSolve64Threads = 512;
+
+__global__ void __launch_bounds__(kSolve64Threads)
+    solve64_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D,
+                   int p, int n, float* __restrict__ norms, double inv_count,
+                   float* objective_out, float* rmse_out, int* err, float* G_out) {
+    extern __shared__ __align__(16) double smd[];
+    const int lda = n | 1;
+    double* A = smd;                        // nu x nu (stride lda)
+    double* X = A + (size_t)n * lda;        // p x nu right-hand sides -> D* rows
+    double* tmp = X + (size_t)p * lda;      // one row per warp
+    double* d0 = tmp + (size_t)(kSolve64Threads / 32) * lda;
+    double* nrm = d0 + n;
+    int* idx = reinterpret_cast<int*>(nrm + n);
+    __shared__ int s_nu, s_fail;
+    __shared__ double s_red[kSolve64Threads / 32];
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = nth >> 5;
+    const float* P = red_f;
+    const float* B = red_f + n * n;
+    if (tid < 32) {
+        int base = 0, fail = 0;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const float dl = (i < n) ? P[i * n + i] : 0.f;
+            if (i < n && !isfinite(dl)) fail = SDL_ERR_NONFINITE;
+            const unsigned um = __ballot_sync(0xffffffffu, i < n && dl > 0.f);
+            if (i < n && dl > 0.f) {
+                const int pos = base + __popc(um & ((1u << lane) - 1u));
+                idx[pos] = i;
+                d0[pos] = dl;
+            }
+            base += __popc(um);
+        }
+        fail = __reduce_or_sync(0xffffffffu, fail);
+        if (lane == 0) {
+            s_nu = base;
+            s_fail = fail;
+        }
+    }
+    __syncthreads();
+    const int nu = s_nu;
+    for (int e = tid; e < nu * nu; e += nth) {
+        const int r = e / nu, c = e - r * nu;
+        A[r * lda + c] = (double)P[idx[r] * n + idx[c]];
+    }
+    for (int e = tid; e < p * nu; e += nth) {
+        const int r = e / nu, c = e - r * nu;
+        X[r * lda + c] = (double)B[r * n + idx[c]];
+    }
+    __syncthreads();
+    for (int k = 0; k < nu && s_fail == 0; ++k) {
+        const double piv = A[k * lda + k];
+        if (!(piv > (double)kSolvePivotRel * d0[k])) {
+            __syncthreads();
+            if (tid == 0) s_fail = SDL_ERR_SINGULAR;
+            __syncthreads();
+            break;
+        }
+        const double inv = 1.0 / piv;
+        for (int e = tid; e < nu * nu; e += nth) {
+            const int i = e / nu, j = e - i * nu;
+            if (i != k && j != k) A[i * lda + j] -= A[i * lda + k] * inv * A[k * lda + j];
+        }
+        __syncthreads();
+        for (int e = tid; e < 2 * nu; e += nth) {
+            if (e < nu) {
+                if (e != k) A[k * lda + e] *= inv;
+            } else if (e - nu != k) {
+                A[(e - nu) * lda + k] *= -inv;
+            }
+        }
+        if (tid == 0) A[k * lda + k] = inv;
+        __syncthreads();
+    }
+    const bool ok_inv = s_fail == 0;
+    double part = 0.0;
+    if (ok_inv) {
+        // D* rows: X[a, :] <- X[a, :] A^{-1}, one warp per row through a copy
+        for (int a = warp; a < p; a += nw) {
+            double* t = tmp + warp * lda;
+            for (int c = lane; c < nu; c += 32) t[c] = X[a * lda + c];
+            __syncwarp();
+            for (int c = lane; c < nu; c += 32) {
+                double x = 0.0;
+                for (int k = 0; k < nu; ++k) x += t[k] * A[k * lda + c];
+                X[a * lda + c] = x;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        // delta^T P delta per row, P and D_old read back in FP32
+        for (int e = tid; e < p * nu; e += nth) {
+            const int a = e / nu, c = e - a * nu;
+            double w = 0.0;
+            const float* prow = P + (size_t)idx[c] * n;
+            for (int k = 0; k < nu; ++k)
+                w += (double)prow[idx[k]] * ((double)D[a + p * idx[k]] - X[a * lda + k]);
+            part += w * ((double)D[a + p * idx[c]] - X[a * lda + c]);
+        }
+        for (int c = tid; c < nu; c += nth) {
+            double ss = 0.0;
+            for (int a = 0; a < p; ++a) ss += X[a * lda + c] * X[a * lda + c];
+            nrm[c] = sqrt(ss);
+            if (!(nrm[c] > 0.0) || !isfinite(nrm[c])) s_fail = SDL_ERR_SINGULAR;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) s_red[warp] = part;
+    __syncthreads();
+    const bool ok = s_fail == 0;
+    for (int i = tid; i < n; i += nth) norms[i] = 1.f;
+    __syncthreads();
+    if (ok) {
+        for (int c = tid; c < nu; c += nth) norms[idx[c]] = (float)nrm[c];
+        for (int e = tid; e < p * nu; e += nth) {
+            const int a = e / nu, c = e - a * nu;
+            D[a + p * idx[c]] = (float)(X[a * lda + c] / nrm[c]);
+        }
+        __syncthreads();
+        if (G_out) {
+            for (int e = tid; e < n * n; e += nth) {
+                const int i = e / n, j = e - i * n;
+                float g = 0.f;
+                for (int a = 0; a < p; ++a) g = fmaf(D[a + p * i], D[a + p * j], g);
+                G_out[e] = g;
+            }
+        }
+    }
+    if (tid == 0) {
+        double trace = 0.0;
+        for (int w = 0; w < nw; ++w) trace += s_red[w];
+        if (!ok) record_error(err, s_fail);
+        const double before = red_d[0];
+        const double after = ok ? before - trace : before;
+        if (objective_out) {
+            objective_out[0] = (float)before;
+            objective_out[1] = (float)after;
+        }
+        if (rmse_out) rmse_out[0] = (float)sqrt(fmax(after, 0.0) * inv_count);
+    }
+}
+
 // X <- W^{-1} X: slot l of every code times the norm of its D1 atom (side 1,
 // Corollary 1) or D2 atom (side 2, Result 1).
 __global__ void rescale_kernel(const int32_t* __restrict__ support, float* __restrict__ coef,
@@ -400,6 +547,22 @@ void launch_reduce_partials(const float* part_f, const double* part_d, int n_slo
     const int blocks = std::max(1, (nf + 31) / 32);
     reduce_partials_kernel<<<blocks, kReduceWarps * 32, 0, st>>>(part_f, part_d, n_slots, nf,
                                                                  red_f, red_d);
+}
+
+int launch_solve64(const float* red_f, const double* red_d, float* D, int p, int n, float* norms,
+                   double inv_count, float* objective_out, float* rmse_out, int* err,
+                   cudaStream_t st, float* G_out) {
+    const size_t lda = (size_t)(n | 1);
+    const size_t bytes = sizeof(double) * ((size_t)n * lda + (size_t)p * lda +
+                                           (size_t)(kSolve64Threads / 32) * lda + 2 * (size_t)n) +
+                         sizeof(int) * (size_t)n;
+    if (bytes > 227 * 1024) return SDL_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(solve64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes) != cudaSuccess)
+        return SDL_ERR_CUDA;
+    solve64_kernel<<<1, kSolve64Threads, bytes, st>>>(red_f, red_d, D, p, n, norms, inv_count,
+                                                      objective_out, rmse_out, err, G_out);
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
 }
 
 int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n, float* norms,

@@ -63,6 +63,8 @@ SIGNATURES = {
     "sdl_mlp_forward": [_P, _P, _L, _P, _P],
     "sdl_sparse_code_learned": [_P, _P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P,
                                 _P, _P, _P],
+    "sdl_set_precision": [_P, _I],
+    "sdl_precision_stats": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "sdl_profile_enable": [_P, _I],
     "sdl_profile_collect": [_P, _P, _P, _I],
 }
@@ -221,6 +223,18 @@ class Context:
         if k < 0:
             raise SDLError(k, "sdl_profile_collect")
         return {self._lib.sdl_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(k)}
+
+    PREC_FP32, PREC_BF16_CORR, PREC_NO_RESCORE, PREC_FP64_SOLVE = 0, 1, 2, 4
+
+    def set_precision(self, flags: int) -> None:
+        """SDL_PREC_* flags (see include/sdl.h)."""
+        _check(self._lib.sdl_set_precision(self._h, int(flags)), "sdl_set_precision")
+
+    def precision_stats(self) -> int:
+        """Correlation entries re-scored in FP32 since the last call."""
+        v = ctypes.c_uint64()
+        _check(self._lib.sdl_precision_stats(self._h, ctypes.byref(v)), "sdl_precision_stats")
+        return v.value
 
     def reserve(self, p1, p2, n1, n2, s) -> None:
         _check(self._lib.sdl_reserve(self._h, p1, p2, n1, n2, s), "sdl_reserve")
