@@ -34,7 +34,7 @@ def test_bf16_correlation_error_within_bound(prec_ctx):
     # C0 through the public GEMM with the same operands the coder uses
     Yb = Yg.transpose(1, 2).reshape(300, -1).contiguous().to(torch.bfloat16)
     KT = torch.einsum("ai,bj->jiba", torch.tensor(D1), torch.tensor(D2)).reshape(32 * 128, -1)
-    KT = KT.to(torch.float32).to(torch.bfloat16).cuda()
+    KT = KT.to(torch.float32).to(torch.bfloat16).contiguous().cuda()
     sdl.gemm_bf16(prec_ctx, Yb, KT, C=C0)
     got = C0.cpu().numpy().reshape(300, 128, 32).transpose(0, 2, 1)
     bound = 2.0 ** -7 * 1.03 * np.linalg.norm(Y, axis=(1, 2))
