@@ -414,6 +414,185 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ studies
+# Extra measurements on the other synthetic workloads (one JSON line each,
+# "study": name).  They are not the headline line and touch no oracle.
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _device_dict(D, dev):
+    import torch
+
+    from paper_2007_03800_gb300 import sdl
+    return sdl.dictionary(torch.tensor(D, dtype=torch.float32, device=dev))
+
+
+def study_precision(args):
+    """Hyperspectral-shaped signals, N = 50000 of 16x64, D1 16x32, D2 64x128,
+    s = 10, 15 iterations from the same start in each precision mode: device
+    time per iteration, the per-kernel split of one iteration, the RMSE
+    trajectory and the entries re-scored in FP32.  Y is 205 MB (> L2), so no
+    flush is needed between iterations."""
+    import torch
+
+    from paper_2007_03800_gb300 import sdl, synth
+    dev = torch.device("cuda:0")
+    N, s, iters = 50_000, 10, 15
+    Y = synth.hyperspectral(N, seed=31)
+    D1, D2 = synth.init_dictionaries(16, 64, 32, 128, seed=1)
+    ctx = sdl.Context(0)
+    Yg = sdl.signals(torch.tensor(Y, dtype=torch.float32, device=dev))
+    codes = sdl.Codes.empty(N, s, dev)
+    rmse = torch.zeros(2, dtype=torch.float32, device=dev)
+    C = sdl.Context
+    modes = {"fp32": C.PREC_FP32, "bf16_rescored": C.PREC_BF16_CORR,
+             "fp64_solve": C.PREC_FP64_SOLVE, "bf16_fp64": C.PREC_BF16_CORR | C.PREC_FP64_SOLVE}
+    out = {}
+    for name, flags in modes.items():
+        ctx.set_precision(flags)
+        D1w, D2w = _device_dict(D1, dev), _device_dict(D2, dev)
+        for _ in range(args.warmup):
+            ctx.iterate(Yg, D1w, D2w, s, out=codes, rmse_out=rmse)
+        ctx.status()
+        ctx.precision_stats()
+        D1g, D2g = _device_dict(D1, dev), _device_dict(D2, dev)
+        ms, traj, resc, st = [], [], [], []
+        for _ in range(iters):
+            a, b = _events()
+            a.record()
+            ctx.iterate(Yg, D1g, D2g, s, out=codes, rmse_out=rmse)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            traj.append(rmse.tolist())
+            resc.append(ctx.precision_stats())
+            # a singular normal matrix leaves that dictionary unchanged and is
+            # recorded here; the run goes on
+            rc = ctx.status()
+            st.append(sdl.ERRORS.get(rc, str(rc)) if rc else "ok")
+        ctx.profile_collect()
+        ctx.profile(True)
+        ctx.iterate(Yg, D1w, D2w, s, out=codes, rmse_out=rmse)
+        ctx.profile(False)
+        split = {k: round(v[0], 4) for k, v in ctx.profile_collect().items() if v[1] > 0}
+        ctx.status()
+        out[name] = {"ms_per_iteration": statistics.median(ms), "signals_per_s":
+                     N / (statistics.median(ms) / 1e3), "final_rmse": traj[-1],
+                     "rmse_trajectory_after_D2": [round(t[1], 7) for t in traj],
+                     "status_per_iteration": st,
+                     "rescored_per_iteration": resc, "kernel_ms_one_iteration": split}
+    ref = out["fp32"]["final_rmse"][1]
+    for name in out:
+        out[name]["final_rmse_rel_vs_fp32"] = out[name]["final_rmse"][1] / ref - 1.0
+    ctx.close()
+    print(json.dumps({"study": "precision", "workload": "hyperspectral-shaped 16x64 signals, "
+                      "N=50000, D1 16x32, D2 64x128, s=10, 15 iterations",
+                      "unit": "signals/s per iteration", "modes": out}), flush=True)
+    return 0
+
+
+def study_learned(args):
+    """Learned support proposal on 12x12 image patches: dictionaries from 20
+    plain iterations on 1M training patches, labels = the plain 2D-OMP codes
+    of those patches, network 144 -> 512 (GELU) -> 576 trained on the GPU,
+    then 1M fresh patches (other images) coded by both coders (k = 32)."""
+    import torch
+
+    from paper_2007_03800_gb300 import learned, sdl, synth
+    dev = torch.device("cuda:0")
+    p, n, s, k, N = 12, 24, 6, 32, 1_000_000
+    t0 = time.perf_counter()
+    imgs_tr = np.stack([synth.synthetic_image(100 + i) for i in range(64)])
+    imgs_te = np.stack([synth.synthetic_image(300 + i) for i in range(64)])
+    Ytr = synth.random_patches(imgs_tr, N, p, seed=7).astype(np.float32)
+    Yte = synth.random_patches(imgs_te, N, p, seed=8).astype(np.float32)
+    t_data = time.perf_counter() - t0
+    ctx = sdl.Context(0)
+    Yg = sdl.signals(torch.from_numpy(Ytr).to(dev))
+    Yt = sdl.signals(torch.from_numpy(Yte).to(dev))
+    D1, D2 = synth.init_dictionaries(p, p, n, n, seed=1)
+    D1g, D2g = _device_dict(D1, dev), _device_dict(D2, dev)
+    codes = sdl.Codes.empty(N, s, dev)
+    rmse = torch.zeros(2, dtype=torch.float32, device=dev)
+    a, b = _events()
+    a.record()
+    for _ in range(20):
+        ctx.iterate(Yg, D1g, D2g, s, out=codes, rmse_out=rmse)
+    labels = ctx.sparse_code(Yg, D1g, D2g, s)
+    b.record()
+    b.synchronize()
+    ms_dl = a.elapsed_time(b)
+    net = sdl.MLP(ctx, p, p, n, n, hidden=512, max_batch=65536)
+    net.init(seed=3)
+    a, b = _events()
+    a.record()
+    hist = learned.train(net, Yg, labels, epochs=3, batch=4096, lr=2e-3)
+    b.record()
+    b.synchronize()
+    ms_train = a.elapsed_time(b)
+    for _ in range(args.warmup):
+        learned.compare(ctx, net, Yt[:65536], D1g, D2g, s, k=k, reps=1)
+    res = learned.compare(ctx, net, Yt, D1g, D2g, s, k=k, reps=max(args.steps, 1))
+    ctx.profile_collect()
+    ctx.profile(True)
+    net.sparse_code(Yt, D1g, D2g, s, k=k)
+    ctx.profile(False)
+    split = {kk: round(v[0], 4) for kk, v in ctx.profile_collect().items() if v[1] > 0}
+    ctx.check()
+    net.close()
+    ctx.close()
+    res.update({"train_loss_per_epoch": hist, "ms_train": ms_train, "ms_dl_20_iterations": ms_dl,
+                "train_rmse_after_D2": rmse[1].item(), "k": k,
+                "learned_kernel_ms": split, "host_data_s": t_data,
+                "signals_per_s_plain": N / (res["ms_plain"] / 1e3),
+                "signals_per_s_learned": N / (res["ms_learned"] / 1e3)})
+    print(json.dumps({"study": "learned", "workload": "12x12 image patches, D 12x24, s=6, "
+                      "1M training pairs, 1M fresh patches", "result": res}), flush=True)
+    return 0
+
+
+def study_denoise(args):
+    """Denoising with one batch of three patch sizes (8, 12, 16; D p x 2p;
+    error-driven stop at 1.15 sigma p, s <= p/2) on a 512x512 synthetic image
+    with sigma = 20 noise, 10 iterations: PSNRs and device time of the whole
+    pipeline (patch extraction, learning, coding, averaging)."""
+    import torch
+
+    from paper_2007_03800_gb300 import denoise as dn
+    from paper_2007_03800_gb300 import sdl, synth
+    dev = torch.device("cuda:0")
+    sigma = 20.0
+    clean = synth.synthetic_image(7)
+    noisy = clean + np.random.default_rng(8).standard_normal(clean.shape) * sigma
+    cg = torch.tensor(clean, dtype=torch.float32, device=dev)
+    ng = torch.tensor(noisy, dtype=torch.float32, device=dev)
+    ctx = sdl.Context(0)
+    for _ in range(args.warmup):
+        dn.denoise(ctx, ng, sigma, iterations=1, clean=cg)
+    ms = []
+    r = None
+    for _ in range(max(args.steps, 1)):
+        a, b = _events()
+        a.record()
+        r = dn.denoise(ctx, ng, sigma, iterations=10, clean=cg)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    ctx.check()
+    n_patches = sum((512 - p + 1) ** 2 for p, _, _ in dn.DEFAULT_GROUPS)
+    res = {"psnr_noisy": sdl.psnr(ng, cg).item(), "psnr_denoised": [x.item() for x in r["psnr"]],
+           "nnz_mean": [x.item() for x in r["nnz_mean"]], "rmse_final": r["rmse"][-1].tolist(),
+           "ms_pipeline": statistics.median(ms), "patches": n_patches,
+           "patch_iterations_per_s": 10 * n_patches / (statistics.median(ms) / 1e3),
+           "tuning": r["tuning"]}
+    ctx.close()
+    print(json.dumps({"study": "denoise", "workload": "512x512 synthetic image, sigma=20, "
+                      "all 8x8, 12x12, 16x16 patches, 10 iterations", "result": res}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,11 +602,16 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed region only: no e2e loop, CPU baseline or clock sampling "
                          "(for profiler runs; its numbers are not bench values)")
+    ap.add_argument("--study", choices=["precision", "learned", "denoise"],
+                    help="run one extra study on its own workload instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.study:
+        return {"precision": study_precision, "learned": study_learned,
+                "denoise": study_denoise}[args.study](args)
     return run_ours(args)
 
 

@@ -136,8 +136,11 @@ __global__ void __launch_bounds__(kReduceWarps * 32)
 //      SPD matrix the k-th pivot is the k-th Cholesky pivot squared, so the
 //      same relative-pivot test flags a singular P;
 //   2. D* = B_u P_u^{-1} (rows of the right-hand side times the inverse);
-//   3. objective after = before - tr(Delta P Delta^T), Delta = D_old - D*
-//      (the exact decrease of the least-squares objective, Result 1);
+//   3. objective after = before + sum_a Delta_a (P (D*_a + D_old_a) - 2 B_a),
+//      Delta = D* - D_old by rows a: the change of the least-squares objective
+//      of Result 1 for ANY D*, so an inexact solve (an ill-conditioned P)
+//      enters only to second order, unlike before - tr(Delta P Delta^T),
+//      which holds at the exact minimiser only;
 //   4. norms of the columns of D*, D <- D* diag(1/norm), optional G = D^T D.
 // Every step is a data-parallel sweep with two barriers per pivot.  On any
 // failure D is left untouched and the norms are set to 1.
@@ -159,7 +162,7 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
     float* d0 = nrm + n;                            // n
     int* idx = reinterpret_cast<int*>(d0 + n);      // n
     __shared__ int s_nu, s_fail;
-    __shared__ float s_red[kSolveThreads / 32];
+    __shared__ double s_red[kSolveThreads / 32];
 
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -234,7 +237,7 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
         __syncthreads();
     }
     const bool ok_inv = (s_fail == 0);
-    float part = 0.f;
+    double part = 0.0;
     if (ok_inv) {
         // 2. D* rows
         for (int e = tid; e < p * nu; e += nth) {
@@ -244,18 +247,19 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
             X[a * lda + c] = x;
         }
         __syncthreads();
-        // 3. delta^T P delta per row a, with P (used block) read back from red_f
+        // 3. objective change, row a and used atom c at a time, P (used
+        //    block) from the kept copy or read back from red_f
         for (int e = tid; e < p * nu; e += nth) {
             const int a = e / nu, c = e - a * nu;
-            float w = 0.f;
+            float w = -2.f * Bc[a * lda + c];
             if (keep_p) {
                 const float* prow = P0 + c * lda;
-                for (int k = 0; k < nu; ++k) w = fmaf(prow[k], Dn[a * lda + idx[k]] - X[a * lda + k], w);
+                for (int k = 0; k < nu; ++k) w = fmaf(prow[k], Dn[a * lda + idx[k]] + X[a * lda + k], w);
             } else {
                 const float* prow = P + (size_t)idx[c] * n;
-                for (int k = 0; k < nu; ++k) w = fmaf(prow[idx[k]], Dn[a * lda + idx[k]] - X[a * lda + k], w);
+                for (int k = 0; k < nu; ++k) w = fmaf(prow[idx[k]], Dn[a * lda + idx[k]] + X[a * lda + k], w);
             }
-            part = fmaf(w, Dn[a * lda + idx[c]] - X[a * lda + c], part);
+            part += (double)(X[a * lda + c] - Dn[a * lda + idx[c]]) * (double)w;
         }
         // 4. column norms of D*
         for (int c = tid; c < nu; c += nth) {
@@ -292,11 +296,11 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
         }
     }
     if (tid == 0) {
-        double trace = 0.0;
-        for (int w = 0; w < nth / 32; ++w) trace += (double)s_red[w];
+        double change = 0.0;
+        for (int w = 0; w < nth / 32; ++w) change += s_red[w];
         if (!ok) record_error(err, s_fail);
         const double before = red_d[0];
-        const double after = ok ? before - trace : before;
+        const double after = ok ? before + change : before;
         if (objective_out) {
             objective_out[0] = (float)before;
             objective_out[1] = (float)after;
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_multi_kernel(const SolveD
 }
 
 // FP64 version of solve_kernel (precision extension): the same steps with
-// the normal matrix, its inverse, D*, the objective decrease and the column
+// the normal matrix, its inverse, D*, the objective change and the column
 // norms in double precision (inputs are the FP32 partial sums).
 constexpr int kSolve64Threads = 512;
 
@@ -415,14 +419,14 @@ __global__ void __launch_bounds__(kSolve64Threads)
             __syncwarp();
         }
         __syncthreads();
-        // delta^T P delta per row, P and D_old read back in FP32
+        // objective change (as in solve_body), P, B and D_old read back in FP32
         for (int e = tid; e < p * nu; e += nth) {
             const int a = e / nu, c = e - a * nu;
-            double w = 0.0;
+            double w = -2.0 * (double)B[a * n + idx[c]];
             const float* prow = P + (size_t)idx[c] * n;
             for (int k = 0; k < nu; ++k)
-                w += (double)prow[idx[k]] * ((double)D[a + p * idx[k]] - X[a * lda + k]);
-            part += w * ((double)D[a + p * idx[c]] - X[a * lda + c]);
+                w += (double)prow[idx[k]] * ((double)D[a + p * idx[k]] + X[a * lda + k]);
+            part += w * (X[a * lda + c] - (double)D[a + p * idx[c]]);
         }
         for (int c = tid; c < nu; c += nth) {
             double ss = 0.0;
@@ -455,11 +459,11 @@ __global__ void __launch_bounds__(kSolve64Threads)
         }
     }
     if (tid == 0) {
-        double trace = 0.0;
-        for (int w = 0; w < nw; ++w) trace += s_red[w];
+        double change = 0.0;
+        for (int w = 0; w < nw; ++w) change += s_red[w];
         if (!ok) record_error(err, s_fail);
         const double before = red_d[0];
-        const double after = ok ? before - trace : before;
+        const double after = ok ? before + change : before;
         if (objective_out) {
             objective_out[0] = (float)before;
             objective_out[1] = (float)after;
