@@ -55,8 +55,9 @@ struct Layout {
         acc = g2 + align4(N2P * N2P);
         accd = acc + align4(nf_smem);       // 2 doubles = 4 floats, 16-byte aligned
         team0 = accd + 4;
-        // team region: Y (p1*p2) | Z (p1*N2P) | slab
-        int ys = align4(p1 * p2), zs = align4(p1 * N2P);
+        // team region: Y (p1*p2) | Z (p1*N2P), or W = D1^T Y (N1P*p2) when
+        // C0 comes from the tensor cores | slab
+        int ys = align4(p1 * p2), zs = align4(p1 * N2P > N1P * p2 ? p1 * N2P : N1P * p2);
         slab_L = ys + zs;
         slab_invd = slab_L + s * s;
         slab_y = slab_invd + s;
@@ -258,7 +259,19 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
 #pragma unroll
                     for (int c = 0; c < RJ; ++c)
                         c0[r][c] = (i0 + r < n1 && j0 + c < n2) ? cg[(i0 + r) + n1 * (j0 + c)] : 0.f;
-                if (bound > 0.f) exact = 0u;
+                if (bound > 0.f) {
+                    exact = 0u;
+                    // W = D1^T Y (n1 x p2, row i contiguous) in the Z area:
+                    // a re-scored entry is then w_i . d2_j, p2 FMAs
+                    float* Ws = Zs;
+                    for (int e = tau; e < n1 * p2; e += T) {
+                        const int i = e / p2, b = e - i * p2;
+                        float w = 0.f;
+                        for (int aa = 0; aa < p1; ++aa) w = fmaf(D1r[aa * N1P + i], Ys[aa + p1 * b], w);
+                        Ws[e] = w;
+                    }
+                    team_sync<TW>(team);
+                }
             }
 #pragma unroll
             for (int r = 0; r < RI; ++r)
@@ -296,7 +309,7 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                 if (bound > 0.f) {
                     // FP32 re-scoring: every approximate entry within 2*bound of
                     // the running maximum gets its FP32 correlation
-                    // d1_i^T Y d2_j; repeat until the maximum and every entry
+                    // (d1_i^T Y) d2_j; repeat until the maximum and every entry
                     // that could reach it are FP32 values
                     for (;;) {
                         const float thr = __uint_as_float(Mu) - 2.f * bound;
@@ -308,13 +321,9 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                                 const int e = r * RJ + c;
                                 if (!((exact >> e) & 1u) && fabsf(sc[r][c]) >= thr) {
                                     const int i = i0 + r, j = j0 + c;
+                                    const float* wi = Zs + i * p2;
                                     float ex = 0.f;
-                                    for (int aa = 0; aa < p1; ++aa) {
-                                        float z = 0.f;
-                                        for (int b = 0; b < p2; ++b)
-                                            z = fmaf(Ys[aa + p1 * b], D2r[b * N2P + j], z);
-                                        ex = fmaf(D1r[aa * N1P + i], z, ex);
-                                    }
+                                    for (int b = 0; b < p2; ++b) ex = fmaf(wi[b], D2r[b * N2P + j], ex);
                                     sc[r][c] = ex - (c0[r][c] - sc[r][c]);
                                     c0[r][c] = ex;
                                     exact |= 1u << e;

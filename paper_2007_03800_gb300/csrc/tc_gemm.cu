@@ -7,6 +7,10 @@
 // FP32 accumulator in tensor memory; tcgen05.commit releases ring stages back
 // to the producer; the four warps then read the accumulator with tcgen05.ld
 // (warp w owns TMEM lanes 32w..32w+31 = output rows) and apply the epilogue.
+// Row-major outputs (and the GELU-derivative input) pass through a per-warp
+// 32 x 33 shared-memory transpose, so that every global access of the
+// epilogue is a coalesced 128-byte row segment.  Two CTAs share an SM, so
+// one CTA's epilogue overlaps the other's main loop.
 // Every wait is bounded: on a timeout the CTA records SDL_ERR_TIMEOUT, lets
 // its in-flight copies land and frees its tensor memory.
 #include <cuda.h>
@@ -22,7 +26,8 @@ using namespace sdl;
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, UMMA_K = 16;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3, UMMA_K = 16;
+constexpr int kStageLd = 33;   // epilogue transpose row stride (floats)
 constexpr int TILE_A = BM * BK * 2;   // bytes
 constexpr int TILE_B = BN * BK * 2;
 constexpr long long kSpin = 1ll << 26;
@@ -93,7 +98,7 @@ __host__ __device__ constexpr uint32_t instr_desc() {
            ((uint32_t)(BM >> 4) << 24);
 }
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    int M, int N, int K, Epi epi, int* err) {
     extern __shared__ uint8_t smem_raw[];
@@ -186,11 +191,44 @@ __global__ void __launch_bounds__(128, 1)
     __syncwarp();
     __syncthreads();   // s_fail is final here (the MMAs themselves may still run)
 
-    // ---- epilogue: thread = output row, 32 accumulator columns per load
+    // ---- epilogue: thread = output row, 32 accumulator columns per load.
+    // The operand ring is idle once the accumulator barrier has fired (every
+    // MMA, hence every copy it consumed, has completed): it holds the
+    // per-warp transpose buffers.
     const bool got = !s_fail && mbar_wait(accb, 0);
     tc_fence_after();
     const int r = warp * 32 + lane;
     const int m = m0 + r;
+    float* stage = reinterpret_cast<float*>(sA) + warp * 32 * kStageLd;
+    // row-major [m, n] block of 32 rows (this warp) x 32 columns: lane holds
+    // row `lane`; stored (or added) one coalesced row segment at a time
+    auto store_rows = [&](const float (&x)[32], int c0, float* dst, int ld, int accumulate) {
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage[lane * kStageLd + j] = x[j];
+        __syncwarp();
+        const int n = n0 + c0 + lane;
+        for (int rr = 0; rr < 32; ++rr) {
+            const int mm = m0 + warp * 32 + rr;
+            if (mm < M && n < N) {
+                float* d = dst + (size_t)mm * ld + n;
+                const float val = stage[rr * kStageLd + lane];
+                *d = accumulate ? *d + val : val;
+            }
+        }
+    };
+    auto store_rows_bf16 = [&](const float (&x)[32], int c0, __nv_bfloat16* dst, int ld) {
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage[lane * kStageLd + j] = x[j];
+        __syncwarp();
+        const int n = n0 + c0 + lane;
+        for (int rr = 0; rr < 32; ++rr) {
+            const int mm = m0 + warp * 32 + rr;
+            if (mm < M && n < N)
+                dst[(size_t)mm * ld + n] = __float2bfloat16_rn(stage[rr * kStageLd + lane]);
+        }
+    };
     if (__all_sync(0xffffffffu, got)) {
         for (int c0 = 0; c0 < BN; c0 += 32) {
             uint32_t v[32];
@@ -207,29 +245,45 @@ __global__ void __launch_bounds__(128, 1)
                   "=r"(v[30]), "=r"(v[31])
                 : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (m < M) {
+            float x[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int n = n0 + c0 + j;
+                x[j] = epi.alpha * __uint_as_float(v[j]);
+                if (epi.bias && n < N) x[j] += epi.bias[n];
+            }
+            if (epi.pre) store_rows(x, c0, epi.pre, epi.ldpre, 0);
+            if (epi.act == 1) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    x[j] = 0.5f * x[j] * (1.f + erff(x[j] * 0.70710678118654752f));
+            } else if (epi.act == 2) {
+                // chain rule through GELU: d/du [u Phi(u)] = Phi(u) + u phi(u);
+                // the gin block arrives through the transpose buffer
+                __syncwarp();
+                const int n = n0 + c0 + lane;
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int mm = m0 + warp * 32 + rr;
+                    stage[rr * kStageLd + lane] =
+                        (mm < M && n < N) ? epi.gin[(size_t)mm * epi.ldgin + n] : 0.f;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float u = stage[lane * kStageLd + j];
+                    const float Phi = 0.5f * (1.f + erff(u * 0.70710678118654752f));
+                    const float phi = 0.3989422804014327f * expf(-0.5f * u * u);
+                    x[j] *= Phi + u * phi;
+                }
+            }
+            if (epi.C) store_rows(x, c0, epi.C, epi.ldc, epi.accumulate);
+            if (epi.Cb) store_rows_bf16(x, c0, epi.Cb, epi.ldcb);
+            if (epi.Ct && m < M) {
+                // transposed: for a fixed column the lanes write consecutive m
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int n = n0 + c0 + j;
-                    if (n >= N) break;
-                    float x = epi.alpha * __uint_as_float(v[j]);
-                    if (epi.bias) x += epi.bias[n];
-                    if (epi.pre) epi.pre[(size_t)m * epi.ldpre + n] = x;
-                    if (epi.act == 1) {
-                        x = 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
-                    } else if (epi.act == 2) {
-                        // chain rule through GELU: d/du [u Phi(u)] = Phi(u) + u phi(u)
-                        const float u = epi.gin[(size_t)m * epi.ldgin + n];
-                        const float Phi = 0.5f * (1.f + erff(u * 0.70710678118654752f));
-                        const float phi = 0.3989422804014327f * expf(-0.5f * u * u);
-                        x *= Phi + u * phi;
-                    }
-                    if (epi.C) {
-                        float* c = epi.C + (size_t)m * epi.ldc + n;
-                        *c = epi.accumulate ? *c + x : x;
-                    }
-                    if (epi.Cb) epi.Cb[(size_t)m * epi.ldcb + n] = __float2bfloat16_rn(x);
-                    if (epi.Ct) epi.Ct[(size_t)n * epi.ldct + m] = __float2bfloat16_rn(x);
+                    if (n < N) epi.Ct[(size_t)n * epi.ldct + m] = __float2bfloat16_rn(x[j]);
                 }
             }
         }

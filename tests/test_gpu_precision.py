@@ -138,7 +138,8 @@ def test_hsi_precision_study(prec_ctx):
     after one Algorithm-1 iteration.  These normal equations are badly
     conditioned (cond(M) ~ 6e4 with 26 of 128 D2 atoms used), so an FP32
     perturbation of D1 of 1e-6 moves the oracle's own D2 by ~1e-5: the
-    dictionary error of every mode is reported, and bounded by 1e-3.  The
+    dictionary error of every mode is reported, and bounded by 1e-3 (D2:
+    when no tie of the second pass went the other way).  The
     RMSE of every re-scored mode stays within 1e-4: the solve kernels compute
     the objective through an identity in which the solve error enters only
     to second order."""
@@ -152,5 +153,11 @@ def test_hsi_precision_study(prec_ctx):
     for name in ("fp32", "bf16", "fp64_solve", "bf16_fp64"):
         e = rows[name]
         assert e["rmse_rel"] < RMSE_RTOL, (name, e)
-        assert e["D1_abs"] < 1e-3 and e["D2_abs"] < 1e-3, (name, e)
+        assert e["bad"] == 0, (name, e)
+        assert e["D1_abs"] < 1e-3, (name, e)
+        # one tie resolved the other way in the second pass changes M by that
+        # signal's terms, which cond(M) ~ 6e4 amplifies: D2 is compared only
+        # when every pick of the second pass agrees
+        if e["ties"] == 0:
+            assert e["D2_abs"] < 1e-3, (name, e)
     assert rows["bf16_norescore"]["exact"] < rows["bf16"]["exact"], rows
