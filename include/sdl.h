@@ -271,13 +271,16 @@ int sdl_gemm_bf16(sdl_ctx* ctx, const void* A, int lda, const void* B, int ldb, 
  *    Kronecker dictionary D2 (x) D1 (Sec. I), FP32 accumulation.  Every entry
  *    is within 2^-7 (1.03) ||Y_k||_F of its FP32 value; at every greedy step
  *    each entry that close to the running maximum is re-scored in FP32
- *    (d1_i^T Y_k d2_j), so the picks are FP32 picks.  The Gram-domain updates,
+ *    ((d1_i^T Y_k) d2_j, from the rows of D1^T Y_k formed once per signal),
+ *    so the picks are FP32 picks.  The Gram-domain updates,
  *    the Cholesky factor and the partial sums stay FP32.  Needs p1*p2 a
  *    multiple of 8; uses N x n1n2 FP32 of workspace.
  *  SDL_PREC_NO_RESCORE: with BF16_CORR, skip the re-scoring (pure BF16 picks;
  *    for precision studies).
- *  SDL_PREC_FP64_SOLVE: the normal-equation solves, the objective decrease and
- *    the atom renormalisation in FP64 (partial sums stay FP32).
+ *  SDL_PREC_FP64_SOLVE: the normal-equation solves, the objective change and
+ *    the atom renormalisation in FP64 (partial sums stay FP32); a pivot is
+ *    rejected (SDL_ERR_SINGULAR) below 1e-12 of its diagonal entry instead of
+ *    the FP32 solve's 1e-7.
  */
 #define SDL_PREC_FP32 0
 #define SDL_PREC_BF16_CORR 1
@@ -339,16 +342,24 @@ int sdl_mlp_forward(sdl_mlp* mlp, const float* Y, int64_t N, float* scores, void
  *   3. a signal is flagged when some check-set pair correlates with the final
  *      residual more strongly than 0.7 x the weakest greedy score of its picks,
  *      or its data is not finite; flagged signals are coded again by the full
- *      coder.
- * Outputs as sdl_sparse_code plus fallback[N] (1 = re-coded) and device
- * int n_fallback[1].  Compiled for (p1,p2,n1,n2,s_max) = (12,12,24,24,6) and
- * (8,8,16,16,4); the network must match the shape.
+ *      coder;
+ *   4. the full coder also codes a strided sample of max(4096, N/16) signals
+ *      (all of them when N is smaller) and judges the learned codes there: if
+ *      their RMSE on the sample exceeds the full coder's by more than 1 %,
+ *      every signal is coded again by the full coder (fallback[] all 1,
+ *      n_fallback = N).
+ * Outputs as sdl_sparse_code plus fallback[N] (1 = re-coded), device
+ * int n_fallback[1] and guard_out: NULL or device float[3] = {RMSE of the
+ * learned codes on the sample (after step 3), RMSE of the full coder there,
+ * 1 if step 4 re-coded everything else 0}.  N <= 2^31 - 1.  Compiled for
+ * (p1,p2,n1,n2,s_max) = (12,12,24,24,6) and (8,8,16,16,4); the network must
+ * match the shape.
  */
 int sdl_sparse_code_learned(sdl_ctx* ctx, sdl_mlp* mlp, const float* Y, int p1, int p2,
                             int64_t N, const float* D1, int n1, const float* D2, int n2,
                             int s_max, int k, int32_t* support, float* coef, int32_t* nnz,
                             float* res_energy, int32_t* fallback, int32_t* n_fallback,
-                            void* stream);
+                            float* guard_out, void* stream);
 
 /*
  * sdl_sparse_code_static - the sparse coder of sdl_sparse_code with no

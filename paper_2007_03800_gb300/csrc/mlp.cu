@@ -445,6 +445,70 @@ __global__ void write_index_kernel(const int32_t* __restrict__ flag, long long N
     if (f) idx[blockoff[blockIdx.x] + woff[w] + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
+// ---------------------------------------------------------------- RMSE guard
+// The plain coder judges the learned one on a strided sample of the signals:
+// if the learned codes' RMSE there exceeds the plain coder's by more than 1 %,
+// every signal is coded again by the plain coder.
+constexpr double kGuardRmseRatio = 1.01;
+constexpr int kGuardThreads = 1024;
+constexpr long long kGuardMinSample = 4096;
+
+__global__ void sample_index_kernel(int32_t* __restrict__ idx, int m, long long stride,
+                                    int* __restrict__ count) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < m) idx[r] = (int32_t)(r * stride);
+    if (r == 0) *count = m;
+}
+
+// fixed-order FP64 sums of the two residual energies over the sample
+__global__ void __launch_bounds__(kGuardThreads)
+    guard_kernel(const float* __restrict__ plainE, const float* __restrict__ learnedE,
+                 const int32_t* __restrict__ idx, int m, long long N, int P, int* __restrict__ recode_count,
+                 int32_t* __restrict__ n_fallback, float* __restrict__ guard_out) {
+    __shared__ double sp[kGuardThreads / 32], sl[kGuardThreads / 32];
+    double a = 0.0, b = 0.0;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        a += (double)plainE[r];
+        b += (double)learnedE[idx[r]];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(kFull, a, o);
+        b += __shfl_down_sync(kFull, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sp[threadIdx.x >> 5] = a;
+        sl[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < kGuardThreads / 32; ++w) {
+            ta += sp[w];
+            tb += sl[w];
+        }
+        const bool fail = tb > kGuardRmseRatio * kGuardRmseRatio * ta;
+        *recode_count = fail ? (int)N : 0;
+        if (fail) *n_fallback = (int32_t)N;
+        if (guard_out) {
+            const double scale = 1.0 / ((double)m * P);
+            guard_out[0] = (float)sqrt(tb * scale);
+            guard_out[1] = (float)sqrt(ta * scale);
+            guard_out[2] = fail ? 1.f : 0.f;
+        }
+    }
+}
+
+__global__ void mark_all_kernel(const int* __restrict__ recode_count, long long N,
+                                int32_t* __restrict__ idx, int32_t* __restrict__ fallback) {
+    if (*recode_count == 0) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        idx[i] = (int32_t)i;
+        fallback[i] = 1;
+    }
+}
+
 template <class T>
 T* carve(char*& p, size_t n) {
     T* r = reinterpret_cast<T*>(p);
@@ -686,9 +750,9 @@ extern "C" int sdl_sparse_code_learned(sdl_ctx* c, sdl_mlp* m, const float* Y, i
                                        int64_t N, const float* D1, int n1, const float* D2, int n2,
                                        int s_max, int k, int32_t* support, float* coef,
                                        int32_t* nnz, float* res_energy, int32_t* fallback,
-                                       int32_t* n_fallback, void* stream) {
+                                       int32_t* n_fallback, float* guard_out, void* stream) {
     if (!c || !m || m->ctx != c || !Y || !D1 || !D2 || !support || !coef || !nnz || !fallback ||
-        !n_fallback || N < 1)
+        !n_fallback || N < 1 || N > 0x7fffffffLL)
         return SDL_ERR_ARG;
     if (m->P != p1 * p2 || m->Q != n1 * n2 || k < 1 || k > 32) return SDL_ERR_ARG;
     const bool shape_a = p1 == 12 && p2 == 12 && n1 == 24 && n2 == 24 && s_max == 6;
@@ -700,9 +764,12 @@ extern "C" int sdl_sparse_code_learned(sdl_ctx* c, sdl_mlp* m, const float* Y, i
     // workspace: scores of one chunk, candidates, Grams, scan buffers, index list
     const long long chunk = m->Bmax;
     const int nblk = (int)((N + kScanBlock - 1) / kScanBlock);
+    const long long m_s = std::min<long long>(N, std::max<long long>(kGuardMinSample, N / 16));
+    const long long stride_s = N / m_s;
     const size_t need = sizeof(float) * (size_t)chunk * Q + sizeof(int32_t) * (size_t)N * k2 +
                         sizeof(float) * (size_t)(n1 * n1 + n2 * n2) + sizeof(int) * (nblk + 8) +
-                        sizeof(int32_t) * (size_t)N + 5 * 256;
+                        sizeof(int32_t) * (size_t)N + sizeof(int32_t) * (size_t)m_s +
+                        sizeof(float) * (size_t)m_s + sizeof(float) * (size_t)N + 10 * 256;
     if (need > c->cap_learn) {
         if (c->learn) cudaFree(c->learn);
         c->learn = nullptr;
@@ -720,6 +787,10 @@ extern "C" int sdl_sparse_code_learned(sdl_ctx* c, sdl_mlp* m, const float* Y, i
     float* G2 = carve<float>(p, (size_t)n2 * n2);
     int* blockcnt = carve<int>(p, nblk + 8);
     int32_t* idx = carve<int32_t>(p, (size_t)N);
+    int32_t* idx_s = carve<int32_t>(p, (size_t)m_s);
+    float* plainE = carve<float>(p, (size_t)m_s);
+    float* learnedE = res_energy ? res_energy : carve<float>(p, (size_t)N);
+    int* cnt_s = carve<int>(p, 2);
     int rc;
     {
         Trace tr(c, kGram, st);
@@ -741,10 +812,10 @@ extern "C" int sdl_sparse_code_learned(sdl_ctx* c, sdl_mlp* m, const float* Y, i
     {
         Trace tr(c, kShortlist, st);
         rc = shape_a ? launch_shortlist<12, 12, 24, 24, 6>(Y, N, D1, D2, G1, G2, cand, k, k2, support,
-                                                          coef, nnz, res_energy, fallback,
+                                                          coef, nnz, learnedE, fallback,
                                                           c->num_sms, st)
                      : launch_shortlist<8, 8, 16, 16, 4>(Y, N, D1, D2, G1, G2, cand, k, k2, support,
-                                                        coef, nnz, res_energy, fallback, c->num_sms,
+                                                        coef, nnz, learnedE, fallback, c->num_sms,
                                                         st);
         if (rc) return rc;
     }
@@ -767,12 +838,40 @@ extern "C" int sdl_sparse_code_learned(sdl_ctx* c, sdl_mlp* m, const float* Y, i
     a.support = support;
     a.coef = coef;
     a.nnz = nnz;
-    a.res_energy = res_energy;
+    a.res_energy = learnedE;
     a.n_slots = 1;
     a.err = c->err;
     a.idx = idx;
     a.idx_count = n_fallback;
-    Trace tr(c, kCode, st);
-    rc = launch_code_pass_fast(a, kCodeOnly, st, c->num_sms);
+    {
+        Trace tr(c, kCode, st);
+        rc = launch_code_pass_fast(a, kCodeOnly, st, c->num_sms);
+        if (rc < 0) return rc;
+    }
+    // 4. the plain coder on the strided sample (residual energies only)
+    sample_index_kernel<<<blocks_for(m_s, 256), 256, 0, st>>>(idx_s, (int)m_s, stride_s, cnt_s);
+    PassArgs g = a;
+    g.support = nullptr;
+    g.coef = nullptr;
+    g.nnz = nullptr;
+    g.res_energy = plainE;
+    g.idx = idx_s;
+    g.idx_count = cnt_s;
+    g.idx_compact = 1;
+    {
+        Trace tr(c, kCode, st);
+        rc = launch_code_pass_fast(g, kCodeOnly, st, c->num_sms);
+        if (rc < 0) return rc;
+    }
+    // 5. RMSE guard; when it trips, every signal is coded again by the plain coder
+    guard_kernel<<<1, kGuardThreads, 0, st>>>(plainE, learnedE, idx_s, (int)m_s, N, p1 * p2,
+                                              cnt_s + 1, n_fallback, guard_out);
+    mark_all_kernel<<<std::max(1, std::min(blocks_for(N, 256), c->num_sms * 8)), 256, 0, st>>>(
+        cnt_s + 1, N, idx, fallback);
+    a.idx_count = cnt_s + 1;
+    {
+        Trace tr(c, kCode, st);
+        rc = launch_code_pass_fast(a, kCodeOnly, st, c->num_sms);
+    }
     return rc < 0 ? rc : SDL_OK;
 }

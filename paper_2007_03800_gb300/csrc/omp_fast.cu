@@ -448,13 +448,14 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
         }
 
         // ---- emit the code (lane l holds pick l)
+        const long long ko = (a.idx && a.idx_compact) ? j : k;
         if (a.support && lane < S) {
-            a.support[(size_t)k * S + lane] = (lane < cnt) ? myi + N1 * myj : -1;
-            a.coef[(size_t)k * S + lane] = (lane < cnt) ? myx : 0.f;
+            a.support[(size_t)ko * S + lane] = (lane < cnt) ? myi + N1 * myj : -1;
+            a.coef[(size_t)ko * S + lane] = (lane < cnt) ? myx : 0.f;
         }
         if (lane == 0) {
-            if (a.nnz) a.nnz[k] = cnt;
-            if (a.res_energy) a.res_energy[k] = finite ? fmaxf(E2, 0.f) : __int_as_float(0x7fc00000);
+            if (a.nnz) a.nnz[ko] = cnt;
+            if (a.res_energy) a.res_energy[ko] = finite ? fmaxf(E2, 0.f) : __int_as_float(0x7fc00000);
             if (!finite) record_error(a.err, SDL_ERR_NONFINITE);
         }
 

@@ -51,6 +51,7 @@ struct PassArgs {
     int* err;
     const int32_t* idx;   // optional: code only the signals idx[0 .. *idx_count)
     const int* idx_count; //   (specialised kernels only; device count)
+    int idx_compact;      // with idx: outputs at list position j, not at idx[j]
     // optional correlations C0 from outside (BF16 tensor-core path), N x ldc0
     // FP32 with entry q = i + n1*j, each within c0_err_rel * ||Y_k|| of the
     // FP32 value; entries near the running maximum are re-scored in FP32

@@ -329,6 +329,10 @@ __global__ void __launch_bounds__(kSolveThreads) solve_multi_kernel(const SolveD
 // the normal matrix, its inverse, D*, the objective change and the column
 // norms in double precision (inputs are the FP32 partial sums).
 constexpr int kSolve64Threads = 512;
+// FP64 elimination of the FP32 normal matrix: a pivot is rejected only when
+// it is at the level of the FP64 rounding of the diagonal (the FP32 solve
+// rejects at 1e-7, its own rounding level)
+constexpr double kSolvePivotRel64 = 1e-12;
 
 __global__ void __launch_bounds__(kSolve64Threads)
     solve64_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D,
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(kSolve64Threads)
     __syncthreads();
     for (int k = 0; k < nu && s_fail == 0; ++k) {
         const double piv = A[k * lda + k];
-        if (!(piv > (double)kSolvePivotRel * d0[k])) {
+        if (!(piv > kSolvePivotRel64 * d0[k])) {
             __syncthreads();
             if (tid == 0) s_fail = SDL_ERR_SINGULAR;
             __syncthreads();

@@ -33,20 +33,28 @@ def fresh_signals(N, p, n, s, snr_db=20.0, seed=52, device="cuda:0"):
     return sdl.signals(torch.tensor(Y, dtype=torch.float32, device=device))
 
 
-def train(mlp: sdl.MLP, Y, labels: sdl.Codes, epochs=3, batch=4096, lr=2e-3, stream=None):
-    """Adam over contiguous batches (the generator's signals are i.i.d.).
+def train(mlp: sdl.MLP, Y, labels: sdl.Codes, epochs=3, batch=4096, lr=2e-3, cosine=False,
+          stream=None):
+    """Adam over contiguous batches (the generator's signals are i.i.d.),
+    optionally with a cosine decay of the step size over all steps.
     Returns the mean loss of every epoch."""
+    import math
     N = Y.shape[0]
     loss = torch.zeros(1, dtype=torch.float32, device=Y.device)
     hist = []
+    per_epoch = max((N - batch) // batch + 1, 0)
+    total = max(epochs * per_epoch, 1)
+    step = 0
     for _ in range(epochs):
         acc = torch.zeros(1, dtype=torch.float32, device=Y.device)
         nb = 0
         for a in range(0, N - batch + 1, batch):
-            mlp.train_step(Y[a:a + batch], labels.support[a:a + batch], lr, loss_out=loss,
+            lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * step / total)) if cosine else lr
+            mlp.train_step(Y[a:a + batch], labels.support[a:a + batch], lr_t, loss_out=loss,
                            stream=stream)
             acc += loss
             nb += 1
+            step += 1
         hist.append((acc / max(nb, 1)).item())
     return hist
 
@@ -54,7 +62,9 @@ def train(mlp: sdl.MLP, Y, labels: sdl.Codes, epochs=3, batch=4096, lr=2e-3, str
 def compare(ctx: sdl.Context, mlp: sdl.MLP, Y, D1, D2, s, k=32, reps=3):
     """Learned coder vs plain coder on the same signals: RMSE of both (from
     the least-squares residual energies), fallback rate, share of signals
-    with identical codes, and device time of each (CUDA events, best of reps)."""
+    with identical codes, the guard's view of its judging sample (learned and
+    plain RMSE there, whether it re-coded everything), and device time of
+    each (CUDA events, best of reps)."""
     N, p1, p2 = Y.shape
 
     def timed(fn):
@@ -71,13 +81,16 @@ def compare(ctx: sdl.Context, mlp: sdl.MLP, Y, D1, D2, s, k=32, reps=3):
         return out, best
 
     plain, t_plain = timed(lambda: ctx.sparse_code(Y, D1, D2, s))
-    (learned, flags, nfb), t_learned = timed(lambda: mlp.sparse_code(Y, D1, D2, s, k=k))
+    (learned, flags, nfb, guard), t_learned = timed(lambda: mlp.sparse_code(Y, D1, D2, s, k=k))
     ctx.check()
     scale = p1 * p2 * N
     rmse_plain = (plain.res_energy.double().sum() / scale).sqrt().item()
     rmse_learned = (learned.res_energy.double().sum() / scale).sqrt().item()
     same = (learned.support == plain.support).all(dim=1).double().mean().item()
+    g = guard.tolist()
     return dict(rmse_plain=rmse_plain, rmse_learned=rmse_learned,
                 rmse_gap=rmse_learned / rmse_plain - 1.0,
                 fallback_rate=nfb.item() / N, identical_codes=same,
+                guard_sample_rmse_learned=g[0], guard_sample_rmse_plain=g[1],
+                guard_sample_gap=g[0] / g[1] - 1.0 if g[1] > 0 else 0.0, guard_tripped=bool(g[2]),
                 ms_plain=t_plain, ms_learned=t_learned, speedup=t_plain / t_learned, N=N)

@@ -62,7 +62,7 @@ SIGNATURES = {
     "sdl_mlp_gradients": [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P, _P],
     "sdl_mlp_forward": [_P, _P, _L, _P, _P],
     "sdl_sparse_code_learned": [_P, _P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P,
-                                _P, _P, _P],
+                                _P, _P, _P, _P],
     "sdl_set_precision": [_P, _I],
     "sdl_precision_stats": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "sdl_profile_enable": [_P, _I],
@@ -491,18 +491,21 @@ class MLP:
         return out
 
     def sparse_code(self, Y, D1, D2, s, k=32, out: Codes | None = None, stream=None):
-        """``sdl_sparse_code_learned``: returns (codes, fallback flags, n_fallback)."""
+        """``sdl_sparse_code_learned``: returns (codes, fallback flags, n_fallback,
+        guard) with guard = device float[3]: the learned and the full coder's RMSE
+        on the judging sample, and 1.0 when the guard re-coded every signal."""
         N, p1, p2 = _check_Y(Y)
         n1, n2 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2")
         if out is None:
             out = Codes.empty(N, s, Y.device, with_energy=True)
         flags = torch.empty(N, dtype=torch.int32, device=Y.device)
         nfb = torch.zeros(1, dtype=torch.int32, device=Y.device)
+        guard = torch.zeros(3, dtype=torch.float32, device=Y.device)
         _check(self._lib.sdl_sparse_code_learned(
             self.ctx._h, self._h, _ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2, s, k,
             _ptr(out.support), _ptr(out.coef), _ptr(out.nnz), _ptr(out.res_energy), _ptr(flags),
-            _ptr(nfb), _stream(stream)), "sdl_sparse_code_learned")
-        return out, flags, nfb
+            _ptr(nfb), _ptr(guard), _stream(stream)), "sdl_sparse_code_learned")
+        return out, flags, nfb, guard
 
     def close(self):
         if getattr(self, "_h", None):

@@ -75,3 +75,33 @@ def test_training_lowers_loss_and_beats_untrained_network(gpu_ctx):
     assert after["rmse_gap"] < 0.01, after
     net.close()
     untrained.close()
+
+
+def test_rmse_guard_recodes_everything_when_the_shortlists_miss(gpu_ctx):
+    """A network that proposes the same pairs for every signal (zero output
+    weights, fixed biases), with a shortlist shorter than s (k = 2 < s = 4):
+    the shortlist coder ends every signal after two picks, which the
+    per-signal check does not judge (it judges complete codes).  The full
+    coder, judging a strided sample, must then re-code every signal, so the
+    result equals the plain coder's bit for bit."""
+    p, n, s = 8, 16, 4
+    N = 20000
+    Y, D1g, D2g, _ = learned.kron_problem(gpu_ctx, 8192, p, n, s, dl_iterations=2)
+    Yt = learned.fresh_signals(N, p, n, s)
+    plain = gpu_ctx.sparse_code(Yt, D1g, D2g, s)
+    net = sdl.MLP(gpu_ctx, p, p, n, n, hidden=64, max_batch=4096)
+    rng = np.random.default_rng(0)
+    net.set_weights(rng.standard_normal((64, p * p)) * 0.1, np.zeros(64),
+                    np.zeros((n * n, 64)), -np.arange(n * n, dtype=np.float64))
+    codes, flags, nfb, guard = net.sparse_code(Yt, D1g, D2g, s, k=2)
+    gpu_ctx.check()
+    g = guard.cpu().numpy()
+    assert g[2] == 1.0 and g[0] > 1.01 * g[1], g
+    assert nfb.item() == N and bool((flags == 1).all())
+    assert torch.equal(codes.support, plain.support) and torch.equal(codes.coef, plain.coef)
+    # the judging sample: every (N // m)-th signal, m = max(4096, N // 16)
+    m = max(4096, N // 16)
+    rows = np.arange(m) * (N // m)
+    e = plain.res_energy.double().cpu().numpy()[rows]
+    assert abs(g[1] - np.sqrt(e.sum() / (m * p * p))) < 1e-5 * g[1]
+    net.close()
