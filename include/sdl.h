@@ -267,14 +267,17 @@ int sdl_gemm_bf16(sdl_ctx* ctx, const void* A, int lda, const void* B, int ldb, 
 /*
  * Precision modes (an extension beyond the paper; default SDL_PREC_FP32).
  *  SDL_PREC_BF16_CORR: the correlations C0 = D1^T Y_k D2 of a coding pass come
- *    from ONE BF16 tensor-core GEMM of the vectorised signals with the
- *    Kronecker dictionary D2 (x) D1 (Sec. I), FP32 accumulation.  Every entry
- *    is within 2^-7 (1.03) ||Y_k||_F of its FP32 value; at every greedy step
- *    each entry that close to the running maximum is re-scored in FP32
+ *    from ONE tensor-core GEMM of the vectorised signals with the Kronecker
+ *    dictionary D2 (x) D1 (Sec. I): both operands split into BF16 high and
+ *    low parts, the three products hi*hi + hi*lo + lo*hi summed in one FP32
+ *    accumulator.  Every entry is within
+ *    e(p1 p2) = (3 + 1/64) 2^-16 + 2^-24 + 3 Kp 2^-23 (Kp = p1 p2 rounded up
+ *    to 8) times ||Y_k||_F of its exact value; at every greedy step each
+ *    entry within 2 e ||Y_k||_F of the running maximum is re-scored in FP32
  *    ((d1_i^T Y_k) d2_j, from the rows of D1^T Y_k formed once per signal),
- *    so the picks are FP32 picks.  The Gram-domain updates,
- *    the Cholesky factor and the partial sums stay FP32.  Needs p1*p2 a
- *    multiple of 8; uses N x n1n2 FP32 of workspace.
+ *    so the picks are FP32 picks.  The Gram-domain updates, the Cholesky
+ *    factor and the partial sums stay FP32.  Uses N x n1n2 FP32 and
+ *    2 (N + n1n2) x Kp BF16 of workspace.
  *  SDL_PREC_NO_RESCORE: with BF16_CORR, skip the re-scoring (pure BF16 picks;
  *    for precision studies).
  *  SDL_PREC_FP64_SOLVE: the normal-equation solves, the objective change and

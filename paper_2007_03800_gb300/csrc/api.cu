@@ -87,14 +87,13 @@ void grams(sdl_ctx* c, const float* D1, int p1, int n1, const float* D2, int p2,
 
 // Tensor-core correlations for a coding pass (precision extension): fills
 // ctx->C0 and points the pass at it.
-constexpr float kC0ErrRel = 0.0081f;   // 2^-7 (1 + 3%): BF16 operands, FP32 accumulation
-
 int prepare_tc_pass(sdl_ctx* c, PassArgs& a, bool fill_y, cudaStream_t st) {
     const long long N = a.N;
     const int Kp = (a.p1 * a.p2 + 7) & ~7, Q = a.n1 * a.n2;
     int rc;
-    if ((rc = grow(reinterpret_cast<char*&>(c->Yb), c->cap_yb, (size_t)N * Kp * 2)) != SDL_OK) return rc;
-    if ((rc = grow(reinterpret_cast<char*&>(c->KT), c->cap_kt, (size_t)Q * Kp * 2)) != SDL_OK) return rc;
+    // hi and lo BF16 parts of the signals and of the Kronecker dictionary
+    if ((rc = grow(reinterpret_cast<char*&>(c->Yb), c->cap_yb, (size_t)N * Kp * 4)) != SDL_OK) return rc;
+    if ((rc = grow(reinterpret_cast<char*&>(c->KT), c->cap_kt, (size_t)Q * Kp * 4)) != SDL_OK) return rc;
     if ((rc = grow(c->C0, c->cap_c0, (size_t)N * Q)) != SDL_OK) return rc;
     if (!c->rescored) {
         if (cudaMalloc(&c->rescored, sizeof(unsigned long long)) != cudaSuccess) return SDL_ERR_WORKSPACE;
@@ -109,7 +108,7 @@ int prepare_tc_pass(sdl_ctx* c, PassArgs& a, bool fill_y, cudaStream_t st) {
     if (rc) return rc;
     a.c0ext = c->C0;
     a.ldc0 = Q;
-    a.c0_err_rel = (c->prec & SDL_PREC_NO_RESCORE) ? 0.f : kC0ErrRel;
+    a.c0_err_rel = (c->prec & SDL_PREC_NO_RESCORE) ? 0.f : c0_split_err_rel(a.p1 * a.p2);
     a.rescored = c->rescored;
     return SDL_OK;
 }

@@ -142,7 +142,9 @@ int launch_solve64(const float* red_f, const double* red_d, float* D, int p, int
 }  // namespace sdl
 #include <cuda_bf16.h>
 namespace sdl {
-// precision.cu: C0 of N signals by one BF16 tensor-core GEMM (FP32 out, N x n1n2)
+// precision.cu: C0 of N signals by one split-BF16 tensor-core GEMM (FP32 out,
+// N x n1n2); every entry within c0_split_err_rel(p1 p2) ||Y_k||_F of exact
+float c0_split_err_rel(int p1p2);
 int tc_correlations(const float* Y, long long N, int p1, int p2, const float* D1, int n1,
                     const float* D2, int n2, __nv_bfloat16* Yb, bool fill_y, __nv_bfloat16* KT,
                     float* C0, int* err, cudaStream_t st);
@@ -153,6 +155,12 @@ int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
             const float* bias, int act, float* C, int ldc, int accumulate, void* Cb, int ldcb,
             void* Ct, int ldct, float* pre, int ldpre, int* err, cudaStream_t st,
             const float* gin = nullptr, int ldgin = 0);
+// The same with the sum of `terms` (1..3) operand pairs in one accumulator:
+// C = alpha sum_t A[t] B[t]^T (...), all pairs with the shapes and strides given.
+int tc_gemm_terms(const void* const* A, int lda, const void* const* B, int ldb, int terms, int M,
+                  int N, int K, float alpha, const float* bias, int act, float* C, int ldc,
+                  int accumulate, void* Cb, int ldcb, void* Ct, int ldct, float* pre, int ldpre,
+                  int* err, cudaStream_t st, const float* gin = nullptr, int ldgin = 0);
 
 // Record the first device-side error (first writer wins).
 __device__ __forceinline__ void record_error(int* err, int code) {

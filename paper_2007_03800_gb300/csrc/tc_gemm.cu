@@ -1,24 +1,35 @@
-// BF16 tensor-core GEMM for sm_103a: C = alpha * A B^T (+ bias, activation),
-// A (M x K) and B (N x K) row-major with K contiguous, FP32 accumulation.
+// BF16 tensor-core GEMM for sm_103a: C = alpha * sum_t A_t B_t^T (+ bias,
+// activation), A_t (M x K) and B_t (N x K) row-major with K contiguous,
+// FP32 accumulation; t runs over 1 to 3 operand pairs summed into one
+// accumulator (the split-precision products of the correlation path).
 //
-// Blackwell path: operand tiles arrive by TMA (cp.async.bulk.tensor, 128-byte
-// swizzle) into a 4-stage shared-memory ring guarded by mbarriers; one
-// thread issues tcgen05.mma (128 x 128 x 16 per instruction) into a 128 x 128
-// FP32 accumulator in tensor memory; tcgen05.commit releases ring stages back
-// to the producer; the four warps then read the accumulator with tcgen05.ld
-// (warp w owns TMEM lanes 32w..32w+31 = output rows) and apply the epilogue.
-// Row-major outputs (and the GELU-derivative input) pass through a per-warp
-// 32 x 33 shared-memory transpose, so that every global access of the
-// epilogue is a coalesced 128-byte row segment.  Two CTAs share an SM, so
-// one CTA's epilogue overlaps the other's main loop.
-// Every wait is bounded: on a timeout the CTA records SDL_ERR_TIMEOUT, lets
-// its in-flight copies land and frees its tensor memory.
+// Blackwell path, persistent and warp-specialised (one CTA per SM, 192
+// threads):
+//   warp 0  TMA producer: operand tiles by cp.async.bulk.tensor (128-byte
+//           swizzle) into a 4-stage shared-memory ring guarded by mbarriers;
+//   warp 1  MMA issuer: one thread issues tcgen05.mma (128 x 128 x 16) into
+//           one of two 128-column FP32 accumulators in tensor memory;
+//           tcgen05.commit releases ring stages and hands a finished
+//           accumulator to the epilogue;
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//           lanes 32 (w % 4) .. +31 = output rows), bias / GELU / GELU'
+//           and the outputs, row-major ones through a per-warp 32 x 33
+//           shared-memory transpose so that every global access is a
+//           coalesced 128-byte row segment.
+// With two accumulators the epilogue of one tile overlaps the main loop of
+// the next.  Tiles are visited m-block-major, so CTAs running at the same
+// time share A rows and the whole of B in L2.
+// Every wait is bounded (clock-based limit) and also ends when another role
+// has failed: the CTA then records SDL_ERR_TIMEOUT, lets its copies land and
+// frees its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "ctx.cuh"
 
@@ -26,16 +37,19 @@ using namespace sdl;
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3, UMMA_K = 16;
-constexpr int kStageLd = 33;   // epilogue transpose row stride (floats)
-constexpr int TILE_A = BM * BK * 2;   // bytes
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, UMMA_K = 16;
+constexpr int kMaxTerms = 3;
+constexpr int kThreads = 192;
+constexpr int kEpiWarps = 4;
+constexpr int kStageLd = 33;                  // epilogue transpose row stride (floats)
+constexpr int TILE_A = BM * BK * 2;           // bytes
 constexpr int TILE_B = BN * BK * 2;
-constexpr long long kSpin = 1ll << 26;
+constexpr long long kWaitCycles = 1ll << 31;  // about one second at 2 GHz
 
 struct Epi {
     float alpha;
     const float* bias;   // [N] or null
-    int act;             // 0 none, 1 GELU (erf form)
+    int act;             // 0 none, 1 GELU (erf form), 2 times GELU'(gin)
     float* C;            // FP32 output or null
     int ldc;
     int accumulate;      // C += result
@@ -49,6 +63,11 @@ struct Epi {
     int ldgin;
 };
 
+struct Maps {
+    CUtensorMap a[kMaxTerms];
+    CUtensorMap b[kMaxTerms];
+};
+
 __device__ __forceinline__ uint32_t saddr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -59,19 +78,38 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bounded wait; false on timeout or when *fail is set by another role
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* fail) {
     const uint32_t a = saddr(b);
-    for (long long i = 0; i < kSpin; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_test(a, parity)) return true;
+        if (*fail) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *fail = 1;
+            return false;
+        }
     }
-    return false;
+}
+// bounded wait used only to let copies land before exit
+__device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t parity) {
+    const uint32_t a = saddr(b);
+    const long long t0 = clock64();
+    while (!mbar_test(a, parity) && clock64() - t0 < kWaitCycles) {
+    }
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* bar) {
@@ -98,34 +136,59 @@ __host__ __device__ constexpr uint32_t instr_desc() {
            ((uint32_t)(BM >> 4) << 24);
 }
 
-__global__ void __launch_bounds__(128, 2)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   int M, int N, int K, Epi epi, int* err) {
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+        "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+        "%26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ Maps maps, int terms, int M, int N, int K, Epi epi,
+                   int* err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~uintptr_t(1023));
     uint8_t* sA = base;
     uint8_t* sB = base + STAGES * TILE_A;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * TILE_B);
+    float* stage_all = reinterpret_cast<float*>(sB + STAGES * TILE_B);
+    uint64_t* full = reinterpret_cast<uint64_t*>(stage_all + kEpiWarps * 32 * kStageLd);
     uint64_t* empty = full + STAGES;
-    uint64_t* accb = empty + STAGES;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+    uint64_t* acc_full = empty + STAGES;      // [2] MMA -> epilogue
+    uint64_t* acc_empty = acc_full + 2;       // [2] epilogue -> MMA
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    __shared__ int s_fail;
+    volatile int* fail = &s_fail;
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nk = (K + BK - 1) / BK;
+    const int ksteps = nk * terms;             // k-blocks per tile, all terms
+    const int nt = (N + BN - 1) / BN;
+    const long long tiles = (long long)((M + BM - 1) / BM) * nt;
 
     if (threadIdx.x == 0) {
+        s_fail = 0;
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kEpiWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          saddr(tslot)),
-                     "r"(BN)
+                     "r"(2 * BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -133,167 +196,177 @@ __global__ void __launch_bounds__(128, 2)
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    __shared__ int s_fail;
-    if (threadIdx.x == 0) s_fail = 0;
-    __syncthreads();
-
-    if (warp == 0 && lane == 0) {
-        // ---- TMA producer
-        int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
-                s_fail = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer
+            long long g = 0;   // k-blocks issued so far (ring position)
+            for (long long t = blockIdx.x; t < tiles && !*fail; t += gridDim.x) {
+                const int m0 = (int)(t / nt) * BM, n0 = (int)(t % nt) * BN;
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    const int s = (int)(g % STAGES);
+                    const long long use = g / STAGES;
+                    if (use > 0 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), fail)) break;
+                    const int term = ks / nk, kb = ks - term * nk;
+                    mbar_arrive_tx(&full[s], TILE_A + TILE_B);
+                    tma_load_2d(sA + s * TILE_A, &maps.a[term], kb * BK, m0, &full[s]);
+                    tma_load_2d(sB + s * TILE_B, &maps.b[term], kb * BK, n0, &full[s]);
+                    ++g;
+                }
             }
-            mbar_arrive_tx(&full[s], TILE_A + TILE_B);
-            tma_load_2d(sA + s * TILE_A, &tmA, kb * BK, m0, &full[s]);
-            tma_load_2d(sB + s * TILE_B, &tmB, kb * BK, n0, &full[s]);
-            ++issued;
-        }
-        if (s_fail) {
-            // let the copies already issued land before shared memory is released
-            for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; ++kb)
-                mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer
-        const uint32_t idesc = instr_desc();
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
-                s_fail = 1;
-                break;
+            if (*fail) {
+                // let the copies in flight land before shared memory is released
+                for (long long h = g - STAGES > 0 ? g - STAGES : 0; h < g; ++h)
+                    mbar_drain(&full[h % STAGES], (uint32_t)((h / STAGES) & 1));
             }
-            tc_fence_after();
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            const uint32_t idesc = instr_desc();
+            long long g = 0;
+            int i = 0;   // local tile counter
+            for (long long t = blockIdx.x; t < tiles && !*fail; t += gridDim.x, ++i) {
+                const int b = i & 1, use_b = i >> 1;
+                if (use_b > 0 && !mbar_wait(&acc_empty[b], (uint32_t)((use_b - 1) & 1), fail)) break;
+                tc_fence_after();
+                const uint32_t acc_addr = tmem + (uint32_t)(b * BN);
+                bool ok = true;
+                for (int ks = 0; ks < ksteps; ++ks, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (!mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1), fail)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
 #pragma unroll
-            for (int kk = 0; kk < BK / UMMA_K; ++kk) {
-                const uint64_t ad = smem_desc(sA + s * TILE_A + kk * UMMA_K * 2);
-                const uint64_t bd = smem_desc(sB + s * TILE_B + kk * UMMA_K * 2);
-                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                        const uint64_t ad = smem_desc(sA + s * TILE_A + kk * UMMA_K * 2);
+                        const uint64_t bd = smem_desc(sB + s * TILE_B + kk * UMMA_K * 2);
+                        const uint32_t accum = (ks > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                acc_addr),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                            : "memory");
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+                        "[%0];" ::"r"(saddr(&empty[s]))
+                        : "memory");
+                }
+                if (!ok) break;
                 asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        saddr(&acc_full[b]))
                     : "memory");
             }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    saddr(&empty[s]))
-                : "memory");
         }
-        if (!s_fail)
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    saddr(accb))
-                : "memory");
-    }
-    __syncwarp();
-    __syncthreads();   // s_fail is final here (the MMAs themselves may still run)
-
-    // ---- epilogue: thread = output row, 32 accumulator columns per load.
-    // The operand ring is idle once the accumulator barrier has fired (every
-    // MMA, hence every copy it consumed, has completed): it holds the
-    // per-warp transpose buffers.
-    const bool got = !s_fail && mbar_wait(accb, 0);
-    tc_fence_after();
-    const int r = warp * 32 + lane;
-    const int m = m0 + r;
-    float* stage = reinterpret_cast<float*>(sA) + warp * 32 * kStageLd;
-    // row-major [m, n] block of 32 rows (this warp) x 32 columns: lane holds
-    // row `lane`; stored (or added) one coalesced row segment at a time
-    auto store_rows = [&](const float (&x)[32], int c0, float* dst, int ld, int accumulate) {
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) stage[lane * kStageLd + j] = x[j];
-        __syncwarp();
-        const int n = n0 + c0 + lane;
-        for (int rr = 0; rr < 32; ++rr) {
-            const int mm = m0 + warp * 32 + rr;
-            if (mm < M && n < N) {
-                float* d = dst + (size_t)mm * ld + n;
-                const float val = stage[rr * kStageLd + lane];
-                *d = accumulate ? *d + val : val;
-            }
-        }
-    };
-    auto store_rows_bf16 = [&](const float (&x)[32], int c0, __nv_bfloat16* dst, int ld) {
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) stage[lane * kStageLd + j] = x[j];
-        __syncwarp();
-        const int n = n0 + c0 + lane;
-        for (int rr = 0; rr < 32; ++rr) {
-            const int mm = m0 + warp * 32 + rr;
-            if (mm < M && n < N)
-                dst[(size_t)mm * ld + n] = __float2bfloat16_rn(stage[rr * kStageLd + lane]);
-        }
-    };
-    if (__all_sync(0xffffffffu, got)) {
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            uint32_t v[32];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-                "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
-                "%26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-                  "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                  "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-                  "=r"(v[30]), "=r"(v[31])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            float x[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int n = n0 + c0 + j;
-                x[j] = epi.alpha * __uint_as_float(v[j]);
-                if (epi.bias && n < N) x[j] += epi.bias[n];
-            }
-            if (epi.pre) store_rows(x, c0, epi.pre, epi.ldpre, 0);
-            if (epi.act == 1) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    x[j] = 0.5f * x[j] * (1.f + erff(x[j] * 0.70710678118654752f));
-            } else if (epi.act == 2) {
-                // chain rule through GELU: d/du [u Phi(u)] = Phi(u) + u phi(u);
-                // the gin block arrives through the transpose buffer
-                __syncwarp();
-                const int n = n0 + c0 + lane;
-                for (int rr = 0; rr < 32; ++rr) {
-                    const int mm = m0 + warp * 32 + rr;
-                    stage[rr * kStageLd + lane] =
-                        (mm < M && n < N) ? epi.gin[(size_t)mm * epi.ldgin + n] : 0.f;
+    } else {
+        // ---- epilogue warps
+        const int quarter = warp & 3;              // TMEM lanes this warp may access
+        float* stage = stage_all + (warp - 2) * 32 * kStageLd;
+        int i = 0;
+        for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const int b = i & 1, use_b = i >> 1;
+            int got = 0;
+            if (lane == 0) got = mbar_wait(&acc_full[b], (uint32_t)(use_b & 1), fail) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) break;
+            tc_fence_after();
+            const int m0 = (int)(t / nt) * BM, n0 = (int)(t % nt) * BN;
+            const int row0 = m0 + quarter * 32;    // first output row of this warp
+            const int m = row0 + lane;
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), v);
+                if (c0 + 32 == BN) {
+                    // the whole accumulator has been read: hand it back
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[b]);
                 }
-                __syncwarp();
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float u = stage[lane * kStageLd + j];
-                    const float Phi = 0.5f * (1.f + erff(u * 0.70710678118654752f));
-                    const float phi = 0.3989422804014327f * expf(-0.5f * u * u);
-                    x[j] *= Phi + u * phi;
-                }
-            }
-            if (epi.C) store_rows(x, c0, epi.C, epi.ldc, epi.accumulate);
-            if (epi.Cb) store_rows_bf16(x, c0, epi.Cb, epi.ldcb);
-            if (epi.Ct && m < M) {
-                // transposed: for a fixed column the lanes write consecutive m
+                float x[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int n = n0 + c0 + j;
-                    if (n < N) epi.Ct[(size_t)n * epi.ldct + m] = __float2bfloat16_rn(x[j]);
+                    x[j] = epi.alpha * __uint_as_float(v[j]);
+                    if (epi.bias && n < N) x[j] += epi.bias[n];
+                }
+                // row-major [m, n] block (32 rows of this warp x 32 columns),
+                // stored (or added) one coalesced row segment at a time
+                auto store_rows = [&](float* dst, int ld, int accumulate) {
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) stage[lane * kStageLd + j] = x[j];
+                    __syncwarp();
+                    const int n = n0 + c0 + lane;
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int mm = row0 + rr;
+                        if (mm < M && n < N) {
+                            float* d = dst + (size_t)mm * ld + n;
+                            const float val = stage[rr * kStageLd + lane];
+                            *d = accumulate ? *d + val : val;
+                        }
+                    }
+                };
+                if (epi.pre) store_rows(epi.pre, epi.ldpre, 0);
+                if (epi.act == 1) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        x[j] = 0.5f * x[j] * (1.f + erff(x[j] * 0.70710678118654752f));
+                } else if (epi.act == 2) {
+                    // chain rule through GELU: d/du [u Phi(u)] = Phi(u) + u phi(u); the
+                    // gin block arrives through the transpose buffer
+                    __syncwarp();
+                    const int n = n0 + c0 + lane;
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int mm = row0 + rr;
+                        stage[rr * kStageLd + lane] =
+                            (mm < M && n < N) ? epi.gin[(size_t)mm * epi.ldgin + n] : 0.f;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float u = stage[lane * kStageLd + j];
+                        const float Phi = 0.5f * (1.f + erff(u * 0.70710678118654752f));
+                        const float phi = 0.3989422804014327f * expf(-0.5f * u * u);
+                        x[j] *= Phi + u * phi;
+                    }
+                }
+                if (epi.C) store_rows(epi.C, epi.ldc, epi.accumulate);
+                if (epi.Cb) {
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) stage[lane * kStageLd + j] = x[j];
+                    __syncwarp();
+                    const int n = n0 + c0 + lane;
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int mm = row0 + rr;
+                        if (mm < M && n < N)
+                            epi.Cb[(size_t)mm * epi.ldcb + n] =
+                                __float2bfloat16_rn(stage[rr * kStageLd + lane]);
+                    }
+                }
+                if (epi.Ct && m < M) {
+                    // transposed: for a fixed column the lanes write consecutive m
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int n = n0 + c0 + j;
+                        if (n < N) epi.Ct[(size_t)n * epi.ldct + m] = __float2bfloat16_rn(x[j]);
+                    }
                 }
             }
         }
-    } else if (threadIdx.x == 0) {
-        record_error(err, SDL_ERR_TIMEOUT);
     }
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+    if (threadIdx.x == 0 && s_fail) record_error(err, SDL_ERR_TIMEOUT);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(2 * BN)
                      : "memory");
     }
 }
@@ -329,24 +402,42 @@ int make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
     return r == CUDA_SUCCESS ? SDL_OK : SDL_ERR_ARG;
 }
 
-constexpr size_t kSmemBytes = 1024 + STAGES * (TILE_A + TILE_B) + 256;
+constexpr size_t kSmemBytes = 1024 + STAGES * (TILE_A + TILE_B) +
+                              sizeof(float) * kEpiWarps * 32 * kStageLd + 256;
+
+int sm_count() {
+    static int count[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!count[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+        count[dev] = n;
+    }
+    return count[dev];
+}
 
 }  // namespace
 
 namespace sdl {
-int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float alpha,
-            const float* bias, int act, float* C, int ldc, int accumulate, void* Cb, int ldcb,
-            void* Ct, int ldct, float* pre, int ldpre, int* err, cudaStream_t st,
-            const float* gin, int ldgin) {
-    if (!A || !B || M < 1 || N < 1 || K < 1) return SDL_ERR_ARG;
+int tc_gemm_terms(const void* const* A, int lda, const void* const* B, int ldb, int terms, int M,
+                  int N, int K, float alpha, const float* bias, int act, float* C, int ldc,
+                  int accumulate, void* Cb, int ldcb, void* Ct, int ldct, float* pre, int ldpre,
+                  int* err, cudaStream_t st, const float* gin, int ldgin) {
+    if (!A || !B || terms < 1 || terms > kMaxTerms || M < 1 || N < 1 || K < 1) return SDL_ERR_ARG;
     if (act == 2 && !gin) return SDL_ERR_ARG;
     if ((lda % 8) || (ldb % 8) || lda < K || ldb < K) return SDL_ERR_ARG;
-    if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u))
-        return SDL_ERR_ARG;
-    CUtensorMap ma, mb;
+    Maps maps;
+    std::memset(&maps, 0, sizeof(maps));
     int rc;
-    if ((rc = make_map(&ma, A, M, K, lda)) != SDL_OK) return rc;
-    if ((rc = make_map(&mb, B, N, K, ldb)) != SDL_OK) return rc;
+    for (int t = 0; t < terms; ++t) {
+        if (!A[t] || !B[t] || (reinterpret_cast<uintptr_t>(A[t]) & 15u) ||
+            (reinterpret_cast<uintptr_t>(B[t]) & 15u))
+            return SDL_ERR_ARG;
+        if ((rc = make_map(&maps.a[t], A[t], M, K, lda)) != SDL_OK) return rc;
+        if ((rc = make_map(&maps.b[t], B[t], N, K, ldb)) != SDL_OK) return rc;
+    }
     Epi e;
     e.alpha = alpha;
     e.bias = bias;
@@ -365,9 +456,20 @@ int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
     if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSmemBytes) != cudaSuccess)
         return SDL_ERR_CUDA;
-    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    tc_gemm_kernel<<<grid, 128, kSmemBytes, st>>>(ma, mb, M, N, K, e, err);
+    const long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const int grid = (int)std::min<long long>(tiles, sm_count());
+    tc_gemm_kernel<<<grid, kThreads, kSmemBytes, st>>>(maps, terms, M, N, K, e, err);
     return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float alpha,
+            const float* bias, int act, float* C, int ldc, int accumulate, void* Cb, int ldcb,
+            void* Ct, int ldct, float* pre, int ldpre, int* err, cudaStream_t st,
+            const float* gin, int ldgin) {
+    const void* a[1] = {A};
+    const void* b[1] = {B};
+    return tc_gemm_terms(a, lda, b, ldb, 1, M, N, K, alpha, bias, act, C, ldc, accumulate, Cb,
+                         ldcb, Ct, ldct, pre, ldpre, err, st, gin, ldgin);
 }
 }  // namespace sdl
 

@@ -41,6 +41,34 @@ def test_bf16_correlation_error_within_bound(prec_ctx):
     assert np.all(np.abs(got - ref) <= bound[:, None, None])
 
 
+def split_bf16(t):
+    hi = t.to(torch.bfloat16)
+    lo = (t - hi.to(torch.float32)).to(torch.bfloat16)
+    return hi.contiguous(), lo.contiguous()
+
+
+def test_split_bf16_correlation_error_within_bound(prec_ctx):
+    """hi*hi + hi*lo + lo*hi of the split operands, FP32 accumulation: every
+    entry within ((3 + 1/64) 2^-16 + 2^-24 + 3 Kp 2^-23) ||Y||_F."""
+    Y, D1, D2 = hsi_problem(300)
+    ref = np.einsum("ai,kab,bj->kij", D1, Y, D2)
+    Yg, _, _ = to_gpu_problem(Y, D1, D2)
+    Yh, Yl = split_bf16(Yg.transpose(1, 2).reshape(300, -1).contiguous())
+    KT = torch.einsum("ai,bj->jiba", torch.tensor(D1), torch.tensor(D2)).reshape(32 * 128, -1)
+    Kh, Kl = split_bf16(KT.to(torch.float32).cuda())
+    C0 = torch.zeros((300, 32 * 128), dtype=torch.float32, device="cuda:0")
+    for A, B in ((Yh, Kh), (Yh, Kl), (Yl, Kh)):
+        sdl.gemm_bf16(prec_ctx, A, B, C=C0, accumulate=True)
+    got = C0.cpu().numpy().reshape(300, 128, 32).transpose(0, 2, 1)
+    Kp = 16 * 64
+    e = (3 + 1 / 64) * 2.0 ** -16 + 2.0 ** -24 + 3 * Kp * 2.0 ** -23
+    bound = e * np.linalg.norm(Y, axis=(1, 2))
+    err = np.abs(got - ref)
+    assert np.all(err <= bound[:, None, None])
+    # and far inside the single-BF16 bound
+    assert err.max() < 2.0 ** -7 * np.linalg.norm(Y, axis=(1, 2)).max() / 50
+
+
 def test_bf16_rescored_picks_match_oracle(prec_ctx):
     Y, D1, D2 = hsi_problem(257)
     ref = oracle.omp2d(Y, D1, D2, 10)
