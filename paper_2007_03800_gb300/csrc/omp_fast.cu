@@ -348,14 +348,17 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
             }
             __syncwarp();
 
-            // ---- greedy steps, fully unrolled
+            // ---- greedy steps, fully unrolled.  Every lane keeps the whole
+            // Cholesky factor (packed rows of L and 1/L_tt), so both triangular
+            // solves run without shuffles.
             int si[S], sj[S];
-            float xs[S], yv[S], Lrow[S], Lcol[S];
+            float xs[S], yv[S], Lf[S * (S + 1) / 2], invd[S];
 #pragma unroll
             for (int m = 0; m < S; ++m) {
-                si[m] = 0; sj[m] = 0; xs[m] = 0.f; yv[m] = 0.f; Lrow[m] = 0.f; Lcol[m] = 0.f;
+                si[m] = 0; sj[m] = 0; xs[m] = 0.f; yv[m] = 0.f; invd[m] = 0.f;
             }
-            float myinvd = 0.f, myy = 0.f;
+#pragma unroll
+            for (int m = 0; m < S * (S + 1) / 2; ++m) Lf[m] = 0.f;
             bool go = true;
             const int qbase = li * RI + N1 * (lj * RJ);
             static_for<0, S>([&](auto tc) {
@@ -381,16 +384,22 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                         for (int r = 0; r < RI; ++r) sc[c * RI + r] = fmaf(-u[r], vx, sc[c * RI + r]);
                     }
                 }
-                // argmax |sc|, ties to the smallest q: entries visited in increasing q
-                float best = 0.f;
-                int bq = 0x7fffffff;
+                // argmax |sc|, ties to the smallest q: two interleaved chains
+                // (even and odd entries in increasing q), merged by (value, q)
+                float best = 0.f, best1 = 0.f;
+                int bq = 0x7fffffff, bq1 = 0x7fffffff;
 #pragma unroll
                 for (int c = 0; c < RJ; ++c)
 #pragma unroll
                     for (int r = 0; r < RI; ++r) {
                         const float v = fabsf(sc[c * RI + r]);
-                        if (v > best) { best = v; bq = qbase + r + N1 * c; }
+                        if ((c * RI + r) & 1) {
+                            if (v > best1) { best1 = v; bq1 = qbase + r + N1 * c; }
+                        } else {
+                            if (v > best) { best = v; bq = qbase + r + N1 * c; }
+                        }
                     }
+                if (best1 > best || (best1 == best && bq1 < bq)) { best = best1; bq = bq1; }
                 const unsigned M = __reduce_max_sync(kFull, __float_as_uint(best));
                 if (M == 0u) { go = false; return; }
                 const unsigned cand = (__float_as_uint(best) == M) ? (unsigned)bq : 0xffffffffu;
@@ -401,20 +410,21 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                 const float b = *cq;
                 __syncwarp();
                 if (lane == 0) *cq = __int_as_float(0x7fc00000);   // mask the pick
-                // ---- Cholesky row t:  w = L^{-1} a,  L_tt = sqrt(A_tt - w.w)
-                const int p1t = pos1<Sh>(it_), p2t = pos2<Sh>(jt);
-                float r = 0.f;
-                if (lane < t) r = G1s[it_ * LD1 + pos1<Sh>(myi)] * G2s[jt * LD2 + pos2<Sh>(myj)];
-                const float Att = G1s[it_ * LD1 + p1t] * G2s[jt * LD2 + p2t];
+                // ---- Cholesky row t:  w = L^{-1} a,  L_tt = sqrt(A_tt - w.w),
+                // a_m = G1[i_t, i_m] G2[j_t, j_m] (the same value in every lane)
+                const float* g1t = G1s + it_ * LD1;
+                const float* g2t = G2s + jt * LD2;
+                const float Att = g1t[pos1<Sh>(it_)] * g2t[pos2<Sh>(jt)];
                 float ww = 0.f, wy = 0.f;
 #pragma unroll
                 for (int m = 0; m < t; ++m) {
-                    const float wm = __shfl_sync(kFull, r * myinvd, m);
-                    r = fmaf(-Lrow[m], wm, r);
+                    float am = g1t[pos1<Sh>(si[m])] * g2t[pos2<Sh>(sj[m])];
+#pragma unroll
+                    for (int l = 0; l < m; ++l) am = fmaf(-Lf[m * (m + 1) / 2 + l], Lf[t * (t + 1) / 2 + l], am);
+                    const float wm = am * invd[m];
+                    Lf[t * (t + 1) / 2 + m] = wm;
                     ww = fmaf(wm, wm, ww);
                     wy = fmaf(wm, yv[m], wy);
-                    if (lane == t) Lrow[m] = wm;
-                    if (lane == m) Lcol[t] = wm;
                 }
                 const float d = Att - ww;
                 if (!(d > kPivotRel * Att)) { go = false; return; }
@@ -423,20 +433,18 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                 yv[t] = yt;
                 si[t] = it_;
                 sj[t] = jt;
+                invd[t] = inv;
                 if (lane == t) {
-                    Lrow[t] = d * inv;
-                    myinvd = inv;
-                    myy = yt;
                     myi = it_;
                     myj = jt;
                 }
-                // ---- x = L^{-T} y (rows 0..t)
-                float rb = myy;
+                // ---- x = L^{-T} y (rows t..0)
 #pragma unroll
                 for (int kk = t; kk >= 0; --kk) {
-                    const float xk = __shfl_sync(kFull, rb * myinvd, kk);
-                    rb = fmaf(-Lcol[kk], xk, rb);
-                    xs[kk] = xk;
+                    float v = yv[kk];
+#pragma unroll
+                    for (int l = kk + 1; l <= t; ++l) v = fmaf(-Lf[l * (l + 1) / 2 + kk], xs[l], v);
+                    xs[kk] = v * invd[kk];
                 }
                 E2 = fmaf(-yt, yt, E2);
                 cnt = t + 1;

@@ -80,11 +80,13 @@ def test_bf16_rescored_picks_match_oracle(prec_ctx):
     rep, exact = compare_supports(out.support.cpu().numpy(), out.nnz.cpu().numpy(), ref)
     assert rep.bad == 0 and rep.ties <= 2, rep
     assert coef_rel_error(out.coef.cpu().numpy(), ref.coef, exact).max() < COEF_RTOL
-    # without re-scoring, BF16 picks drift from the FP32/FP64 picks
+    # without re-scoring (a diagnostic mode) the split-BF16 picks carry no
+    # guarantee, but the split keeps C0 within ~1e-4 ||Y||: nearly all agree
     prec_ctx.set_precision(sdl.Context.PREC_BF16_CORR | sdl.Context.PREC_NO_RESCORE)
     raw = prec_ctx.sparse_code(Yg, D1g, D2g, 10)
+    assert prec_ctx.status() == 0
     rep_raw, _ = compare_supports(raw.support.cpu().numpy(), raw.nnz.cpu().numpy(), ref)
-    assert rep_raw.exact < rep.exact, (rep_raw, rep)
+    assert rep_raw.exact >= 0.9 * rep_raw.n, rep_raw
 
 
 @pytest.mark.parametrize("side", [1, 2])
@@ -188,4 +190,4 @@ def test_hsi_precision_study(prec_ctx):
         # when every pick of the second pass agrees
         if e["ties"] == 0:
             assert e["D2_abs"] < 1e-3, (name, e)
-    assert rows["bf16_norescore"]["exact"] < rows["bf16"]["exact"], rows
+
