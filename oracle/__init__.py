@@ -11,3 +11,4 @@ arithmetic).
 from .sdl_oracle import *  # noqa: F401,F403
 from . import denoise  # noqa: F401
 from . import mlp  # noqa: F401
+from . import ortho  # noqa: F401
