@@ -549,6 +549,64 @@ def study_learned(args):
     return 0
 
 
+def study_ortho(args):
+    """Orthonormal variant (Remark 1) on the bench's 200k 12x12 patches: square
+    orthonormal D1, D2 (12 x 12, random orthogonal start from seed 1), s = 6,
+    20 iterations of thresholded coding + Procrustes updates; device time per
+    iteration and the RMSE trajectory, next to the general variant (D 12x24)
+    on the same patches for context."""
+    import torch
+
+    from paper_2007_03800_gb300 import sdl
+    dev = torch.device("cuda:0")
+    Y, D1g_init, D2g_init = make_inputs()
+    p, s, N = 12, 6, W["N"]
+    rng = np.random.default_rng(1)
+    Qs = []
+    for _ in range(2):
+        Q, R = np.linalg.qr(rng.standard_normal((p, p)))
+        Qs.append(Q * np.sign(np.diag(R)))
+    ctx = sdl.Context(0)
+    Yg = sdl.signals(torch.tensor(Y, dtype=torch.float32, device=dev))
+    codes = sdl.Codes.empty(N, s, dev)
+    rmse = torch.zeros(2, dtype=torch.float32, device=dev)
+    D1w, D2w = _device_dict(Qs[0], dev), _device_dict(Qs[1], dev)
+    for _ in range(args.warmup):
+        ctx.ortho_iterate(Yg, D1w, D2w, s, out=codes, rmse_out=rmse)
+    ctx.check()
+    D1g, D2g = _device_dict(Qs[0], dev), _device_dict(Qs[1], dev)
+    ms, traj = [], []
+    for _ in range(20):
+        a, b = _events()
+        a.record()
+        ctx.ortho_iterate(Yg, D1g, D2g, s, out=codes, rmse_out=rmse)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        traj.append(round(rmse[1].item(), 5))
+    ctx.profile_collect()
+    ctx.profile(True)
+    ctx.ortho_iterate(Yg, D1w, D2w, s, out=codes, rmse_out=rmse)
+    ctx.profile(False)
+    split = {k: round(v[0], 4) for k, v in ctx.profile_collect().items() if v[1] > 0}
+    ctx.check()
+    # general variant, same patches, same number of iterations (context)
+    D1a, D2a = _device_dict(D1g_init, dev), _device_dict(D2g_init, dev)
+    gen = []
+    for _ in range(20):
+        ctx.iterate(Yg, D1a, D2a, s, out=codes, rmse_out=rmse)
+        gen.append(round(rmse[1].item(), 5))
+    ctx.check()
+    ctx.close()
+    med = statistics.median(ms)
+    print(json.dumps({"study": "ortho", "workload": "200000 12x12 patches, orthonormal D 12x12, "
+                      "s=6, 20 iterations", "ms_per_iteration": med,
+                      "signals_per_s": N / (med / 1e3), "rmse_trajectory": traj,
+                      "kernel_ms_one_iteration": split,
+                      "general_variant_rmse_trajectory_D12x24": gen}), flush=True)
+    return 0
+
+
 def study_denoise(args):
     """Denoising with one batch of three patch sizes (8, 12, 16; D p x 2p;
     error-driven stop at 1.15 sigma p, s <= p/2) on a 512x512 synthetic image
@@ -598,7 +656,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed region only: no e2e loop, CPU baseline or clock sampling "
                          "(for profiler runs; its numbers are not bench values)")
-    ap.add_argument("--study", choices=["precision", "learned", "denoise"],
+    ap.add_argument("--study", choices=["precision", "learned", "denoise", "ortho"],
                     help="run one extra study on its own workload instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -607,7 +665,7 @@ def main():
         return run_reference(args)
     if args.study:
         return {"precision": study_precision, "learned": study_learned,
-                "denoise": study_denoise}[args.study](args)
+                "denoise": study_denoise, "ortho": study_ortho}[args.study](args)
     return run_ours(args)
 
 

@@ -365,6 +365,36 @@ int sdl_sparse_code_learned(sdl_ctx* ctx, sdl_mlp* mlp, const float* Y, int p1, 
                             float* guard_out, void* stream);
 
 /*
+ * Orthonormal variant (Remark 1): square orthonormal dictionaries
+ * (n1 = p1, n2 = p2, D^T D = I), codes X_k = T_s(D1^T Y_k D2) (the s largest
+ * |entries|, ties to the smallest q = i + p1 j; a signal keeps fewer when the
+ * remaining entries are exactly 0), and orthogonal-Procrustes updates
+ * D1 = U V^T of B1 = sum_k Y_k D2 X_k^T = U S V^T, D2 = U2 V2^T of
+ * B2 = sum_k Y_k^T D1 X_k (the trace-maximisation reading of the garbled SVD
+ * argument printed in Remark 1).  1 <= p1, p2 <= 32, 1 <= s <= min(32, p1 p2).
+ * Layouts as sdl_sparse_code (D1 p1 x p1, D2 p2 x p2 column-major).
+ *
+ * sdl_ortho_sparse_code - the thresholded codes only (res_energy may be NULL).
+ */
+int sdl_ortho_sparse_code(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
+                          const float* D1, const float* D2, int s, int32_t* support,
+                          float* coef, int32_t* nnz, float* res_energy, void* stream);
+
+/*
+ * sdl_ortho_iterate - one iteration of Algorithm 1 - Orthonormal: codes with
+ * (D1, D2), D1 by Procrustes (singular values by an FP64 one-sided Jacobi
+ * SVD), codes again with the new D1, D2 by Procrustes.  D1, D2 in/out (must
+ * be orthonormal on entry); support/coef/nnz receive the second codes.
+ * rmse_out: NULL or device float[2], the RMSE right after each update (with
+ * the codes of the preceding coding pass).  A numerically rank-deficient B
+ * (smallest singular value <= 1e-12 of the largest) records SDL_ERR_SINGULAR
+ * and leaves that dictionary unchanged.  N >= 1.
+ */
+int sdl_ortho_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N, float* D1,
+                      float* D2, int s, int32_t* support, float* coef, int32_t* nnz,
+                      float* rmse_out, void* stream);
+
+/*
  * sdl_sparse_code_static - the sparse coder of sdl_sparse_code with no
  * context and no device allocation.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory once running
@@ -416,8 +446,10 @@ int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
  *  13 topk          shortlist selection from the network's scores
  *  14 shortlist     2D-OMP restricted to the shortlists, with the fallback test
  *  15 tc_corr       tensor-core correlations (precision extension)
+ *  16 ortho_code    thresholded coding pass of the orthonormal variant
+ *  17 procrustes    Procrustes update of the orthonormal variant
  */
-#define SDL_NUM_KERNEL_KINDS 16
+#define SDL_NUM_KERNEL_KINDS 18
 
 /* Enable (1) or disable (0) event timing of every kernel this context
  * enqueues.  Launch counts are kept either way.  Host-side, synchronous. */

@@ -135,6 +135,12 @@ int finish_update(sdl_ctx* c, int slots, int side, float* D, int p1, int p2, int
 
 }  // namespace
 
+namespace sdl {
+int ctx_workspace(sdl_ctx* c, int p1, int p2, int n1, int n2) {
+    return ensure_workspace(c, p1, p2, n1, n2);
+}
+}  // namespace sdl
+
 extern "C" {
 
 const char* sdl_strerror(int code) {
@@ -406,7 +412,7 @@ const char* sdl_kernel_name(int kind) {
     static const char* names[SDL_NUM_KERNEL_KINDS] = {
         "gram", "code", "code_D1", "code_D2", "accum_D1", "accum_D2",
         "reduce", "solve", "rescale", "memset", "batch_graph", "mlp", "adam", "topk",
-        "shortlist", "tc_corr"};
+        "shortlist", "tc_corr", "ortho_code", "procrustes"};
     return (kind >= 0 && kind < SDL_NUM_KERNEL_KINDS) ? names[kind] : "?";
 }
 

@@ -45,8 +45,12 @@ namespace sdl {
 
 enum Kind {
     kGram = 0, kCode, kCodeD1, kCodeD2, kAccD1, kAccD2, kReduce, kSolve, kRescale, kMemset,
-    kBatchGraph, kMlp, kAdam, kTopk, kShortlist, kTcCorr
+    kBatchGraph, kMlp, kAdam, kTopk, kShortlist, kTcCorr, kOrthoCode, kProcrustes
 };
+
+// Grow the context's Gram, partial-sum and reduction buffers for a problem
+// shape (api.cu).
+int ctx_workspace(sdl_ctx* c, int p1, int p2, int n1, int n2);
 constexpr size_t kMaxRecs = 1 << 16;
 
 // Bracket one launch of `kind` on `st` with timing events (when enabled).

@@ -1,0 +1,473 @@
+// Orthonormal variant of Algorithm 1 (Remark 1): square orthonormal
+// dictionaries (n1 = p1, n2 = p2), codes X_k = T_s(D1^T Y_k D2) (the s
+// largest |entries|, no pursuit), and orthogonal-Procrustes updates
+// D1 = U V^T of B1 = sum_k Y_k D2 X_k^T (D2 = U2 V2^T of B2 = sum_k Y_k^T D1 X_k).
+// B1 and B2 are the sums of the general update (Corollary 1, Result 1); the
+// printed SVD argument of Remark 1 carries an extra sum X X^T factor, which
+// the trace maximisation behind the Procrustes problem does not have.
+//
+//   ortho_code_kernel  one warp per signal: Y staged in shared memory,
+//                      Z = Y D2, C = D1^T Z, s rounds of warp argmax with
+//                      masking (ties to the smallest q), the code, and B1 or
+//                      B2 accumulated in warp-private shared memory, combined
+//                      in warp order per CTA (deterministic slots);
+//   procrustes_kernel  one CTA: one-sided Jacobi SVD of B in FP64 (column
+//                      pairs in round-robin order, one warp per pair),
+//                      D = U V^T, the objective change 2 (tr(D_old^T B) -
+//                      sum sigma) and the RMSE.
+#include <algorithm>
+#include <cmath>
+
+#include "ctx.cuh"
+
+using namespace sdl;
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kOrthoMaxP = 32;       // p1, p2 <= 32
+constexpr int kOrthoWarps = 8;       // warps (signals in flight) per CTA
+constexpr double kRankRel = 1e-12;   // smallest / largest singular value
+constexpr int kMaxSweeps = 40;
+
+__host__ __device__ constexpr int al4(int x) { return (x + 3) & ~3; }
+
+// shared memory (floats): D1 (p1 x n1 column-major), D2 row-major (p2 x n2),
+// then per warp Y | Z | C | accumulator (p x n of the side) | 2 energies
+struct OrthoLayout {
+    int d1, d2, warp0, y, z, c, acc, en, wstride, total;
+    __host__ __device__ OrthoLayout(int p1, int p2, int side, int wpc) {
+        const int n1 = p1, n2 = p2;
+        d1 = 0;
+        d2 = d1 + al4(p1 * n1);
+        warp0 = d2 + al4(p2 * n2);
+        y = 0;
+        z = y + al4(p1 * p2);
+        c = z + al4(p1 * n2);
+        acc = c + al4(n1 * n2);
+        const int nacc = side == kSideD1 ? p1 * n1 : side == kSideD2 ? p2 * n2 : 0;
+        en = acc + al4(nacc);
+        wstride = en + 4;
+        total = warp0 + wpc * wstride;
+    }
+};
+
+template <int SIDE>
+__global__ void __launch_bounds__(kOrthoWarps * 32)
+    ortho_code_kernel(const float* __restrict__ Y, int p1, int p2, long long N,
+                      const float* __restrict__ D1, const float* __restrict__ D2, int s,
+                      int32_t* __restrict__ support, float* __restrict__ coef,
+                      int32_t* __restrict__ nnz, float* __restrict__ res_energy,
+                      float* __restrict__ part_f, double* __restrict__ part_d, int* err) {
+    extern __shared__ __align__(16) float sm[];
+    const int n1 = p1, n2 = p2, P = p1 * p2, Q = n1 * n2;
+    const int wpc = blockDim.x >> 5;
+    const OrthoLayout L(p1, p2, SIDE, wpc);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* D1s = sm + L.d1;
+    float* D2r = sm + L.d2;
+    float* wb = sm + L.warp0 + w * L.wstride;
+    float* Ys = wb + L.y;
+    float* Zs = wb + L.z;
+    float* Cs = wb + L.c;
+    float* acc = wb + L.acc;
+    const int nacc = SIDE == kSideD1 ? p1 * n1 : SIDE == kSideD2 ? p2 * n2 : 0;
+
+    for (int e = threadIdx.x; e < p1 * n1; e += blockDim.x) D1s[e] = D1[e];
+    for (int e = threadIdx.x; e < p2 * n2; e += blockDim.x) {
+        const int b = e / n2, j = e - b * n2;
+        D2r[e] = D2[b + p2 * j];
+    }
+    for (int e = lane; e < nacc; e += 32) acc[e] = 0.f;
+    __syncthreads();
+
+    float e_res = 0.f, e_res_c = 0.f, e_y = 0.f, e_y_c = 0.f;   // compensated sums (lane 0)
+    const long long stride = (long long)gridDim.x * wpc;
+    for (long long k = (long long)blockIdx.x * wpc + w; k < N; k += stride) {
+        // ---- Y_k and ||Y_k||^2
+        float ss = 0.f;
+        for (int e = lane; e < P; e += 32) {
+            const float v = Y[(size_t)k * P + e];
+            Ys[e] = v;
+            ss = fmaf(v, v, ss);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+        __syncwarp();
+        const bool finite = isfinite(ss);
+        int cnt = 0;
+        float E2 = ss;
+        int my_q = -1;
+        float my_x = 0.f;
+        if (finite) {
+            // ---- Z = Y D2 (p1 x n2), C = D1^T Z (entry q = i + n1 j)
+            for (int e = lane; e < p1 * n2; e += 32) {
+                const int a = e / n2, j = e - a * n2;
+                float z = 0.f;
+                for (int b = 0; b < p2; ++b) z = fmaf(Ys[a + p1 * b], D2r[b * n2 + j], z);
+                Zs[e] = z;
+            }
+            __syncwarp();
+            for (int q = lane; q < Q; q += 32) {
+                const int i = q % n1, j = q / n1;
+                float c = 0.f;
+                for (int a = 0; a < p1; ++a) c = fmaf(D1s[a + p1 * i], Zs[a * n2 + j], c);
+                Cs[q] = c;
+            }
+            __syncwarp();
+            // ---- T_s: s rounds of argmax |C| over unmasked entries
+            for (int t = 0; t < s; ++t) {
+                float best = 0.f;
+                int bq = 0x7fffffff;
+                for (int q = lane; q < Q; q += 32) {
+                    const float v = fabsf(Cs[q]);
+                    if (v > best) { best = v; bq = q; }   // NaN (masked) never wins
+                }
+                const unsigned M = __reduce_max_sync(kFull, __float_as_uint(best));
+                if (M == 0u) break;   // every remaining entry is 0
+                const unsigned cand = (__float_as_uint(best) == M) ? (unsigned)bq : 0xffffffffu;
+                const int q = (int)__reduce_min_sync(kFull, cand);
+                const float x = Cs[q];
+                __syncwarp();
+                if (lane == 0) Cs[q] = __int_as_float(0x7fc00000);
+                if (lane == t) {
+                    my_q = q;
+                    my_x = x;
+                }
+                E2 = fmaf(-x, x, E2);
+                cnt = t + 1;
+                __syncwarp();
+            }
+        }
+        // ---- emit the code (lane l holds pick l)
+        if (support && lane < s) {
+            support[(size_t)k * s + lane] = lane < cnt ? my_q : -1;
+            coef[(size_t)k * s + lane] = lane < cnt ? my_x : 0.f;
+        }
+        if (lane == 0) {
+            if (nnz) nnz[k] = cnt;
+            if (res_energy) res_energy[k] = finite ? fmaxf(E2, 0.f) : __int_as_float(0x7fc00000);
+            if (!finite) record_error(err, SDL_ERR_NONFINITE);
+        }
+        // ---- fused partial sums (warp-private accumulators)
+        if constexpr (SIDE == kSideD1) {
+            // B1[a, i_l] += x_l Z[a, j_l]
+            for (int l = 0; l < cnt; ++l) {
+                const int ql = __shfl_sync(kFull, my_q, l);
+                const float xl = __shfl_sync(kFull, my_x, l);
+                const int il = ql % n1, jl = ql / n1;
+                for (int a = lane; a < p1; a += 32) acc[a * n1 + il] = fmaf(xl, Zs[a * n2 + jl], acc[a * n1 + il]);
+                __syncwarp();
+            }
+        } else if constexpr (SIDE == kSideD2) {
+            // B2[b, j_l] += x_l (Y^T D1)[b, i_l]
+            for (int l = 0; l < cnt; ++l) {
+                const int ql = __shfl_sync(kFull, my_q, l);
+                const float xl = __shfl_sync(kFull, my_x, l);
+                const int il = ql % n1, jl = ql / n1;
+                for (int b = lane; b < p2; b += 32) {
+                    float wv = 0.f;
+                    for (int a = 0; a < p1; ++a) wv = fmaf(Ys[a + p1 * b], D1s[a + p1 * il], wv);
+                    acc[b * n2 + jl] = fmaf(xl, wv, acc[b * n2 + jl]);
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0 && finite) {
+            const float ye = fmaxf(E2, 0.f) - e_res_c;
+            const float te = e_res + ye;
+            e_res_c = (te - e_res) - ye;
+            e_res = te;
+            const float yy = ss - e_y_c;
+            const float ty = e_y + yy;
+            e_y_c = (ty - e_y) - yy;
+            e_y = ty;
+        }
+        __syncwarp();
+    }
+    if constexpr (SIDE != kCodeOnly) {
+        float* en = wb + L.en;
+        if (lane == 0) {
+            en[0] = e_res - e_res_c;
+            en[1] = e_y - e_y_c;
+        }
+        __syncthreads();
+        // combine the warps' accumulators in warp order into this CTA's slot
+        float* dst = part_f + (size_t)blockIdx.x * nacc;
+        for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
+            float v = 0.f;
+            for (int ww = 0; ww < wpc; ++ww) v += sm[L.warp0 + ww * L.wstride + L.acc + e];
+            dst[e] = v;
+        }
+        if (threadIdx.x < 2) {
+            double d = 0.0;
+            for (int ww = 0; ww < wpc; ++ww) d += (double)sm[L.warp0 + ww * L.wstride + L.en + threadIdx.x];
+            part_d[(size_t)blockIdx.x * 2 + threadIdx.x] = d;
+        }
+    }
+}
+
+// One CTA, 32 * ceil(m/2) threads (m = n rounded up to even): one-sided
+// Jacobi SVD of B (p x n row-major, p = n) in FP64 and D = U V^T.
+//   red_f = B, red_d[0] = objective before (sum of residual energies with
+//   the old dictionary and these codes).  The old D must be orthonormal: then
+//   f(D) = sum ||Y||^2 - 2 tr(D^T B) + sum ||X||^2, and the change is
+//   -2 (sum sigma - tr(D_old^T B)).
+__global__ void procrustes_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d,
+                                  float* D, int n, double inv_count, float* objective_out,
+                                  float* rmse_out, int* err) {
+    extern __shared__ __align__(16) double smd[];
+    const int m = (n + 1) & ~1;             // even number of columns (a zero column pads)
+    double* A = smd;                         // m columns of length n (column-major)
+    double* V = A + (size_t)m * n;           // m x m (column-major)
+    __shared__ int s_fail, s_rot;
+    __shared__ double s_tr;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_fail = 0;
+        s_tr = 0.0;
+    }
+    for (int e = tid; e < m * n; e += nth) {
+        const int c = e / n, r = e - c * n;
+        const float v = c < n ? red_f[r * n + c] : 0.f;
+        A[e] = (double)v;
+        if (!isfinite(v)) s_fail = SDL_ERR_NONFINITE;
+    }
+    for (int e = tid; e < m * m; e += nth) V[e] = (e / m == e % m) ? 1.0 : 0.0;
+    __syncthreads();
+    // tr(D_old^T B)
+    if (warp == 0) {
+        double t = 0.0;
+        for (int e = lane; e < n * n; e += 32) {
+            const int r = e / n, c = e - r * n;
+            t += (double)D[r + n * c] * (double)red_f[e];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+        if (lane == 0) s_tr = t;
+    }
+    __syncthreads();
+    // sweeps: m - 1 rounds of m/2 disjoint pairs (round-robin tournament)
+    for (int sweep = 0; sweep < kMaxSweeps && s_fail == 0; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int round = 0; round < m - 1; ++round) {
+            // pair `warp`: positions warp and m-1-warp of the rotated list
+            const int pa = warp, pb = m - 1 - warp;
+            auto player = [&](int pos) {
+                if (pos == 0) return 0;
+                return 1 + (pos - 1 + round) % (m - 1);
+            };
+            int ci = player(pa), cj = player(pb);
+            if (ci > cj) {
+                const int t = ci;
+                ci = cj;
+                cj = t;
+            }
+            double al = 0.0, be = 0.0, ga = 0.0;
+            for (int r = lane; r < n; r += 32) {
+                const double x = A[ci * n + r], y = A[cj * n + r];
+                al += x * x;
+                be += y * y;
+                ga += x * y;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                al += __shfl_xor_sync(kFull, al, o);
+                be += __shfl_xor_sync(kFull, be, o);
+                ga += __shfl_xor_sync(kFull, ga, o);
+            }
+            if (ga != 0.0 && fabs(ga) > 1e-14 * sqrt(al * be)) {
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                for (int r = lane; r < n; r += 32) {
+                    const double x = A[ci * n + r], y = A[cj * n + r];
+                    A[ci * n + r] = c * x - sn * y;
+                    A[cj * n + r] = sn * x + c * y;
+                }
+                for (int r = lane; r < m; r += 32) {
+                    const double x = V[ci * m + r], y = V[cj * m + r];
+                    V[ci * m + r] = c * x - sn * y;
+                    V[cj * m + r] = sn * x + c * y;
+                }
+                if (lane == 0) atomicAdd(&s_rot, 1);
+            }
+            __syncthreads();
+        }
+        const int rot = s_rot;
+        __syncthreads();
+        if (rot == 0) break;
+    }
+    // singular values, rank check, D = sum_i (a_i / sigma_i) v_i^T over the n true columns
+    double* sig = V + (size_t)m * m;         // m
+    for (int c = tid; c < m; c += nth) {
+        double t = 0.0;
+        for (int r = 0; r < n; ++r) t += A[c * n + r] * A[c * n + r];
+        sig[c] = sqrt(t);
+    }
+    __syncthreads();
+    if (tid == 0 && s_fail == 0) {
+        double smax = 0.0, smin = INFINITY;
+        int zeros = 0;
+        for (int c = 0; c < m; ++c) {
+            smax = fmax(smax, sig[c]);
+        }
+        // the padding column (odd n) carries a zero singular value: skip one zero
+        for (int c = 0; c < m; ++c) {
+            if (m != n && sig[c] == 0.0 && zeros == 0) {
+                ++zeros;
+                continue;
+            }
+            smin = fmin(smin, sig[c]);
+        }
+        if (!(smax > 0.0) || !(smin > kRankRel * smax)) s_fail = SDL_ERR_SINGULAR;
+    }
+    __syncthreads();
+    const bool ok = s_fail == 0;
+    if (ok) {
+        // rows r < n of U V^T restricted to the n true columns of V
+        for (int e = tid; e < n * n; e += nth) {
+            const int r = e / n, c = e - r * n;   // D[r, c]
+            double d = 0.0;
+            for (int i = 0; i < m; ++i)
+                if (sig[i] > 0.0) d += A[i * n + r] / sig[i] * V[i * m + c];
+            D[r + n * c] = (float)d;
+        }
+    }
+    if (tid == 0) {
+        if (!ok) record_error(err, s_fail);
+        double ssum = 0.0;
+        for (int c = 0; c < m; ++c) ssum += sig[c];
+        const double before = red_d[0];
+        const double after = ok ? before - 2.0 * (ssum - s_tr) : before;
+        if (objective_out) {
+            objective_out[0] = (float)before;
+            objective_out[1] = (float)after;
+        }
+        if (rmse_out) rmse_out[0] = (float)sqrt(fmax(after, 0.0) * inv_count);
+    }
+}
+
+size_t code_smem(int p1, int p2, int side, int wpc) {
+    return sizeof(float) * (size_t)OrthoLayout(p1, p2, side, wpc).total;
+}
+
+template <int SIDE>
+int launch_ortho_code_impl(const float* Y, int p1, int p2, long long N, const float* D1,
+                           const float* D2, int s, int32_t* support, float* coef, int32_t* nnz,
+                           float* res, float* part_f, double* part_d, int max_slots, int* err,
+                           int num_sms, cudaStream_t st) {
+    const size_t bytes = code_smem(p1, p2, SIDE, kOrthoWarps);
+    auto kern = ortho_code_kernel<SIDE>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return SDL_ERR_CUDA;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kOrthoWarps * 32, bytes) !=
+        cudaSuccess)
+        return SDL_ERR_CUDA;
+    bps = std::max(1, std::min(bps, 8));
+    const long long need = (N + kOrthoWarps - 1) / kOrthoWarps;
+    long long grid = std::max<long long>(1, std::min<long long>(need, (long long)num_sms * bps));
+    if (SIDE != kCodeOnly) grid = std::min<long long>(grid, max_slots);
+    kern<<<(int)grid, kOrthoWarps * 32, bytes, st>>>(Y, p1, p2, N, D1, D2, s, support, coef, nnz,
+                                                     res, part_f, part_d, err);
+    if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
+    return SIDE == kCodeOnly ? 0 : (int)grid;
+}
+
+}  // namespace
+
+namespace sdl {
+
+bool ortho_shape_supported(int p1, int p2, int s) {
+    return p1 >= 1 && p2 >= 1 && p1 <= kOrthoMaxP && p2 <= kOrthoMaxP && s >= 1 && s <= 32 &&
+           s <= p1 * p2;
+}
+
+int launch_ortho_code(const float* Y, int p1, int p2, long long N, const float* D1,
+                      const float* D2, int s, int32_t* support, float* coef, int32_t* nnz,
+                      float* res, float* part_f, double* part_d, int max_slots, int side,
+                      int* err, int num_sms, cudaStream_t st) {
+    switch (side) {
+        case kCodeOnly:
+            return launch_ortho_code_impl<kCodeOnly>(Y, p1, p2, N, D1, D2, s, support, coef, nnz,
+                                                     res, part_f, part_d, max_slots, err, num_sms, st);
+        case kSideD1:
+            return launch_ortho_code_impl<kSideD1>(Y, p1, p2, N, D1, D2, s, support, coef, nnz,
+                                                   res, part_f, part_d, max_slots, err, num_sms, st);
+        case kSideD2:
+            return launch_ortho_code_impl<kSideD2>(Y, p1, p2, N, D1, D2, s, support, coef, nnz,
+                                                   res, part_f, part_d, max_slots, err, num_sms, st);
+        default:
+            return SDL_ERR_ARG;
+    }
+}
+
+int launch_procrustes(const float* red_f, const double* red_d, float* D, int n, double inv_count,
+                      float* objective_out, float* rmse_out, int* err, cudaStream_t st) {
+    const int m = (n + 1) & ~1;
+    const size_t bytes = sizeof(double) * ((size_t)m * n + (size_t)m * m + m);
+    if (cudaFuncSetAttribute(procrustes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes) != cudaSuccess)
+        return SDL_ERR_CUDA;
+    procrustes_kernel<<<1, 32 * (m / 2), bytes, st>>>(red_f, red_d, D, n, inv_count, objective_out,
+                                                      rmse_out, err);
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+}  // namespace sdl
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+int sdl_ortho_sparse_code(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const float* D1,
+                          const float* D2, int s, int32_t* support, float* coef, int32_t* nnz,
+                          float* res_energy, void* stream) {
+    if (!c || N < 0 || (N > 0 && (!Y || !D1 || !D2 || !support || !coef || !nnz)))
+        return SDL_ERR_ARG;
+    if (!ortho_shape_supported(p1, p2, s)) return SDL_ERR_ARG;
+    if (N == 0) return SDL_OK;
+    DeviceGuard g(c->device);
+    Trace tr(c, kOrthoCode, (cudaStream_t)stream);
+    const int rc = launch_ortho_code(Y, p1, p2, N, D1, D2, s, support, coef, nnz, res_energy,
+                                     nullptr, nullptr, 0, kCodeOnly, c->err, c->num_sms,
+                                     (cudaStream_t)stream);
+    return rc < 0 ? rc : SDL_OK;
+}
+
+int sdl_ortho_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1, float* D2,
+                      int s, int32_t* support, float* coef, int32_t* nnz, float* rmse_out,
+                      void* stream) {
+    if (!c || N < 1 || !Y || !D1 || !D2 || !support || !coef || !nnz) return SDL_ERR_ARG;
+    if (!ortho_shape_supported(p1, p2, s)) return SDL_ERR_ARG;
+    DeviceGuard g(c->device);
+    int rc = ctx_workspace(c, p1, p2, p1, p2);
+    if (rc != SDL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int max_slots = max_partial_slots(c->num_sms);
+    const double inv_count = 1.0 / ((double)p1 * p2 * (double)N);
+    for (int side = kSideD1; side <= kSideD2; ++side) {
+        const int p = side == kSideD1 ? p1 : p2;
+        int slots;
+        {
+            Trace tr(c, kOrthoCode, st);
+            slots = launch_ortho_code(Y, p1, p2, N, D1, D2, s, side == kSideD2 ? support : nullptr,
+                                      coef, nnz, nullptr, c->part_f, c->part_d, max_slots, side,
+                                      c->err, c->num_sms, st);
+        }
+        if (slots < 0) return slots;
+        {
+            Trace tr(c, kReduce, st);
+            launch_reduce_partials(c->part_f, c->part_d, slots, p * p, c->red_f, c->red_d, st);
+        }
+        Trace tr(c, kProcrustes, st);
+        rc = launch_procrustes(c->red_f, c->red_d, side == kSideD1 ? D1 : D2, p, inv_count, nullptr,
+                               rmse_out ? rmse_out + (side - kSideD1) : nullptr, c->err, st);
+        if (rc != SDL_OK) return rc;
+    }
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -63,6 +63,8 @@ SIGNATURES = {
     "sdl_mlp_forward": [_P, _P, _L, _P, _P],
     "sdl_sparse_code_learned": [_P, _P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P,
                                 _P, _P, _P, _P],
+    "sdl_ortho_sparse_code": [_P, _P, _I, _I, _L, _P, _P, _I, _P, _P, _P, _P, _P],
+    "sdl_ortho_iterate": [_P, _P, _I, _I, _L, _P, _P, _I, _P, _P, _P, _P, _P],
     "sdl_set_precision": [_P, _I],
     "sdl_precision_stats": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "sdl_profile_enable": [_P, _I],
@@ -216,7 +218,7 @@ class Context:
 
     def profile_collect(self) -> dict:
         """{kernel name: (total device ms, launches)} since the last collect."""
-        n = 16
+        n = 18
         ms = (ctypes.c_double * n)()
         cnt = (ctypes.c_int64 * n)()
         k = self._lib.sdl_profile_collect(self._h, ms, cnt, n)
@@ -291,6 +293,37 @@ class Context:
                                    float(eps), _ptr(out.support), _ptr(out.coef), _ptr(out.nnz),
                                    _ptr(rmse_out), _stream(stream))
         _check(rc, "sdl_iterate")
+        return out
+
+    # ---- orthonormal variant (Remark 1)
+    def ortho_sparse_code(self, Y, D1, D2, s, out: Codes | None = None, stream=None) -> Codes:
+        """``sdl_ortho_sparse_code``: X_k = T_s(D1^T Y_k D2) for square orthonormal D."""
+        N, p1, p2 = _check_Y(Y)
+        if _check_D(D1, p1, "D1") != p1 or _check_D(D2, p2, "D2") != p2:
+            raise ValueError("the orthonormal variant needs square dictionaries")
+        if out is None:
+            out = Codes.empty(N, s, Y.device, with_energy=True)
+        _check(self._lib.sdl_ortho_sparse_code(
+            self._h, _ptr(Y), p1, p2, N, _ptr(D1), _ptr(D2), s, _ptr(out.support), _ptr(out.coef),
+            _ptr(out.nnz), _ptr(out.res_energy), _stream(stream)), "sdl_ortho_sparse_code")
+        return out
+
+    def ortho_iterate(self, Y, D1, D2, s, out: Codes | None = None, rmse_out=None,
+                      stream=None) -> Codes:
+        """``sdl_ortho_iterate``: one iteration of Algorithm 1 - Orthonormal."""
+        N, p1, p2 = _check_Y(Y)
+        if _check_D(D1, p1, "D1") != p1 or _check_D(D2, p2, "D2") != p2:
+            raise ValueError("the orthonormal variant needs square dictionaries")
+        if out is None:
+            out = Codes.empty(N, s, Y.device)
+        _need(out.support, torch.int32, (N, s), None, "support")
+        _need(out.coef, torch.float32, (N, s), None, "coef")
+        _need(out.nnz, torch.int32, (N,), None, "nnz")
+        if rmse_out is not None:
+            _need(rmse_out, torch.float32, (2,), None, "rmse_out")
+        _check(self._lib.sdl_ortho_iterate(
+            self._h, _ptr(Y), p1, p2, N, _ptr(D1), _ptr(D2), s, _ptr(out.support), _ptr(out.coef),
+            _ptr(out.nnz), _ptr(rmse_out), _stream(stream)), "sdl_ortho_iterate")
         return out
 
 
