@@ -382,12 +382,12 @@ int sdl_ortho_sparse_code(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t 
 
 /*
  * sdl_ortho_iterate - one iteration of Algorithm 1 - Orthonormal: codes with
- * (D1, D2), D1 by Procrustes (singular values by an FP64 one-sided Jacobi
- * SVD), codes again with the new D1, D2 by Procrustes.  D1, D2 in/out (must
+ * (D1, D2), D1 by Procrustes (a one-sided Jacobi SVD of the FP32 sum B, in
+ * FP32), codes again with the new D1, D2 by Procrustes.  D1, D2 in/out (must
  * be orthonormal on entry); support/coef/nnz receive the second codes.
  * rmse_out: NULL or device float[2], the RMSE right after each update (with
  * the codes of the preceding coding pass).  A numerically rank-deficient B
- * (smallest singular value <= 1e-12 of the largest) records SDL_ERR_SINGULAR
+ * (smallest singular value <= 1e-6 of the largest) records SDL_ERR_SINGULAR
  * and leaves that dictionary unchanged.  N >= 1.
  */
 int sdl_ortho_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N, float* D1,
@@ -450,6 +450,13 @@ int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
  *  17 procrustes    Procrustes update of the orthonormal variant
  */
 #define SDL_NUM_KERNEL_KINDS 18
+
+/* Failure-detection self-test: enqueue one tiny kernel that waits, bounded
+ * by max_cycles SM clock cycles (1 .. 2^31, about one second at most), on an
+ * mbarrier that nothing completes, exactly as the library's waiting kernels
+ * do; when the bound runs out it records SDL_ERR_TIMEOUT in the context (read
+ * by sdl_status) and returns.  The context stays usable. */
+int sdl_selftest_timeout(sdl_ctx* ctx, long long max_cycles, void* stream);
 
 /* Enable (1) or disable (0) event timing of every kernel this context
  * enqueues.  Launch counts are kept either way.  Host-side, synchronous. */

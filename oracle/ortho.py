@@ -21,9 +21,10 @@ Readings where the paper is garbled or silent (also listed in the design doc):
     D1 gives the SVD of B1 = sum_k Y_k D2 X_k^T alone (and of
     B2 = sum_k Y_k^T D1 X_k for D2), which is what is computed here.  B1 and
     B2 are the same sums as in the general update (Corollary 1, Result 1).
-  * A numerically rank-deficient B (smallest singular value <= 1e-12 of the
-    largest) has no unique Procrustes solution: SingularError, dictionary
-    unchanged.
+  * A numerically rank-deficient B has no unique Procrustes solution:
+    SingularError, dictionary unchanged.  B is a sum of FP32 data, so rank
+    deficiency is judged at that precision: smallest singular value <= 1e-6 of
+    the largest.
 """
 from __future__ import annotations
 
@@ -34,14 +35,15 @@ from .sdl_oracle import SingularError, densify
 __all__ = ["threshold_code", "procrustes_D1", "procrustes_D2", "ortho_iterate",
            "SVD_RANK_REL", "OrthoIterResult"]
 
-SVD_RANK_REL = 1e-12
+SVD_RANK_REL = 1e-6
 _CHUNK = 4096
 
 
 def threshold_code(Y, D1, D2, s: int):
     """T_s(D1^T Y_k D2) for every k.  Returns (support (N, s) int64 in order of
-    decreasing |value|, ties by smaller q; coef (N, s); res_energy (N,) =
-    ||Y_k - D1 X_k D2^T||^2 formed explicitly)."""
+    decreasing |value|, ties by smaller q, -1 for slots whose entry is exactly
+    0; coef (N, s); res_energy (N,) = ||Y_k - D1 X_k D2^T||^2 formed
+    explicitly)."""
     Y = np.asarray(Y, dtype=np.float64)
     N, p1, p2 = Y.shape
     n1, n2 = D1.shape[1], D2.shape[1]
@@ -51,6 +53,10 @@ def threshold_code(Y, D1, D2, s: int):
     order = np.argsort(-np.abs(flat), axis=1, kind="stable")[:, :s]
     coef = np.take_along_axis(flat, order, axis=1)
     support = order.astype(np.int64)
+    # exactly-zero entries are not picks (a signal then keeps fewer than s)
+    zero = coef == 0.0
+    support[zero] = -1
+    coef[zero] = 0.0
     X = densify(support, coef, n1, n2)
     R = Y - np.einsum("ai,kij,bj->kab", D1, X, D2, optimize=True)
     return support, coef, np.einsum("kab,kab->k", R, R)

@@ -27,7 +27,7 @@ namespace sdl {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr long long kWaitLimit = 1ll << 26;   // bounded mbarrier wait (polls)
+constexpr long long kWaitCycles = 1ll << 31;  // bounded mbarrier wait: about one second
 
 __host__ __device__ constexpr int pad_vec(int r) { return r <= 2 ? r : ((r + 3) & ~3); }
 __host__ __device__ constexpr int al4(int x) { return (x + 3) & ~3; }
@@ -132,10 +132,11 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
-// bounded wait for phase `parity` of `bar`; false on timeout
+// bounded wait for phase `parity` of `bar` (SM clock); false on timeout
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
     const unsigned a = smem_addr(bar);
-    for (long long it = 0; it < kWaitLimit; ++it) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < kWaitCycles) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"

@@ -6,12 +6,14 @@
 // printed SVD argument of Remark 1 carries an extra sum X X^T factor, which
 // the trace maximisation behind the Procrustes problem does not have.
 //
-//   ortho_code_kernel  one warp per signal: Y staged in shared memory,
+//   ortho_code_sq_kernel  square shapes compiled ahead (8, 12, 16): a
+//                      half-warp per signal with register-blocked Z and C;
+//   ortho_code_kernel  any other shape, one warp per signal: Y staged in shared memory,
 //                      Z = Y D2, C = D1^T Z, s rounds of warp argmax with
 //                      masking (ties to the smallest q), the code, and B1 or
 //                      B2 accumulated in warp-private shared memory, combined
 //                      in warp order per CTA (deterministic slots);
-//   procrustes_kernel  one CTA: one-sided Jacobi SVD of B in FP64 (column
+//   procrustes_kernel  one CTA: one-sided Jacobi SVD of B in FP32 (column
 //                      pairs in round-robin order, one warp per pair),
 //                      D = U V^T, the objective change 2 (tr(D_old^T B) -
 //                      sum sigma) and the RMSE.
@@ -27,8 +29,9 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kOrthoMaxP = 32;       // p1, p2 <= 32
 constexpr int kOrthoWarps = 8;       // warps (signals in flight) per CTA
-constexpr double kRankRel = 1e-12;   // smallest / largest singular value
-constexpr int kMaxSweeps = 40;
+constexpr float kRankRel = 1e-6f;    // smallest / largest singular value (FP32 level)
+constexpr float kJacobiTol = 1e-7f;  // rotate while |a_i . a_j| > tol ||a_i|| ||a_j||
+constexpr int kMaxSweeps = 30;
 
 __host__ __device__ constexpr int al4(int x) { return (x + 3) & ~3; }
 
@@ -207,34 +210,283 @@ __global__ void __launch_bounds__(kOrthoWarps * 32)
     }
 }
 
+// Square shapes compiled ahead (P = p1 = p2 in {8, 12, 16}): a half-warp
+// (16 lanes, a 4 x 4 lane grid) per signal, each lane owning an R x R block
+// (R = P / 4) of Z = Y D2 and of C = D1^T Z in registers, so each shared-memory
+// operand load feeds R multiply-adds.  Same selection, codes and partial sums
+// as ortho_code_kernel; the two half-warps of a warp code different signals
+// and keep separate accumulators, combined in a fixed order.
+constexpr int kHalfTeams = 2 * kOrthoWarps;   // signals in flight per CTA
+
+template <int P>
+struct SqLayout {
+    static constexpr int PP = P * P, LDZ = P + 1;
+    static constexpr int d1r = 0;                       // D1 row-major (a, i)
+    static constexpr int d2r = d1r + al4(PP);           // D2 row-major (b, j)
+    static constexpr int team0 = d2r + al4(PP);
+    static constexpr int y = 0, z = al4(PP), acc = z + al4(P * LDZ), en = acc + al4(PP);
+    static constexpr int tstride = en + 4;
+    static constexpr int total = team0 + kHalfTeams * tstride;
+};
+
+template <int P, int SIDE>
+__global__ void __launch_bounds__(kOrthoWarps * 32)
+    ortho_code_sq_kernel(const float* __restrict__ Y, long long N, const float* __restrict__ D1,
+                         const float* __restrict__ D2, int s, int32_t* __restrict__ support,
+                         float* __restrict__ coef, int32_t* __restrict__ nnz,
+                         float* __restrict__ res_energy, float* __restrict__ part_f,
+                         double* __restrict__ part_d, int* err) {
+    using L = SqLayout<P>;
+    constexpr int R = P / 4, PP = P * P, LDZ = L::LDZ;
+    extern __shared__ __align__(16) float sm[];
+    const int lane = threadIdx.x & 31, half = lane >> 4, l16 = lane & 15;
+    const int team = (threadIdx.x >> 5) * 2 + half;
+    const unsigned hm = 0xffffu << (16 * half);
+    const int li = l16 & 3, lj = l16 >> 2, i0 = li * R, j0 = lj * R;
+    float* D1r = sm + L::d1r;
+    float* D2r = sm + L::d2r;
+    float* tb = sm + L::team0 + team * L::tstride;
+    float* Ys = tb + L::y;
+    float* Zs = tb + L::z;
+    float* acc = tb + L::acc;
+    for (int e = threadIdx.x; e < PP; e += blockDim.x) {
+        const int r = e / P, c = e - r * P;
+        D1r[e] = D1[r + P * c];
+        D2r[e] = D2[r + P * c];
+    }
+    if constexpr (SIDE != kCodeOnly)
+        for (int e = l16; e < PP; e += 16) acc[e] = 0.f;
+    __syncthreads();
+
+    float e_res = 0.f, e_res_c = 0.f, e_y = 0.f, e_y_c = 0.f;
+    const long long stride = (long long)gridDim.x * kHalfTeams;
+    for (long long k = (long long)blockIdx.x * kHalfTeams + team; k < N; k += stride) {
+        float ss = 0.f;
+        for (int e = l16; e < PP; e += 16) {
+            const float v = Y[(size_t)k * PP + e];
+            Ys[e] = v;
+            ss = fmaf(v, v, ss);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) ss += __shfl_xor_sync(hm, ss, o);
+        __syncwarp(hm);
+        const bool finite = isfinite(ss);
+        int cnt = 0;
+        float E2 = ss;
+        int my_q = -1;
+        float my_x = 0.f;
+        if (finite) {
+            // Z block: rows i0.., cols j0.. of Y D2
+            float z[R][R];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < R; ++c) z[r][c] = 0.f;
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                float u[R], v[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) u[r] = Ys[(i0 + r) + P * b];
+#pragma unroll
+                for (int c = 0; c < R; ++c) v[c] = D2r[b * P + j0 + c];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int c = 0; c < R; ++c) z[r][c] = fmaf(u[r], v[c], z[r][c]);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < R; ++c) Zs[(i0 + r) * LDZ + j0 + c] = z[r][c];
+            __syncwarp(hm);
+            // C block: C[i][j] = sum_a D1[a][i] Z[a][j]
+            float cv[R][R];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < R; ++c) cv[r][c] = 0.f;
+#pragma unroll
+            for (int aa = 0; aa < P; ++aa) {
+                float u[R], v[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) u[r] = D1r[aa * P + i0 + r];
+#pragma unroll
+                for (int c = 0; c < R; ++c) v[c] = Zs[aa * LDZ + j0 + c];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int c = 0; c < R; ++c) cv[r][c] = fmaf(u[r], v[c], cv[r][c]);
+            }
+            // T_s: s rounds of (max |C|, smallest q) over the half-warp
+            for (int t = 0; t < s; ++t) {
+                float best = 0.f, bestv = 0.f;
+                int bq = 0x7fffffff;
+#pragma unroll
+                for (int c = 0; c < R; ++c)
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {           // increasing q = i + P j
+                        const float v = fabsf(cv[r][c]);
+                        if (v > best) { best = v; bestv = cv[r][c]; bq = (i0 + r) + P * (j0 + c); }
+                    }
+                const unsigned M = __reduce_max_sync(hm, __float_as_uint(best));
+                if (M == 0u) break;
+                const unsigned cand = (__float_as_uint(best) == M) ? (unsigned)bq : 0xffffffffu;
+                const int q = (int)__reduce_min_sync(hm, cand);
+                const int qi = q % P, qj = q / P;
+                const int owner = (qi / R) + 4 * (qj / R) + 16 * half;
+                const float x = __shfl_sync(hm, bestv, owner);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int c = 0; c < R; ++c)
+                        if (i0 + r == qi && j0 + c == qj) cv[r][c] = __int_as_float(0x7fc00000);
+                if (l16 == t) {
+                    my_q = q;
+                    my_x = x;
+                }
+                E2 = fmaf(-x, x, E2);
+                cnt = t + 1;
+            }
+        }
+        if (support && l16 < s) {
+            support[(size_t)k * s + l16] = l16 < cnt ? my_q : -1;
+            coef[(size_t)k * s + l16] = l16 < cnt ? my_x : 0.f;
+        }
+        if (l16 == 0) {
+            if (nnz) nnz[k] = cnt;
+            if (res_energy) res_energy[k] = finite ? fmaxf(E2, 0.f) : __int_as_float(0x7fc00000);
+            if (!finite) record_error(err, SDL_ERR_NONFINITE);
+        }
+        if constexpr (SIDE == kSideD1) {
+            // B1[a, i_l] += x_l Z[a, j_l], lane a
+            for (int l = 0; l < cnt; ++l) {
+                const int ql = __shfl_sync(hm, my_q, l + 16 * half);
+                const float xl = __shfl_sync(hm, my_x, l + 16 * half);
+                const int il = ql % P, jl = ql / P;
+                if (l16 < P) acc[l16 * P + il] = fmaf(xl, Zs[l16 * LDZ + jl], acc[l16 * P + il]);
+                __syncwarp(hm);
+            }
+        } else if constexpr (SIDE == kSideD2) {
+            // B2[b, j_l] += x_l (Y^T D1)[b, i_l], lane b
+            for (int l = 0; l < cnt; ++l) {
+                const int ql = __shfl_sync(hm, my_q, l + 16 * half);
+                const float xl = __shfl_sync(hm, my_x, l + 16 * half);
+                const int il = ql % P, jl = ql / P;
+                if (l16 < P) {
+                    float wv = 0.f;
+#pragma unroll
+                    for (int aa = 0; aa < P; ++aa) wv = fmaf(Ys[aa + P * l16], D1r[aa * P + il], wv);
+                    acc[l16 * P + jl] = fmaf(xl, wv, acc[l16 * P + jl]);
+                }
+                __syncwarp(hm);
+            }
+        }
+        if (l16 == 0 && finite) {
+            const float ye = fmaxf(E2, 0.f) - e_res_c;
+            const float te = e_res + ye;
+            e_res_c = (te - e_res) - ye;
+            e_res = te;
+            const float yy = ss - e_y_c;
+            const float ty = e_y + yy;
+            e_y_c = (ty - e_y) - yy;
+            e_y = ty;
+        }
+        __syncwarp(hm);
+    }
+    if constexpr (SIDE != kCodeOnly) {
+        if (l16 == 0) {
+            tb[L::en] = e_res - e_res_c;
+            tb[L::en + 1] = e_y - e_y_c;
+        }
+        __syncthreads();
+        float* dst = part_f + (size_t)blockIdx.x * PP;
+        for (int e = threadIdx.x; e < PP; e += blockDim.x) {
+            float v = 0.f;
+            for (int tt = 0; tt < kHalfTeams; ++tt) v += sm[L::team0 + tt * L::tstride + L::acc + e];
+            dst[e] = v;
+        }
+        if (threadIdx.x < 2) {
+            double d = 0.0;
+            for (int tt = 0; tt < kHalfTeams; ++tt)
+                d += (double)sm[L::team0 + tt * L::tstride + L::en + threadIdx.x];
+            part_d[(size_t)blockIdx.x * 2 + threadIdx.x] = d;
+        }
+    }
+}
+
+template <int P, int SIDE>
+int launch_sq(const float* Y, long long N, const float* D1, const float* D2, int s,
+              int32_t* support, float* coef, int32_t* nnz, float* res, float* part_f,
+              double* part_d, int max_slots, int* err, int num_sms, cudaStream_t st) {
+    const size_t bytes = sizeof(float) * (size_t)SqLayout<P>::total;
+    auto kern = ortho_code_sq_kernel<P, SIDE>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return SDL_ERR_CUDA;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kOrthoWarps * 32, bytes) !=
+        cudaSuccess)
+        return SDL_ERR_CUDA;
+    bps = std::max(1, std::min(bps, 8));
+    const long long need = (N + kHalfTeams - 1) / kHalfTeams;
+    long long grid = std::max<long long>(1, std::min<long long>(need, (long long)num_sms * bps));
+    if (SIDE != kCodeOnly) grid = std::min<long long>(grid, max_slots);
+    kern<<<(int)grid, kOrthoWarps * 32, bytes, st>>>(Y, N, D1, D2, s, support, coef, nnz, res,
+                                                     part_f, part_d, err);
+    if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
+    return SIDE == kCodeOnly ? 0 : (int)grid;
+}
+
+template <int P>
+int launch_sq_side(const float* Y, long long N, const float* D1, const float* D2, int s,
+                   int32_t* support, float* coef, int32_t* nnz, float* res, float* part_f,
+                   double* part_d, int max_slots, int side, int* err, int num_sms,
+                   cudaStream_t st) {
+    switch (side) {
+        case kCodeOnly:
+            return launch_sq<P, kCodeOnly>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+                                           max_slots, err, num_sms, st);
+        case kSideD1:
+            return launch_sq<P, kSideD1>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+                                         max_slots, err, num_sms, st);
+        default:
+            return launch_sq<P, kSideD2>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+                                         max_slots, err, num_sms, st);
+    }
+}
+
 // One CTA, 32 * ceil(m/2) threads (m = n rounded up to even): one-sided
-// Jacobi SVD of B (p x n row-major, p = n) in FP64 and D = U V^T.
+// Jacobi SVD of B (p x n row-major, p = n) in FP32 and D = U V^T.  B itself
+// is an FP32 sum, so FP32 rotations add no error beyond its own (FP64 is a
+// narrow, long-latency pipe on this part: a 12 x 12 FP64 Jacobi took ~0.3 ms).
 //   red_f = B, red_d[0] = objective before (sum of residual energies with
 //   the old dictionary and these codes).  The old D must be orthonormal: then
 //   f(D) = sum ||Y||^2 - 2 tr(D^T B) + sum ||X||^2, and the change is
-//   -2 (sum sigma - tr(D_old^T B)).
+//   -2 (sum sigma - tr(D_old^T B)) (accumulated in FP64).
 __global__ void procrustes_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d,
                                   float* D, int n, double inv_count, float* objective_out,
                                   float* rmse_out, int* err) {
-    extern __shared__ __align__(16) double smd[];
+    extern __shared__ __align__(16) float smf[];
     const int m = (n + 1) & ~1;             // even number of columns (a zero column pads)
-    double* A = smd;                         // m columns of length n (column-major)
-    double* V = A + (size_t)m * n;           // m x m (column-major)
+    float* A = smf;                          // m columns of length n (column-major)
+    float* V = A + m * n;                    // m x m (column-major)
+    float* sig = V + m * m;                  // m
     __shared__ int s_fail, s_rot;
-    __shared__ double s_tr;
+    __shared__ double s_tr, s_sig;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         s_fail = 0;
         s_tr = 0.0;
+        s_sig = 0.0;
     }
+    __syncthreads();
     for (int e = tid; e < m * n; e += nth) {
         const int c = e / n, r = e - c * n;
         const float v = c < n ? red_f[r * n + c] : 0.f;
-        A[e] = (double)v;
+        A[e] = v;
         if (!isfinite(v)) s_fail = SDL_ERR_NONFINITE;
     }
-    for (int e = tid; e < m * m; e += nth) V[e] = (e / m == e % m) ? 1.0 : 0.0;
-    __syncthreads();
+    for (int e = tid; e < m * m; e += nth) V[e] = (e / m == e % m) ? 1.f : 0.f;
     // tr(D_old^T B)
     if (warp == 0) {
         double t = 0.0;
@@ -247,12 +499,11 @@ __global__ void procrustes_kernel(const float* __restrict__ red_f, const double*
         if (lane == 0) s_tr = t;
     }
     __syncthreads();
-    // sweeps: m - 1 rounds of m/2 disjoint pairs (round-robin tournament)
+    // sweeps: m - 1 rounds of m/2 disjoint column pairs (round-robin tournament)
     for (int sweep = 0; sweep < kMaxSweeps && s_fail == 0; ++sweep) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int round = 0; round < m - 1; ++round) {
-            // pair `warp`: positions warp and m-1-warp of the rotated list
             const int pa = warp, pb = m - 1 - warp;
             auto player = [&](int pos) {
                 if (pos == 0) return 0;
@@ -264,12 +515,12 @@ __global__ void procrustes_kernel(const float* __restrict__ red_f, const double*
                 ci = cj;
                 cj = t;
             }
-            double al = 0.0, be = 0.0, ga = 0.0;
+            float al = 0.f, be = 0.f, ga = 0.f;
             for (int r = lane; r < n; r += 32) {
-                const double x = A[ci * n + r], y = A[cj * n + r];
-                al += x * x;
-                be += y * y;
-                ga += x * y;
+                const float x = A[ci * n + r], y = A[cj * n + r];
+                al = fmaf(x, x, al);
+                be = fmaf(y, y, be);
+                ga = fmaf(x, y, ga);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -277,17 +528,17 @@ __global__ void procrustes_kernel(const float* __restrict__ red_f, const double*
                 be += __shfl_xor_sync(kFull, be, o);
                 ga += __shfl_xor_sync(kFull, ga, o);
             }
-            if (ga != 0.0 && fabs(ga) > 1e-14 * sqrt(al * be)) {
-                const double zeta = (be - al) / (2.0 * ga);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+            if (ga != 0.f && fabsf(ga) > kJacobiTol * sqrtf(al) * sqrtf(be)) {
+                const float zeta = (be - al) / (2.f * ga);
+                const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+                const float c = rsqrtf(fmaf(t, t, 1.f)), sn = c * t;
                 for (int r = lane; r < n; r += 32) {
-                    const double x = A[ci * n + r], y = A[cj * n + r];
+                    const float x = A[ci * n + r], y = A[cj * n + r];
                     A[ci * n + r] = c * x - sn * y;
                     A[cj * n + r] = sn * x + c * y;
                 }
                 for (int r = lane; r < m; r += 32) {
-                    const double x = V[ci * m + r], y = V[cj * m + r];
+                    const float x = V[ci * m + r], y = V[cj * m + r];
                     V[ci * m + r] = c * x - sn * y;
                     V[cj * m + r] = sn * x + c * y;
                 }
@@ -299,48 +550,45 @@ __global__ void procrustes_kernel(const float* __restrict__ red_f, const double*
         __syncthreads();
         if (rot == 0) break;
     }
-    // singular values, rank check, D = sum_i (a_i / sigma_i) v_i^T over the n true columns
-    double* sig = V + (size_t)m * m;         // m
     for (int c = tid; c < m; c += nth) {
-        double t = 0.0;
-        for (int r = 0; r < n; ++r) t += A[c * n + r] * A[c * n + r];
-        sig[c] = sqrt(t);
+        float t = 0.f;
+        for (int r = 0; r < n; ++r) t = fmaf(A[c * n + r], A[c * n + r], t);
+        sig[c] = sqrtf(t);
     }
     __syncthreads();
     if (tid == 0 && s_fail == 0) {
-        double smax = 0.0, smin = INFINITY;
-        int zeros = 0;
+        float smax = 0.f, smin = INFINITY;
+        int pad = m != n ? 1 : 0;   // the padding column carries one zero singular value
+        double ssum = 0.0;
         for (int c = 0; c < m; ++c) {
-            smax = fmax(smax, sig[c]);
+            smax = fmaxf(smax, sig[c]);
+            ssum += (double)sig[c];
         }
-        // the padding column (odd n) carries a zero singular value: skip one zero
         for (int c = 0; c < m; ++c) {
-            if (m != n && sig[c] == 0.0 && zeros == 0) {
-                ++zeros;
+            if (pad && sig[c] == 0.f) {
+                pad = 0;
                 continue;
             }
-            smin = fmin(smin, sig[c]);
+            smin = fminf(smin, sig[c]);
         }
-        if (!(smax > 0.0) || !(smin > kRankRel * smax)) s_fail = SDL_ERR_SINGULAR;
+        if (!(smax > 0.f) || !(smin > kRankRel * smax)) s_fail = SDL_ERR_SINGULAR;
+        s_sig = ssum;
     }
     __syncthreads();
     const bool ok = s_fail == 0;
     if (ok) {
-        // rows r < n of U V^T restricted to the n true columns of V
         for (int e = tid; e < n * n; e += nth) {
-            const int r = e / n, c = e - r * n;   // D[r, c]
-            double d = 0.0;
+            const int r = e / n, c = e - r * n;   // D[r, c] = sum_i U[r, i] V[c, i]
+            float d = 0.f;
             for (int i = 0; i < m; ++i)
-                if (sig[i] > 0.0) d += A[i * n + r] / sig[i] * V[i * m + c];
-            D[r + n * c] = (float)d;
+                if (sig[i] > 0.f) d = fmaf(A[i * n + r] / sig[i], V[i * m + c], d);
+            D[r + n * c] = d;
         }
     }
     if (tid == 0) {
         if (!ok) record_error(err, s_fail);
-        double ssum = 0.0;
-        for (int c = 0; c < m; ++c) ssum += sig[c];
         const double before = red_d[0];
-        const double after = ok ? before - 2.0 * (ssum - s_tr) : before;
+        const double after = ok ? before - 2.0 * (s_sig - s_tr) : before;
         if (objective_out) {
             objective_out[0] = (float)before;
             objective_out[1] = (float)after;
@@ -390,6 +638,17 @@ int launch_ortho_code(const float* Y, int p1, int p2, long long N, const float* 
                       const float* D2, int s, int32_t* support, float* coef, int32_t* nnz,
                       float* res, float* part_f, double* part_d, int max_slots, int side,
                       int* err, int num_sms, cudaStream_t st) {
+    // compiled square shapes (s <= 16: the half-warp holds one pick per lane)
+    if (p1 == p2 && s <= 16 && (p1 == 8 || p1 == 12 || p1 == 16)) {
+        if (p1 == 8)
+            return launch_sq_side<8>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+                                     max_slots, side, err, num_sms, st);
+        if (p1 == 12)
+            return launch_sq_side<12>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+                                      max_slots, side, err, num_sms, st);
+        return launch_sq_side<16>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+                                  max_slots, side, err, num_sms, st);
+    }
     switch (side) {
         case kCodeOnly:
             return launch_ortho_code_impl<kCodeOnly>(Y, p1, p2, N, D1, D2, s, support, coef, nnz,
@@ -408,7 +667,7 @@ int launch_ortho_code(const float* Y, int p1, int p2, long long N, const float* 
 int launch_procrustes(const float* red_f, const double* red_d, float* D, int n, double inv_count,
                       float* objective_out, float* rmse_out, int* err, cudaStream_t st) {
     const int m = (n + 1) & ~1;
-    const size_t bytes = sizeof(double) * ((size_t)m * n + (size_t)m * m + m);
+    const size_t bytes = sizeof(float) * ((size_t)m * n + (size_t)m * m + m);
     if (cudaFuncSetAttribute(procrustes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) != cudaSuccess)
         return SDL_ERR_CUDA;

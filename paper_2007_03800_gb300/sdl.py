@@ -65,6 +65,7 @@ SIGNATURES = {
                                 _P, _P, _P, _P],
     "sdl_ortho_sparse_code": [_P, _P, _I, _I, _L, _P, _P, _I, _P, _P, _P, _P, _P],
     "sdl_ortho_iterate": [_P, _P, _I, _I, _L, _P, _P, _I, _P, _P, _P, _P, _P],
+    "sdl_selftest_timeout": [_P, ctypes.c_longlong, _P],
     "sdl_set_precision": [_P, _I],
     "sdl_precision_stats": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "sdl_profile_enable": [_P, _I],
@@ -208,6 +209,11 @@ class Context:
     def status(self, stream=None) -> int:
         """Synchronise and return (and clear) the recorded device-side error."""
         return self._lib.sdl_status(self._h, _stream(stream))
+
+    def selftest_timeout(self, max_cycles: int = 1 << 24, stream=None) -> None:
+        """``sdl_selftest_timeout``: a bounded wait that runs out on the GPU."""
+        _check(self._lib.sdl_selftest_timeout(self._h, int(max_cycles), _stream(stream)),
+               "sdl_selftest_timeout")
 
     def check(self, stream=None) -> None:
         _check(self.status(stream), "device")

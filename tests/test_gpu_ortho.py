@@ -46,8 +46,10 @@ def compare_threshold(gpu_sup, Y, D1, D2, ref_sup):
     return same, ties
 
 
-def test_threshold_codes_match_oracle(gpu_ctx):
-    p, s = 8, 4
+@pytest.mark.parametrize("p,s", [(8, 4), (12, 6), (6, 3), (8, 20)])
+def test_threshold_codes_match_oracle(gpu_ctx, p, s):
+    """Compiled square shapes (8, 12 with s <= 16) and the generic kernel
+    (6 x 6; s = 20 > 16)."""
     Y = ortho_model(4096, p, s)
     D1, D2 = orth(1, p), orth(2, p)
     sup, coef, res = ortho.threshold_code(Y, D1, D2, s)

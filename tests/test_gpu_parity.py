@@ -259,3 +259,15 @@ def test_host_argument_errors(gpu_ctx):
     assert e.value.code == -7
     with pytest.raises(ValueError):
         gpu_ctx.sparse_code(Yg.contiguous(), D1g, D2g, 4)   # wrong memory layout
+
+
+def test_bounded_wait_times_out_and_context_survives(gpu_ctx):
+    """A wait on an mbarrier that nothing completes runs out after its cycle
+    bound (here 2^24 cycles, about 8 ms) and records SDL_ERR_TIMEOUT; the
+    next status read is clean and the context still codes correctly."""
+    gpu_ctx.selftest_timeout(1 << 24)
+    assert sdl.ERRORS[gpu_ctx.status()] == "SDL_ERR_TIMEOUT"
+    assert gpu_ctx.status() == 0
+    Y, _, _, _, _ = synth.kron_model(512, 8, 8, 16, 16, 4, 20.0, seed=11)
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    check_code(gpu_ctx, Y, D1, D2, 4)

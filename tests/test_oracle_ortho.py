@@ -58,6 +58,15 @@ def test_threshold_equals_omp_for_orthonormal_dictionaries():
     assert np.allclose(res, omp.res_energy, rtol=1e-10, atol=1e-12)
 
 
+def test_threshold_skips_exact_zeros():
+    D = np.eye(3)
+    Y = np.zeros((2, 3, 3))
+    Y[1, 0, 0] = 2.0                               # one nonzero entry
+    sup, coef, res = ortho.threshold_code(Y, D, D, 2)
+    assert list(sup[0]) == [-1, -1] and list(sup[1]) == [0, -1]
+    assert list(coef[1]) == [2.0, 0.0] and res[1] == 0.0
+
+
 def test_threshold_tie_goes_to_smaller_q():
     D = np.eye(2)
     Y = np.array([[[1.0, -1.0], [0.5, 1.0]]])     # |C| = 1 at q = 0, 2, 3
