@@ -607,6 +607,56 @@ def study_ortho(args):
     return 0
 
 
+def study_gemm(args):
+    """The tcgen05 BF16 GEMM on the shapes the library runs it at: the split
+    correlations of the 50k hyperspectral-shaped signals (three operand pairs,
+    M = 50000, N = n1 n2 = 4096, K = p1 p2 = 1024), the same with one pair,
+    and the support network's forward GEMMs at a 65536-signal chunk.  Device
+    time (CUDA events, median of steps) and the fraction of the measured BF16
+    peak; the operands of the first shape are 300 MB (> L2)."""
+    import torch
+
+    from paper_2007_03800_gb300 import sdl
+    dev = torch.device("cuda:0")
+    ctx = sdl.Context(0)
+    peak = float(measured_peaks().get("bf16_tflops", 1900.0))
+    out = {}
+    g = torch.Generator(device=dev).manual_seed(0)
+    for name, (M, N, K, terms) in {"corr_split_50000x4096x1024x3": (50000, 4096, 1024, 3),
+                                   "corr_50000x4096x1024": (50000, 4096, 1024, 1),
+                                   "mlp_fwd1_65536x512x144": (65536, 512, 144, 1),
+                                   "mlp_fwd2_65536x576x512": (65536, 576, 512, 1)}.items():
+        A = [torch.randn(M, K, device=dev, generator=g).to(torch.bfloat16) for _ in range(terms)]
+        B = [torch.randn(N, K, device=dev, generator=g).to(torch.bfloat16) for _ in range(terms)]
+        C = torch.empty(M, N, device=dev)
+
+        def run():
+            sdl.gemm_bf16(ctx, A[0], B[0], C=C)
+            for t in range(1, terms):
+                sdl.gemm_bf16(ctx, A[t], B[t], C=C, accumulate=True)
+
+        for _ in range(args.warmup):
+            run()
+        ms = []
+        for _ in range(max(args.steps, 1)):
+            a, b = _events()
+            a.record()
+            run()
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        med = statistics.median(ms)
+        tf = 2.0 * M * N * K * terms / (med / 1e3) / 1e12
+        out[name] = {"ms": med, "tflops": tf, "frac_of_measured_bf16": tf / peak,
+                     "launches": terms}
+        del A, B, C
+    ctx.check()
+    ctx.close()
+    print(json.dumps({"study": "gemm", "peak_bf16_tflops_measured": peak, "shapes": out}),
+          flush=True)
+    return 0
+
+
 def study_denoise(args):
     """Denoising with one batch of three patch sizes (8, 12, 16; D p x 2p;
     error-driven stop at 1.15 sigma p, s <= p/2) on a 512x512 synthetic image
@@ -656,7 +706,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed region only: no e2e loop, CPU baseline or clock sampling "
                          "(for profiler runs; its numbers are not bench values)")
-    ap.add_argument("--study", choices=["precision", "learned", "denoise", "ortho"],
+    ap.add_argument("--study", choices=["precision", "learned", "denoise", "ortho", "gemm"],
                     help="run one extra study on its own workload instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -665,7 +715,8 @@ def main():
         return run_reference(args)
     if args.study:
         return {"precision": study_precision, "learned": study_learned,
-                "denoise": study_denoise, "ortho": study_ortho}[args.study](args)
+                "denoise": study_denoise, "ortho": study_ortho,
+                "gemm": study_gemm}[args.study](args)
     return run_ours(args)
 
 

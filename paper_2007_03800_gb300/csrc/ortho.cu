@@ -260,12 +260,33 @@ __global__ void __launch_bounds__(kOrthoWarps * 32)
 
     float e_res = 0.f, e_res_c = 0.f, e_y = 0.f, e_y_c = 0.f;
     const long long stride = (long long)gridDim.x * kHalfTeams;
+    // the next signal of this half-warp is loaded into registers while the
+    // current one is coded
+    constexpr int NV = (PP + 15) / 16;
+    float yn[NV];
+    {
+        const long long k0 = (long long)blockIdx.x * kHalfTeams + team;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int e = l16 + 16 * v;
+            yn[v] = (k0 < N && e < PP) ? __ldg(Y + (size_t)k0 * PP + e) : 0.f;
+        }
+    }
     for (long long k = (long long)blockIdx.x * kHalfTeams + team; k < N; k += stride) {
         float ss = 0.f;
-        for (int e = l16; e < PP; e += 16) {
-            const float v = Y[(size_t)k * PP + e];
-            Ys[e] = v;
-            ss = fmaf(v, v, ss);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int e = l16 + 16 * v;
+            if (e < PP) {
+                Ys[e] = yn[v];
+                ss = fmaf(yn[v], yn[v], ss);
+            }
+        }
+        const long long kn = k + stride;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int e = l16 + 16 * v;
+            yn[v] = (kn < N && e < PP) ? __ldg(Y + (size_t)kn * PP + e) : 0.f;
         }
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) ss += __shfl_xor_sync(hm, ss, o);

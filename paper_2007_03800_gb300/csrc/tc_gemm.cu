@@ -301,12 +301,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int j = 0; j < 32; ++j) stage[lane * kStageLd + j] = x[j];
                     __syncwarp();
                     const int n = n0 + c0 + lane;
-                    for (int rr = 0; rr < 32; ++rr) {
-                        const int mm = row0 + rr;
-                        if (mm < M && n < N) {
-                            float* d = dst + (size_t)mm * ld + n;
-                            const float val = stage[rr * kStageLd + lane];
-                            *d = accumulate ? *d + val : val;
+                    if (accumulate) {
+                        // all 32 old values first (independent loads), then the stores
+                        float old[32];
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const int mm = row0 + rr;
+                            old[rr] = (mm < M && n < N) ? dst[(size_t)mm * ld + n] : 0.f;
+                        }
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const int mm = row0 + rr;
+                            if (mm < M && n < N)
+                                dst[(size_t)mm * ld + n] = old[rr] + stage[rr * kStageLd + lane];
+                        }
+                    } else {
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const int mm = row0 + rr;
+                            if (mm < M && n < N) dst[(size_t)mm * ld + n] = stage[rr * kStageLd + lane];
                         }
                     }
                 };
