@@ -804,6 +804,9 @@ extern "C" int sdl_sparse_code_learned(sdl_ctx* c, sdl_mlp* m, const float* Y, i
         if (Q <= 256)
             topk_kernel<8><<<blocks_for((long long)B * 32, 256), 256, 0, st>>>(
                 scores, Q, B, Q, k, k2, cand + (size_t)r0 * k2);
+        else if (Q <= 576)
+            topk_kernel<18><<<blocks_for((long long)B * 32, 256), 256, 0, st>>>(
+                scores, Q, B, Q, k, k2, cand + (size_t)r0 * k2);
         else
             topk_kernel<32><<<blocks_for((long long)B * 32, 256), 256, 0, st>>>(
                 scores, Q, B, Q, k, k2, cand + (size_t)r0 * k2);

@@ -134,6 +134,25 @@ __device__ __forceinline__ float team_sum_f32(float v, float* scratch, int wit, 
     }
 }
 
+// FP32 re-scoring of one correlation: w_i . d2_j over p2 terms (w_i contiguous,
+// d2_j with stride ld), four interleaved partial sums so the loads and
+// multiply-adds overlap.  Kept out of line: it runs for a few flagged entries
+// per step, and inlining it into the unrolled per-entry loops only inflates
+// register pressure.
+__device__ __noinline__ float rescore_dot(const float* __restrict__ w, const float* __restrict__ d,
+                                          int ld, int p2) {
+    float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
+    int b = 0;
+    for (; b + 4 <= p2; b += 4) {
+        e0 = fmaf(w[b], d[b * ld], e0);
+        e1 = fmaf(w[b + 1], d[(b + 1) * ld], e1);
+        e2 = fmaf(w[b + 2], d[(b + 2) * ld], e2);
+        e3 = fmaf(w[b + 3], d[(b + 3) * ld], e3);
+    }
+    for (; b < p2; ++b) e0 = fmaf(w[b], d[b * ld], e0);
+    return (e0 + e1) + (e2 + e3);
+}
+
 // misc area of the slab (32 words): [0,8) max scratch, [8,16) min scratch,
 // [16,24) sum scratch, 24 = broadcast b, 25 = accept flag.
 enum { kMiscMax = 0, kMiscMin = 8, kMiscSum = 16, kMiscB = 24, kMiscOk = 25 };
@@ -321,9 +340,7 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                                 const int e = r * RJ + c;
                                 if (!((exact >> e) & 1u) && fabsf(sc[r][c]) >= thr) {
                                     const int i = i0 + r, j = j0 + c;
-                                    const float* wi = Zs + i * p2;
-                                    float ex = 0.f;
-                                    for (int b = 0; b < p2; ++b) ex = fmaf(wi[b], D2r[b * N2P + j], ex);
+                                    const float ex = rescore_dot(Zs + i * p2, D2r + j, N2P, p2);
                                     sc[r][c] = ex - (c0[r][c] - sc[r][c]);
                                     c0[r][c] = ex;
                                     exact |= 1u << e;

@@ -492,6 +492,7 @@ __global__ void procrustes_kernel(const float* __restrict__ red_f, const double*
     float* A = smf;                          // m columns of length n (column-major)
     float* V = A + m * n;                    // m x m (column-major)
     float* sig = V + m * m;                  // m
+    int* sched = reinterpret_cast<int*>(sig + m);   // (m - 1) x m/2 column pairs
     __shared__ int s_fail, s_rot;
     __shared__ double s_tr, s_sig;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -520,22 +521,27 @@ __global__ void procrustes_kernel(const float* __restrict__ red_f, const double*
         if (lane == 0) s_tr = t;
     }
     __syncthreads();
-    // sweeps: m - 1 rounds of m/2 disjoint column pairs (round-robin tournament)
+    // round-robin tournament: in round r, positions w and m-1-w meet; position
+    // 0 is fixed and the others rotate (every pair meets once per sweep)
+    for (int e = tid; e < (m - 1) * (m / 2); e += nth) {
+        const int round = e / (m / 2), w = e - round * (m / 2);
+        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (m - 1); };
+        int ci = player(w), cj = player(m - 1 - w);
+        if (ci > cj) {
+            const int t = ci;
+            ci = cj;
+            cj = t;
+        }
+        sched[e] = ci | (cj << 16);
+    }
+    __syncthreads();
+    // sweeps: m - 1 rounds of m/2 disjoint column pairs
     for (int sweep = 0; sweep < kMaxSweeps && s_fail == 0; ++sweep) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int round = 0; round < m - 1; ++round) {
-            const int pa = warp, pb = m - 1 - warp;
-            auto player = [&](int pos) {
-                if (pos == 0) return 0;
-                return 1 + (pos - 1 + round) % (m - 1);
-            };
-            int ci = player(pa), cj = player(pb);
-            if (ci > cj) {
-                const int t = ci;
-                ci = cj;
-                cj = t;
-            }
+            const int pr = sched[round * (m / 2) + warp];
+            const int ci = pr & 0xffff, cj = pr >> 16;
             float al = 0.f, be = 0.f, ga = 0.f;
             for (int r = lane; r < n; r += 32) {
                 const float x = A[ci * n + r], y = A[cj * n + r];
@@ -543,15 +549,29 @@ __global__ void procrustes_kernel(const float* __restrict__ red_f, const double*
                 be = fmaf(y, y, be);
                 ga = fmaf(x, y, ga);
             }
+            if (n > 16) {
+                al += __shfl_xor_sync(kFull, al, 16);
+                be += __shfl_xor_sync(kFull, be, 16);
+                ga += __shfl_xor_sync(kFull, ga, 16);
+            }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 8; o > 0; o >>= 1) {
                 al += __shfl_xor_sync(kFull, al, o);
                 be += __shfl_xor_sync(kFull, be, o);
                 ga += __shfl_xor_sync(kFull, ga, o);
             }
-            if (ga != 0.f && fabsf(ga) > kJacobiTol * sqrtf(al) * sqrtf(be)) {
-                const float zeta = (be - al) / (2.f * ga);
-                const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+            // rotate while ga^2 > tol^2 al be; the angle only needs to be
+            // approximate (fast reciprocal / square root): a rotation is
+            // orthogonal for any (c, s) with c^2 + s^2 = 1 to rounding
+            if (ga != 0.f && ga * ga > kJacobiTol * kJacobiTol * al * be) {
+                const float zeta = __fdividef(be - al, 2.f * ga);
+                float t;
+                if (fabsf(zeta) < 1e18f) {
+                    const float q = fmaf(zeta, zeta, 1.f);
+                    t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + q * rsqrtf(q));
+                } else {
+                    t = __fdividef(0.5f, zeta);
+                }
                 const float c = rsqrtf(fmaf(t, t, 1.f)), sn = c * t;
                 for (int r = lane; r < n; r += 32) {
                     const float x = A[ci * n + r], y = A[cj * n + r];
@@ -688,7 +708,8 @@ int launch_ortho_code(const float* Y, int p1, int p2, long long N, const float* 
 int launch_procrustes(const float* red_f, const double* red_d, float* D, int n, double inv_count,
                       float* objective_out, float* rmse_out, int* err, cudaStream_t st) {
     const int m = (n + 1) & ~1;
-    const size_t bytes = sizeof(float) * ((size_t)m * n + (size_t)m * m + m);
+    const size_t bytes = sizeof(float) * ((size_t)m * n + (size_t)m * m + m) +
+                         sizeof(int) * (size_t)(m - 1) * (m / 2);
     if (cudaFuncSetAttribute(procrustes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) != cudaSuccess)
         return SDL_ERR_CUDA;
