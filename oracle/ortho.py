@@ -39,11 +39,13 @@ SVD_RANK_REL = 1e-6
 _CHUNK = 4096
 
 
-def threshold_code(Y, D1, D2, s: int):
+def threshold_code(Y, D1, D2, s: int, eps: float | None = None):
     """T_s(D1^T Y_k D2) for every k.  Returns (support (N, s) int64 in order of
     decreasing |value|, ties by smaller q, -1 for slots whose entry is exactly
     0; coef (N, s); res_energy (N,) = ||Y_k - D1 X_k D2^T||^2 formed
-    explicitly)."""
+    explicitly).  With eps, error-driven: before each kept entry, stop once
+    the residual norm is <= eps (for orthonormal D the residual energy after
+    keeping entries c_1..c_t is ||Y_k||^2 - sum c_l^2), at most s entries."""
     Y = np.asarray(Y, dtype=np.float64)
     N, p1, p2 = Y.shape
     n1, n2 = D1.shape[1], D2.shape[1]
@@ -55,6 +57,11 @@ def threshold_code(Y, D1, D2, s: int):
     support = order.astype(np.int64)
     # exactly-zero entries are not picks (a signal then keeps fewer than s)
     zero = coef == 0.0
+    if eps is not None:
+        energy = np.einsum("kab,kab->k", Y, Y)
+        kept_before = np.concatenate([np.zeros((N, 1)), np.cumsum(coef ** 2, axis=1)[:, :-1]], axis=1)
+        zero |= (energy[:, None] - kept_before) <= eps * eps
+        zero = np.logical_or.accumulate(zero, axis=1)
     support[zero] = -1
     coef[zero] = 0.0
     X = densify(support, coef, n1, n2)

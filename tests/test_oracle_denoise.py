@@ -55,3 +55,39 @@ def test_denoise_with_orthonormal_dictionary_is_thresholding():
     Y, _ = dn.extract_patches(img, 4)
     r = oracle.residual(Y, I, I, code.support, code.coef)
     assert np.all(np.sqrt(np.sum(r * r, axis=(1, 2))) <= 1e-9 + 1e-12)
+
+
+def test_ssim_identity_and_symmetry():
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0, 255, (20, 23))
+    y = np.clip(x + rng.normal(0, 15, x.shape), 0, 255)
+    assert np.isclose(dn.ssim(x, x), 1.0, atol=1e-12)
+    assert np.isclose(dn.ssim(x, y), dn.ssim(y, x), rtol=1e-12)
+    assert dn.ssim(x, y) < 1.0
+
+
+def test_ssim_of_constant_images_closed_form():
+    """Constant images a and b: every window has zero variances, so SSIM is the
+    luminance term (2ab + C1) / (a^2 + b^2 + C1)."""
+    a, b = 100.0, 140.0
+    C1 = (0.01 * 255) ** 2
+    got = dn.ssim(np.full((15, 15), a), np.full((15, 15), b))
+    assert np.isclose(got, (2 * a * b + C1) / (a * a + b * b + C1), rtol=1e-12)
+
+
+def test_ssim_by_brute_force_weighted_sums():
+    """One window position (11 x 11 image), the weights written out from the
+    Gaussian formula and every moment summed term by term."""
+    rng = np.random.default_rng(6)
+    x = rng.uniform(0, 255, (11, 11))
+    y = rng.uniform(0, 255, (11, 11))
+    w = np.array([[np.exp(-((i - 5) ** 2 + (j - 5) ** 2) / 4.5) for j in range(11)] for i in range(11)])
+    w /= w.sum()
+    mx = sum(w[i, j] * x[i, j] for i in range(11) for j in range(11))
+    my = sum(w[i, j] * y[i, j] for i in range(11) for j in range(11))
+    vx = sum(w[i, j] * x[i, j] ** 2 for i in range(11) for j in range(11)) - mx * mx
+    vy = sum(w[i, j] * y[i, j] ** 2 for i in range(11) for j in range(11)) - my * my
+    cxy = sum(w[i, j] * x[i, j] * y[i, j] for i in range(11) for j in range(11)) - mx * my
+    C1, C2 = (0.01 * 255) ** 2, (0.03 * 255) ** 2
+    want = ((2 * mx * my + C1) * (2 * cxy + C2)) / ((mx * mx + my * my + C1) * (vx + vy + C2))
+    assert np.isclose(dn.ssim(x, y), want, rtol=1e-10)

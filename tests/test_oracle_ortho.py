@@ -152,3 +152,20 @@ def test_ortho_iteration_is_monotone_and_orthonormal():
         for D in (it.D1, it.D2):
             assert np.allclose(D.T @ D, np.eye(p), atol=1e-12)
         D1, D2 = it.D1, it.D2
+
+
+def test_error_driven_threshold_equals_error_driven_omp():
+    """With an eps stop, thresholding on orthonormal dictionaries is error-driven
+    OMP (the denoising coder of Sec. IV)."""
+    rng = np.random.default_rng(49)
+    p, s = 6, 5
+    D1, D2 = orth(rng, p), orth(rng, p)
+    Y = rng.standard_normal((80, p, p)) * rng.uniform(0.2, 2.0, (80, 1, 1))
+    eps = 3.0
+    sup, coef, res = ortho.threshold_code(Y, D1, D2, s, eps=eps)
+    omp = oracle.omp2d(Y, D1, D2, s, eps=eps)
+    assert np.array_equal(sup, omp.support)
+    assert np.allclose(coef, omp.coef, atol=1e-12)
+    assert np.allclose(res, omp.res_energy, rtol=1e-10, atol=1e-10)
+    nnz = (sup >= 0).sum(axis=1)
+    assert nnz.min() < nnz.max() <= s and np.any((nnz > 0) & (nnz < s))
