@@ -657,6 +657,54 @@ def study_gemm(args):
     return 0
 
 
+def study_table3(args):
+    """The denoising protocol of Table III on synthetic stand-ins for its five
+    512x512 test images: sigma in {5, 10, 20, 30, 50}, one noise realisation
+    per case, 8x8 patches; general dictionaries 8x16 and orthonormal 8x8
+    learned on 4000 noisy patches with s = 6 (50 iterations), error-driven
+    coding of all 255 025 patches (eps = 1.15 sigma 8, at most 4 atoms); PSNR
+    and SSIM of every case and the device time of each pipeline."""
+    import torch
+
+    from paper_2007_03800_gb300 import denoise as dn
+    from paper_2007_03800_gb300 import sdl, synth
+    dev = torch.device("cuda:0")
+    ctx = sdl.Context(0)
+    rows = []
+    sigmas = (5.0, 10.0, 20.0, 30.0, 50.0)
+    for img_seed in range(200, 205):
+        clean = synth.synthetic_image(img_seed)
+        cg = torch.tensor(clean, dtype=torch.float32, device=dev)
+        for sigma in sigmas:
+            noisy = clean + np.random.default_rng(img_seed * 100 + int(sigma)).normal(0, sigma, clean.shape)
+            ng = torch.tensor(noisy, dtype=torch.float32, device=dev)
+            row = {"image_seed": img_seed, "sigma": sigma,
+                   "psnr_noisy": sdl.psnr(ng, cg).item()}
+            for variant in ("general", "ortho"):
+                a, b = _events()
+                a.record()
+                r = dn.table3_case(ctx, cg, ng, sigma, variant=variant)
+                b.record()
+                b.synchronize()
+                row[variant] = {"psnr": round(r["psnr"].item(), 3), "ssim": round(r["ssim"].item(), 4),
+                                "nnz_mean": round(r["nnz_mean"].item(), 3),
+                                "ms": round(a.elapsed_time(b), 2)}
+            rows.append(row)
+    ctx.check()
+    ctx.close()
+    mean = {}
+    for sigma in sigmas:
+        sel = [r for r in rows if r["sigma"] == sigma]
+        mean[str(sigma)] = {v: {"psnr": round(float(np.mean([r[v]["psnr"] for r in sel])), 3),
+                                "ssim": round(float(np.mean([r[v]["ssim"] for r in sel])), 4)}
+                            for v in ("general", "ortho")}
+        mean[str(sigma)]["psnr_noisy"] = round(float(np.mean([r["psnr_noisy"] for r in sel])), 3)
+    print(json.dumps({"study": "table3", "workload": "5 synthetic 512x512 images x sigma "
+                      "{5,10,20,30,50}, 8x8 patches, general 8x16 and orthonormal 8x8",
+                      "mean_over_images": mean, "cases": rows}), flush=True)
+    return 0
+
+
 def study_denoise(args):
     """Denoising with one batch of three patch sizes (8, 12, 16; D p x 2p;
     error-driven stop at 1.15 sigma p, s <= p/2) on a 512x512 synthetic image
@@ -706,7 +754,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed region only: no e2e loop, CPU baseline or clock sampling "
                          "(for profiler runs; its numbers are not bench values)")
-    ap.add_argument("--study", choices=["precision", "learned", "denoise", "ortho", "gemm"],
+    ap.add_argument("--study", choices=["precision", "learned", "denoise", "ortho", "gemm", "table3"],
                     help="run one extra study on its own workload instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -716,7 +764,7 @@ def main():
     if args.study:
         return {"precision": study_precision, "learned": study_learned,
                 "denoise": study_denoise, "ortho": study_ortho,
-                "gemm": study_gemm}[args.study](args)
+                "gemm": study_gemm, "table3": study_table3}[args.study](args)
     return run_ours(args)
 
 

@@ -243,6 +243,15 @@ int sdl_patch_average(sdl_ctx* ctx, const int32_t* support, const float* coef,
                       const float* D2, int n2, int p, int H, int W, float* image_out,
                       void* stream);
 
+/* sdl_ssim - mean SSIM index (Wang, Bovik, Sheikh, Simoncelli 2004; the index
+ * of Table III) of image x against ref (H x W row-major device floats, H, W
+ * >= 11) over every 11 x 11 window position inside the image, Gaussian window
+ * weights (sigma 1.5, normalised to sum 1), C1 = (0.01 peak)^2,
+ * C2 = (0.03 peak)^2; written to device float out[0].  Deterministic (fixed
+ * summation order); per-block sums use a context workspace. */
+int sdl_ssim(sdl_ctx* ctx, const float* x, const float* ref, int H, int W, float peak,
+             float* out, void* stream);
+
 /* sdl_psnr - 10 log10(peak^2 / MSE(x, ref)) over `count` floats, written to
  * device float out[0]. */
 int sdl_psnr(const float* x, const float* ref, int64_t count, float peak, float* out,
@@ -374,10 +383,15 @@ int sdl_sparse_code_learned(sdl_ctx* ctx, sdl_mlp* mlp, const float* Y, int p1, 
  * argument printed in Remark 1).  1 <= p1, p2 <= 32, 1 <= s <= min(32, p1 p2).
  * Layouts as sdl_sparse_code (D1 p1 x p1, D2 p2 x p2 column-major).
  *
+ * eps > 0: error-driven, a signal stops before keeping another entry once
+ * ||Y_k - D1 X_k D2^T||_F <= eps (the residual energy of orthonormal
+ * dictionaries is ||Y_k||^2 - sum of the kept entries squared), at most s;
+ * eps <= 0: s entries.
+ *
  * sdl_ortho_sparse_code - the thresholded codes only (res_energy may be NULL).
  */
 int sdl_ortho_sparse_code(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
-                          const float* D1, const float* D2, int s, int32_t* support,
+                          const float* D1, const float* D2, int s, float eps, int32_t* support,
                           float* coef, int32_t* nnz, float* res_energy, void* stream);
 
 /*
@@ -391,7 +405,7 @@ int sdl_ortho_sparse_code(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t 
  * and leaves that dictionary unchanged.  N >= 1.
  */
 int sdl_ortho_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N, float* D1,
-                      float* D2, int s, int32_t* support, float* coef, int32_t* nnz,
+                      float* D2, int s, float eps, int32_t* support, float* coef, int32_t* nnz,
                       float* rmse_out, void* stream);
 
 /*

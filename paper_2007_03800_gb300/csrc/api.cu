@@ -197,6 +197,7 @@ int sdl_destroy(sdl_ctx* c) {
     cudaFree(c->norms);
     cudaFree(c->rec);
     cudaFree(c->learn);
+    cudaFree(c->ssim_part);
     cudaFree(c->Yb);
     cudaFree(c->KT);
     cudaFree(c->C0);

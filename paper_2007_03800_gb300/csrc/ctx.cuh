@@ -21,6 +21,8 @@ struct sdl_ctx {
     size_t cap_rec = 0;
     char* learn = nullptr;       // learned-coder workspace
     size_t cap_learn = 0;
+    double* ssim_part = nullptr; // per-block SSIM sums
+    size_t cap_ssim = 0;
     // precision extension
     int prec = 0;                // SDL_PREC_* flags
     void* Yb = nullptr;          // BF16 signals (N x Kp)

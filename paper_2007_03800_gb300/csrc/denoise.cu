@@ -1,7 +1,7 @@
 // Patch-based denoising around the sparse coder (the experiment of Sec. IV):
 // gather every stride-1 p x p patch of an image with its mean removed, put
 // the coded patches back by averaging overlapping reconstructions, and the
-// PSNR of the result.
+// PSNR and SSIM of the result.
 #include <algorithm>
 #include <cmath>
 
@@ -120,6 +120,82 @@ __global__ void __launch_bounds__(1024) psnr_kernel(const float* __restrict__ a,
     }
 }
 
+// SSIM index (Wang, Bovik, Sheikh, Simoncelli 2004) of x against ref: one
+// thread per window position inside the image (valid region), 11 x 11
+// Gaussian window (sigma 1.5, normalised to sum 1), per-block sums in FP64
+// combined in a fixed order by ssim_finish_kernel.
+constexpr int kSsimWin = 11;
+constexpr float kSsimSigma = 1.5f;
+constexpr int kSsimThreads = 256;
+
+__global__ void __launch_bounds__(kSsimThreads)
+    ssim_kernel(const float* __restrict__ x, const float* __restrict__ y, int H, int W,
+                float peak, double* __restrict__ part) {
+    __shared__ float w[kSsimWin * kSsimWin];
+    __shared__ double red[kSsimThreads / 32];
+    constexpr int G = kSsimWin;
+    if (threadIdx.x < G * G) {
+        const int u = threadIdx.x / G - G / 2, v = threadIdx.x % G - G / 2;
+        w[threadIdx.x] = expf(-(float)(u * u + v * v) / (2.f * kSsimSigma * kSsimSigma));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int e = 0; e < G * G; ++e) t += (double)w[e];
+        red[0] = t;
+    }
+    __syncthreads();
+    const float inv = (float)(1.0 / red[0]);
+    __syncthreads();
+    if (threadIdx.x < G * G) w[threadIdx.x] *= inv;
+    __syncthreads();
+    const int wc = W - G + 1;
+    const long long P = (long long)(H - G + 1) * wc;
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double val = 0.0;
+    if (k < P) {
+        const int r = (int)(k / wc), c = (int)(k % wc);
+        float mx = 0.f, my = 0.f;
+        for (int a = 0; a < G; ++a)
+            for (int b = 0; b < G; ++b) {
+                const float wt = w[a * G + b];
+                mx = fmaf(wt, x[(size_t)(r + a) * W + c + b], mx);
+                my = fmaf(wt, y[(size_t)(r + a) * W + c + b], my);
+            }
+        float vx = 0.f, vy = 0.f, cxy = 0.f;
+        for (int a = 0; a < G; ++a)
+            for (int b = 0; b < G; ++b) {
+                const float wt = w[a * G + b];
+                const float dx = x[(size_t)(r + a) * W + c + b] - mx;
+                const float dy = y[(size_t)(r + a) * W + c + b] - my;
+                vx = fmaf(wt * dx, dx, vx);
+                vy = fmaf(wt * dy, dy, vy);
+                cxy = fmaf(wt * dx, dy, cxy);
+            }
+        const double C1 = (0.01 * peak) * (0.01 * peak), C2 = (0.03 * peak) * (0.03 * peak);
+        val = ((2.0 * mx * my + C1) * (2.0 * cxy + C2)) /
+              (((double)mx * mx + (double)my * my + C1) * ((double)vx + vy + C2));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(kFull, val, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int e = 0; e < kSsimThreads / 32; ++e) t += red[e];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void ssim_finish_kernel(const double* __restrict__ part, int nblocks, long long P,
+                                   float* __restrict__ out) {
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nblocks; ++b) t += part[b];
+        out[0] = (float)(t / (double)P);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -159,6 +235,29 @@ int sdl_patch_average(sdl_ctx* c, const int32_t* support, const float* coef, con
     reconstruct_patches_kernel<<<(unsigned)blocks, threads, 0, st>>>(support, coef, means, N, s_max,
                                                                      D1, n1, D2, n2, p, c->rec);
     average_patches_kernel<<<dim3((W + 127) / 128, H), 128, 0, st>>>(c->rec, H, W, p, image_out);
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+int sdl_ssim(sdl_ctx* c, const float* x, const float* ref, int H, int W, float peak, float* out,
+             void* stream) {
+    if (!c || !x || !ref || !out || H < kSsimWin || W < kSsimWin || !(peak > 0.f))
+        return SDL_ERR_ARG;
+    DeviceGuard g(c->device);
+    const long long P = (long long)(H - kSsimWin + 1) * (W - kSsimWin + 1);
+    const int nblocks = (int)((P + kSsimThreads - 1) / kSsimThreads);
+    if ((size_t)nblocks > c->cap_ssim) {
+        if (c->ssim_part) cudaFree(c->ssim_part);
+        c->ssim_part = nullptr;
+        c->cap_ssim = 0;
+        if (cudaMalloc(&c->ssim_part, sizeof(double) * nblocks) != cudaSuccess) {
+            cudaGetLastError();
+            return SDL_ERR_WORKSPACE;
+        }
+        c->cap_ssim = nblocks;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    ssim_kernel<<<nblocks, kSsimThreads, 0, st>>>(x, ref, H, W, peak, c->ssim_part);
+    ssim_finish_kernel<<<1, 32, 0, st>>>(c->ssim_part, nblocks, P, out);
     return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
 }
 

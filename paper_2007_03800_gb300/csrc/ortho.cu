@@ -58,7 +58,7 @@ struct OrthoLayout {
 template <int SIDE>
 __global__ void __launch_bounds__(kOrthoWarps * 32)
     ortho_code_kernel(const float* __restrict__ Y, int p1, int p2, long long N,
-                      const float* __restrict__ D1, const float* __restrict__ D2, int s,
+                      const float* __restrict__ D1, const float* __restrict__ D2, int s, float eps2,
                       int32_t* __restrict__ support, float* __restrict__ coef,
                       int32_t* __restrict__ nnz, float* __restrict__ res_energy,
                       float* __restrict__ part_f, double* __restrict__ part_d, int* err) {
@@ -118,8 +118,10 @@ __global__ void __launch_bounds__(kOrthoWarps * 32)
                 Cs[q] = c;
             }
             __syncwarp();
-            // ---- T_s: s rounds of argmax |C| over unmasked entries
+            // ---- T_s: s rounds of argmax |C| over unmasked entries (with an
+            // error-driven stop before a round once ||R||^2 <= eps^2)
             for (int t = 0; t < s; ++t) {
+                if (eps2 > 0.f && E2 <= eps2) break;
                 float best = 0.f;
                 int bq = 0x7fffffff;
                 for (int q = lane; q < Q; q += 32) {
@@ -232,7 +234,7 @@ struct SqLayout {
 template <int P, int SIDE>
 __global__ void __launch_bounds__(kOrthoWarps * 32)
     ortho_code_sq_kernel(const float* __restrict__ Y, long long N, const float* __restrict__ D1,
-                         const float* __restrict__ D2, int s, int32_t* __restrict__ support,
+                         const float* __restrict__ D2, int s, float eps2, int32_t* __restrict__ support,
                          float* __restrict__ coef, int32_t* __restrict__ nnz,
                          float* __restrict__ res_energy, float* __restrict__ part_f,
                          double* __restrict__ part_d, int* err) {
@@ -338,8 +340,10 @@ __global__ void __launch_bounds__(kOrthoWarps * 32)
 #pragma unroll
                     for (int c = 0; c < R; ++c) cv[r][c] = fmaf(u[r], v[c], cv[r][c]);
             }
-            // T_s: s rounds of (max |C|, smallest q) over the half-warp
+            // T_s: s rounds of (max |C|, smallest q) over the half-warp, with
+            // the error-driven stop
             for (int t = 0; t < s; ++t) {
+                if (eps2 > 0.f && E2 <= eps2) break;
                 float best = 0.f, bestv = 0.f;
                 int bq = 0x7fffffff;
 #pragma unroll
@@ -436,7 +440,7 @@ __global__ void __launch_bounds__(kOrthoWarps * 32)
 }
 
 template <int P, int SIDE>
-int launch_sq(const float* Y, long long N, const float* D1, const float* D2, int s,
+int launch_sq(const float* Y, long long N, const float* D1, const float* D2, int s, float eps2,
               int32_t* support, float* coef, int32_t* nnz, float* res, float* part_f,
               double* part_d, int max_slots, int* err, int num_sms, cudaStream_t st) {
     const size_t bytes = sizeof(float) * (size_t)SqLayout<P>::total;
@@ -452,26 +456,26 @@ int launch_sq(const float* Y, long long N, const float* D1, const float* D2, int
     const long long need = (N + kHalfTeams - 1) / kHalfTeams;
     long long grid = std::max<long long>(1, std::min<long long>(need, (long long)num_sms * bps));
     if (SIDE != kCodeOnly) grid = std::min<long long>(grid, max_slots);
-    kern<<<(int)grid, kOrthoWarps * 32, bytes, st>>>(Y, N, D1, D2, s, support, coef, nnz, res,
-                                                     part_f, part_d, err);
+    kern<<<(int)grid, kOrthoWarps * 32, bytes, st>>>(Y, N, D1, D2, s, eps2, support, coef, nnz,
+                                                     res, part_f, part_d, err);
     if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
     return SIDE == kCodeOnly ? 0 : (int)grid;
 }
 
 template <int P>
-int launch_sq_side(const float* Y, long long N, const float* D1, const float* D2, int s,
+int launch_sq_side(const float* Y, long long N, const float* D1, const float* D2, int s, float eps2,
                    int32_t* support, float* coef, int32_t* nnz, float* res, float* part_f,
                    double* part_d, int max_slots, int side, int* err, int num_sms,
                    cudaStream_t st) {
     switch (side) {
         case kCodeOnly:
-            return launch_sq<P, kCodeOnly>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+            return launch_sq<P, kCodeOnly>(Y, N, D1, D2, s, eps2, support, coef, nnz, res, part_f, part_d,
                                            max_slots, err, num_sms, st);
         case kSideD1:
-            return launch_sq<P, kSideD1>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+            return launch_sq<P, kSideD1>(Y, N, D1, D2, s, eps2, support, coef, nnz, res, part_f, part_d,
                                          max_slots, err, num_sms, st);
         default:
-            return launch_sq<P, kSideD2>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+            return launch_sq<P, kSideD2>(Y, N, D1, D2, s, eps2, support, coef, nnz, res, part_f, part_d,
                                          max_slots, err, num_sms, st);
     }
 }
@@ -644,7 +648,7 @@ size_t code_smem(int p1, int p2, int side, int wpc) {
 
 template <int SIDE>
 int launch_ortho_code_impl(const float* Y, int p1, int p2, long long N, const float* D1,
-                           const float* D2, int s, int32_t* support, float* coef, int32_t* nnz,
+                           const float* D2, int s, float eps2, int32_t* support, float* coef, int32_t* nnz,
                            float* res, float* part_f, double* part_d, int max_slots, int* err,
                            int num_sms, cudaStream_t st) {
     const size_t bytes = code_smem(p1, p2, SIDE, kOrthoWarps);
@@ -660,8 +664,8 @@ int launch_ortho_code_impl(const float* Y, int p1, int p2, long long N, const fl
     const long long need = (N + kOrthoWarps - 1) / kOrthoWarps;
     long long grid = std::max<long long>(1, std::min<long long>(need, (long long)num_sms * bps));
     if (SIDE != kCodeOnly) grid = std::min<long long>(grid, max_slots);
-    kern<<<(int)grid, kOrthoWarps * 32, bytes, st>>>(Y, p1, p2, N, D1, D2, s, support, coef, nnz,
-                                                     res, part_f, part_d, err);
+    kern<<<(int)grid, kOrthoWarps * 32, bytes, st>>>(Y, p1, p2, N, D1, D2, s, eps2, support, coef,
+                                                     nnz, res, part_f, part_d, err);
     if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
     return SIDE == kCodeOnly ? 0 : (int)grid;
 }
@@ -676,29 +680,29 @@ bool ortho_shape_supported(int p1, int p2, int s) {
 }
 
 int launch_ortho_code(const float* Y, int p1, int p2, long long N, const float* D1,
-                      const float* D2, int s, int32_t* support, float* coef, int32_t* nnz,
+                      const float* D2, int s, float eps2, int32_t* support, float* coef, int32_t* nnz,
                       float* res, float* part_f, double* part_d, int max_slots, int side,
                       int* err, int num_sms, cudaStream_t st) {
     // compiled square shapes (s <= 16: the half-warp holds one pick per lane)
     if (p1 == p2 && s <= 16 && (p1 == 8 || p1 == 12 || p1 == 16)) {
         if (p1 == 8)
-            return launch_sq_side<8>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+            return launch_sq_side<8>(Y, N, D1, D2, s, eps2, support, coef, nnz, res, part_f, part_d,
                                      max_slots, side, err, num_sms, st);
         if (p1 == 12)
-            return launch_sq_side<12>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+            return launch_sq_side<12>(Y, N, D1, D2, s, eps2, support, coef, nnz, res, part_f, part_d,
                                       max_slots, side, err, num_sms, st);
-        return launch_sq_side<16>(Y, N, D1, D2, s, support, coef, nnz, res, part_f, part_d,
+        return launch_sq_side<16>(Y, N, D1, D2, s, eps2, support, coef, nnz, res, part_f, part_d,
                                   max_slots, side, err, num_sms, st);
     }
     switch (side) {
         case kCodeOnly:
-            return launch_ortho_code_impl<kCodeOnly>(Y, p1, p2, N, D1, D2, s, support, coef, nnz,
+            return launch_ortho_code_impl<kCodeOnly>(Y, p1, p2, N, D1, D2, s, eps2, support, coef, nnz,
                                                      res, part_f, part_d, max_slots, err, num_sms, st);
         case kSideD1:
-            return launch_ortho_code_impl<kSideD1>(Y, p1, p2, N, D1, D2, s, support, coef, nnz,
+            return launch_ortho_code_impl<kSideD1>(Y, p1, p2, N, D1, D2, s, eps2, support, coef, nnz,
                                                    res, part_f, part_d, max_slots, err, num_sms, st);
         case kSideD2:
-            return launch_ortho_code_impl<kSideD2>(Y, p1, p2, N, D1, D2, s, support, coef, nnz,
+            return launch_ortho_code_impl<kSideD2>(Y, p1, p2, N, D1, D2, s, eps2, support, coef, nnz,
                                                    res, part_f, part_d, max_slots, err, num_sms, st);
         default:
             return SDL_ERR_ARG;
@@ -724,23 +728,24 @@ int launch_procrustes(const float* red_f, const double* red_d, float* D, int n, 
 extern "C" {
 
 int sdl_ortho_sparse_code(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const float* D1,
-                          const float* D2, int s, int32_t* support, float* coef, int32_t* nnz,
-                          float* res_energy, void* stream) {
+                          const float* D2, int s, float eps, int32_t* support, float* coef,
+                          int32_t* nnz, float* res_energy, void* stream) {
     if (!c || N < 0 || (N > 0 && (!Y || !D1 || !D2 || !support || !coef || !nnz)))
         return SDL_ERR_ARG;
     if (!ortho_shape_supported(p1, p2, s)) return SDL_ERR_ARG;
     if (N == 0) return SDL_OK;
     DeviceGuard g(c->device);
     Trace tr(c, kOrthoCode, (cudaStream_t)stream);
-    const int rc = launch_ortho_code(Y, p1, p2, N, D1, D2, s, support, coef, nnz, res_energy,
+    const int rc = launch_ortho_code(Y, p1, p2, N, D1, D2, s, eps > 0.f ? eps * eps : 0.f, support,
+                                     coef, nnz, res_energy,
                                      nullptr, nullptr, 0, kCodeOnly, c->err, c->num_sms,
                                      (cudaStream_t)stream);
     return rc < 0 ? rc : SDL_OK;
 }
 
 int sdl_ortho_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1, float* D2,
-                      int s, int32_t* support, float* coef, int32_t* nnz, float* rmse_out,
-                      void* stream) {
+                      int s, float eps, int32_t* support, float* coef, int32_t* nnz,
+                      float* rmse_out, void* stream) {
     if (!c || N < 1 || !Y || !D1 || !D2 || !support || !coef || !nnz) return SDL_ERR_ARG;
     if (!ortho_shape_supported(p1, p2, s)) return SDL_ERR_ARG;
     DeviceGuard g(c->device);
@@ -754,7 +759,8 @@ int sdl_ortho_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, flo
         int slots;
         {
             Trace tr(c, kOrthoCode, st);
-            slots = launch_ortho_code(Y, p1, p2, N, D1, D2, s, side == kSideD2 ? support : nullptr,
+            slots = launch_ortho_code(Y, p1, p2, N, D1, D2, s, eps > 0.f ? eps * eps : 0.f,
+                                      side == kSideD2 ? support : nullptr,
                                       coef, nnz, nullptr, c->part_f, c->part_d, max_slots, side,
                                       c->err, c->num_sms, st);
         }

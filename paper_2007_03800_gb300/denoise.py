@@ -48,3 +48,53 @@ def denoise(ctx: sdl.Context, noisy: torch.Tensor, sigma: float, groups=DEFAULT_
             out["psnr"].append(sdl.psnr(img, clean, stream=stream))
     batch.close()
     return out
+
+
+def orthonormal_start(p: int, seed: int):
+    """Q factor (signs fixed by R's diagonal) of a seeded p x p N(0,1) matrix."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    Q, R = np.linalg.qr(rng.standard_normal((p, p)))
+    return Q * np.sign(np.diag(R))
+
+
+def table3_case(ctx: sdl.Context, clean: torch.Tensor, noisy: torch.Tensor, sigma: float,
+                variant: str = "general", p: int = 8, n: int = 16, train_patches: int = 4000,
+                train_s: int = 6, iterations: int = 50, patch_seed: int = 0, dict_seed: int = 1,
+                stream=None):
+    """The denoising protocol of Table III (Sec. IV) on the GPU: dictionaries
+    learned on `train_patches` mean-removed p x p patches of the noisy image at
+    seeded positions with sparsity `train_s` (general: D1, D2 p x n by
+    Algorithm 1; ortho: p x p orthonormal by Algorithm 1 - Orthonormal), then
+    every overlapping patch coded error-driven (eps = 1.15 sigma p, at most p/2
+    atoms), the image rebuilt by averaging, and PSNR / SSIM against `clean`."""
+    import numpy as np
+    H, W = noisy.shape
+    dev = noisy.device
+    imgs = noisy.detach().cpu().numpy()[None].astype(np.float64)
+    Ytr = synth.random_patches(imgs, train_patches, p, seed=patch_seed)
+    Yg = sdl.signals(torch.tensor(Ytr, dtype=torch.float32, device=dev))
+    if variant == "general":
+        D1, D2 = synth.init_dictionaries(p, p, n, n, seed=dict_seed)
+    elif variant == "ortho":
+        D1, D2 = orthonormal_start(p, dict_seed), orthonormal_start(p, dict_seed + 1)
+    else:
+        raise ValueError(variant)
+    D1g = sdl.dictionary(torch.tensor(D1, dtype=torch.float32, device=dev))
+    D2g = sdl.dictionary(torch.tensor(D2, dtype=torch.float32, device=dev))
+    codes = None
+    for _ in range(iterations):
+        if variant == "general":
+            codes = ctx.iterate(Yg, D1g, D2g, train_s, out=codes, stream=stream)
+        else:
+            codes = ctx.ortho_iterate(Yg, D1g, D2g, train_s, out=codes, stream=stream)
+    Y, means = sdl.extract_patches(noisy, p, stream=stream)
+    eps = 1.15 * sigma * p
+    if variant == "general":
+        code = ctx.sparse_code(Y, D1g, D2g, p // 2, eps=eps, stream=stream)
+    else:
+        code = ctx.ortho_sparse_code(Y, D1g, D2g, p // 2, eps=eps, stream=stream)
+    img = sdl.patch_average(ctx, code, means, D1g, D2g, p, H, W, stream=stream)
+    return dict(image=img, psnr=sdl.psnr(img, clean, stream=stream),
+                ssim=sdl.ssim(ctx, img, clean, stream=stream),
+                nnz_mean=code.nnz.float().mean(), dictionaries=(D1g, D2g))

@@ -63,9 +63,10 @@ SIGNATURES = {
     "sdl_mlp_forward": [_P, _P, _L, _P, _P],
     "sdl_sparse_code_learned": [_P, _P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P,
                                 _P, _P, _P, _P],
-    "sdl_ortho_sparse_code": [_P, _P, _I, _I, _L, _P, _P, _I, _P, _P, _P, _P, _P],
-    "sdl_ortho_iterate": [_P, _P, _I, _I, _L, _P, _P, _I, _P, _P, _P, _P, _P],
+    "sdl_ortho_sparse_code": [_P, _P, _I, _I, _L, _P, _P, _I, _F, _P, _P, _P, _P, _P],
+    "sdl_ortho_iterate": [_P, _P, _I, _I, _L, _P, _P, _I, _F, _P, _P, _P, _P, _P],
     "sdl_selftest_timeout": [_P, ctypes.c_longlong, _P],
+    "sdl_ssim": [_P, _P, _P, _I, _I, _F, _P, _P],
     "sdl_set_precision": [_P, _I],
     "sdl_precision_stats": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "sdl_profile_enable": [_P, _I],
@@ -302,19 +303,22 @@ class Context:
         return out
 
     # ---- orthonormal variant (Remark 1)
-    def ortho_sparse_code(self, Y, D1, D2, s, out: Codes | None = None, stream=None) -> Codes:
-        """``sdl_ortho_sparse_code``: X_k = T_s(D1^T Y_k D2) for square orthonormal D."""
+    def ortho_sparse_code(self, Y, D1, D2, s, eps=0.0, out: Codes | None = None,
+                          stream=None) -> Codes:
+        """``sdl_ortho_sparse_code``: X_k = T_s(D1^T Y_k D2) for square orthonormal D
+        (error-driven with eps > 0)."""
         N, p1, p2 = _check_Y(Y)
         if _check_D(D1, p1, "D1") != p1 or _check_D(D2, p2, "D2") != p2:
             raise ValueError("the orthonormal variant needs square dictionaries")
         if out is None:
             out = Codes.empty(N, s, Y.device, with_energy=True)
         _check(self._lib.sdl_ortho_sparse_code(
-            self._h, _ptr(Y), p1, p2, N, _ptr(D1), _ptr(D2), s, _ptr(out.support), _ptr(out.coef),
-            _ptr(out.nnz), _ptr(out.res_energy), _stream(stream)), "sdl_ortho_sparse_code")
+            self._h, _ptr(Y), p1, p2, N, _ptr(D1), _ptr(D2), s, float(eps), _ptr(out.support),
+            _ptr(out.coef), _ptr(out.nnz), _ptr(out.res_energy), _stream(stream)),
+            "sdl_ortho_sparse_code")
         return out
 
-    def ortho_iterate(self, Y, D1, D2, s, out: Codes | None = None, rmse_out=None,
+    def ortho_iterate(self, Y, D1, D2, s, eps=0.0, out: Codes | None = None, rmse_out=None,
                       stream=None) -> Codes:
         """``sdl_ortho_iterate``: one iteration of Algorithm 1 - Orthonormal."""
         N, p1, p2 = _check_Y(Y)
@@ -328,8 +332,8 @@ class Context:
         if rmse_out is not None:
             _need(rmse_out, torch.float32, (2,), None, "rmse_out")
         _check(self._lib.sdl_ortho_iterate(
-            self._h, _ptr(Y), p1, p2, N, _ptr(D1), _ptr(D2), s, _ptr(out.support), _ptr(out.coef),
-            _ptr(out.nnz), _ptr(rmse_out), _stream(stream)), "sdl_ortho_iterate")
+            self._h, _ptr(Y), p1, p2, N, _ptr(D1), _ptr(D2), s, float(eps), _ptr(out.support),
+            _ptr(out.coef), _ptr(out.nnz), _ptr(rmse_out), _stream(stream)), "sdl_ortho_iterate")
         return out
 
 
@@ -425,6 +429,17 @@ def psnr(x: torch.Tensor, ref: torch.Tensor, peak: float = 255.0, stream=None) -
     _check(lib().sdl_psnr(_ptr(x), _ptr(ref), x.numel(), float(peak), _ptr(out), _stream(stream)),
            "sdl_psnr")
     return out
+
+
+def ssim(ctx: Context, x: torch.Tensor, ref: torch.Tensor, peak: float = 255.0,
+         stream=None) -> torch.Tensor:
+    """Device scalar mean SSIM of x against ref (``sdl_ssim``)."""
+    if x.shape != ref.shape or x.dim() != 2 or not x.is_contiguous() or not ref.is_contiguous():
+        raise ValueError("x and ref must be contiguous 2-D images of one shape")
+    out = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(ctx._lib.sdl_ssim(ctx._h, _ptr(x), _ptr(ref), x.shape[0], x.shape[1], float(peak),
+                             _ptr(out), _stream(stream)), "sdl_ssim")
+    return out[0]
 
 
 def patch_average(ctx: Context, codes: Codes, means, D1, D2, p: int, H: int, W: int,

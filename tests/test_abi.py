@@ -60,9 +60,9 @@ def test_host_argument_errors_without_gpu(lib):
                                None, None, None, None, None) == -1
     assert lib.sdl_iterate(None, None, 8, 8, 10, None, 16, None, 16, 4, 0.0,
                            None, None, None, None, None) == -1
-    assert lib.sdl_ortho_iterate(None, None, 8, 8, 10, None, None, 4, None, None, None, None,
-                                 None) == -1
-    assert lib.sdl_ortho_sparse_code(None, None, 8, 8, 10, None, None, 4, None, None, None,
+    assert lib.sdl_ortho_iterate(None, None, 8, 8, 10, None, None, 4, 0.0, None, None, None,
+                                 None, None) == -1
+    assert lib.sdl_ortho_sparse_code(None, None, 8, 8, 10, None, None, 4, 0.0, None, None, None,
                                      None, None) == -1
     assert lib.sdl_create(None, 0) == -1
     assert lib.sdl_destroy(None) == 0

@@ -82,3 +82,55 @@ def test_pipeline_full_size_properties(gpu_ctx):
         assert 0.0 < res["nnz_mean"][g].item() <= s
         r = res["rmse"].cpu().numpy()
         assert np.all(np.isfinite(r))
+
+
+def test_ssim_matches_oracle(gpu_ctx):
+    rng = np.random.default_rng(12)
+    clean = synth.synthetic_image(9, size=64)
+    noisy = np.clip(clean + rng.normal(0, 20, clean.shape), 0, 255)
+    want = dn.ssim(noisy, clean)
+    cg = torch.tensor(clean, dtype=torch.float32, device="cuda:0")
+    ng = torch.tensor(noisy, dtype=torch.float32, device="cuda:0")
+    got = sdl.ssim(gpu_ctx, ng, cg).item()
+    assert abs(got - want) < 1e-5, (got, want)
+    assert abs(sdl.ssim(gpu_ctx, cg, cg).item() - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("variant", ["general", "ortho"])
+def test_table3_pipeline_matches_oracle(gpu_ctx, variant):
+    """Fixed dictionaries (no learning), error-driven coding of every patch,
+    averaging, PSNR and SSIM: the GPU pipeline against the oracle's."""
+    from oracle import ortho as ortho_oracle
+    from paper_2007_03800_gb300 import denoise as dn_gpu
+    sigma, p, n = 20.0, 8, 16
+    clean = synth.synthetic_image(10, size=48)
+    noisy = clean + np.random.default_rng(13).normal(0, sigma, clean.shape)
+    if variant == "general":
+        D1, D2 = synth.init_dictionaries(p, p, n, n, seed=1)
+    else:
+        D1, D2 = dn_gpu.orthonormal_start(p, 1), dn_gpu.orthonormal_start(p, 2)
+    eps = 1.15 * sigma * p
+    Y, means = dn.extract_patches(noisy, p)
+    if variant == "general":
+        ref = oracle.omp2d(Y, D1, D2, p // 2, eps=eps)
+        sup, coef = ref.support, ref.coef
+    else:
+        sup, coef, _ = ortho_oracle.threshold_code(Y, D1, D2, p // 2, eps=eps)
+    rec = oracle.reconstruct(D1, D2, sup, coef) + means[:, None, None]
+    want = dn.patch_average(rec, 48, 48)
+    ng = torch.tensor(noisy, dtype=torch.float32, device="cuda:0")
+    cg = torch.tensor(clean, dtype=torch.float32, device="cuda:0")
+    Yg, mg = sdl.extract_patches(ng, p)
+    D1g = sdl.dictionary(torch.tensor(D1, dtype=torch.float32, device="cuda:0"))
+    D2g = sdl.dictionary(torch.tensor(D2, dtype=torch.float32, device="cuda:0"))
+    if variant == "general":
+        code = gpu_ctx.sparse_code(Yg, D1g, D2g, p // 2, eps=eps)
+    else:
+        code = gpu_ctx.ortho_sparse_code(Yg, D1g, D2g, p // 2, eps=eps)
+    img = sdl.patch_average(gpu_ctx, code, mg, D1g, D2g, p, 48, 48)
+    gpu_ctx.check()
+    got = img.cpu().numpy().astype(np.float64)
+    close = np.abs(got - want) < 1e-3
+    assert close.mean() > 0.999, close.mean()
+    assert abs(sdl.psnr(img, cg).item() - dn.psnr(want, clean)) < 1e-3
+    assert abs(sdl.ssim(gpu_ctx, img, cg).item() - dn.ssim(want, clean)) < 1e-4
