@@ -95,6 +95,35 @@ __device__ __forceinline__ void vload(float (&v)[R], const float* p) {
     }
 }
 
+// d = a * b + c on two FP32 lanes at once (one packed fma.rn.f32x2: each half
+// rounds exactly as fmaf, so results are bit-identical to two scalar FMAs)
+__device__ __forceinline__ void ffma2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+    const unsigned long long A = ((unsigned long long)__float_as_uint(a1) << 32) | __float_as_uint(a0);
+    const unsigned long long B = ((unsigned long long)__float_as_uint(b1) << 32) | __float_as_uint(b0);
+    const unsigned long long C = ((unsigned long long)__float_as_uint(d1) << 32) | __float_as_uint(d0);
+    unsigned long long D;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D) : "l"(A), "l"(B), "l"(C));
+    d0 = __uint_as_float((unsigned)(D & 0xffffffffu));
+    d1 = __uint_as_float((unsigned)(D >> 32));
+}
+
+// block[c * R + r] += a[r] * b[c] for an R x C register block, packed in
+// pairs along r when R is even
+template <int R, int C>
+__device__ __forceinline__ void rank1_update(float* blk, const float (&a)[R], const float (&b)[C]) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        if constexpr (R % 2 == 0) {
+#pragma unroll
+            for (int r = 0; r < R; r += 2)
+                ffma2(blk[c * R + r], blk[c * R + r + 1], a[r], a[r + 1], b[c], b[c]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) blk[c * R + r] = fmaf(a[r], b[c], blk[c * R + r]);
+        }
+    }
+}
+
 template <int B, int E, class F>
 __device__ __forceinline__ void static_for(F&& f) {
     if constexpr (B < E) {
@@ -331,10 +360,7 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                 float u[RI], v[RJ];
                 vload<RI>(u, D1r + aa * LD1 + li * RIP);
                 vload<RJ>(v, Zs + aa * LD2 + lj * RJP);
-#pragma unroll
-                for (int c = 0; c < RJ; ++c)
-#pragma unroll
-                    for (int r = 0; r < RI; ++r) c0[c * RI + r] = fmaf(u[r], v[c], c0[c * RI + r]);
+                rank1_update<RI, RJ>(c0, u, v);
             }
 
             // keep C0 in shared memory: re-read once per step, masked by one store
@@ -378,12 +404,10 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                     float u[RI], v[RJ];
                     vload<RI>(u, G1s + si[l] * LD1 + li * RIP);
                     vload<RJ>(v, G2s + sj[l] * LD2 + lj * RJP);
+                    const float nx = -xs[l];
 #pragma unroll
-                    for (int c = 0; c < RJ; ++c) {
-                        const float vx = v[c] * xs[l];
-#pragma unroll
-                        for (int r = 0; r < RI; ++r) sc[c * RI + r] = fmaf(-u[r], vx, sc[c * RI + r]);
-                    }
+                    for (int c = 0; c < RJ; ++c) v[c] *= nx;
+                    rank1_update<RI, RJ>(sc, u, v);
                 }
                 // argmax |sc|, ties to the smallest q: two interleaved chains
                 // (even and odd entries in increasing q), merged by (value, q)
