@@ -134,6 +134,33 @@ __device__ __forceinline__ float team_sum_f32(float v, float* scratch, int wit, 
     }
 }
 
+// blk[r][c] += a[r] * b[c] over an R x C register block, packed in pairs along
+// c with fma.rn.f32x2 when C is even (each half rounds exactly as fmaf)
+template <int R, int C>
+__device__ __forceinline__ void rank1_rc(float (&blk)[R][C], const float (&a)[R], const float (&b)[C]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if constexpr (C % 2 == 0) {
+#pragma unroll
+            for (int c = 0; c < C; c += 2) {
+                const unsigned long long A =
+                    ((unsigned long long)__float_as_uint(a[r]) << 32) | __float_as_uint(a[r]);
+                const unsigned long long B =
+                    ((unsigned long long)__float_as_uint(b[c + 1]) << 32) | __float_as_uint(b[c]);
+                const unsigned long long Cc =
+                    ((unsigned long long)__float_as_uint(blk[r][c + 1]) << 32) | __float_as_uint(blk[r][c]);
+                unsigned long long D;
+                asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D) : "l"(A), "l"(B), "l"(Cc));
+                blk[r][c] = __uint_as_float((unsigned)(D & 0xffffffffu));
+                blk[r][c + 1] = __uint_as_float((unsigned)(D >> 32));
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) blk[r][c] = fmaf(a[r], b[c], blk[r][c]);
+        }
+    }
+}
+
 // FP32 re-scoring of one correlation: w_i . d2_j over p2 terms (w_i contiguous,
 // d2_j with stride ld), four interleaved partial sums so the loads and
 // multiply-adds overlap.  Kept out of line: it runs for a few flagged entries
@@ -265,10 +292,7 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                     for (int r = 0; r < RI; ++r) u[r] = D1r[aa * N1P + i0 + r];
 #pragma unroll
                     for (int c = 0; c < RJ; ++c) v[c] = Zs[aa * N2P + j0 + c];
-#pragma unroll
-                    for (int r = 0; r < RI; ++r)
-#pragma unroll
-                        for (int c = 0; c < RJ; ++c) c0[r][c] = fmaf(u[r], v[c], c0[r][c]);
+                    rank1_rc<RI, RJ>(c0, u, v);
                 }
             } else {
                 // ---- C0 from the tensor-core correlations (approximate)
@@ -313,11 +337,8 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
 #pragma unroll
                     for (int r = 0; r < RI; ++r) u[r] = G1s[il * N1P + i0 + r];
 #pragma unroll
-                    for (int c = 0; c < RJ; ++c) v[c] = xl * G2s[jl * N2P + j0 + c];
-#pragma unroll
-                    for (int r = 0; r < RI; ++r)
-#pragma unroll
-                        for (int c = 0; c < RJ; ++c) sc[r][c] = fmaf(-u[r], v[c], sc[r][c]);
+                    for (int c = 0; c < RJ; ++c) v[c] = -xl * G2s[jl * N2P + j0 + c];
+                    rank1_rc<RI, RJ>(sc, u, v);
                 }
                 float m = 0.f;
 #pragma unroll
