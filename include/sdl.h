@@ -409,6 +409,37 @@ int sdl_ortho_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N, f
                       float* rmse_out, void* stream);
 
 /*
+ * Three-mode generalisation (Remark 3): signals Y_k of shape p1 x p2 x p3
+ * (element (a, b, c) at a + p1 b + p1 p2 c + p1 p2 p3 k), dictionaries D1
+ * (p1 x n1), D2 (p2 x n2), D3 (p3 x n3) column-major with unit columns, codes
+ * over atom triples q = i + n1 j + n1 n2 l (the column of D3 (x) D2 (x) D1).
+ * Limits: 1 <= p_m <= 16, p1 p2 p3 <= 1024, n1 n2 n3 <= 1024,
+ * 1 <= s <= min(16, p1 p2 p3, n1 n2 n3).
+ *
+ * sdl_sparse_code3 - greedy pursuit over atom triples (argmax |correlation|
+ * over unselected triples, ties to the smallest q, full least-squares re-fit,
+ * the degenerate-pick rule of sdl_sparse_code), fixed s.
+ */
+int sdl_sparse_code3(sdl_ctx* ctx, const float* Y, int p1, int p2, int p3, int64_t N,
+                     const float* D1, int n1, const float* D2, int n2, const float* D3, int n3,
+                     int s, int32_t* support, float* coef, int32_t* nnz, float* res_energy,
+                     void* stream);
+
+/*
+ * sdl_iterate3 - one iteration of the three-mode algorithm: for mode k = 1,
+ * 2, 3 in turn, code all signals with the current dictionaries and update
+ * D_k by Corollary 1 applied to the mode-k unfolding
+ * Y_(k) = D_k X_(k) T_k^T (T_k the Kronecker product of the other two
+ * dictionaries), with the column normalisation.  D1, D2, D3 in/out;
+ * support/coef/nnz receive the codes of the third pass rescaled by W3^{-1};
+ * rmse_out: NULL or device float[3], the RMSE right after each update.
+ * Singular normal matrices follow sdl_update_D1.  N >= 1.
+ */
+int sdl_iterate3(sdl_ctx* ctx, const float* Y, int p1, int p2, int p3, int64_t N, float* D1,
+                 int n1, float* D2, int n2, float* D3, int n3, int s, int32_t* support,
+                 float* coef, int32_t* nnz, float* rmse_out, void* stream);
+
+/*
  * sdl_sparse_code_static - the sparse coder of sdl_sparse_code with no
  * context and no device allocation.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory once running

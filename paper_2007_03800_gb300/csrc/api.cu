@@ -198,6 +198,7 @@ int sdl_destroy(sdl_ctx* c) {
     cudaFree(c->rec);
     cudaFree(c->learn);
     cudaFree(c->ssim_part);
+    cudaFree(c->G3);
     cudaFree(c->Yb);
     cudaFree(c->KT);
     cudaFree(c->C0);

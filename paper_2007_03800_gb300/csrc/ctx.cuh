@@ -23,6 +23,8 @@ struct sdl_ctx {
     size_t cap_learn = 0;
     double* ssim_part = nullptr; // per-block SSIM sums
     size_t cap_ssim = 0;
+    float* G3 = nullptr;         // three-mode Gram matrices (G1 | G2 | G3 | spare)
+    size_t cap_g3 = 0;
     // precision extension
     int prec = 0;                // SDL_PREC_* flags
     void* Yb = nullptr;          // BF16 signals (N x Kp)

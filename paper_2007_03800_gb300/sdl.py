@@ -66,6 +66,8 @@ SIGNATURES = {
     "sdl_ortho_sparse_code": [_P, _P, _I, _I, _L, _P, _P, _I, _F, _P, _P, _P, _P, _P],
     "sdl_ortho_iterate": [_P, _P, _I, _I, _L, _P, _P, _I, _F, _P, _P, _P, _P, _P],
     "sdl_selftest_timeout": [_P, ctypes.c_longlong, _P],
+    "sdl_sparse_code3": [_P, _P, _I, _I, _I, _L, _P, _I, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P],
+    "sdl_iterate3": [_P, _P, _I, _I, _I, _L, _P, _I, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P],
     "sdl_ssim": [_P, _P, _P, _I, _I, _F, _P, _P],
     "sdl_set_precision": [_P, _I],
     "sdl_precision_stats": [_P, ctypes.POINTER(ctypes.c_uint64)],
@@ -109,6 +111,12 @@ def signals(Y: torch.Tensor) -> torch.Tensor:
     return Y.transpose(1, 2).contiguous().transpose(1, 2)
 
 
+def signals3(Y: torch.Tensor) -> torch.Tensor:
+    """(N, p1, p2, p3) tensor -> same values, memory column-major per signal
+    (element (a, b, c) of signal k at a + p1 b + p1 p2 c + p1 p2 p3 k)."""
+    return Y.permute(0, 3, 2, 1).contiguous().permute(0, 3, 2, 1)
+
+
 def dictionary(D: torch.Tensor) -> torch.Tensor:
     """(p, n) tensor -> same values, column-major memory."""
     return D.t().contiguous().t()
@@ -140,6 +148,14 @@ def _check_Y(Y):
     N, p1, p2 = Y.shape
     _need(Y, torch.float32, (N, p1, p2), (p1 * p2, 1, p1), "Y")
     return N, p1, p2
+
+
+def _check_Y3(Y):
+    if Y.dim() != 4:
+        raise ValueError("Y must be (N, p1, p2, p3)")
+    N, p1, p2, p3 = Y.shape
+    _need(Y, torch.float32, (N, p1, p2, p3), (p1 * p2 * p3, 1, p1, p1 * p2), "Y")
+    return N, p1, p2, p3
 
 
 def _check_D(D, p, name):
@@ -300,6 +316,35 @@ class Context:
                                    float(eps), _ptr(out.support), _ptr(out.coef), _ptr(out.nnz),
                                    _ptr(rmse_out), _stream(stream))
         _check(rc, "sdl_iterate")
+        return out
+
+    # ---- three modes (Remark 3)
+    def sparse_code3(self, Y, D1, D2, D3, s, out: Codes | None = None, stream=None) -> Codes:
+        """``sdl_sparse_code3``: Y a (N, p1, p2, p3) CUDA tensor whose signals are
+        stored column-major (see ``signals3``), D_m (p_m, n_m) column-major."""
+        N, p1, p2, p3 = _check_Y3(Y)
+        n1, n2, n3 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2"), _check_D(D3, p3, "D3")
+        if out is None:
+            out = Codes.empty(N, s, Y.device, with_energy=True)
+        _check(self._lib.sdl_sparse_code3(
+            self._h, _ptr(Y), p1, p2, p3, N, _ptr(D1), n1, _ptr(D2), n2, _ptr(D3), n3, s,
+            _ptr(out.support), _ptr(out.coef), _ptr(out.nnz), _ptr(out.res_energy),
+            _stream(stream)), "sdl_sparse_code3")
+        return out
+
+    def iterate3(self, Y, D1, D2, D3, s, out: Codes | None = None, rmse_out=None,
+                 stream=None) -> Codes:
+        """``sdl_iterate3``: one three-mode iteration; D1, D2, D3 updated in place."""
+        N, p1, p2, p3 = _check_Y3(Y)
+        n1, n2, n3 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2"), _check_D(D3, p3, "D3")
+        if out is None:
+            out = Codes.empty(N, s, Y.device)
+        if rmse_out is not None:
+            _need(rmse_out, torch.float32, (3,), None, "rmse_out")
+        _check(self._lib.sdl_iterate3(
+            self._h, _ptr(Y), p1, p2, p3, N, _ptr(D1), n1, _ptr(D2), n2, _ptr(D3), n3, s,
+            _ptr(out.support), _ptr(out.coef), _ptr(out.nnz), _ptr(rmse_out), _stream(stream)),
+            "sdl_iterate3")
         return out
 
     # ---- orthonormal variant (Remark 1)

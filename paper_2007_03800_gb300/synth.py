@@ -20,7 +20,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "unit_columns", "random_dictionary", "init_dictionaries", "kron_model",
+    "unit_columns", "random_dictionary", "init_dictionaries", "kron_model", "kron_model3",
     "synthetic_image", "random_patches", "all_patches", "hyperspectral",
     "to_colmajor", "dict_to_colmajor",
 ]
@@ -82,6 +82,35 @@ def kron_model(N: int, p1: int, p2: int, n1: int, n2: int, s: int,
         sigma2 = energy / (p1 * p2 * 10.0 ** (snr_db / 10.0))
         Y = clean + rng.standard_normal(clean.shape) * np.sqrt(sigma2)[:, None, None]
     return Y, D1t, D2t, support, coef
+
+
+def kron_model3(N: int, p: tuple, n: tuple, s: int, snr_db: float | None = 20.0,
+                seed: int = 81):
+    """Three-mode signals Y_k = X_k x_1 D1* x_2 D2* x_3 D3* + noise (the
+    generative model of the three-mode generalisation): D_m* (p_m x n_m)
+    N(0,1) with unit columns from seeds seed, seed+1, seed+2; s distinct atom
+    triples per signal (q = i + n1 j + n1 n2 l) with N(0,1) values; white noise
+    at snr_db per signal.  Returns (Y (N, p1, p2, p3), [D1*, D2*, D3*],
+    support, coef)."""
+    Ds = [random_dictionary(p[m], n[m], np.random.default_rng(seed + m)) for m in range(3)]
+    rng = np.random.default_rng(seed + 1000)
+    Q = n[0] * n[1] * n[2]
+    keys = rng.random((N, Q), dtype=np.float32)
+    part = np.argpartition(keys, s - 1, axis=1)[:, :s]
+    order = np.argsort(np.take_along_axis(keys, part, axis=1), axis=1)
+    support = np.take_along_axis(part, order, axis=1).astype(np.int64)
+    coef = rng.standard_normal((N, s))
+    ii, jj, ll = support % n[0], (support // n[0]) % n[1], support // (n[0] * n[1])
+    Y = np.empty((N,) + tuple(p))
+    for a in range(0, N, 32768):                          # memory only
+        b = slice(a, a + 32768)
+        Y[b] = np.einsum("km,akm,bkm,ckm->kabc", coef[b], Ds[0][:, ii[b]], Ds[1][:, jj[b]],
+                         Ds[2][:, ll[b]], optimize=True)
+    if snr_db is not None:
+        energy = np.einsum("kabc,kabc->k", Y, Y)
+        sigma2 = energy / (np.prod(p) * 10.0 ** (snr_db / 10.0))
+        Y = Y + rng.standard_normal(Y.shape) * np.sqrt(sigma2)[:, None, None, None]
+    return Y, Ds, support, coef
 
 
 def synthetic_image(seed: int, size: int = 512, n_regions: int = 24,

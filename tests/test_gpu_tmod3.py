@@ -1,0 +1,57 @@
+"""Three-mode generalisation (Remark 3) on the GPU against the FP64 oracle:
+codes over atom triples and one three-mode iteration."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import tmod3
+from paper_2007_03800_gb300 import sdl, synth
+from parity import COEF_RTOL, DICT_RTOL, RMSE_RTOL, coef_rel_error, compare_supports
+
+pytestmark = pytest.mark.gpu
+
+
+def problem(N, p, n, s, seed=81):
+    Y, _, _, _ = synth.kron_model3(N, p, n, s, 20.0, seed=seed)
+    rng = np.random.default_rng(1)
+    Ds = [synth.random_dictionary(p[m], n[m], rng) for m in range(3)]
+    return Y, Ds
+
+
+def to_gpu(Y, Ds):
+    Yg = sdl.signals3(torch.tensor(Y, dtype=torch.float32, device="cuda:0"))
+    Dg = [sdl.dictionary(torch.tensor(D, dtype=torch.float32, device="cuda:0")) for D in Ds]
+    return Yg, Dg
+
+
+@pytest.mark.parametrize("p,n,s", [((4, 4, 4), (8, 8, 8), 4), ((3, 5, 6), (6, 8, 10), 5)])
+def test_codes_match_oracle(gpu_ctx, p, n, s):
+    Y, Ds = problem(2000, p, n, s)
+    ref = tmod3.omp3d(Y, *Ds, s)
+    Yg, Dg = to_gpu(Y, Ds)
+    out = gpu_ctx.sparse_code3(Yg, *Dg, s)
+    assert gpu_ctx.status() == 0
+    rep, exact = compare_supports(out.support.cpu().numpy(), out.nnz.cpu().numpy(), ref)
+    assert rep.bad == 0 and rep.ties <= 4, rep
+    assert coef_rel_error(out.coef.cpu().numpy(), ref.coef, exact).max() < COEF_RTOL
+    e = out.res_energy.cpu().numpy().astype(np.float64)[exact]
+    yy = np.einsum("kabc,kabc->k", Y, Y)[exact]
+    assert np.all(np.abs(e - ref.res_energy[exact]) <= 1e-5 * yy)
+
+
+def test_three_mode_iteration_matches_oracle(gpu_ctx):
+    p, n, s = (4, 4, 4), (8, 8, 8), 4
+    Y, Ds = problem(3000, p, n, s, seed=82)
+    ref = tmod3.iterate3(Y, *Ds, s)
+    Yg, Dg = to_gpu(Y, Ds)
+    rmse = torch.zeros(3, dtype=torch.float32, device="cuda:0")
+    out = gpu_ctx.iterate3(Yg, *Dg, s, rmse_out=rmse)
+    assert gpu_ctx.status() == 0
+    r = rmse.cpu().numpy()
+    for k in range(3):
+        assert abs(r[k] - ref.rmse[k]) / ref.rmse[k] < RMSE_RTOL, (k, r, ref.rmse)
+        assert np.abs(Dg[k].cpu().numpy() - ref.D[k]).max() < DICT_RTOL, k
+    last_code = ref.passes[-1][0]
+    rep, exact = compare_supports(out.support.cpu().numpy(), out.nnz.cpu().numpy(), last_code)
+    assert rep.bad == 0 and rep.ties <= 4, rep
+    assert coef_rel_error(out.coef.cpu().numpy(), ref.coef, exact).max() < COEF_RTOL
