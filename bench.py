@@ -705,6 +705,53 @@ def study_table3(args):
     return 0
 
 
+def study_tmod3(args):
+    """Three-mode learning (Remark 3) on hyperspectral-shaped cubes: 4 x 4
+    pixels x 16 bands (every 4th of 64) of the hyperspectral generator,
+    N = 50000, D1, D2 4 x 8, D3 16 x 16, s = 8, 10 iterations; device time per
+    iteration and the RMSE after each mode update."""
+    import torch
+
+    from paper_2007_03800_gb300 import sdl, synth
+    dev = torch.device("cuda:0")
+    N, s = 50_000, 8
+    H = synth.hyperspectral(N, seed=31)                     # (N, 16 pixels, 64 bands)
+    Y = H.reshape(N, 4, 4, 64)[..., ::4]                    # (N, 4, 4, 16)
+    rng = np.random.default_rng(1)
+    Ds = [synth.random_dictionary(4, 8, rng), synth.random_dictionary(4, 8, rng),
+          synth.random_dictionary(16, 16, rng)]
+    ctx = sdl.Context(0)
+    Yg = sdl.signals3(torch.tensor(Y, dtype=torch.float32, device=dev))
+
+    def dicts():
+        return [sdl.dictionary(torch.tensor(D, dtype=torch.float32, device=dev)) for D in Ds]
+
+    codes = sdl.Codes.empty(N, s, dev)
+    rmse = torch.zeros(3, dtype=torch.float32, device=dev)
+    Dw = dicts()
+    for _ in range(args.warmup):
+        ctx.iterate3(Yg, *Dw, s, out=codes, rmse_out=rmse)
+    ctx.check()
+    Dg = dicts()
+    ms, traj = [], []
+    for _ in range(10):
+        a, b = _events()
+        a.record()
+        ctx.iterate3(Yg, *Dg, s, out=codes, rmse_out=rmse)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        traj.append([round(v, 6) for v in rmse.tolist()])
+    ctx.check()
+    ctx.close()
+    med = statistics.median(ms)
+    print(json.dumps({"study": "tmod3", "workload": "50000 hyperspectral-shaped 4x4x16 cubes, "
+                      "D 4x8, 4x8, 16x16, s=8, 10 iterations", "ms_per_iteration": med,
+                      "signals_per_s": N / (med / 1e3), "rmse_after_each_update": traj}),
+          flush=True)
+    return 0
+
+
 def study_denoise(args):
     """Denoising with one batch of three patch sizes (8, 12, 16; D p x 2p;
     error-driven stop at 1.15 sigma p, s <= p/2) on a 512x512 synthetic image
@@ -754,7 +801,8 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed region only: no e2e loop, CPU baseline or clock sampling "
                          "(for profiler runs; its numbers are not bench values)")
-    ap.add_argument("--study", choices=["precision", "learned", "denoise", "ortho", "gemm", "table3"],
+    ap.add_argument("--study", choices=["precision", "learned", "denoise", "ortho", "gemm", "table3",
+                                        "tmod3"],
                     help="run one extra study on its own workload instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -764,7 +812,8 @@ def main():
     if args.study:
         return {"precision": study_precision, "learned": study_learned,
                 "denoise": study_denoise, "ortho": study_ortho,
-                "gemm": study_gemm, "table3": study_table3}[args.study](args)
+                "gemm": study_gemm, "table3": study_table3,
+                "tmod3": study_tmod3}[args.study](args)
     return run_ours(args)
 
 
