@@ -215,6 +215,15 @@ int sdl_batch_iterate(sdl_batch* batch, float* rmse_out, void* stream);
  * coding passes in microseconds.  Returns n_groups. */
 int sdl_batch_tuning(const sdl_batch* batch, int* shape_id, int* ctas, float* cost_us);
 
+/* Every measurement the autotuner took (empty without SDL_BATCH_AUTOTUNE): for
+ * entry e, the group, the tiling id, the CTAs per SM and the time of one D1-side
+ * coding pass of that group alone in microseconds.  Host arrays of max_entries
+ * (each may be NULL); returns the number of entries (which may exceed
+ * max_entries: only the first max_entries are written), SDL_ERR_ARG on a NULL
+ * batch or a negative max_entries. */
+int sdl_batch_tuning_log(const sdl_batch* batch, int* group, int* shape_id, int* ctas_per_sm,
+                         float* cost_us, int max_entries);
+
 /* Synchronise the device and free the batch (NULL accepted). */
 int sdl_batch_destroy(sdl_batch* batch);
 
@@ -299,6 +308,35 @@ int sdl_gemm_bf16(sdl_ctx* ctx, const void* A, int lda, const void* B, int ldb, 
 #define SDL_PREC_NO_RESCORE 2
 #define SDL_PREC_FP64_SOLVE 4
 int sdl_set_precision(sdl_ctx* ctx, int flags);
+
+/* ---- Tilings of the specialised coder (Algorithm 1, step "sparse coding").
+ * The shapes (p1, p2, n1, n2, s) = (8, 8, 16, 16, 4), (12, 12, 24, 24, 6) and
+ * (16, 16, 32, 32, 8) have coders compiled for several tilings: one signal per
+ * warp on two lane grids, and two signals per warp (each half-warp codes one
+ * signal).  Every tiling of a shape forms each correlation, update and solve
+ * with the same FMA chains, so the codes (support, coef, nnz) do not depend on
+ * the tiling; the TMOD partial sums are added in a tiling-dependent order.
+ *
+ * sdl_tilings: the tiling ids compiled for the shape (host array of max_ids,
+ *   may be NULL); returns their number (0: no specialised coder, the generic
+ *   kernel runs), SDL_ERR_ARG for max_ids < 0.
+ * sdl_set_tiling: pin `tiling` (one of those ids) and ctas_per_sm (0 = as many
+ *   CTAs per SM as fit, else 1..8) for the shape in this context; tiling < 0
+ *   unpins.  SDL_ERR_UNSUPPORTED if the shape has no such tiling.
+ * sdl_tune_tiling: time one D1-side coding pass (Y p1 x p2 x N and D1, D2 as
+ *   in sdl_iterate, device pointers, Y 16-byte aligned; nothing is written but
+ *   workspace) with every tiling at 1 and 2 CTAs per SM, pin the fastest and
+ *   return its id in *tiling_out (may be NULL).  Synchronises the stream.
+ *   SDL_ERR_UNSUPPORTED if the shape has no specialised coder or Y is not
+ *   16-byte aligned.
+ * sdl_tune_log: the measurements of the last sdl_tune_tiling (tiling id, CTAs
+ *   per SM, microseconds per pass; host arrays of max_entries, each may be
+ *   NULL); returns the number of entries. */
+int sdl_tilings(int p1, int p2, int n1, int n2, int s, int* ids, int max_ids);
+int sdl_set_tiling(sdl_ctx* ctx, int p1, int p2, int n1, int n2, int s, int tiling, int ctas_per_sm);
+int sdl_tune_tiling(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N, const float* D1, int n1,
+                    const float* D2, int n2, int s, int* tiling_out, void* stream);
+int sdl_tune_log(const sdl_ctx* ctx, int* tiling, int* ctas_per_sm, float* cost_us, int max_entries);
 
 /* Number of correlation entries re-scored in FP32 since the previous call
  * (synchronises the device). */

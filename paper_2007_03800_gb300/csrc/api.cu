@@ -2,6 +2,7 @@
 // context workspace, and the launch sequences of the entry points.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -76,7 +77,22 @@ PassArgs base_args(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const 
     a.part_d = c->part_d;
     a.n_slots = 1;
     a.err = c->err;
+    for (const auto& pin : c->pins)
+        if (pin.p1 == p1 && pin.p2 == p2 && pin.n1 == n1 && pin.n2 == n2 && pin.s == s) {
+            a.tiling = pin.id + 1;
+            a.tiling_cps = pin.cps;
+        }
     return a;
+}
+
+void pin_tiling(sdl_ctx* c, int p1, int p2, int n1, int n2, int s, int id, int cps) {
+    for (auto& pin : c->pins)
+        if (pin.p1 == p1 && pin.p2 == p2 && pin.n1 == n1 && pin.n2 == n2 && pin.s == s) {
+            pin.id = id;
+            pin.cps = cps;
+            return;
+        }
+    c->pins.push_back(sdl_ctx::Pin{p1, p2, n1, n2, s, id, cps});
 }
 
 void grams(sdl_ctx* c, const float* D1, int p1, int n1, const float* D2, int p2, int n2,
@@ -355,6 +371,102 @@ int sdl_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1
         launch_rescale(support, coef, N * (long long)s, n1, n2, kSideD2, c->norms, st);
     }
     return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+int sdl_tilings(int p1, int p2, int n1, int n2, int s, int* ids, int max_ids) {
+    if (max_ids < 0) return SDL_ERR_ARG;
+    int all[64];
+    const int n = fast_shape_variants(p1, p2, n1, n2, s, all, 64);
+    for (int v = 0; v < n && v < max_ids; ++v)
+        if (ids) ids[v] = all[v];
+    return n;
+}
+
+int sdl_set_tiling(sdl_ctx* c, int p1, int p2, int n1, int n2, int s, int tiling, int ctas_per_sm) {
+    if (!c || ctas_per_sm < 0 || ctas_per_sm > 8) return SDL_ERR_ARG;
+    if (tiling < 0) {
+        for (size_t k = 0; k < c->pins.size(); ++k)
+            if (c->pins[k].p1 == p1 && c->pins[k].p2 == p2 && c->pins[k].n1 == n1 &&
+                c->pins[k].n2 == n2 && c->pins[k].s == s) {
+                c->pins.erase(c->pins.begin() + (long)k);
+                break;
+            }
+        return SDL_OK;
+    }
+    int all[64];
+    const int n = fast_shape_variants(p1, p2, n1, n2, s, all, 64);
+    for (int v = 0; v < n; ++v)
+        if (all[v] == tiling) {
+            pin_tiling(c, p1, p2, n1, n2, s, tiling, ctas_per_sm);
+            return SDL_OK;
+        }
+    return SDL_ERR_UNSUPPORTED;
+}
+
+int sdl_tune_tiling(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const float* D1, int n1,
+                    const float* D2, int n2, int s, int* tiling_out, void* stream) {
+    if (!valid_common(c, Y, p1, p2, N, n1, n2, s) || !D1 || !D2 || N < 1) return SDL_ERR_ARG;
+    int rc = check_shape(p1, p2, n1, n2, s);
+    if (rc != SDL_OK) return rc;
+    if ((reinterpret_cast<uintptr_t>(Y) & 15u) != 0) return SDL_ERR_UNSUPPORTED;
+    int ids[64];
+    const int n = fast_shape_variants(p1, p2, n1, n2, s, ids, 64);
+    if (n == 0) return SDL_ERR_UNSUPPORTED;
+    DeviceGuard g(c->device);
+    if ((rc = ensure_workspace(c, p1, p2, n1, n2)) != SDL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    grams(c, D1, p1, n1, D2, p2, n2, st);
+    PassArgs a = base_args(c, Y, p1, p2, N, D1, n1, D2, n2, s);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SDL_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SDL_ERR_CUDA;
+    }
+    c->tune_log.clear();
+    int best_id = -1, best_cps = 0;
+    float best = 1e30f;
+    for (int v = 0; v < n; ++v) {
+        for (int cps = 1; cps <= 2; ++cps) {
+            // one untimed launch, then the mean of three (D1-side passes, the
+            // heavier of the two epilogues)
+            if (launch_code_pass_variant(a, kSideD1, ids[v], cps, st, c->num_sms) < 0) continue;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3; ++r) launch_code_pass_variant(a, kSideD1, ids[v], cps, st, c->num_sms);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return SDL_ERR_CUDA;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const float us = ms * 1000.f / 3.f;
+            c->tune_log.push_back(sdl_ctx::TuneRec{ids[v], cps, us});
+            if (us < best) {
+                best = us;
+                best_id = ids[v];
+                best_cps = cps;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_id < 0) return SDL_ERR_CUDA;
+    pin_tiling(c, p1, p2, n1, n2, s, best_id, best_cps);
+    if (tiling_out) *tiling_out = best_id;
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+int sdl_tune_log(const sdl_ctx* c, int* tiling, int* ctas_per_sm, float* cost_us, int max_entries) {
+    if (!c || max_entries < 0) return SDL_ERR_ARG;
+    const int n = (int)c->tune_log.size();
+    for (int e = 0; e < n && e < max_entries; ++e) {
+        if (tiling) tiling[e] = c->tune_log[e].id;
+        if (ctas_per_sm) ctas_per_sm[e] = c->tune_log[e].cps;
+        if (cost_us) cost_us[e] = c->tune_log[e].us;
+    }
+    return n;
 }
 
 int sdl_set_precision(sdl_ctx* c, int flags) {

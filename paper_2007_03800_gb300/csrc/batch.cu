@@ -21,6 +21,9 @@ struct sdl_batch {
     std::vector<int> shape;        // compiled tiling per group
     std::vector<int> cta_begin;    // G + 1 prefix of CTAs per group
     std::vector<float> cost_us;    // time of one fused pass of the group alone
+    // every (group, tiling, CTAs per SM, cost) the autotuner measured
+    std::vector<int> log_group, log_shape, log_cps;
+    std::vector<float> log_cost;
     int total_ctas = 0;
     size_t smem[3] = {0, 0, 0};    // multi-kernel dynamic smem per side
     size_t solve_smem[2] = {0, 0};
@@ -45,6 +48,7 @@ struct sdl_batch {
 namespace {
 
 constexpr int kSlotsPerSm = 8;   // partial-sum slots reserved per SM and group
+constexpr int kMultiWarps = 8;   // warps per CTA of the persistent multi-problem kernel
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -95,7 +99,11 @@ int enqueue_iteration(sdl_batch* b, cudaStream_t st, bool trace) {
 bool valid_group(const sdl_group& g, int* shape_ids, int* n_ids) {
     if (!g.Y || !g.D1 || !g.D2 || !g.support || !g.coef || !g.nnz || g.N < 1) return false;
     if ((reinterpret_cast<uintptr_t>(g.Y) & 15u) != 0) return false;
-    *n_ids = fast_shape_variants(g.p1, g.p2, g.n1, g.n2, g.s_max, shape_ids, 4);
+    int all[16];
+    const int n = fast_shape_variants(g.p1, g.p2, g.n1, g.n2, g.s_max, all, 16);
+    *n_ids = 0;
+    for (int v = 0; v < n && *n_ids < 8; ++v)
+        if (fast_variant_warps(all[v]) == kMultiWarps) shape_ids[(*n_ids)++] = all[v];
     return *n_ids > 0;
 }
 
@@ -125,7 +133,7 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
     const int G = n_groups;
     std::vector<std::vector<int>> variants(G);
     for (int g = 0; g < G; ++g) {
-        int ids[4], n = 0;
+        int ids[8], n = 0;
         if (!valid_group(groups[g], ids, &n)) {
             destroy(b);
             return SDL_ERR_UNSUPPORTED;
@@ -258,6 +266,10 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
                     float ms = 0.f;
                     cudaEventElapsedTime(&ms, e0, e1);
                     const float us = ms * 1000.f / 3.f;
+                    b->log_group.push_back(g);
+                    b->log_shape.push_back(v);
+                    b->log_cps.push_back(cps);
+                    b->log_cost.push_back(us);
                     if (us < best) {
                         best = us;
                         b->shape[g] = v;
@@ -467,6 +479,19 @@ int sdl_batch_tuning(const sdl_batch* b, int* shape_id, int* ctas, float* cost_u
         if (cost_us) cost_us[g] = b->cost_us[g];
     }
     return b->G;
+}
+
+int sdl_batch_tuning_log(const sdl_batch* b, int* group, int* shape_id, int* ctas_per_sm,
+                         float* cost_us, int max_entries) {
+    if (!b || max_entries < 0) return SDL_ERR_ARG;
+    const int n = (int)b->log_cost.size();
+    for (int e = 0; e < n && e < max_entries; ++e) {
+        if (group) group[e] = b->log_group[e];
+        if (shape_id) shape_id[e] = b->log_shape[e];
+        if (ctas_per_sm) ctas_per_sm[e] = b->log_cps[e];
+        if (cost_us) cost_us[e] = b->log_cost[e];
+    }
+    return n;
 }
 
 }  // extern "C"

@@ -34,6 +34,17 @@ struct sdl_ctx {
     unsigned long long* rescored = nullptr;
     size_t cap_g1 = 0, cap_g2 = 0, cap_part = 0, cap_slots = 0, cap_red = 0, cap_redd = 0,
            cap_norms = 0;
+    // coder tilings pinned per shape (sdl_tune_tiling / sdl_set_tiling) and
+    // the measurements of the last sdl_tune_tiling
+    struct Pin {
+        int p1, p2, n1, n2, s, id, cps;
+    };
+    std::vector<Pin> pins;
+    struct TuneRec {
+        int id, cps;
+        float us;
+    };
+    std::vector<TuneRec> tune_log;
     // tracing: launch counters and (optionally) one event pair per launch
     struct Rec {
         int kind;

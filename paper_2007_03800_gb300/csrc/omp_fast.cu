@@ -15,10 +15,15 @@
 //     block of the n1 x n2 correlation matrix loads with 64/128-bit accesses.
 // Correlation C0 = D1^T (Y D2): Z = Y D2 is formed cooperatively (a ZA x ZB
 // block per lane) into shared memory, then each lane contracts its RI x RJ
-// block.  Scores are recomputed from C0 every step (Gram domain):
+// block.  The D2-side pass associates the other way, C0 = (D1^T Y) D2, because
+// its partial sum B2 = sum (Y^T D1) X takes rows of W = D1^T Y.  Every tiling
+// of a shape forms each entry with the same FMA chains, so all tilings give
+// bit-identical results.  Scores are recomputed from C0 every step (Gram
+// domain):
 //   C = C0 - sum_l x_l G1[:, i_l] G2[j_l, :].
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <utility>
 
 #include "sdl_internal.cuh"
@@ -33,23 +38,62 @@ __host__ __device__ constexpr int pad_vec(int r) { return r <= 2 ? r : ((r + 3) 
 __host__ __device__ constexpr int al4(int x) { return (x + 3) & ~3; }
 
 template <int P1_, int P2_, int N1_, int N2_, int S_, int LI_, int RI_, int RJ_, int ZA_, int ZB_,
-          int WPC_, int MINB_>
+          int WI_, int WB_, int WPC_, int MINB_>
 struct Shape {
     static constexpr int P1 = P1_, P2 = P2_, N1 = N1_, N2 = N2_, S = S_;
+    static constexpr bool kHalf = false;
     static constexpr int WPC = WPC_;     // warps (= signals in flight) per CTA
+    static constexpr int SPC = WPC_;     // signals in flight per CTA
     static constexpr int MINB = MINB_;   // CTAs per SM the register budget must allow
     static constexpr int LI = LI_, LJ = 32 / LI_, RI = RI_, RJ = RJ_, E = RI_ * RJ_;
     static constexpr int RIP = pad_vec(RI_), RJP = pad_vec(RJ_);
     static constexpr int LD1 = LI * RIP, LD2 = LJ * RJP;     // padded row strides
     static constexpr int ZA = ZA_, ZB = ZB_;
     static constexpr int ZLA = P1_ / ZA_, ZLB = N2_ / ZB_;   // Z-stage lane grid
+    static constexpr int WI = WI_, WB = WB_;
+    static constexpr int WLI = N1_ / WI_, WLB = P2_ / WB_;   // W-stage lane grid
     static constexpr int PP = P1_ * P2_;
     // lane stride of the C0 blocks in shared memory: an odd multiple of 4
     // floats, so the 8 lanes of a 128-bit load phase hit distinct banks
     static constexpr int EP = ((al4(E) / 4) % 2 == 0) ? al4(E) + 4 : al4(E);
     static_assert(LI * RI == N1 && LJ * RJ == N2, "lane grid must tile n1 x n2 exactly");
     static_assert(ZLA * ZA == P1 && ZLB * ZB == N2 && ZLA * ZLB <= 32, "Z tiling");
+    static_assert(WLI * WI == N1 && WLB * WB == P2 && WLI * WLB <= 32, "W tiling");
     static_assert(S <= 32 && S <= P1 * P2 && S <= N1 * N2, "s");
+    static_assert((PP * 4) % 16 == 0, "TMA bulk copies need 16-byte multiples");
+};
+
+// Two signals per warp: lanes 0-15 code one signal, lanes 16-31 another, each
+// half on a 16-lane grid LI x LJ of RI x RJ blocks of the n1 x n2 correlation
+// matrix.  The per-signal scalar work (pick decoding, the Cholesky recurrences
+// and both triangular solves, which every lane of a signal replicates) is then
+// issued once for two signals.  The first contraction is Z = Y D2 (ZA x ZB
+// block per lane) for coding and the D1-side pass, and W = D1^T Y (WI x WB
+// block per lane) for the D2-side pass, whose partial sum B2 takes rows of W.
+// Both halves run every greedy step together (a half that has stopped only
+// stops changing its state), so the maxima and picks of the two halves are
+// reduced with full-warp redux.sync; each lane scans its scores in four
+// interleaved argmax chains, and the Cholesky state lives in shared memory so
+// that it holds no registers while the scores are live.
+template <int P1_, int P2_, int N1_, int N2_, int S_, int LI_, int RI_, int RJ_, int ZA_, int ZB_,
+          int WI_, int WB_, int WPC_, int MINB_>
+struct HalfShape {
+    static constexpr bool kHalf = true;
+    static constexpr int P1 = P1_, P2 = P2_, N1 = N1_, N2 = N2_, S = S_;
+    static constexpr int WPC = WPC_, MINB = MINB_;
+    static constexpr int SPC = 2 * WPC_;
+    static constexpr int LI = LI_, LJ = 16 / LI_, RI = RI_, RJ = RJ_, E = RI_ * RJ_;
+    static constexpr int RIP = pad_vec(RI_), RJP = pad_vec(RJ_);
+    static constexpr int LD1 = LI * RIP, LD2 = LJ * RJP;
+    static constexpr int ZA = ZA_, ZB = ZB_, ZLA = P1_ / ZA_, ZLB = N2_ / ZB_;
+    static constexpr int WI = WI_, WB = WB_, WLI = N1_ / WI_, WLB = P2_ / WB_;
+    static constexpr int PP = P1_ * P2_;
+    static constexpr int EP = ((al4(E) / 4) % 2 == 0) ? al4(E) + 4 : al4(E);
+    static_assert(16 % LI_ == 0 && LI * RI == N1 && LJ * RJ == N2, "lane grid must tile n1 x n2 exactly");
+    static_assert(ZLA * ZA == P1 && ZLB * ZB == N2 && ZLA * ZLB == 16 && ZA % 2 == 0, "Z tiling");
+    static_assert(WLI * WI == N1 && WLB * WB == P2 && WLI * WLB == 16 && WI % 2 == 0, "W tiling");
+    static_assert(P1 % 2 == 0 && N1 % 2 == 0 && P1 <= 16 && P2 <= 16, "row pairs, epilogue lanes");
+    static_assert(S <= 16 && S <= P1 * P2 && S <= N1 * N2, "s");
     static_assert((PP * 4) % 16 == 0, "TMA bulk copies need 16-byte multiples");
 };
 
@@ -124,6 +168,18 @@ __device__ __forceinline__ void rank1_update(float* blk, const float (&a)[R], co
     }
 }
 
+// R floats (R even) from an 8-byte-aligned address
+template <int R>
+__device__ __forceinline__ void vload2(float (&v)[R], const float* p) {
+    static_assert(R % 2 == 0, "pairs");
+#pragma unroll
+    for (int k = 0; k < R; k += 2) {
+        const float2 t = *reinterpret_cast<const float2*>(p + k);
+        v[k] = t.x;
+        v[k + 1] = t.y;
+    }
+}
+
 template <int B, int E, class F>
 __device__ __forceinline__ void static_for(F&& f) {
     if constexpr (B < E) {
@@ -183,9 +239,10 @@ template <class Sh>
 struct FastLayout {
     // floats; every region starts 16-byte aligned
     static constexpr int d1r = 0;                                   // P1 x LD1
-    static constexpr int d1c = d1r + al4(Sh::P1 * Sh::LD1);         // N1 x P1 (D1 columns)
-    static constexpr int d2r = d1c + al4(Sh::N1 * Sh::P1);          // P2 x N2
-    static constexpr int g1 = d2r + al4(Sh::P2 * Sh::N2);           // N1 x LD1
+    static constexpr int d1w = d1r + al4(Sh::P1 * Sh::LD1);         // P1 x N1 (rows of D1)
+    static constexpr int d2r = d1w + al4(Sh::P1 * Sh::N1);          // P2 x N2
+    static constexpr int d2p = d2r + al4(Sh::P2 * Sh::N2);          // P2 x LD2
+    static constexpr int g1 = d2p + al4(Sh::P2 * Sh::LD2);          // N1 x LD1
     static constexpr int g2 = g1 + al4(Sh::N1 * Sh::LD1);           // N2 x LD2
     static constexpr int acc = g2 + al4(Sh::N2 * Sh::LD2);
     __host__ __device__ static constexpr int nf(int side) {
@@ -197,13 +254,14 @@ struct FastLayout {
     // per-warp energy sums: WPC x 2 floats
     __host__ __device__ static constexpr int acce(int side) { return acc + accw(side); }
     __host__ __device__ static constexpr int warp0(int side) { return acce(side) + al4(2 * Sh::WPC); }
-    // per warp: mbarriers (4 floats), Y double buffer, Z, the C0 blocks of
-    // the 32 lanes (lane-major, stride EP: conflict-free 128-bit loads)
+    // per warp: mbarriers (4 floats), Y double buffer, Z or W, the C0 blocks
+    // of the 32 lanes (lane-major, stride EP: conflict-free 128-bit loads)
     static constexpr int EP = Sh::EP;
     static constexpr int w_bar = 0;
     static constexpr int w_y = 4;
+    static constexpr int TZ = Sh::P1 * Sh::LD2, TW = Sh::P2 * Sh::LD1;
     static constexpr int w_z = w_y + 2 * al4(Sh::PP);
-    static constexpr int w_c0 = w_z + al4(Sh::P1 * Sh::LD2);
+    static constexpr int w_c0 = w_z + al4(TZ > TW ? TZ : TW);
     static constexpr int w_stride = w_c0 + 32 * EP;
     __host__ __device__ static constexpr int total(int side, int wpc) { return warp0(side) + wpc * w_stride; }
 };
@@ -223,9 +281,11 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
     const int wpc = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int li = lane % LI, lj = lane / LI;
+    constexpr bool kW = (SIDE == kSideD2);   // C0 = (D1^T Y) D2 rather than D1^T (Y D2)
     float* D1r = smem + L::d1r;
-    float* D1c = smem + L::d1c;
+    float* D1w = smem + L::d1w;
     float* D2r = smem + L::d2r;
+    float* D2p = smem + L::d2p;
     float* G1s = smem + L::g1;
     float* G2s = smem + L::g2;
     float* acc = smem + L::acc;
@@ -246,10 +306,18 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
         const int blk = pp / RIP, off = pp % RIP;
         D1r[e] = (off < RI) ? a.D1[r + P1 * (blk * RI + off)] : 0.f;
     }
-    for (int e = threadIdx.x; e < N1 * P1; e += blockDim.x) D1c[e] = a.D1[e];
+    for (int e = threadIdx.x; e < P1 * N1; e += blockDim.x) {
+        const int r = e / N1, i = e % N1;
+        D1w[e] = a.D1[r + P1 * i];
+    }
     for (int e = threadIdx.x; e < P2 * N2; e += blockDim.x) {
         const int r = e / N2, j = e % N2;
         D2r[e] = a.D2[r + P2 * j];
+    }
+    for (int e = threadIdx.x; e < P2 * LD2; e += blockDim.x) {
+        const int r = e / LD2, pp = e % LD2;
+        const int blk = pp / RJP, off = pp % RJP;
+        D2p[e] = (off < RJ) ? a.D2[r + P2 * (blk * RJ + off)] : 0.f;
     }
     for (int e = threadIdx.x; e < N1 * LD1; e += blockDim.x) {
         const int c = e / LD1, pp = e % LD1;
@@ -324,8 +392,29 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
         int myi = 0, myj = 0;
         float myx = 0.f;
         if (finite) {
-            // ---- Z = Y D2 (ZA x ZB block per lane)
-            if (lane < Sh::ZLA * Sh::ZLB) {
+            // ---- Z = Y D2 (ZA x ZB block per lane) or W = D1^T Y (WI x WB block per lane)
+            if constexpr (kW) {
+                if (lane < Sh::WLI * Sh::WLB) {
+                    const int wi = lane % Sh::WLI, wb = lane / Sh::WLI;
+                    const int i0 = wi * Sh::WI, b0 = wb * Sh::WB;
+                    float wv[Sh::WI * Sh::WB];
+#pragma unroll
+                    for (int e = 0; e < Sh::WI * Sh::WB; ++e) wv[e] = 0.f;
+#pragma unroll
+                    for (int aa = 0; aa < P1; ++aa) {
+                        float dv[Sh::WI], yw[Sh::WB];
+#pragma unroll
+                        for (int r = 0; r < Sh::WI; ++r) dv[r] = D1w[aa * N1 + i0 + r];
+#pragma unroll
+                        for (int c = 0; c < Sh::WB; ++c) yw[c] = Ys[(b0 + c) * P1 + aa];
+                        rank1_update<Sh::WI, Sh::WB>(wv, dv, yw);
+                    }
+#pragma unroll
+                    for (int c = 0; c < Sh::WB; ++c)
+#pragma unroll
+                        for (int r = 0; r < Sh::WI; ++r) Zs[(b0 + c) * LD1 + pos1<Sh>(i0 + r)] = wv[c * Sh::WI + r];
+                }
+            } else if (lane < Sh::ZLA * Sh::ZLB) {
                 const int za = lane % Sh::ZLA, zb = lane / Sh::ZLA;
                 const int a0 = za * Sh::ZA, j0 = zb * Sh::ZB;
                 float z[Sh::ZA][Sh::ZB];
@@ -351,16 +440,26 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                     for (int c = 0; c < Sh::ZB; ++c) Zs[(a0 + r) * LD2 + pos2<Sh>(j0 + c)] = z[r][c];
             }
             __syncwarp();
-            // ---- C0 = D1^T Z on the lane's RI x RJ block (flat index e = c*RI + r)
+            // ---- C0 = D1^T Z or W D2 on the lane's RI x RJ block (flat index e = c*RI + r)
             float c0[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) c0[e] = 0.f;
+            if constexpr (!kW) {
 #pragma unroll
-            for (int aa = 0; aa < P1; ++aa) {
-                float u[RI], v[RJ];
-                vload<RI>(u, D1r + aa * LD1 + li * RIP);
-                vload<RJ>(v, Zs + aa * LD2 + lj * RJP);
-                rank1_update<RI, RJ>(c0, u, v);
+                for (int aa = 0; aa < P1; ++aa) {
+                    float u[RI], v[RJ];
+                    vload<RI>(u, D1r + aa * LD1 + li * RIP);
+                    vload<RJ>(v, Zs + aa * LD2 + lj * RJP);
+                    rank1_update<RI, RJ>(c0, u, v);
+                }
+            } else {
+#pragma unroll
+                for (int bb = 0; bb < P2; ++bb) {
+                    float u[RI], v[RJ];
+                    vload<RI>(u, Zs + bb * LD1 + li * RIP);
+                    vload<RJ>(v, D2p + bb * LD2 + lj * RJP);
+                    rank1_update<RI, RJ>(c0, u, v);
+                }
             }
 
             // keep C0 in shared memory: re-read once per step, masked by one store
@@ -520,20 +619,14 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
         } else if constexpr (SIDE == kSideD2) {
             float* wM = wacc;
             float* wB = wacc + N2 * N2;
+            // B2[b, j_l] += x_l W[i_l, b]
 #pragma unroll
             for (int e0 = 0; e0 < P2 * S; e0 += 32) {
                 const int e = e0 + lane;
                 const int l = e / P2, bb = e % P2;
                 const int il = __shfl_sync(kFull, myi, l & 31), jl = __shfl_sync(kFull, myj, l & 31);
                 const float xl = __shfl_sync(kFull, myx, l & 31);
-                if (l < cnt) {
-                    float wsum = 0.f;
-                    const float* yc = Ys + bb * P1;
-                    const float* dc = D1c + il * P1;
-#pragma unroll
-                    for (int r = 0; r < P1; ++r) wsum = fmaf(yc[r], dc[r], wsum);
-                    atomicAdd(&wB[bb * N2 + jl], xl * wsum);
-                }
+                if (l < cnt) atomicAdd(&wB[bb * N2 + jl], xl * Zs[bb * LD1 + pos1<Sh>(il)]);
             }
 #pragma unroll
             for (int e0 = 0; e0 < S * S; e0 += 32) {
@@ -586,16 +679,492 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
     }
 }
 
+// ------------------------------------------------------------ two signals per warp
+template <class Sh>
+struct HalfLayout {
+    static constexpr int P1 = Sh::P1, P2 = Sh::P2, N1 = Sh::N1, N2 = Sh::N2;
+    // floats; every region starts 16-byte aligned
+    static constexpr int d1r = 0;                                  // P1 x LD1: rows of D1, lane blocks
+    static constexpr int d1w = d1r + al4(P1 * Sh::LD1);            // P1 x N1: rows of D1
+    static constexpr int d2r = d1w + al4(P1 * N1);                 // P2 x N2: rows of D2
+    static constexpr int d2p = d2r + al4(P2 * N2);                 // P2 x LD2: rows of D2, lane blocks
+    static constexpr int g1 = d2p + al4(P2 * Sh::LD2);             // N1 x LD1
+    static constexpr int g2 = g1 + al4(N1 * Sh::LD1);              // N2 x LD2
+    static constexpr int acc = g2 + al4(N2 * Sh::LD2);
+    __host__ __device__ static constexpr int nf(int side) {
+        return side == kSideD1 ? N1 * N1 + P1 * N1 : side == kSideD2 ? N2 * N2 + P2 * N2 : 0;
+    }
+    // warp-private accumulators (both halves of a warp add into them)
+    __host__ __device__ static constexpr int accw(int side) { return al4(nf(side)) * Sh::WPC; }
+    // per-half energy sums: 2 WPC x 2 floats
+    __host__ __device__ static constexpr int acce(int side) { return acc + accw(side); }
+    __host__ __device__ static constexpr int half0(int side) { return acce(side) + al4(4 * Sh::WPC); }
+    // per half: mbarrier, Y (one buffer: the next signal is fetched into it as
+    // soon as the first contraction has read it), Z or W, the C0 blocks of the
+    // 16 lanes (lane-major, stride EP)
+    static constexpr int TZ = P1 * Sh::LD2, TW = P2 * Sh::LD1;
+    static constexpr int h_bar = 0;
+    static constexpr int h_y = 4;
+    static constexpr int h_t = h_y + al4(Sh::PP);
+    static constexpr int h_c0 = h_t + al4(TZ > TW ? TZ : TW);
+    // Cholesky state: packed rows of L, 1/L_tt, y
+    static constexpr int h_chol = h_c0 + 16 * Sh::EP;
+    static constexpr int h_stride = h_chol + al4(Sh::S * (Sh::S + 1) / 2) + 2 * al4(Sh::S);
+    __host__ __device__ static constexpr int total(int side, int wpc) {
+        return half0(side) + 2 * wpc * h_stride;
+    }
+};
+
+template <class Sh, int SIDE>
+__device__ __forceinline__ void code_half_body(const PassArgs& a, int cta, int n_ctas, int slot) {
+    using L = HalfLayout<Sh>;
+    constexpr int P1 = Sh::P1, P2 = Sh::P2, N1 = Sh::N1, N2 = Sh::N2, S = Sh::S;
+    constexpr int RI = Sh::RI, RJ = Sh::RJ, E = Sh::E, LI = Sh::LI;
+    constexpr int LD1 = Sh::LD1, LD2 = Sh::LD2, RIP = Sh::RIP, RJP = Sh::RJP;
+    constexpr int PP = Sh::PP;
+    constexpr unsigned kBytes = PP * 4;
+    constexpr bool kW = (SIDE == kSideD2);   // C0 = (D1^T Y) D2 rather than D1^T (Y D2)
+    extern __shared__ __align__(16) float smem[];
+
+    const int wpc = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int h = lane >> 4, hl = lane & 15;
+    const unsigned hm = 0xffffu << (16 * h);
+    const int li = hl % LI, lj = hl / LI;
+    float* D1r = smem + L::d1r;
+    float* D1w = smem + L::d1w;
+    float* D2r = smem + L::d2r;
+    float* D2p = smem + L::d2p;
+    float* G1s = smem + L::g1;
+    float* G2s = smem + L::g2;
+    float* acc = smem + L::acc;
+    float* acce = smem + L::acce(SIDE);
+    float* hb = smem + L::half0(SIDE) + (2 * w + h) * L::h_stride;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(hb + L::h_bar);
+    float* Ys = hb + L::h_y;
+    float* Ts = hb + L::h_t;    // Z (rows a, lane-block columns j) or W (rows b, lane-block columns i)
+    float* C0s = hb + L::h_c0;
+    float* myc0 = C0s + hl * Sh::EP;
+    float* Lsm = hb + L::h_chol;
+    float* ivsm = Lsm + al4(S * (S + 1) / 2);
+    float* yvsm = ivsm + al4(S);
+    constexpr int nf = L::nf(SIDE);
+    constexpr int nfa = al4(nf);
+    float* wacc = acc + w * nfa;
+
+    // ---- CTA set-up
+    for (int e = threadIdx.x; e < P1 * LD1; e += blockDim.x) {
+        const int r = e / LD1, pp = e % LD1;
+        const int blk = pp / RIP, off = pp % RIP;
+        D1r[e] = (off < RI) ? a.D1[r + P1 * (blk * RI + off)] : 0.f;
+    }
+    for (int e = threadIdx.x; e < P1 * N1; e += blockDim.x) {
+        const int r = e / N1, i = e % N1;
+        D1w[e] = a.D1[r + P1 * i];
+    }
+    for (int e = threadIdx.x; e < P2 * N2; e += blockDim.x) {
+        const int r = e / N2, j = e % N2;
+        D2r[e] = a.D2[r + P2 * j];
+    }
+    for (int e = threadIdx.x; e < P2 * LD2; e += blockDim.x) {
+        const int r = e / LD2, pp = e % LD2;
+        const int blk = pp / RJP, off = pp % RJP;
+        D2p[e] = (off < RJ) ? a.D2[r + P2 * (blk * RJ + off)] : 0.f;
+    }
+    for (int e = threadIdx.x; e < N1 * LD1; e += blockDim.x) {
+        const int c = e / LD1, pp = e % LD1;
+        const int blk = pp / RIP, off = pp % RIP;
+        G1s[e] = (off < RI) ? a.G1[c * N1 + blk * RI + off] : 0.f;
+    }
+    for (int e = threadIdx.x; e < N2 * LD2; e += blockDim.x) {
+        const int c = e / LD2, pp = e % LD2;
+        const int blk = pp / RJP, off = pp % RJP;
+        G2s[e] = (off < RJ) ? a.G2[c * N2 + blk * RJ + off] : 0.f;
+    }
+    if constexpr (SIDE != kCodeOnly) {
+        for (int e = threadIdx.x; e < L::accw(SIDE) + al4(4 * Sh::WPC); e += blockDim.x) acc[e] = 0.f;
+    }
+    for (int e = threadIdx.x; e < 2 * wpc * L::h_stride; e += blockDim.x) smem[L::half0(SIDE) + e] = 0.f;
+    __syncthreads();
+
+    // Positions: this warp takes pairs (jb, jb + 1), jb = first, first + stride,
+    // ...; half h codes position jb + h.  The trip count is the same for both
+    // halves (half 1 idles when only jb is left), so the warp meets at every
+    // full-warp synchronisation point.
+    const long long stride = (long long)n_ctas * wpc * 2;
+    const long long count = a.idx ? (long long)*a.idx_count : a.N;
+    const long long first = ((long long)cta * wpc + w) * 2;
+    if (hl == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    bool inflight = first + h < count;   // a copy into Ys is outstanding
+    if (hl == 0 && inflight) {
+        const long long k0 = a.idx ? (long long)a.idx[first + h] : first + h;
+        mbar_arrive_tx(bar, kBytes);
+        tma_load_1d(Ys, a.Y + (size_t)k0 * PP, kBytes, bar);
+    }
+    unsigned phase = 0;
+    float w_energy = 0.f, w_energy_c = 0.f, w_ynorm = 0.f, w_ynorm_c = 0.f;
+    bool alive = true;
+
+    for (long long jb = first; jb < count && alive; jb += stride) {
+        const long long jj = jb + h;
+        const bool act = jj < count;
+        const long long k = act ? (a.idx ? (long long)a.idx[jj] : jj) : 0;
+        bool got = true;
+        if (act) got = mbar_wait(bar, phase);
+        if (!__all_sync(kFull, got)) {
+            if (lane == 0) record_error(a.err, SDL_ERR_TIMEOUT);
+            alive = false;
+            break;
+        }
+        if (act) {
+            phase ^= 1u;
+            inflight = false;
+        }
+
+        // ---- ||Y||^2, with the partial sums and the combining order of a full warp
+        float ss = 0.f;
+        if (act) {
+            float lo = 0.f, hi = 0.f;
+#pragma unroll
+            for (int e = hl; e < PP; e += 32) lo = fmaf(Ys[e], Ys[e], lo);
+#pragma unroll
+            for (int e = hl + 16; e < PP; e += 32) hi = fmaf(Ys[e], Ys[e], hi);
+            ss = lo + hi;
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+        const bool finite = act && isfinite(ss);
+
+        // ---- first contraction: Z = Y D2 or W = D1^T Y (packed FMAs along row pairs)
+        if (finite) {
+            if constexpr (!kW) {
+                const int za = hl % Sh::ZLA, zb = hl / Sh::ZLA;
+                const int a0 = za * Sh::ZA, jz = zb * Sh::ZB;
+                float z[Sh::ZA * Sh::ZB];
+#pragma unroll
+                for (int e = 0; e < Sh::ZA * Sh::ZB; ++e) z[e] = 0.f;
+#pragma unroll
+                for (int b = 0; b < P2; ++b) {
+                    float yv[Sh::ZA], dv[Sh::ZB];
+                    vload2<Sh::ZA>(yv, Ys + b * P1 + a0);
+#pragma unroll
+                    for (int c = 0; c < Sh::ZB; ++c) dv[c] = D2r[b * N2 + jz + c];
+                    rank1_update<Sh::ZA, Sh::ZB>(z, yv, dv);
+                }
+#pragma unroll
+                for (int c = 0; c < Sh::ZB; ++c)
+#pragma unroll
+                    for (int r = 0; r < Sh::ZA; ++r) Ts[(a0 + r) * LD2 + pos2<Sh>(jz + c)] = z[c * Sh::ZA + r];
+            } else {
+                const int wi = hl % Sh::WLI, wb = hl / Sh::WLI;
+                const int i0 = wi * Sh::WI, b0 = wb * Sh::WB;
+                float wv[Sh::WI * Sh::WB];
+#pragma unroll
+                for (int e = 0; e < Sh::WI * Sh::WB; ++e) wv[e] = 0.f;
+#pragma unroll
+                for (int aa = 0; aa < P1; ++aa) {
+                    float dv[Sh::WI], yv[Sh::WB];
+                    vload2<Sh::WI>(dv, D1w + aa * N1 + i0);
+#pragma unroll
+                    for (int c = 0; c < Sh::WB; ++c) yv[c] = Ys[(b0 + c) * P1 + aa];
+                    rank1_update<Sh::WI, Sh::WB>(wv, dv, yv);
+                }
+#pragma unroll
+                for (int c = 0; c < Sh::WB; ++c)
+#pragma unroll
+                    for (int r = 0; r < Sh::WI; ++r) Ts[(b0 + c) * LD1 + pos1<Sh>(i0 + r)] = wv[c * Sh::WI + r];
+            }
+        }
+        __syncwarp(hm);   // Y is consumed: fetch this half's next signal into it
+        {
+            const long long jn = jj + stride;
+            if (act && jn < count) {
+                inflight = true;
+                if (hl == 0) {
+                    const long long kn = a.idx ? (long long)a.idx[jn] : jn;
+                    fence_proxy_async();
+                    mbar_arrive_tx(bar, kBytes);
+                    tma_load_1d(Ys, a.Y + (size_t)kn * PP, kBytes, bar);
+                }
+            }
+        }
+
+        int cnt = 0;
+        float E2 = ss;
+        int myi = 0, myj = 0;
+        float myx = 0.f;
+        int si[S], sj[S];
+        float xs[S];
+#pragma unroll
+        for (int m = 0; m < S; ++m) {
+            si[m] = 0; sj[m] = 0; xs[m] = 0.f;
+        }
+        if (__any_sync(kFull, finite)) {
+            // ---- C0 on the lane's RI x RJ block (flat index e = c*RI + r)
+            float c0[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) c0[e] = 0.f;
+            if constexpr (!kW) {
+#pragma unroll
+                for (int aa = 0; aa < P1; ++aa) {
+                    float u[RI], v[RJ];
+                    vload<RI>(u, D1r + aa * LD1 + li * RIP);
+                    vload<RJ>(v, Ts + aa * LD2 + lj * RJP);
+                    rank1_update<RI, RJ>(c0, u, v);
+                }
+            } else {
+#pragma unroll
+                for (int bb = 0; bb < P2; ++bb) {
+                    float u[RI], v[RJ];
+                    vload<RI>(u, Ts + bb * LD1 + li * RIP);
+                    vload<RJ>(v, D2p + bb * LD2 + lj * RJP);
+                    rank1_update<RI, RJ>(c0, u, v);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; e += 4) {
+                if (e + 4 <= E) {
+                    *reinterpret_cast<float4*>(myc0 + e) = make_float4(c0[e], c0[e + 1], c0[e + 2], c0[e + 3]);
+                } else {
+#pragma unroll
+                    for (int k2 = e; k2 < E; ++k2) myc0[k2] = c0[k2];
+                }
+            }
+            __syncwarp(hm);
+
+            // ---- greedy steps: every lane of a half computes the whole Cholesky
+            // update of its signal (identical values), lane 0 stores it
+            bool go = finite;
+            const int qbase = li * RI + N1 * (lj * RJ);
+            static_for<0, S>([&](auto tc) {
+                constexpr int t = decltype(tc)::value;
+                const bool live = go && !(a.eps2 > 0.f && E2 <= a.eps2);
+                float sc[E];
+                if constexpr (t == 0) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) sc[e] = c0[e];
+                } else {
+                    vload<E>(sc, myc0);
+                }
+#pragma unroll
+                for (int l = 0; l < t; ++l) {
+                    float u[RI], v[RJ];
+                    vload<RI>(u, G1s + si[l] * LD1 + li * RIP);
+                    vload<RJ>(v, G2s + sj[l] * LD2 + lj * RJP);
+                    const float nx = -xs[l];
+#pragma unroll
+                    for (int c = 0; c < RJ; ++c) v[c] *= nx;
+                    rank1_update<RI, RJ>(sc, u, v);
+                }
+                // argmax |sc|, ties to the smallest q: four interleaved chains
+                // (entries e = 4m + ch in increasing q), merged by (value, q)
+                float bv[4] = {0.f, 0.f, 0.f, 0.f};
+                int bqv[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
+#pragma unroll
+                for (int c = 0; c < RJ; ++c)
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) {
+                        const int e = c * RI + r;
+                        const float v = fabsf(sc[e]);
+                        if (v > bv[e & 3]) { bv[e & 3] = v; bqv[e & 3] = qbase + r + N1 * c; }
+                    }
+#pragma unroll
+                for (int ch = 1; ch < 4; ch += 2)
+                    if (bv[ch] > bv[ch - 1] || (bv[ch] == bv[ch - 1] && bqv[ch] < bqv[ch - 1])) {
+                        bv[ch - 1] = bv[ch];
+                        bqv[ch - 1] = bqv[ch];
+                    }
+                if (bv[2] > bv[0] || (bv[2] == bv[0] && bqv[2] < bqv[0])) {
+                    bv[0] = bv[2];
+                    bqv[0] = bqv[2];
+                }
+                // the Cholesky state of steps 0..t-1 (shared memory, so that it
+                // holds no registers while the scores are live)
+                constexpr int kOld = t * (t + 1) / 2;
+                float Lo[kOld > 0 ? kOld : 1], io[t > 0 ? t : 1], yo[t > 0 ? t : 1];
+#pragma unroll
+                for (int m = 0; m < kOld; ++m) Lo[m] = Lsm[m];
+#pragma unroll
+                for (int m = 0; m < t; ++m) {
+                    io[m] = ivsm[m];
+                    yo[m] = yvsm[m];
+                }
+                // each half's maximum and smallest q holding it, by full-warp
+                // reductions in which the other half contributes the identity
+                const unsigned bb = live ? __float_as_uint(bv[0]) : 0u;
+                const unsigned m0 = __reduce_max_sync(kFull, h ? 0u : bb);
+                const unsigned m1 = __reduce_max_sync(kFull, h ? bb : 0u);
+                const unsigned M = h ? m1 : m0;
+                const bool pick = live && M != 0u;
+                const unsigned cand = (pick && bb == M) ? (unsigned)bqv[0] : 0xffffffffu;
+                const unsigned q0 = __reduce_min_sync(kFull, h ? 0xffffffffu : cand);
+                const unsigned q1 = __reduce_min_sync(kFull, h ? cand : 0xffffffffu);
+                const int q = pick ? (int)(h ? q1 : q0) : 0;
+                const int it_ = q % N1, jt = q / N1;
+                const int owner = it_ / RI + LI * (jt / RJ);
+                float* cq = C0s + owner * Sh::EP + (jt % RJ) * RI + it_ % RI;
+                const float b = *cq;
+                __syncwarp();
+                if (hl == 0 && pick) *cq = __int_as_float(0x7fc00000);   // mask the pick
+                // ---- Cholesky row t (row t of a half that does not keep this
+                // pick is never read again)
+                const float* g1t = G1s + it_ * LD1;
+                const float* g2t = G2s + jt * LD2;
+                const float Att = g1t[pos1<Sh>(it_)] * g2t[pos2<Sh>(jt)];
+                float wr[t > 0 ? t : 1];   // row t of L
+                float ww = 0.f, wy = 0.f;
+#pragma unroll
+                for (int m = 0; m < t; ++m) {
+                    float am = g1t[pos1<Sh>(si[m])] * g2t[pos2<Sh>(sj[m])];
+#pragma unroll
+                    for (int l = 0; l < m; ++l) am = fmaf(-Lo[m * (m + 1) / 2 + l], wr[l], am);
+                    wr[m] = am * io[m];
+                    ww = fmaf(wr[m], wr[m], ww);
+                    wy = fmaf(wr[m], yo[m], wy);
+                }
+                const float d = Att - ww;
+                const bool ok = pick && (d > kPivotRel * Att);
+                const float inv = rsqrtf(d);
+                const float yt = (b - wy) * inv;
+                si[t] = it_;
+                sj[t] = jt;
+                if (hl == t && ok) {
+                    myi = it_;
+                    myj = jt;
+                }
+                // ---- x = L^{-T} y, kept only by a half that keeps the pick
+                float xn[t + 1];
+                xn[t] = yt * inv;
+#pragma unroll
+                for (int kk = t - 1; kk >= 0; --kk) {
+                    float v = yo[kk];
+#pragma unroll
+                    for (int l = kk + 1; l < t; ++l) v = fmaf(-Lo[l * (l + 1) / 2 + kk], xn[l], v);
+                    v = fmaf(-wr[kk], xn[t], v);
+                    xn[kk] = v * io[kk];
+                }
+#pragma unroll
+                for (int kk = 0; kk <= t; ++kk) xs[kk] = ok ? xn[kk] : xs[kk];
+                if (hl == 0) {
+#pragma unroll
+                    for (int m = 0; m < t; ++m) Lsm[kOld + m] = wr[m];
+                    ivsm[t] = inv;
+                    yvsm[t] = yt;
+                }
+                E2 = ok ? fmaf(-yt, yt, E2) : E2;
+                cnt = ok ? t + 1 : cnt;
+                go = ok;
+                __syncwarp();   // the masked C0 entry is visible to the next step
+            });
+#pragma unroll
+            for (int m = 0; m < S; ++m)
+                if (hl == m) myx = xs[m];
+        }
+
+        // ---- emit the code (lane hl of the half holds pick hl)
+        if (act) {
+            const long long ko = (a.idx && a.idx_compact) ? jj : k;
+            if (a.support && hl < S) {
+                a.support[(size_t)ko * S + hl] = (hl < cnt) ? myi + N1 * myj : -1;
+                a.coef[(size_t)ko * S + hl] = (hl < cnt) ? myx : 0.f;
+            }
+            if (hl == 0) {
+                if (a.nnz) a.nnz[ko] = cnt;
+                if (a.res_energy) a.res_energy[ko] = finite ? fmaxf(E2, 0.f) : __int_as_float(0x7fc00000);
+                if (!finite) record_error(a.err, SDL_ERR_NONFINITE);
+            }
+        }
+
+        // ---- fused partial sums into the warp's private accumulators; both
+        // halves run these adds together, so their order is fixed
+        __syncwarp();
+        if constexpr (SIDE == kSideD1) {
+            float* wP = wacc;
+            float* wB = wacc + N1 * N1;
+            // B1[r, i_l] += x_l Z[r, j_l]  (lane = r)
+#pragma unroll
+            for (int l = 0; l < S; ++l)
+                if (l < cnt && hl < P1) atomicAdd(&wB[hl * N1 + si[l]], xs[l] * Ts[hl * LD2 + pos2<Sh>(sj[l])]);
+            // P[i_l, i_m] += x_l x_m G2[j_l, j_m]  (lane = m)
+            const int pj = pos2<Sh>(myj);
+#pragma unroll
+            for (int l = 0; l < S; ++l)
+                if (l < cnt && hl < cnt) atomicAdd(&wP[si[l] * N1 + myi], xs[l] * myx * G2s[sj[l] * LD2 + pj]);
+        } else if constexpr (SIDE == kSideD2) {
+            float* wM = wacc;
+            float* wB = wacc + N2 * N2;
+            // B2[b, j_l] += x_l W[i_l, b]  (lane = b)
+#pragma unroll
+            for (int l = 0; l < S; ++l)
+                if (l < cnt && hl < P2) atomicAdd(&wB[hl * N2 + sj[l]], xs[l] * Ts[hl * LD1 + pos1<Sh>(si[l])]);
+            // M[j_l, j_m] += x_l x_m G1[i_l, i_m]  (lane = m)
+            const int pi = pos1<Sh>(myi);
+#pragma unroll
+            for (int l = 0; l < S; ++l)
+                if (l < cnt && hl < cnt) atomicAdd(&wM[sj[l] * N2 + myj], xs[l] * myx * G1s[si[l] * LD1 + pi]);
+        }
+        if (hl == 0 && finite) {
+            const float ye = fmaxf(E2, 0.f) - w_energy_c;
+            const float te = w_energy + ye;
+            w_energy_c = (te - w_energy) - ye;
+            w_energy = te;
+            const float yy = ss - w_ynorm_c;
+            const float ty = w_ynorm + yy;
+            w_ynorm_c = (ty - w_ynorm) - yy;
+            w_ynorm = ty;
+        }
+        __syncwarp();
+    }
+    if (!alive && hl == 0 && inflight) {
+        // give the copy that timed out a last bounded chance to land before the
+        // CTA's shared memory is released
+        mbar_wait(bar, phase);
+    }
+
+    if constexpr (SIDE != kCodeOnly) {
+        if (hl == 0) {
+            acce[2 * (2 * w + h)] = w_energy - w_energy_c;
+            acce[2 * (2 * w + h) + 1] = w_ynorm - w_ynorm_c;
+        }
+        __syncthreads();
+        const int wpc_all = blockDim.x >> 5;
+        float* dst = a.part_f + (size_t)slot * nf;
+        for (int e = threadIdx.x; e < nf; e += blockDim.x) {
+            float v = 0.f;
+            for (int ww = 0; ww < wpc_all; ++ww) v += acc[ww * nfa + e];
+            dst[e] = v;
+        }
+        if (threadIdx.x < 2) {
+            double d = 0.0;
+            for (int hh = 0; hh < 2 * wpc_all; ++hh) d += (double)acce[2 * hh + threadIdx.x];
+            a.part_d[(size_t)slot * 2 + threadIdx.x] = d;
+        }
+    }
+}
+
+template <class Sh>
+using LayoutFor = std::conditional_t<Sh::kHalf, HalfLayout<Sh>, FastLayout<Sh>>;
+
+template <class Sh, int SIDE>
+__device__ __forceinline__ void code_body(const PassArgs& a, int cta, int n_ctas, int slot) {
+    if constexpr (Sh::kHalf) code_half_body<Sh, SIDE>(a, cta, n_ctas, slot);
+    else code_fast_body<Sh, SIDE>(a, cta, n_ctas, slot);
+}
+
 template <class Sh, int SIDE>
 __global__ void __launch_bounds__(Sh::WPC * 32, Sh::MINB) code_fast_kernel(PassArgs a) {
-    code_fast_body<Sh, SIDE>(a, blockIdx.x, gridDim.x, blockIdx.x);
+    code_body<Sh, SIDE>(a, blockIdx.x, gridDim.x, blockIdx.x);
 }
 
 constexpr int kMaxCtasPerSm = 8;
 
 template <class Sh, int SIDE>
 int launch_fast_impl(const PassArgs& a, cudaStream_t st, int num_sms, int ctas_per_sm) {
-    using L = FastLayout<Sh>;
+    using L = LayoutFor<Sh>;
     constexpr int kWarpsPerCta = Sh::WPC;
     const size_t bytes = sizeof(float) * (size_t)L::total(SIDE, kWarpsPerCta);
     auto kern = code_fast_kernel<Sh, SIDE>;
@@ -608,7 +1177,7 @@ int launch_fast_impl(const PassArgs& a, cudaStream_t st, int num_sms, int ctas_p
         return SDL_ERR_CUDA;
     bps = std::max(1, std::min(bps, kMaxCtasPerSm));
     if (ctas_per_sm > 0) bps = std::min(bps, ctas_per_sm);
-    const long long need = (a.N + kWarpsPerCta - 1) / kWarpsPerCta;
+    const long long need = (a.N + Sh::SPC - 1) / Sh::SPC;
     const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms * bps));
     kern<<<grid, kWarpsPerCta * 32, bytes, st>>>(a);
     if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
@@ -625,24 +1194,28 @@ int launch_fast_side(const PassArgs& a, int side, cudaStream_t st, int num_sms, 
     }
 }
 
-// Compiled shapes: <p1, p2, n1, n2, s, LI, RI, RJ, ZA, ZB, warps/CTA, min CTAs/SM>.
+// Compiled shapes: <p1, p2, n1, n2, s, LI, RI, RJ, ZA, ZB, WI, WB, warps/CTA, min CTAs/SM>.
 // Two lane tilings of the n1 x n2 correlation block per problem shape; the
 // batch autotuner times both.
-using F8x16s4 = Shape<8, 8, 16, 16, 4, 4, 4, 2, 2, 2, 8, 3>;
-using F8x16s4b = Shape<8, 8, 16, 16, 4, 8, 2, 4, 2, 2, 8, 2>;
-using F12x24s6 = Shape<12, 12, 24, 24, 6, 4, 6, 3, 3, 3, 8, 2>;
-using F12x24s6b = Shape<12, 12, 24, 24, 6, 8, 3, 6, 3, 3, 8, 2>;
-using F16x32s8 = Shape<16, 16, 32, 32, 8, 4, 8, 4, 4, 4, 8, 2>;
-using F16x32s8b = Shape<16, 16, 32, 32, 8, 8, 4, 8, 4, 4, 8, 2>;
+using F8x16s4 = Shape<8, 8, 16, 16, 4, 4, 4, 2, 2, 2, 2, 2, 8, 3>;
+using F8x16s4b = Shape<8, 8, 16, 16, 4, 8, 2, 4, 2, 2, 2, 2, 8, 2>;
+using F12x24s6 = Shape<12, 12, 24, 24, 6, 4, 6, 3, 3, 3, 3, 3, 8, 2>;
+using F12x24s6b = Shape<12, 12, 24, 24, 6, 8, 3, 6, 3, 3, 3, 3, 8, 2>;
+using F16x32s8 = Shape<16, 16, 32, 32, 8, 4, 8, 4, 4, 4, 4, 4, 8, 2>;
+using F16x32s8b = Shape<16, 16, 32, 32, 8, 8, 4, 8, 4, 4, 4, 4, 8, 2>;
+// two signals per warp: <p1, p2, n1, n2, s, LI, RI, RJ, ZA, ZB, WI, WB, warps/CTA, min CTAs/SM>
+using H8x16s4 = HalfShape<8, 8, 16, 16, 4, 4, 4, 4, 2, 4, 4, 2, 8, 2>;
+using H12x24s6 = HalfShape<12, 12, 24, 24, 6, 2, 12, 3, 6, 3, 6, 3, 8, 2>;
 
-enum FastId { k8x16a = 0, k8x16b, k12x24a, k12x24b, k16x32a, k16x32b, kNumFast };
+enum FastId { k8x16a = 0, k8x16b, k12x24a, k12x24b, k16x32a, k16x32b, k8x16h, k12x24h, kNumFast };
 
 struct FastKey {
     int p1, p2, n1, n2, s;
 };
 constexpr FastKey kFastKeys[kNumFast] = {{8, 8, 16, 16, 4},  {8, 8, 16, 16, 4},
                                          {12, 12, 24, 24, 6}, {12, 12, 24, 24, 6},
-                                         {16, 16, 32, 32, 8}, {16, 16, 32, 32, 8}};
+                                         {16, 16, 32, 32, 8}, {16, 16, 32, 32, 8},
+                                         {8, 8, 16, 16, 4},  {12, 12, 24, 24, 6}};
 
 template <class F>
 int with_shape(int id, F&& f) {
@@ -653,6 +1226,8 @@ int with_shape(int id, F&& f) {
         case k12x24b: return f(F12x24s6b{});
         case k16x32a: return f(F16x32s8{});
         case k16x32b: return f(F16x32s8b{});
+        case k8x16h: return f(H8x16s4{});
+        case k12x24h: return f(H12x24s6{});
         default: return SDL_ERR_UNSUPPORTED;
     }
 }
@@ -676,6 +1251,8 @@ __global__ void __launch_bounds__(256, 2)
         case k12x24b: code_fast_body<F12x24s6b, SIDE>(a, cta, n, cta); break;
         case k16x32a: code_fast_body<F16x32s8, SIDE>(a, cta, n, cta); break;
         case k16x32b: code_fast_body<F16x32s8b, SIDE>(a, cta, n, cta); break;
+        case k8x16h: code_half_body<H8x16s4, SIDE>(a, cta, n, cta); break;
+        case k12x24h: code_half_body<H12x24s6, SIDE>(a, cta, n, cta); break;
         default: break;
     }
 }
@@ -693,6 +1270,10 @@ int launch_multi_impl(const PassArgs* d_groups, const int* d_cta_begin, const in
 
 }  // namespace
 
+int fast_variant_warps(int shape_id) {
+    return with_shape(shape_id, [&](auto sh) { return decltype(sh)::WPC; });
+}
+
 int fast_shape_variants(int p1, int p2, int n1, int n2, int s, int* ids, int max_ids) {
     int k = 0;
     for (int id = 0; id < kNumFast; ++id) {
@@ -706,7 +1287,7 @@ int fast_shape_variants(int p1, int p2, int n1, int n2, int s, int* ids, int max
 size_t fast_smem_bytes(int shape_id, int side) {
     const int r = with_shape(shape_id, [&](auto sh) {
         using Sh = decltype(sh);
-        return (int)(sizeof(float) * (size_t)FastLayout<Sh>::total(side, Sh::WPC));
+        return (int)(sizeof(float) * (size_t)LayoutFor<Sh>::total(side, Sh::WPC));
     });
     return r < 0 ? 0 : (size_t)r;
 }
@@ -748,9 +1329,12 @@ int multi_ctas_per_sm(size_t smem, int side) {
 }
 
 int launch_code_pass_fast(const PassArgs& a, int side, cudaStream_t st, int num_sms) {
-    // default tiling: the first compiled variant of the shape
-    int ids[2];
-    if (fast_shape_variants(a.p1, a.p2, a.n1, a.n2, a.s, ids, 2) == 0) return SDL_ERR_UNSUPPORTED;
+    int ids[kNumFast];
+    const int n = fast_shape_variants(a.p1, a.p2, a.n1, a.n2, a.s, ids, kNumFast);
+    if (n == 0) return SDL_ERR_UNSUPPORTED;
+    // a tiling pinned for this shape, else the first compiled variant
+    for (int v = 0; v < n; ++v)
+        if (a.tiling - 1 == ids[v]) return launch_code_pass_variant(a, side, ids[v], a.tiling_cps, st, num_sms);
     return launch_code_pass_variant(a, side, ids[0], 0, st, num_sms);
 }
 

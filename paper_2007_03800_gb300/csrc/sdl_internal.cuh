@@ -60,6 +60,11 @@ struct PassArgs {
     int ldc0;
     float c0_err_rel;
     unsigned long long* rescored;   // optional counter of re-scored entries
+    // host side only: compiled tiling of the specialised coder (id + 1; 0 =
+    // the first tiling compiled for the shape) and CTAs per SM (0 = as many
+    // as fit)
+    int tiling;
+    int tiling_cps;
 };
 
 // Host launchers (omp_pass.cu).  They return the number of partial-sum
@@ -71,6 +76,9 @@ int launch_accumulate_pass(const PassArgs& a, int side, cudaStream_t st, int num
 int launch_code_pass_fast(const PassArgs& a, int side, cudaStream_t st, int num_sms);
 // Compiled tilings ("shape ids") for a problem shape; returns how many.
 int fast_shape_variants(int p1, int p2, int n1, int n2, int s, int* ids, int max_ids);
+// warps per CTA of a compiled tiling (the persistent multi-problem kernel runs
+// 8-warp CTAs, so only those tilings can join a batch)
+int fast_variant_warps(int shape_id);
 size_t fast_smem_bytes(int shape_id, int side);
 // One problem with a given tiling; ctas_per_sm > 0 caps the resident CTAs per SM.
 int launch_code_pass_variant(const PassArgs& a, int side, int shape_id, int ctas_per_sm,

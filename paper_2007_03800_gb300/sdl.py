@@ -48,6 +48,7 @@ SIGNATURES = {
     "sdl_batch_sparse_code": [_P, _P],
     "sdl_batch_iterate": [_P, _P, _P],
     "sdl_batch_tuning": [_P, _P, _P, _P],
+    "sdl_batch_tuning_log": [_P, _P, _P, _P, _P, _I],
     "sdl_batch_destroy": [_P],
     "sdl_extract_patches": [_P, _I, _I, _I, _P, _P, _P],
     "sdl_patch_average": [_P, _P, _P, _P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _P],
@@ -70,6 +71,10 @@ SIGNATURES = {
     "sdl_iterate3": [_P, _P, _I, _I, _I, _L, _P, _I, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P],
     "sdl_ssim": [_P, _P, _P, _I, _I, _F, _P, _P],
     "sdl_set_precision": [_P, _I],
+    "sdl_tilings": [_I, _I, _I, _I, _I, _P, _I],
+    "sdl_set_tiling": [_P, _I, _I, _I, _I, _I, _I, _I],
+    "sdl_tune_tiling": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _P],
+    "sdl_tune_log": [_P, _P, _P, _P, _I],
     "sdl_precision_stats": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "sdl_profile_enable": [_P, _I],
     "sdl_profile_collect": [_P, _P, _P, _I],
@@ -140,6 +145,15 @@ def _need(t: torch.Tensor, dtype, shape, strides, name: str):
         raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
     if strides is not None and t.numel() > 1 and tuple(t.stride()) != tuple(strides):
         raise ValueError(f"{name} has strides {t.stride()}, expected {strides}")
+
+
+def tilings(p1, p2, n1, n2, s):
+    """Compiled tiling ids of the specialised coder for a shape (empty: none)."""
+    L = lib()
+    n = L.sdl_tilings(p1, p2, n1, n2, s, None, 0)
+    ids = (_I * max(n, 1))()
+    L.sdl_tilings(p1, p2, n1, n2, s, ids, n)
+    return [ids[k] for k in range(n)]
 
 
 def _check_Y(Y):
@@ -318,6 +332,25 @@ class Context:
         _check(rc, "sdl_iterate")
         return out
 
+    # ---- coder tilings
+    def set_tiling(self, p1, p2, n1, n2, s, tiling, ctas_per_sm=0) -> None:
+        """Pin a compiled tiling (see ``tilings``) for the shape; tiling < 0 unpins."""
+        _check(self._lib.sdl_set_tiling(self._h, p1, p2, n1, n2, s, int(tiling), int(ctas_per_sm)),
+               "sdl_set_tiling")
+
+    def tune_tiling(self, Y, D1, D2, s, stream=None):
+        """Time every tiling of the shape on these signals, pin the fastest;
+        returns (tiling id, [dict(tiling, ctas_per_sm, us), ...])."""
+        N, p1, p2 = _check_Y(Y)
+        n1, n2 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2")
+        tid = ctypes.c_int(-1)
+        _check(self._lib.sdl_tune_tiling(self._h, _ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2, s,
+                                         ctypes.byref(tid), _stream(stream)), "sdl_tune_tiling")
+        n = self._lib.sdl_tune_log(self._h, None, None, None, 0)
+        t, c, u = (_I * n)(), (_I * n)(), (_F * n)()
+        self._lib.sdl_tune_log(self._h, t, c, u, n)
+        return tid.value, [dict(tiling=t[e], ctas_per_sm=c[e], us=u[e]) for e in range(n)]
+
     # ---- three modes (Remark 3)
     def sparse_code3(self, Y, D1, D2, D3, s, out: Codes | None = None, stream=None) -> Codes:
         """``sdl_sparse_code3``: Y a (N, p1, p2, p3) CUDA tensor whose signals are
@@ -438,6 +471,16 @@ class Batch:
         sid, ctas, cost = (_I * G)(), (_I * G)(), (_F * G)()
         self._lib.sdl_batch_tuning(self._h, sid, ctas, cost)
         return [dict(shape_id=sid[g], ctas=ctas[g], cost_us=cost[g]) for g in range(G)]
+
+    def tuning_log(self):
+        """Every (group, tiling, CTAs per SM, microseconds) the autotuner timed."""
+        n = self._lib.sdl_batch_tuning_log(self._h, None, None, None, None, 0)
+        if n <= 0:
+            return []
+        g, sid, cps, cost = (_I * n)(), (_I * n)(), (_I * n)(), (_F * n)()
+        self._lib.sdl_batch_tuning_log(self._h, g, sid, cps, cost, n)
+        return [dict(group=g[e], shape_id=sid[e], ctas_per_sm=cps[e], cost_us=cost[e])
+                for e in range(n)]
 
     def close(self):
         if getattr(self, "_h", None):

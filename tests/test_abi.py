@@ -54,6 +54,19 @@ def test_shape_support_rules(lib):
     assert lib.sdl_shape_supported(65, 8, 16, 16, 4) == 0
 
 
+def test_tiling_listing_and_pinning_arguments(lib):
+    from paper_2007_03800_gb300 import sdl
+    t12 = sdl.tilings(12, 12, 24, 24, 6)
+    assert len(t12) >= 3 and len(set(t12)) == len(t12)
+    assert len(sdl.tilings(8, 8, 16, 16, 4)) >= 2 and len(sdl.tilings(16, 16, 32, 32, 8)) >= 2
+    assert sdl.tilings(10, 10, 20, 20, 5) == []               # generic kernel only
+    assert not set(t12) & set(sdl.tilings(8, 8, 16, 16, 4))
+    assert lib.sdl_tilings(12, 12, 24, 24, 6, None, -1) == -1
+    assert lib.sdl_set_tiling(None, 12, 12, 24, 24, 6, t12[0], 0) == -1
+    assert lib.sdl_tune_tiling(None, None, 12, 12, 10, None, 24, None, 24, 6, None, None) == -1
+    assert lib.sdl_tune_log(None, None, None, None, 0) == -1
+
+
 def test_host_argument_errors_without_gpu(lib):
     from paper_2007_03800_gb300 import sdl
     assert lib.sdl_sparse_code(None, None, 8, 8, 10, None, 16, None, 16, 4, 0.0,

@@ -60,6 +60,12 @@ def test_batch_sparse_code_matches_oracle_and_single_calls(gpu_ctx):
         assert torch.equal(single.coef, codes.coef)
     tun = batch.tuning()
     assert len(tun) == 3 and all(t["ctas"] >= 1 and t["cost_us"] > 0 for t in tun)
+    # the autotuner's log holds every timing it took; the chosen tiling is the fastest
+    log = batch.tuning_log()
+    for g, t in enumerate(tun):
+        mine = [e for e in log if e["group"] == g]
+        assert mine and min(e["cost_us"] for e in mine) == t["cost_us"]
+        assert t["shape_id"] in {e["shape_id"] for e in mine}
     batch.close()
 
 

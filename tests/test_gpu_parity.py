@@ -271,3 +271,75 @@ def test_bounded_wait_times_out_and_context_survives(gpu_ctx):
     Y, _, _, _, _ = synth.kron_model(512, 8, 8, 16, 16, 4, 20.0, seed=11)
     D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
     check_code(gpu_ctx, Y, D1, D2, 4)
+
+
+# ------------------------------------------------------------- every tiling
+@pytest.mark.parametrize("p1,n1,s,N", [(8, 16, 4, 4099), (12, 24, 6, 3001)])
+def test_every_tiling_gives_identical_codes_and_matches_oracle(gpu_ctx, p1, n1, s, N):
+    """Pin each compiled tiling in turn (one and two signals per warp, both lane
+    grids, 1 or 2 CTAs per SM): the codes are bit-identical across tilings,
+    with and without the error-driven stop, and one Algorithm-1 iteration
+    matches the oracle with each."""
+    tilings = sdl.tilings(p1, p1, n1, n1, s)
+    assert len(tilings) >= 3
+    rng = np.random.default_rng(77 + p1)
+    Y = rng.standard_normal((N, p1, p1))
+    D1, D2 = synth.init_dictionaries(p1, p1, n1, n1, seed=1)
+    eps = 0.8 * np.sqrt(p1 * p1)            # some signals stop before s picks
+    ref = oracle.omp2d(Y, D1, D2, s)
+    ref_eps = oracle.omp2d(Y, D1, D2, s, eps=eps)
+    it_ref = oracle.iterate(Y, D1, D2, s)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    first = first_eps = None
+    try:
+        for t in tilings:
+            for cps in (1, 2):
+                gpu_ctx.set_tiling(p1, p1, n1, n1, s, t, cps)
+                for e, r in ((0.0, ref), (eps, ref_eps)):
+                    out = gpu_ctx.sparse_code(Yg, D1g, D2g, s, eps=e)
+                    assert gpu_ctx.status() == 0
+                    got = (out.support.cpu(), out.coef.cpu(), out.nnz.cpu(), out.res_energy.cpu())
+                    if e == 0.0:
+                        first = first or got
+                        base = first
+                    else:
+                        first_eps = first_eps or got
+                        base = first_eps
+                    for x, y in zip(got, base):
+                        assert torch.equal(x, y), (t, cps, e)
+                    rep, exact = compare_supports(got[0].numpy(), got[2].numpy(), r,
+                                                  eps=(e or None))
+                    assert rep.bad == 0 and rep.ties <= max(2, 2e-3 * rep.n), (t, rep)
+                    assert coef_rel_error(got[1].numpy(), r.coef, exact).max(initial=0) < COEF_RTOL
+            D1i, D2i = D1g.clone(), D2g.clone()
+            rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+            gpu_ctx.iterate(Yg, D1i, D2i, s, rmse_out=rmse)
+            assert gpu_ctx.status() == 0
+            rm = rmse.cpu().numpy()
+            assert abs(rm[0] - it_ref.rmse_after_D1) / it_ref.rmse_after_D1 < RMSE_RTOL, (t, rm)
+            assert abs(rm[1] - it_ref.rmse_after_D2) / it_ref.rmse_after_D2 < RMSE_RTOL, (t, rm)
+            assert np.abs(D1i.cpu().numpy() - it_ref.D1).max() < DICT_RTOL, t
+            assert np.abs(D2i.cpu().numpy() - it_ref.D2).max() < DICT_RTOL, t
+    finally:
+        gpu_ctx.set_tiling(p1, p1, n1, n1, s, -1)
+
+
+def test_tune_tiling_pins_the_fastest(gpu_ctx):
+    imgs = np.stack([synth.synthetic_image(300 + i) for i in range(2)])
+    Y = synth.random_patches(imgs, 20_000, 12, seed=3)
+    D1, D2 = synth.init_dictionaries(12, 12, 24, 24, seed=1)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    try:
+        tid, log = gpu_ctx.tune_tiling(Yg, D1g, D2g, 6)
+        assert tid in sdl.tilings(12, 12, 24, 24, 6)
+        assert len(log) == 2 * len(sdl.tilings(12, 12, 24, 24, 6))
+        assert min(log, key=lambda e: e["us"])["tiling"] == tid
+        codes = gpu_ctx.sparse_code(Yg, D1g, D2g, 6)
+        rows = np.arange(0, 20_000, 17)
+        ref = oracle.omp2d(Y[rows], D1, D2, 6)
+        rep, exact = compare_supports(codes.support.cpu().numpy()[rows], codes.nnz.cpu().numpy()[rows], ref)
+        assert rep.bad == 0, rep
+    finally:
+        gpu_ctx.set_tiling(12, 12, 24, 24, 6, -1)
+    with pytest.raises(sdl.SDLError):
+        gpu_ctx.set_tiling(12, 12, 24, 24, 6, sdl.tilings(8, 8, 16, 16, 4)[0])
