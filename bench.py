@@ -62,14 +62,12 @@ def flops_per_signal_pass(p1, p2, n1, n2, s, side):
     """Algorithmic FLOPs of one 2D-OMP coding pass of one signal (with the
     fused partial sums of `side`): correlation C0 = D1^T (Y D2) in the cheaper
     association, the Gram-domain correlation updates sum_t 2 t n1 n2, the
-    incremental Cholesky/solves ~2 t^2 per step, and the epilogue sums."""
+    incremental Cholesky/solves ~2 t^2 per step, and the epilogue sums (B1 takes
+    rows of Z = Y D2, B2 rows of W = D1^T Y, both already formed for C0)."""
     c0 = 2 * min(p1 * p2 * n2 + n1 * p1 * n2, n1 * p1 * p2 + n1 * p2 * n2)
     upd = sum(2 * t * n1 * n2 for t in range(s))
     chol = sum(2 * t * t + 4 * t + 4 for t in range(s))
-    if side == 1:
-        epi = 2 * p1 * s + 3 * s * s
-    else:
-        epi = 2 * p1 * p2 * s + 2 * p2 * s + 3 * s * s
+    epi = 2 * (p1 if side == 1 else p2) * s + 3 * s * s
     return c0 + upd + chol + epi
 
 
@@ -247,10 +245,14 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     # the per-call path runs the tiling the tuner measured fastest on these
-    # signals (every tiling gives the same codes)
-    tiling, tune_log = ctx.tune_tiling(Yg, D1g, D2g, s)
-    tune_log = [dict(tiling=e["tiling"], ctas_per_sm=e["ctas_per_sm"], us=round(e["us"], 1))
-                for e in tune_log]
+    # signals (every tiling gives the same codes), or the one --tiling names
+    if args.tiling is None:
+        tiling, tune_log = ctx.tune_tiling(Yg, D1g, D2g, s)
+        tune_log = [dict(tiling=e["tiling"], ctas_per_sm=e["ctas_per_sm"], us=round(e["us"], 1))
+                    for e in tune_log]
+    else:
+        tiling, tune_log = args.tiling, []
+        ctx.set_tiling(p1, p2, n1, n2, s, tiling, 2)
     for _ in range(args.warmup):
         ctx.iterate(Yg, D1g, D2g, s, out=codes, rmse_out=rmse)
     ctx.check()
@@ -381,7 +383,7 @@ def run_ours(args):
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tpath):
             t = json.load(open(tpath))
-            ent = t.get(dom)
+            ent = t.get(f"{dom}/tiling{tiling}")
             if ent and ent.get("source_hash") == source_hash() and ent.get("N") == N:
                 traffic = ent["dram_bytes_per_launch"]
         cpu_times = time_oracle(Y[:CPU_SAMPLE], D1, D2, s, 1)
@@ -404,7 +406,8 @@ def run_ours(args):
                                       "tiling": tiling, "tune_log": tune_log},
             },
             "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in kinds.items()},
-            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+            "roofline": {"bound": "alu", "kernel": f"{dom} (tiling {tiling})", "achieved": achieved,
+                         "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                          "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes "
                                        f"x 2 x {sm_max:.0f} MHz",
@@ -807,6 +810,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tiling", type=int, default=None,
+                    help="pin this coder tiling (sdl_tilings) for the per-call path instead of tuning")
     ap.add_argument("--quick", action="store_true",
                     help="timed region only: no e2e loop, CPU baseline or clock sampling "
                          "(for profiler runs; its numbers are not bench values)")
