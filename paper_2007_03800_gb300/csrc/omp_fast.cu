@@ -72,9 +72,9 @@ struct Shape {
 // block per lane) for the D2-side pass, whose partial sum B2 takes rows of W.
 // Both halves run every greedy step together (a half that has stopped only
 // stops changing its state), so the maxima and picks of the two halves are
-// reduced with full-warp redux.sync; each lane scans its scores in four
-// interleaved argmax chains, and the Cholesky state lives in shared memory so
-// that it holds no registers while the scores are live.
+// reduced with full-warp redux.sync.  A lane updates and scans its block in two
+// row halves (four argmax chains in all), and the Cholesky state lives in
+// shared memory, so that registers hold half a score block at a time.
 template <int P1_, int P2_, int N1_, int N2_, int S_, int LI_, int RI_, int RJ_, int ZA_, int ZB_,
           int WI_, int WB_, int WPC_, int MINB_>
 struct HalfShape {
@@ -93,6 +93,7 @@ struct HalfShape {
     static_assert(ZLA * ZA == P1 && ZLB * ZB == N2 && ZLA * ZLB == 16 && ZA % 2 == 0, "Z tiling");
     static_assert(WLI * WI == N1 && WLB * WB == P2 && WLI * WLB == 16 && WI % 2 == 0, "W tiling");
     static_assert(P1 % 2 == 0 && N1 % 2 == 0 && P1 <= 16 && P2 <= 16, "row pairs, epilogue lanes");
+    static_assert(RI_ % 4 == 0 && RIP == RI_, "two even row halves per lane block, unpadded rows");
     static_assert(S <= 16 && S <= P1 * P2 && S <= N1 * N2, "s");
     static_assert((PP * 4) % 16 == 0, "TMA bulk copies need 16-byte multiples");
 };
@@ -943,35 +944,50 @@ __device__ __forceinline__ void code_half_body(const PassArgs& a, int cta, int n
             static_for<0, S>([&](auto tc) {
                 constexpr int t = decltype(tc)::value;
                 const bool live = go && !(a.eps2 > 0.f && E2 <= a.eps2);
-                float sc[E];
-                if constexpr (t == 0) {
-#pragma unroll
-                    for (int e = 0; e < E; ++e) sc[e] = c0[e];
-                } else {
-                    vload<E>(sc, myc0);
-                }
-#pragma unroll
-                for (int l = 0; l < t; ++l) {
-                    float u[RI], v[RJ];
-                    vload<RI>(u, G1s + si[l] * LD1 + li * RIP);
-                    vload<RJ>(v, G2s + sj[l] * LD2 + lj * RJP);
-                    const float nx = -xs[l];
-#pragma unroll
-                    for (int c = 0; c < RJ; ++c) v[c] *= nx;
-                    rank1_update<RI, RJ>(sc, u, v);
-                }
-                // argmax |sc|, ties to the smallest q: four interleaved chains
-                // (entries e = 4m + ch in increasing q), merged by (value, q)
+                // scores in two row halves of the lane's block (RH x RJ each), so
+                // that only half the block is live at once; half hh feeds argmax
+                // chains 2hh and 2hh + 1 (alternate rows), each visited in
+                // increasing q, merged by (value, q)
+                constexpr int RH = RI / 2, EH = RH * RJ;
                 float bv[4] = {0.f, 0.f, 0.f, 0.f};
                 int bqv[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
+                static_for<0, 2>([&](auto hc) {
+                    constexpr int hh = decltype(hc)::value;
+                    float sc[EH];   // sc[c*RH + r] = score of row hh*RH + r, column c
+                    if constexpr (t == 0) {
 #pragma unroll
-                for (int c = 0; c < RJ; ++c)
+                        for (int c = 0; c < RJ; ++c)
 #pragma unroll
-                    for (int r = 0; r < RI; ++r) {
-                        const int e = c * RI + r;
-                        const float v = fabsf(sc[e]);
-                        if (v > bv[e & 3]) { bv[e & 3] = v; bqv[e & 3] = qbase + r + N1 * c; }
+                            for (int r = 0; r < RH; ++r) sc[c * RH + r] = c0[c * RI + hh * RH + r];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < RJ; ++c)
+#pragma unroll
+                            for (int r = 0; r < RH; r += 2) {
+                                const float2 x2 = *reinterpret_cast<const float2*>(myc0 + c * RI + hh * RH + r);
+                                sc[c * RH + r] = x2.x;
+                                sc[c * RH + r + 1] = x2.y;
+                            }
                     }
+#pragma unroll
+                    for (int l = 0; l < t; ++l) {
+                        float u[RH], v[RJ];
+                        vload2<RH>(u, G1s + si[l] * LD1 + li * RIP + hh * RH);
+                        vload<RJ>(v, G2s + sj[l] * LD2 + lj * RJP);
+                        const float nx = -xs[l];
+#pragma unroll
+                        for (int c = 0; c < RJ; ++c) v[c] *= nx;
+                        rank1_update<RH, RJ>(sc, u, v);
+                    }
+#pragma unroll
+                    for (int c = 0; c < RJ; ++c)
+#pragma unroll
+                        for (int r = 0; r < RH; ++r) {
+                            const int ch = 2 * hh + (r & 1);
+                            const float v = fabsf(sc[c * RH + r]);
+                            if (v > bv[ch]) { bv[ch] = v; bqv[ch] = qbase + hh * RH + r + N1 * c; }
+                        }
+                });
 #pragma unroll
                 for (int ch = 1; ch < 4; ch += 2)
                     if (bv[ch] > bv[ch - 1] || (bv[ch] == bv[ch - 1] && bqv[ch] < bqv[ch - 1])) {
