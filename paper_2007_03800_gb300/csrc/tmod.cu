@@ -53,9 +53,11 @@ __global__ void gram2_kernel(const float* __restrict__ D1, int p1, int n1, float
 
 // Fixed-order compensated sum of the partial-sum slots, no floating-point
 // atomics (deterministic for a given slot count).  A block owns 32 entries;
-// warp w sums slots w, w+8, w+16, ... (coalesced 128-byte rows), then warp 0
-// adds the 8 warp sums in order.
-constexpr int kReduceWarps = 8;
+// warp w sums slots w, w+16, w+32, ... (coalesced 128-byte rows) in eight
+// interleaved compensated sums, so that eight loads per lane are in flight,
+// then warp 0 adds the 16 warp sums in order.
+constexpr int kReduceWarps = 16;
+constexpr int kReduceIlp = 8;
 
 __device__ __forceinline__ void reduce_body(const float* __restrict__ part_f,
                                             const double* __restrict__ part_d, int n_slots,
@@ -64,16 +66,17 @@ __device__ __forceinline__ void reduce_body(const float* __restrict__ part_f,
     __shared__ float ws[kReduceWarps][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int e = blk * 32 + lane;
-    // four interleaved compensated sums keep four loads in flight
-    float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+    float sum[kReduceIlp], comp[kReduceIlp];
+#pragma unroll
+    for (int u = 0; u < kReduceIlp; ++u) sum[u] = comp[u] = 0.f;
     if (e < nf) {
         int c = warp;
-        for (; c + 3 * kReduceWarps < n_slots; c += 4 * kReduceWarps) {
-            float v[4];
+        for (; c + (kReduceIlp - 1) * kReduceWarps < n_slots; c += kReduceIlp * kReduceWarps) {
+            float v[kReduceIlp];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = part_f[(size_t)(c + u * kReduceWarps) * nf + e];
+            for (int u = 0; u < kReduceIlp; ++u) v[u] = part_f[(size_t)(c + u * kReduceWarps) * nf + e];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kReduceIlp; ++u) {
                 const float y = v[u] - comp[u];
                 const float t = sum[u] + y;
                 comp[u] = (t - sum[u]) - y;
@@ -87,7 +90,10 @@ __device__ __forceinline__ void reduce_body(const float* __restrict__ part_f,
             sum[0] = t;
         }
     }
-    ws[warp][lane] = ((sum[0] - comp[0]) + (sum[1] - comp[1])) + ((sum[2] - comp[2]) + (sum[3] - comp[3]));
+    float wsum = 0.f;
+#pragma unroll
+    for (int u = 0; u < kReduceIlp; ++u) wsum += sum[u] - comp[u];
+    ws[warp][lane] = wsum;
     __syncthreads();
     if (warp == 0 && e < nf) {
         float tot = 0.f, c2 = 0.f;
