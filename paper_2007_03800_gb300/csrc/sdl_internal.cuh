@@ -91,6 +91,14 @@ int multi_ctas_per_sm(size_t smem, int side);
 bool code_shape_supported(int p1, int p2, int n1, int n2, int s);
 // Upper bound of the partial-sum slots any pass may use for these sizes.
 int max_partial_slots(int num_sms);
+// tmod3_fast.cu: three-mode coding pass specialised at compile time for the
+// compiled shapes (SDL_ERR_UNSUPPORTED otherwise or for a Y not 16-byte
+// aligned); returns the partial-sum slots written (mode 1-3) or 0 (mode 0)
+int launch_code3_fast(int mode, const float* Y, int p1, int p2, int p3, int n1, int n2, int n3,
+                      long long N, const float* D1, const float* D2, const float* D3,
+                      const float* G1, const float* G2, const float* G3, int s, int32_t* support,
+                      float* coef, int32_t* nnz, float* res, float* part_f, double* part_d,
+                      int max_slots, int* err, int num_sms, cudaStream_t st);
 
 // tmod.cu
 void launch_gram(const float* D, int p, int n, float* G, cudaStream_t st);

@@ -15,7 +15,8 @@
 //                       in warp-private accumulators combined in warp order;
 //   rescale3_kernel     the coefficients of every pick times the norm of its
 //                       mode-k atom (X <- X W_k^{-1}).
-// The reduction and the normal-equation solve are the two-mode kernels.
+// The reduction and the normal-equation solve are the two-mode kernels.  Shapes
+// compiled in tmod3_fast.cu take the specialised coder instead.
 #include <algorithm>
 #include <cmath>
 
@@ -339,6 +340,10 @@ int launch_code3(int mode, const float* Y, const Shape3& h, long long N, const f
                  const float* G3, int s, int32_t* support, float* coef, int32_t* nnz, float* res,
                  float* part_f, double* part_d, int max_slots, int* err, int num_sms,
                  cudaStream_t st) {
+    const int rf = launch_code3_fast(mode, Y, h.p1, h.p2, h.p3, h.n1, h.n2, h.n3, N, D1, D2, D3, G1,
+                                     G2, G3, s, support, coef, nnz, res, part_f, part_d, max_slots,
+                                     err, num_sms, st);
+    if (rf != SDL_ERR_UNSUPPORTED) return rf;
     int wpc = kMaxWarps3;
     while (wpc > 1 && smem3(h, s, mode, wpc) > kMaxSmem3) --wpc;
     const size_t bytes = smem3(h, s, mode, wpc);

@@ -24,7 +24,10 @@ def to_gpu(Y, Ds):
     return Yg, Dg
 
 
-@pytest.mark.parametrize("p,n,s", [((4, 4, 4), (8, 8, 8), 4), ((3, 5, 6), (6, 8, 10), 5)])
+# (4,4,4)/(8,8,8)/s=4 and the hyperspectral-shaped cube (4,4,16)/(8,8,16)/s=8 run
+# the compile-time coder, (3,5,6)/(6,8,10)/s=5 the generic one
+@pytest.mark.parametrize("p,n,s", [((4, 4, 4), (8, 8, 8), 4), ((3, 5, 6), (6, 8, 10), 5),
+                                   ((4, 4, 16), (8, 8, 16), 8)])
 def test_codes_match_oracle(gpu_ctx, p, n, s):
     Y, Ds = problem(2000, p, n, s)
     ref = tmod3.omp3d(Y, *Ds, s)
@@ -39,9 +42,10 @@ def test_codes_match_oracle(gpu_ctx, p, n, s):
     assert np.all(np.abs(e - ref.res_energy[exact]) <= 1e-5 * yy)
 
 
-def test_three_mode_iteration_matches_oracle(gpu_ctx):
-    p, n, s = (4, 4, 4), (8, 8, 8), 4
-    Y, Ds = problem(3000, p, n, s, seed=82)
+@pytest.mark.parametrize("p,n,s,N", [((4, 4, 4), (8, 8, 8), 4, 3000), ((3, 5, 6), (6, 8, 10), 5, 1500),
+                                     ((4, 4, 16), (8, 8, 16), 8, 1500)])
+def test_three_mode_iteration_matches_oracle(gpu_ctx, p, n, s, N):
+    Y, Ds = problem(N, p, n, s, seed=82)
     ref = tmod3.iterate3(Y, *Ds, s)
     Yg, Dg = to_gpu(Y, Ds)
     rmse = torch.zeros(3, dtype=torch.float32, device="cuda:0")
