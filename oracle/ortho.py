@@ -14,7 +14,7 @@ What each routine follows:
   iterate        : code, D1 update, code again with the new D1, D2 update
                    (the main loop of Algorithm 1 with the Procrustes updates)
 
-Readings where the paper is garbled or silent (also listed in the design doc):
+Readings where the paper is garbled or silent:
   * Remark 1 prints the SVD argument as (sum Y_k^T D2 X_k)(sum X_k X_k^T); the
     dimensions only agree for square signals and the extra factor is not the
     Procrustes matrix.  Maximising tr(D1^T sum_k Y_k D2 X_k^T) over orthonormal

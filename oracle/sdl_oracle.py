@@ -22,7 +22,7 @@ What each routine follows:
   update_D2         : Result 1 (optimal D2, then the W2 normalisation)
   iterate           : one pass of the main loop of Algorithm 1 (steps 1-4)
 
-Readings where the paper is silent or garbled (also listed in the design doc):
+Readings where the paper is silent or garbled:
   * Algorithm 1 prints D1 = P^{-1} R W1 and D2 = M^{-1} N W2; the dimensions
     only agree with Corollary 1 / Result 1 as D1* = (sum Y_k T_k^T) P^{-1} and
     D2* = (sum Y_k^T Z_k) M^{-1}, which is what is computed here.

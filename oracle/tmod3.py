@@ -20,7 +20,7 @@ What each routine follows:
   iterate3        : code, D1 update, code, D2 update, code, D3 update (one coding
                     pass before each update, as Algorithm 1 does for two modes)
 
-Readings (also listed in the design doc): the mode order of the iteration and one
+Readings: the mode order of the iteration and one
 coding pass per update are the two-mode algorithm's pattern; unused atoms and
 singular normal matrices follow the two-mode oracle.
 """
