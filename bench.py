@@ -768,7 +768,8 @@ def study_denoise(args):
     """Denoising with one batch of three patch sizes (8, 12, 16; D p x 2p;
     error-driven stop at 1.15 sigma p, s <= p/2) on a 512x512 synthetic image
     with sigma = 20 noise, 10 iterations: PSNRs and device time of the whole
-    pipeline (patch extraction, learning, coding, averaging)."""
+    pipeline (patch extraction, batch set-up with autotuning and graph capture,
+    learning, coding, averaging) and of each of those phases."""
     import torch
 
     from paper_2007_03800_gb300 import denoise as dn
@@ -782,22 +783,27 @@ def study_denoise(args):
     ctx = sdl.Context(0)
     for _ in range(args.warmup):
         dn.denoise(ctx, ng, sigma, iterations=1, clean=cg)
-    ms = []
+    ms, phases = [], []
     r = None
     for _ in range(max(args.steps, 1)):
         a, b = _events()
         a.record()
-        r = dn.denoise(ctx, ng, sigma, iterations=10, clean=cg)
+        r = dn.denoise(ctx, ng, sigma, iterations=10, clean=cg, timing=True)
         b.record()
         b.synchronize()
         ms.append(a.elapsed_time(b))
+        phases.append(r["ms_phases"])
     ctx.check()
     n_patches = sum((512 - p + 1) ** 2 for p, _, _ in dn.DEFAULT_GROUPS)
     res = {"psnr_noisy": sdl.psnr(ng, cg).item(), "psnr_denoised": [x.item() for x in r["psnr"]],
            "nnz_mean": [x.item() for x in r["nnz_mean"]], "rmse_final": r["rmse"][-1].tolist(),
            "ms_pipeline": statistics.median(ms), "patches": n_patches,
            "patch_iterations_per_s": 10 * n_patches / (statistics.median(ms) / 1e3),
-           "tuning": r["tuning"]}
+           "ms_phases": {k: statistics.median(p[k] for p in phases) for k in phases[0]},
+           "ms_per_learning_iteration": statistics.median(p["iterations"] for p in phases) / 10,
+           "tuning": r["tuning"],
+           "tuning_log": [dict(group=t["group"], shape_id=t["shape_id"], ctas_per_sm=t["ctas_per_sm"],
+                               us=round(t["cost_us"], 1)) for t in r["tuning_log"]]}
     ctx.close()
     print(json.dumps({"study": "denoise", "workload": "512x512 synthetic image, sigma=20, "
                       "all 8x8, 12x12, 16x16 patches, 10 iterations", "result": res}), flush=True)

@@ -21,6 +21,7 @@ struct sdl_batch {
     std::vector<int> shape;        // compiled tiling per group
     std::vector<int> cta_begin;    // G + 1 prefix of CTAs per group
     std::vector<float> cost_us;    // time of one fused pass of the group alone
+    int single_cps = 0;            // one group: the CTAs per SM the autotuner chose
     // every (group, tiling, CTAs per SM, cost) the autotuner measured
     std::vector<int> log_group, log_shape, log_cps;
     std::vector<float> log_cost;
@@ -50,6 +51,16 @@ namespace {
 constexpr int kSlotsPerSm = 8;   // partial-sum slots reserved per SM and group
 constexpr int kMultiWarps = 8;   // warps per CTA of the persistent multi-problem kernel
 
+// A coding pass of every group: one persistent multi-problem launch, or for a
+// single group its tiling's own kernel on the same CTAs (no other problem's
+// code shares its register allocation).
+int code_pass(const sdl_batch* b, int side, cudaStream_t st) {
+    if (b->G == 1) return launch_code_pass_grid(b->args[side][0], side, b->shape[0], b->total_ctas, st);
+    return launch_code_multi(b->d_args[side], b->d_cta_begin, b->d_shape, b->G, b->total_ctas,
+                             b->smem[side], side, st);
+}
+
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 double model_cost(const sdl_group& g) {
@@ -77,10 +88,7 @@ int enqueue_iteration(sdl_batch* b, cudaStream_t st, bool trace) {
     if (rc) return rc;
     for (int side = kSideD1; side <= kSideD2; ++side) {
         const int si = side - 1;
-        rc = run(side == kSideD1 ? kCodeD1 : kCodeD2, [&] {
-            return launch_code_multi(b->d_args[side], b->d_cta_begin, b->d_shape, G, b->total_ctas,
-                                     b->smem[side], side, st);
-        });
+        rc = run(side == kSideD1 ? kCodeD1 : kCodeD2, [&] { return code_pass(b, side, st); });
         if (rc) return rc;
         rc = run(kReduce, [&] {
             return launch_multi_update_kernels(1, b->d_red[si], G, b->red_blocks[si], 0, c->err, st);
@@ -250,17 +258,44 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
     b->shape.resize(G);
     b->cost_us.resize(G);
     if (flags & SDL_BATCH_AUTOTUNE) {
+        // each candidate is timed in the multi-problem kernel that will run it
+        // (its register allocation is not the single-problem kernel's): group g
+        // alone, as a one-group launch on num_sms x cps CTAs
+        if (cudaMemcpyAsync(b->d_args[kSideD1], b->args[kSideD1].data(), sizeof(PassArgs) * G,
+                            cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            destroy(b);
+            return SDL_ERR_CUDA;
+        }
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         for (int g = 0; g < G; ++g) {
             float best = 1e30f;
+            int best_cps = 2;
+            b->shape[g] = variants[g][0];
+            b->cost_us[g] = (float)(model_cost(groups[g]) * 1e-6);
             for (int v : variants[g]) {
-                for (int cps = 1; cps <= 2; ++cps) {
-                    const PassArgs& a = b->args[kSideD1][g];
-                    if (launch_code_pass_variant(a, kSideD1, v, cps, st, c->num_sms) < 0) continue;
+                const size_t sm_v = fast_smem_bytes(v, kSideD1);
+                int fit = G == 1 ? fast_variant_ctas_per_sm(v, kSideD1) : multi_ctas_per_sm(sm_v, kSideD1);
+                for (int sd = 0; sd < 3 && G == 1; ++sd) fit = std::min(fit, fast_variant_ctas_per_sm(v, sd));
+                for (int cps = 1; cps <= std::min(2, fit); ++cps) {
+                    const int grid = c->num_sms * cps;
+                    if (G > 1) {
+                        const int hb[3] = {0, grid, v};   // cta_begin[0..1], shape[0]
+                        if (cudaMemcpy(b->d_cta_begin, hb, sizeof(int) * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+                            cudaMemcpy(b->d_shape, hb + 2, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+                            continue;
+                    }
+                    auto pass = [&] {
+                        if (G == 1) return launch_code_pass_grid(b->args[kSideD1][g], kSideD1, v, grid, st);
+                        return launch_code_multi(b->d_args[kSideD1] + g, b->d_cta_begin, b->d_shape, 1,
+                                                 grid, sm_v, kSideD1, st);
+                    };
+                    if (pass() != SDL_OK) continue;
                     cudaEventRecord(e0, st);
-                    for (int r = 0; r < 3; ++r) launch_code_pass_variant(a, kSideD1, v, cps, st, c->num_sms);
+                    for (int r = 0; r < 3; ++r) pass();
                     cudaEventRecord(e1, st);
                     cudaEventSynchronize(e1);
                     float ms = 0.f;
@@ -273,10 +308,12 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
                     if (us < best) {
                         best = us;
                         b->shape[g] = v;
+                        best_cps = cps;
                     }
                 }
             }
-            b->cost_us[g] = best;
+            if (best < 1e30f) b->cost_us[g] = best;
+            if (G == 1) b->single_cps = best_cps;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -293,7 +330,9 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
     }
     int cps = 2;
     for (int side = 0; side < 3; ++side)
-        cps = std::min(cps, std::max(1, multi_ctas_per_sm(b->smem[side], side)));
+        cps = std::min(cps, std::max(1, G == 1 ? fast_variant_ctas_per_sm(b->shape[0], side)
+                                               : multi_ctas_per_sm(b->smem[side], side)));
+    if (G == 1 && b->single_cps > 0) cps = std::min(cps, b->single_cps);
     int total = c->num_sms * cps;
     std::vector<int> n_cta(G, 1);
     {
@@ -440,8 +479,7 @@ int sdl_batch_sparse_code(sdl_batch* b, void* stream) {
     }
     if (rc) return rc;
     Trace tr(c, kCode, st);
-    return launch_code_multi(b->d_args[kCodeOnly], b->d_cta_begin, b->d_shape, b->G, b->total_ctas,
-                             b->smem[kCodeOnly], kCodeOnly, st);
+    return code_pass(b, kCodeOnly, st);
 }
 
 int sdl_batch_iterate(sdl_batch* b, float* rmse_out, void* stream) {

@@ -94,6 +94,7 @@ struct HalfShape {
     static_assert(WLI * WI == N1 && WLB * WB == P2 && WLI * WLB == 16 && WI % 2 == 0, "W tiling");
     static_assert(P1 % 2 == 0 && N1 % 2 == 0 && P1 <= 16 && P2 <= 16, "row pairs, epilogue lanes");
     static_assert(RI_ % 4 == 0 && RIP == RI_, "two even row halves per lane block, unpadded rows");
+    static_assert(E % 4 == 0, "C0 blocks stored as float4");
     static_assert(S <= 16 && S <= P1 * P2 && S <= N1 * N2, "s");
     static_assert((PP * 4) % 16 == 0, "TMA bulk copies need 16-byte multiples");
 };
@@ -927,14 +928,8 @@ __device__ __forceinline__ void code_half_body(const PassArgs& a, int cta, int n
                 }
             }
 #pragma unroll
-            for (int e = 0; e < E; e += 4) {
-                if (e + 4 <= E) {
-                    *reinterpret_cast<float4*>(myc0 + e) = make_float4(c0[e], c0[e + 1], c0[e + 2], c0[e + 3]);
-                } else {
-#pragma unroll
-                    for (int k2 = e; k2 < E; ++k2) myc0[k2] = c0[k2];
-                }
-            }
+            for (int e = 0; e < E; e += 4)
+                *reinterpret_cast<float4*>(myc0 + e) = make_float4(c0[e], c0[e + 1], c0[e + 2], c0[e + 3]);
             __syncwarp(hm);
 
             // ---- greedy steps: every lane of a half computes the whole Cholesky
@@ -944,6 +939,10 @@ __device__ __forceinline__ void code_half_body(const PassArgs& a, int cta, int n
             static_for<0, S>([&](auto tc) {
                 constexpr int t = decltype(tc)::value;
                 const bool live = go && !(a.eps2 > 0.f && E2 <= a.eps2);
+                if (!__any_sync(kFull, live)) {   // both halves done: skip the remaining steps
+                    go = false;
+                    return;
+                }
                 // scores in two row halves of the lane's block (RH x RJ each), so
                 // that only half the block is live at once; half hh feeds argmax
                 // chains 2hh and 2hh + 1 (alternate rows), each visited in
@@ -1285,6 +1284,47 @@ int launch_multi_impl(const PassArgs* d_groups, const int* d_cta_begin, const in
 }
 
 }  // namespace
+
+int launch_code_pass_grid(const PassArgs& a, int side, int shape_id, int grid, cudaStream_t st) {
+    if (grid < 1) return SDL_ERR_ARG;
+    return with_shape(shape_id, [&](auto sh) -> int {
+        using Sh = decltype(sh);
+        const size_t bytes = sizeof(float) * (size_t)LayoutFor<Sh>::total(side, Sh::WPC);
+        auto go = [&](auto kern) -> int {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                cudaSuccess)
+                return SDL_ERR_CUDA;
+            kern<<<grid, Sh::WPC * 32, bytes, st>>>(a);
+            return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+        };
+        switch (side) {
+            case kCodeOnly: return go(code_fast_kernel<Sh, kCodeOnly>);
+            case kSideD1: return go(code_fast_kernel<Sh, kSideD1>);
+            case kSideD2: return go(code_fast_kernel<Sh, kSideD2>);
+            default: return SDL_ERR_ARG;
+        }
+    });
+}
+
+int fast_variant_ctas_per_sm(int shape_id, int side) {
+    return with_shape(shape_id, [&](auto sh) -> int {
+        using Sh = decltype(sh);
+        const size_t bytes = sizeof(float) * (size_t)LayoutFor<Sh>::total(side, Sh::WPC);
+        int bps = 0;
+        auto occ = [&](auto kern) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                    cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, Sh::WPC * 32, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                bps = 0;
+            }
+        };
+        if (side == kCodeOnly) occ(code_fast_kernel<Sh, kCodeOnly>);
+        else if (side == kSideD1) occ(code_fast_kernel<Sh, kSideD1>);
+        else occ(code_fast_kernel<Sh, kSideD2>);
+        return bps;
+    });
+}
 
 int fast_variant_warps(int shape_id) {
     return with_shape(shape_id, [&](auto sh) { return decltype(sh)::WPC; });

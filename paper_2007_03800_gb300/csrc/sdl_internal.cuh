@@ -79,6 +79,10 @@ int fast_shape_variants(int p1, int p2, int n1, int n2, int s, int* ids, int max
 // warps per CTA of a compiled tiling (the persistent multi-problem kernel runs
 // 8-warp CTAs, so only those tilings can join a batch)
 int fast_variant_warps(int shape_id);
+// one compiled tiling on exactly `grid` CTAs (a one-problem batch runs its
+// passes this way), and the CTAs per SM that tiling's kernel fits
+int launch_code_pass_grid(const PassArgs& a, int side, int shape_id, int grid, cudaStream_t st);
+int fast_variant_ctas_per_sm(int shape_id, int side);
 size_t fast_smem_bytes(int shape_id, int side);
 // One problem with a given tiling; ctas_per_sm > 0 caps the resident CTAs per SM.
 int launch_code_pass_variant(const PassArgs& a, int side, int shape_id, int ctas_per_sm,

@@ -16,11 +16,23 @@ DEFAULT_GROUPS = ((8, 16, 4), (12, 24, 6), (16, 32, 8))   # (p, n, s cap): D is 
 
 def denoise(ctx: sdl.Context, noisy: torch.Tensor, sigma: float, groups=DEFAULT_GROUPS,
             iterations: int = 10, clean: torch.Tensor | None = None, dict_seed: int = 1,
-            autotune: bool = True, graph: bool = True, stream=None):
+            autotune: bool = True, graph: bool = True, stream=None, timing: bool = False):
     """Learn one dictionary pair per patch size on the noisy image itself and
     denoise with it.  Returns a dict with per-group images, PSNRs (if clean
-    is given), the RMSE trajectory (iterations x 2*G) and the batch tuning."""
+    is given), the RMSE trajectory (iterations x 2*G) and the batch tuning;
+    with timing, also the device time of each phase in ms (CUDA events on
+    the stream): patch extraction, batch set-up (autotuning and graph
+    capture), the learning iterations, the final coding pass, averaging."""
     H, W = noisy.shape
+    evs = []
+
+    def mark():
+        if timing:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream if stream is not None else torch.cuda.current_stream())
+            evs.append(e)
+
+    mark()
     specs, meta = [], []
     for p, n, s in groups:
         Y, means = sdl.extract_patches(noisy, p, stream=stream)
@@ -29,14 +41,18 @@ def denoise(ctx: sdl.Context, noisy: torch.Tensor, sigma: float, groups=DEFAULT_
         D2g = sdl.dictionary(torch.tensor(D2, dtype=torch.float32, device=noisy.device))
         specs.append(dict(Y=Y, D1=D1g, D2=D2g, s=s, eps=1.15 * sigma * p))
         meta.append(dict(p=p, n=n, s=s, means=means))
+    mark()
     batch = sdl.Batch(ctx, specs, autotune=autotune, graph=graph, stream=stream)
     rmse = torch.zeros(2 * len(specs), dtype=torch.float32, device=noisy.device)
+    mark()
     traj = []
     for _ in range(iterations):
         batch.iterate(rmse_out=rmse, stream=stream)
         traj.append(rmse.clone())
+    mark()
     batch.sparse_code(stream=stream)
-    out = dict(images=[], psnr=[], nnz_mean=[], tuning=batch.tuning(),
+    mark()
+    out = dict(images=[], psnr=[], nnz_mean=[], tuning=batch.tuning(), tuning_log=batch.tuning_log(),
                rmse=torch.stack(traj) if traj else None, dictionaries=[])
     for spec, m in zip(batch.groups, meta):
         img = sdl.patch_average(ctx, spec["codes"], m["means"], spec["D1"], spec["D2"], m["p"],
@@ -46,6 +62,11 @@ def denoise(ctx: sdl.Context, noisy: torch.Tensor, sigma: float, groups=DEFAULT_
         out["dictionaries"].append((spec["D1"], spec["D2"]))
         if clean is not None:
             out["psnr"].append(sdl.psnr(img, clean, stream=stream))
+    mark()
+    if timing:
+        evs[-1].synchronize()
+        names = ("extract", "setup", "iterations", "final_code", "average")
+        out["ms_phases"] = {k: evs[i].elapsed_time(evs[i + 1]) for i, k in enumerate(names)}
     batch.close()
     return out
 
