@@ -117,3 +117,32 @@ def test_batch_rejects_shapes_without_specialisation(gpu_ctx):
     with pytest.raises(sdl.SDLError) as e:
         sdl.Batch(gpu_ctx, [dict(Y=Yg, D1=D1g, D2=D2g, s=10)])
     assert e.value.code == -7
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_one_group_batch_runs_its_tiling_kernel_and_matches_oracle(gpu_ctx, graph):
+    """A one-group batch codes with its tiling's own kernel (no multi-problem
+    launch): one iteration matches the oracle, and the graph replays the
+    direct launches bit for bit."""
+    g = make_groups(seed=5)[1]
+    ref = oracle.iterate(g["Y"], g["D1"], g["D2"], g["s"], eps=g["eps"] or None)
+    results = []
+    for gr in (False, graph):
+        spec = to_specs([g])
+        batch = sdl.Batch(gpu_ctx, spec, autotune=False, graph=gr)
+        rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+        batch.iterate(rmse_out=rmse)
+        assert gpu_ctx.status() == 0
+        s = batch.groups[0]
+        r = rmse.cpu().numpy()
+        assert abs(r[0] - ref.rmse_after_D1) / ref.rmse_after_D1 < RMSE_RTOL
+        assert abs(r[1] - ref.rmse_after_D2) / ref.rmse_after_D2 < RMSE_RTOL
+        assert np.abs(s["D1"].cpu().numpy() - ref.D1).max() < DICT_RTOL
+        assert np.abs(s["D2"].cpu().numpy() - ref.D2).max() < DICT_RTOL
+        rep, exact = compare_supports(s["codes"].support.cpu().numpy(), s["codes"].nnz.cpu().numpy(),
+                                      ref.omp_b, eps=g["eps"] or None)
+        assert rep.bad == 0, rep
+        results.append((s["D1"].clone(), s["D2"].clone(), s["codes"].coef.clone(), rmse.clone()))
+        batch.close()
+    for x, y in zip(*results):
+        assert torch.equal(x, y)
