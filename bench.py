@@ -325,42 +325,83 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return 0
+    # Every step is an independent job through the public API: H2D of the
+    # signals and the starting dictionaries from pinned host memory, one
+    # sdl_iterate, D2H of the codes, the dictionaries and the RMSE.  Two device
+    # buffer sets and two copy streams let the copies of step k+1 and the
+    # results of step k-1 move while step k computes (a set is refilled only
+    # after its previous results have left); the L2 flush before each compute
+    # is inside the timed region.
     Yh = torch.from_numpy(np.ascontiguousarray(Y32.transpose(0, 2, 1))).pin_memory()  # (N, p2, p1)
     D1h = torch.tensor(D1, dtype=torch.float32).t().contiguous().pin_memory()   # column-major
     D2h = torch.tensor(D2, dtype=torch.float32).t().contiguous().pin_memory()
-    out_h = {"D1": torch.empty_like(D1h).pin_memory(), "D2": torch.empty_like(D2h).pin_memory(),
-             "support": torch.empty((N, s), dtype=torch.int32).pin_memory(),
-             "coef": torch.empty((N, s), dtype=torch.float32).pin_memory(),
-             "nnz": torch.empty((N,), dtype=torch.int32).pin_memory(),
-             "rmse": torch.empty(2, dtype=torch.float32).pin_memory()}
-    Ybuf = torch.empty((N, p2, p1), dtype=torch.float32, device=dev)
-    D1buf = torch.empty((n1, p1), dtype=torch.float32, device=dev)
-    D2buf = torch.empty((n2, p2), dtype=torch.float32, device=dev)
+    sets = []
+    for _ in range(2):
+        S = {"Y": torch.empty((N, p2, p1), dtype=torch.float32, device=dev),
+             "D1": torch.empty((n1, p1), dtype=torch.float32, device=dev),
+             "D2": torch.empty((n2, p2), dtype=torch.float32, device=dev),
+             "codes": sdl.Codes.empty(N, s, dev),
+             "rmse": torch.zeros(2, dtype=torch.float32, device=dev),
+             "in": torch.cuda.Event(), "done": torch.cuda.Event(), "out": torch.cuda.Event()}
+        S["host"] = {"D1": torch.empty_like(D1h).pin_memory(), "D2": torch.empty_like(D2h).pin_memory(),
+                     "support": torch.empty((N, s), dtype=torch.int32).pin_memory(),
+                     "coef": torch.empty((N, s), dtype=torch.float32).pin_memory(),
+                     "nnz": torch.empty((N,), dtype=torch.int32).pin_memory(),
+                     "rmse": torch.empty(2, dtype=torch.float32).pin_memory()}
+        sets.append(S)
     h2d = Yh.numel() * 4 + D1h.numel() * 4 + D2h.numel() * 4
-    d2h = sum(t.numel() * t.element_size() for t in out_h.values())
-    e2e_ms = []
-    for k in range(args.warmup + args.steps):
-        flush.fill_(float(k))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        Ybuf.view(-1).copy_(Yh.view(-1), non_blocking=True)
-        D1buf.copy_(D1h, non_blocking=True)
-        D2buf.copy_(D2h, non_blocking=True)
-        Yv = Ybuf.transpose(1, 2)
-        D1v, D2v = D1buf.t(), D2buf.t()
-        ctx.iterate(Yv, D1v, D2v, s, out=codes, rmse_out=rmse)
-        out_h["D1"].copy_(D1buf, non_blocking=True)
-        out_h["D2"].copy_(D2buf, non_blocking=True)
-        out_h["support"].copy_(codes.support, non_blocking=True)
-        out_h["coef"].copy_(codes.coef, non_blocking=True)
-        out_h["nnz"].copy_(codes.nnz, non_blocking=True)
-        out_h["rmse"].copy_(rmse, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        if k >= args.warmup:
-            e2e_ms.append(a.elapsed_time(b))
+    d2h = sum(t.numel() * t.element_size() for t in sets[0]["host"].values())
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    s_run = torch.cuda.Stream(device=dev)
+
+    def put(k):
+        S = sets[k % 2]
+        with torch.cuda.stream(s_in):
+            if k >= 2:
+                s_in.wait_event(S["out"])            # the set's previous results have left
+            S["Y"].view(-1).copy_(Yh.view(-1), non_blocking=True)
+            S["D1"].copy_(D1h, non_blocking=True)
+            S["D2"].copy_(D2h, non_blocking=True)
+            S["in"].record(s_in)
+
+    def run(k):
+        S = sets[k % 2]
+        s_run.wait_event(S["in"])
+        with torch.cuda.stream(s_run):
+            flush.fill_(float(k))
+        ctx.iterate(S["Y"].transpose(1, 2), S["D1"].t(), S["D2"].t(), s, out=S["codes"],
+                    rmse_out=S["rmse"], stream=s_run)
+        S["done"].record(s_run)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(S["done"])
+            H = S["host"]
+            H["D1"].copy_(S["D1"], non_blocking=True)
+            H["D2"].copy_(S["D2"], non_blocking=True)
+            H["support"].copy_(S["codes"].support, non_blocking=True)
+            H["coef"].copy_(S["codes"].coef, non_blocking=True)
+            H["nnz"].copy_(S["codes"].nnz, non_blocking=True)
+            H["rmse"].copy_(S["rmse"], non_blocking=True)
+            S["out"].record(s_out)
+
+    def pipeline(n):
+        put(0)
+        for k in range(n):
+            if k + 1 < n:
+                put(k + 1)
+            run(k)
+
+    pipeline(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(s_in)
+    pipeline(args.steps)
+    t1.record(s_out)
+    t1.synchronize()
+    torch.cuda.synchronize()
     ctx.check()
-    e2e_total = sum(e2e_ms)
+    e2e_total = t0.elapsed_time(t1)
     if dist:
         t = torch.tensor([e2e_total], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -419,7 +460,9 @@ def run_ours(args):
                              "sample": f"first {CPU_SAMPLE} of the 200000 patches, one full "
                                        "Algorithm-1 iteration, FP64 numpy, 1 thread"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / args.steps,
+                    "path": "sdl_iterate per step from pinned host buffers; copies double-buffered on "
+                            "two streams, overlapping the neighbouring steps' compute"},
             "clocks": clk,
         }
     ctx.close()

@@ -146,3 +146,37 @@ def test_one_group_batch_runs_its_tiling_kernel_and_matches_oracle(gpu_ctx, grap
         batch.close()
     for x, y in zip(*results):
         assert torch.equal(x, y)
+
+
+def test_one_group_batch_equals_the_per_call_path_at_full_size(gpu_ctx):
+    """The benchmark workload (200 000 12x12 patches, D 12x24, s = 6) through a
+    one-group autotuned, graph-replayed batch gives, bit for bit, the
+    dictionaries and codes of the per-call iteration pinned to the same tiling
+    and CTAs per SM; the per-call path is checked against the oracle at this
+    size in test_gpu_parity.py."""
+    imgs = np.stack([synth.synthetic_image(100 + i) for i in range(8)])
+    Y = synth.random_patches(imgs, 200_000, 12, seed=5)
+    D1, D2 = synth.init_dictionaries(12, 12, 24, 24, seed=1)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    D1b, D2b = D1g.clone(), D2g.clone()
+    batch = sdl.Batch(gpu_ctx, [dict(Y=Yg, D1=D1b, D2=D2b, s=6, eps=0.0)], autotune=True, graph=True)
+    rmse_b = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    batch.iterate(rmse_out=rmse_b)
+    assert gpu_ctx.status() == 0
+    t = batch.tuning()[0]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert t["ctas"] % sms == 0
+    try:
+        gpu_ctx.set_tiling(12, 12, 24, 24, 6, t["shape_id"], t["ctas"] // sms)
+        rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+        out = gpu_ctx.iterate(Yg, D1g, D2g, 6, rmse_out=rmse)
+        assert gpu_ctx.status() == 0
+    finally:
+        gpu_ctx.set_tiling(12, 12, 24, 24, 6, -1)
+    codes = batch.groups[0]["codes"]
+    assert torch.equal(D1g, batch.groups[0]["D1"]) and torch.equal(D2g, batch.groups[0]["D2"])
+    assert torch.equal(out.support, codes.support) and torch.equal(out.coef, codes.coef)
+    # the objective change is an FP64 sum split over a different number of solve
+    # threads: equal up to its last bit
+    assert torch.allclose(rmse, rmse_b, rtol=1e-6, atol=0)
+    batch.close()
