@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kReduceWarps * 32)
 //      enters only to second order, unlike before - tr(Delta P Delta^T),
 //      which holds at the exact minimiser only;
 //   4. norms of the columns of D*, D <- D* diag(1/norm), optional G = D^T D.
-// Every step is a data-parallel sweep with two barriers per pivot.  On any
+// Every step is a data-parallel sweep, one barrier per pivot.  On any
 // failure D is left untouched and the norms are set to 1.
 constexpr int kSolveThreads = 512;
 
@@ -158,9 +158,15 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
                                            float* objective_out, float* rmse_out, int* err,
                                            float* G_out, int keep_p) {
     extern __shared__ __align__(16) float sm[];
+    // keep_p bit 0: a copy of P_u stays in shared memory; bit 1: the inverse
+    // alternates between two buffers (one barrier per pivot), else it is formed
+    // in place from saved copies of the pivot row and column (two barriers)
+    const bool pingpong = (keep_p & 2) != 0;
+    keep_p &= 1;
     const int lda = n | 1;                          // odd row strides: fewer bank conflicts
-    float* A = sm;                                  // nu x nu (stride lda), becomes P_u^{-1}
-    float* Bc = A + n * lda;                        // p x nu right-hand sides (stride lda)
+    float* A = sm;                                  // nu x nu (stride lda): P_u, then its inverse
+    float* A2 = A + n * lda;                        // second buffer, or pivot row | column (2n)
+    float* Bc = A2 + (pingpong ? n * lda : 2 * n);  // p x nu right-hand sides (stride lda)
     float* X = Bc + p * lda;                        // p x nu, D* rows (stride lda)
     float* Dn = X + p * lda;                        // p x n, old then new D (stride lda)
     float* P0 = Dn + p * lda;                       // nu x nu copy of P_u (stride lda), if kept
@@ -171,7 +177,7 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
     __shared__ double s_red[kSolveThreads / 32];
 
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5;
+    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
     const float* P = red_f;
     const float* B = red_f + n * n;
 
@@ -197,76 +203,98 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
     }
     __syncthreads();
     const int nu = s_nu;
-    for (int e = tid; e < nu * nu; e += nth) {
-        const int r = e / nu, c = e - r * nu;
-        const float v = P[idx[r] * n + idx[c]];
-        A[r * lda + c] = v;
-        if (keep_p) P0[r * lda + c] = v;
-        if (!isfinite(v)) s_fail = SDL_ERR_NONFINITE;
-    }
-    for (int e = tid; e < p * nu; e += nth) {
-        const int r = e / nu, c = e - r * nu;
-        const float v = B[r * n + idx[c]];
-        Bc[r * lda + c] = v;
-        if (!isfinite(v)) s_fail = SDL_ERR_NONFINITE;
-    }
-    for (int e = tid; e < p * n; e += nth) {
-        const int r = e % p, c = e / p;
-        Dn[r * lda + c] = D[r + p * c];
-    }
+    // every loop below maps rows to warps and columns to lanes (no index division)
+    int bad = 0;
+    for (int r = warp; r < nu; r += nw)
+        for (int c = lane; c < nu; c += 32) {
+            const float v = P[idx[r] * n + idx[c]];
+            A[r * lda + c] = v;
+            if (keep_p) P0[r * lda + c] = v;
+            if (!isfinite(v)) bad = SDL_ERR_NONFINITE;
+        }
+    for (int r = warp; r < p; r += nw)
+        for (int c = lane; c < nu; c += 32) {
+            const float v = B[r * n + idx[c]];
+            Bc[r * lda + c] = v;
+            if (!isfinite(v)) bad = SDL_ERR_NONFINITE;
+        }
+    for (int c = warp; c < n; c += nw)
+        for (int r = lane; r < p; r += 32) Dn[r * lda + c] = D[r + p * c];
+    if (bad) s_fail = bad;
     __syncthreads();
 
-    // 1. Gauss-Jordan inverse of the used block
-    for (int k = 0; k < nu && s_fail == 0; ++k) {
-        const float piv = A[k * lda + k];
-        if (!(piv > kSolvePivotRel * d0[k])) {
+    // 1. Gauss-Jordan inverse of the used block: each pivot step reads one
+    //    buffer and writes the other (one barrier per pivot); every thread sees
+    //    the same pivot, so a failed pivot test ends the loop everywhere
+    float* Ain = A;
+    if (s_fail == 0) {
+        float* Aout = A2;
+        float* rowk = A2;           // in-place form: saved pivot row and column
+        float* colk = A2 + n;
+        for (int k = 0; k < nu; ++k) {
+            const float piv = Ain[k * lda + k];
+            if (!(piv > kSolvePivotRel * d0[k])) {
+                if (tid == 0) s_fail = SDL_ERR_SINGULAR;
+                break;
+            }
+            const float inv = 1.f / piv;
+            const float* rk = Ain + k * lda;
+            if (!pingpong) {
+                for (int c = tid; c < nu; c += nth) {
+                    rowk[c] = rk[c];
+                    colk[c] = Ain[c * lda + k];
+                }
+                __syncthreads();
+                rk = rowk;
+            }
+            for (int r = warp; r < nu; r += nw) {
+                const float* ar = Ain + r * lda;
+                const float ark = pingpong ? ar[k] : colk[r];
+                const float f = ark * inv;
+                float* out = (pingpong ? Aout : Ain) + r * lda;
+                for (int c = lane; c < nu; c += 32) {
+                    float v;
+                    if (r != k) v = (c != k) ? fmaf(-f, rk[c], ar[c]) : ark * -inv;
+                    else v = (c != k) ? rk[c] * inv : inv;
+                    out[c] = v;
+                }
+            }
             __syncthreads();
-            if (tid == 0) s_fail = SDL_ERR_SINGULAR;
-            __syncthreads();
-            break;
-        }
-        const float inv = 1.f / piv;
-        for (int e = tid; e < nu * nu; e += nth) {
-            const int i = e / nu, j = e - i * nu;
-            if (i != k && j != k) A[i * lda + j] = fmaf(-A[i * lda + k] * inv, A[k * lda + j], A[i * lda + j]);
-        }
-        __syncthreads();
-        for (int e = tid; e < 2 * nu; e += nth) {
-            if (e < nu) {
-                if (e != k) A[k * lda + e] *= inv;          // row k
-            } else {
-                const int i = e - nu;
-                if (i != k) A[i * lda + k] *= -inv;         // column k
+            if (pingpong) {
+                float* t = Ain;
+                Ain = Aout;
+                Aout = t;
             }
         }
-        if (tid == 0) A[k * lda + k] = inv;
-        __syncthreads();
     }
+    __syncthreads();
     const bool ok_inv = (s_fail == 0);
     double part = 0.0;
     if (ok_inv) {
         // 2. D* rows
-        for (int e = tid; e < p * nu; e += nth) {
-            const int a = e / nu, c = e - a * nu;
-            float x = 0.f;
-            for (int k = 0; k < nu; ++k) x = fmaf(Bc[a * lda + k], A[k * lda + c], x);
-            X[a * lda + c] = x;
-        }
+        for (int a = warp; a < p; a += nw)
+            for (int c = lane; c < nu; c += 32) {
+                float x = 0.f;
+#pragma unroll 4
+                for (int k = 0; k < nu; ++k) x = fmaf(Bc[a * lda + k], Ain[k * lda + c], x);
+                X[a * lda + c] = x;
+            }
         __syncthreads();
         // 3. objective change, row a and used atom c at a time, P (used
         //    block) from the kept copy or read back from red_f
-        for (int e = tid; e < p * nu; e += nth) {
-            const int a = e / nu, c = e - a * nu;
-            float w = -2.f * Bc[a * lda + c];
-            if (keep_p) {
-                const float* prow = P0 + c * lda;
-                for (int k = 0; k < nu; ++k) w = fmaf(prow[k], Dn[a * lda + idx[k]] + X[a * lda + k], w);
-            } else {
-                const float* prow = P + (size_t)idx[c] * n;
-                for (int k = 0; k < nu; ++k) w = fmaf(prow[idx[k]], Dn[a * lda + idx[k]] + X[a * lda + k], w);
+        for (int a = warp; a < p; a += nw)
+            for (int c = lane; c < nu; c += 32) {
+                float w = -2.f * Bc[a * lda + c];
+                if (keep_p) {
+                    const float* prow = P0 + c * lda;
+#pragma unroll 4
+                    for (int k = 0; k < nu; ++k) w = fmaf(prow[k], Dn[a * lda + idx[k]] + X[a * lda + k], w);
+                } else {
+                    const float* prow = P + (size_t)idx[c] * n;
+                    for (int k = 0; k < nu; ++k) w = fmaf(prow[idx[k]], Dn[a * lda + idx[k]] + X[a * lda + k], w);
+                }
+                part += (double)(X[a * lda + c] - Dn[a * lda + idx[c]]) * (double)w;
             }
-            part += (double)(X[a * lda + c] - Dn[a * lda + idx[c]]) * (double)w;
-        }
         // 4. column norms of D*
         for (int c = tid; c < nu; c += nth) {
             float ss = 0.f;
@@ -285,20 +313,20 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
     __syncthreads();
     if (ok) {
         for (int c = tid; c < nu; c += nth) norms[idx[c]] = nrm[c];
-        for (int e = tid; e < p * nu; e += nth) {
-            const int a = e / nu, c = e - a * nu;
-            const float v = X[a * lda + c] / nrm[c];
-            Dn[a * lda + idx[c]] = v;
-            D[a + p * idx[c]] = v;
-        }
+        for (int c = warp; c < nu; c += nw)
+            for (int a = lane; a < p; a += 32) {
+                const float v = X[a * lda + c] / nrm[c];
+                Dn[a * lda + idx[c]] = v;
+                D[a + p * idx[c]] = v;
+            }
         __syncthreads();
         if (G_out) {
-            for (int e = tid; e < n * n; e += nth) {
-                const int i = e / n, j = e - i * n;
-                float g = 0.f;
-                for (int a = 0; a < p; ++a) g = fmaf(Dn[a * lda + i], Dn[a * lda + j], g);
-                G_out[e] = g;
-            }
+            for (int i = warp; i < n; i += nw)
+                for (int j = lane; j < n; j += 32) {
+                    float g = 0.f;
+                    for (int a = 0; a < p; ++a) g = fmaf(Dn[a * lda + i], Dn[a * lda + j], g);
+                    G_out[i * n + j] = g;
+                }
         }
     }
     if (tid == 0) {
@@ -512,10 +540,14 @@ __global__ void rescale_multi_kernel(const RescaleDesc* __restrict__ d) {
 
 size_t solve_smem_bytes(int p, int n, int* keep_p) {
     const size_t lda = (size_t)(n | 1);
-    const size_t base = (size_t)n * lda + 3 * (size_t)p * lda + 3 * (size_t)n;
-    const int keep = sizeof(float) * (base + (size_t)n * lda) <= 200 * 1024 ? 1 : 0;
-    if (keep_p) *keep_p = keep;
-    return sizeof(float) * (base + (keep ? (size_t)n * lda : 0));
+    const size_t rest = 3 * (size_t)p * lda + 3 * (size_t)n;
+    const size_t limit = 200 * 1024 / sizeof(float);
+    // prefer the kept copy of P, then the second inverse buffer
+    const int keep = (size_t)n * lda * 2 + 2 * (size_t)n + rest <= limit ? 1 : 0;
+    const size_t base = (size_t)n * lda * (1 + keep) + rest;
+    const int pp = base + (size_t)n * lda <= limit ? 2 : 0;
+    if (keep_p) *keep_p = keep | pp;
+    return sizeof(float) * (base + (pp ? (size_t)n * lda : 2 * (size_t)n));
 }
 
 int launch_multi_update_kernels(int which, const void* d_desc, int G, int blocks, size_t smem,
