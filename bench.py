@@ -184,6 +184,24 @@ def time_oracle(Y, D1, D2, s, reps):
 
 
 # ------------------------------------------------------------------ arms
+def max_over_ranks(value, dist, dev):
+    """The largest of every rank's value (the job's time is its slowest
+    rank's); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, units_per_rank, ms_per_step):
+    """Whole-job throughput of `world` replicas that each process
+    `units_per_rank` units per step, the step taking `ms_per_step` on the
+    slowest rank."""
+    return world * units_per_rank / (ms_per_step / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -278,11 +296,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        total = sum(a.elapsed_time(b) for a, b in ev)
-        if dist:
-            t = torch.tensor([total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, dev)
         return total / args.steps
 
     batch = sdl.Batch(ctx, [dict(Y=Yg, D1=D1g, D2=D2g, s=s, codes=codes)], autotune=True,
@@ -312,8 +326,8 @@ def run_ours(args):
     tuning_log = [dict(shape_id=t["shape_id"], ctas_per_sm=t["ctas_per_sm"], us=round(t["cost_us"], 1))
                   for t in batch.tuning_log()]
     batch.close()
-    value = world * N / (ms_per_step / 1e3)
-    value_plain = world * N / (ms_plain / 1e3)
+    value = replica_throughput(world, N, ms_per_step)
+    value_plain = replica_throughput(world, N, ms_plain)
     final_rmse = rmse_b.cpu().tolist()
 
     # ---- end to end: host inputs in, results out, every step
@@ -401,12 +415,8 @@ def run_ours(args):
     t1.synchronize()
     torch.cuda.synchronize()
     ctx.check()
-    e2e_total = t0.elapsed_time(t1)
-    if dist:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * N / (e2e_total / args.steps / 1e3)
+    e2e_total = max_over_ranks(t0.elapsed_time(t1), dist, dev)
+    e2e_value = replica_throughput(world, N, e2e_total / args.steps)
 
     line = None
     if rank == 0:
