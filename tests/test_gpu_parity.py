@@ -343,3 +343,33 @@ def test_tune_tiling_pins_the_fastest(gpu_ctx):
         gpu_ctx.set_tiling(12, 12, 24, 24, 6, -1)
     with pytest.raises(sdl.SDLError):
         gpu_ctx.set_tiling(12, 12, 24, 24, 6, sdl.tilings(8, 8, 16, 16, 4)[0])
+
+
+@pytest.mark.parametrize("p1,n1,s", [(8, 16, 4), (12, 24, 6)])
+def test_exact_tie_picks_the_smallest_pair_index_in_every_tiling(gpu_ctx, p1, n1, s):
+    """D1 atoms 3 and 5 are the same column, so every pair (3, j) and (5, j)
+    scores exactly the same in FP32 (the same FMA chains): the first pick must
+    be the smaller q = 3 + n1 j (the oracle's rule), in every tiling, and the
+    second copy never joins (its Cholesky pivot is zero)."""
+    D1, D2 = synth.init_dictionaries(p1, p1, n1, n1, seed=1)
+    D1[:, 5] = D1[:, 3]
+    rng = np.random.default_rng(9)
+    N = 300
+    j = rng.integers(0, n1, N)
+    Y = np.einsum("a,kb->kab", D1[:, 3], D2[:, j].T) * rng.uniform(1.0, 2.0, (N, 1, 1))
+    Y += 1e-3 * rng.standard_normal(Y.shape)
+    ref = oracle.omp2d(Y, D1, D2, s)
+    assert np.all(ref.support[:, 0] == 3 + n1 * j)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    try:
+        for t in sdl.tilings(p1, p1, n1, n1, s):
+            gpu_ctx.set_tiling(p1, p1, n1, n1, s, t, 0)
+            out = gpu_ctx.sparse_code(Yg, D1g, D2g, s)
+            assert gpu_ctx.status() == 0
+            sup = out.support.cpu().numpy()
+            assert np.all(sup[:, 0] == 3 + n1 * j), t
+            assert not np.any(sup == (5 + n1 * j)[:, None]), t     # the duplicate never joins
+            rep, exact = compare_supports(sup, out.nnz.cpu().numpy(), ref)
+            assert rep.bad == 0, (t, rep)
+    finally:
+        gpu_ctx.set_tiling(p1, p1, n1, n1, s, -1)
