@@ -312,8 +312,8 @@ int sdl_set_precision(sdl_ctx* ctx, int flags);
 /* ---- Tilings of the specialised coder (Algorithm 1, step "sparse coding").
  * The shapes (p1, p2, n1, n2, s) = (8, 8, 16, 16, 4), (12, 12, 24, 24, 6) and
  * (16, 16, 32, 32, 8) have coders compiled for several tilings: one signal per
- * warp on two lane grids, and two signals per warp (each half-warp codes one
- * signal).  Every tiling of a shape forms each correlation, update and solve
+ * warp on two lane grids, and for the first two shapes also two signals per
+ * warp (each half-warp codes one signal).  Every tiling of a shape forms each correlation, update and solve
  * with the same FMA chains, so the codes (support, coef, nnz) do not depend on
  * the tiling; the TMOD partial sums are added in a tiling-dependent order.
  *
