@@ -257,7 +257,26 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
     // ---- tiling and CTA split
     b->shape.resize(G);
     b->cost_us.resize(G);
-    if (flags & SDL_BATCH_AUTOTUNE) {
+    std::vector<long long> tkey;
+    for (int g = 0; g < G; ++g) {
+        const sdl_group& q = groups[g];
+        for (long long v : {(long long)q.p1, (long long)q.p2, (long long)q.n1, (long long)q.n2,
+                            (long long)q.s_max, (long long)q.N, (long long)(q.eps > 0.f)})
+            tkey.push_back(v);
+    }
+    const sdl_ctx::BatchTune* known = nullptr;
+    if ((flags & SDL_BATCH_AUTOTUNE) && !(flags & SDL_BATCH_RETUNE))
+        for (const auto& t : c->batch_tunes)
+            if (t.key == tkey) known = &t;
+    if (known) {
+        b->shape = known->shape;
+        b->cost_us = known->cost_us;
+        b->single_cps = known->single_cps;
+        b->log_group = known->log_group;
+        b->log_shape = known->log_shape;
+        b->log_cps = known->log_cps;
+        b->log_cost = known->log_cost;
+    } else if (flags & SDL_BATCH_AUTOTUNE) {
         // each candidate is timed in the multi-problem kernel that will run it
         // (its register allocation is not the single-problem kernel's): group g
         // alone, as a one-group launch on num_sms x cps CTAs
@@ -317,6 +336,15 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        sdl_ctx::BatchTune t{tkey, b->shape, b->cost_us, b->single_cps,
+                             b->log_group, b->log_shape, b->log_cps, b->log_cost};
+        bool replaced = false;
+        for (auto& old : c->batch_tunes)
+            if (old.key == tkey) {
+                old = t;
+                replaced = true;
+            }
+        if (!replaced) c->batch_tunes.push_back(std::move(t));
     } else {
         for (int g = 0; g < G; ++g) {
             b->shape[g] = variants[g][0];

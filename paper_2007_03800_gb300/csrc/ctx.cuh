@@ -45,6 +45,17 @@ struct sdl_ctx {
         float us;
     };
     std::vector<TuneRec> tune_log;
+    // batch autotuning results, remembered per group signature (shapes, sizes,
+    // stopping rule) so that a batch of the same groups is not re-timed
+    struct BatchTune {
+        std::vector<long long> key;
+        std::vector<int> shape;
+        std::vector<float> cost_us;
+        int single_cps;
+        std::vector<int> log_group, log_shape, log_cps;
+        std::vector<float> log_cost;
+    };
+    std::vector<BatchTune> batch_tunes;
     // tracing: launch counters and (optionally) one event pair per launch
     struct Rec {
         int kind;

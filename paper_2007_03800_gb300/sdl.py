@@ -424,6 +424,7 @@ class _Group(ctypes.Structure):
 
 BATCH_AUTOTUNE = 1
 BATCH_GRAPH = 2
+BATCH_RETUNE = 4
 
 
 class Batch:
@@ -435,7 +436,7 @@ class Batch:
     """
 
     def __init__(self, ctx: Context, groups, autotune: bool = True, graph: bool = True,
-                 stream=None):
+                 stream=None, retune: bool = False):
         self.ctx = ctx
         self._lib = ctx._lib
         self.groups = []
@@ -451,7 +452,8 @@ class Batch:
                             float(spec.get("eps", 0.0)), codes.support.data_ptr(),
                             codes.coef.data_ptr(), codes.nnz.data_ptr(),
                             codes.res_energy.data_ptr() if codes.res_energy is not None else None)
-        flags = (BATCH_AUTOTUNE if autotune else 0) | (BATCH_GRAPH if graph else 0)
+        flags = ((BATCH_AUTOTUNE if autotune else 0) | (BATCH_GRAPH if graph else 0) |
+                 (BATCH_RETUNE if retune else 0))
         h = ctypes.c_void_p()
         _check(self._lib.sdl_batch_create(ctx._h, arr, len(groups), flags, _stream(stream),
                                           ctypes.byref(h)), "sdl_batch_create")

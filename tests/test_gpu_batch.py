@@ -60,6 +60,13 @@ def test_batch_sparse_code_matches_oracle_and_single_calls(gpu_ctx):
         assert torch.equal(single.coef, codes.coef)
     tun = batch.tuning()
     assert len(tun) == 3 and all(t["ctas"] >= 1 and t["cost_us"] > 0 for t in tun)
+    # a batch of the same groups reuses the context's result unless asked to re-time
+    again = sdl.Batch(gpu_ctx, to_specs(groups), autotune=True, graph=False)
+    assert again.tuning() == tun and again.tuning_log() == batch.tuning_log()
+    again.close()
+    fresh = sdl.Batch(gpu_ctx, to_specs(groups), autotune=True, graph=False, retune=True)
+    assert [t["shape_id"] for t in fresh.tuning()] and len(fresh.tuning_log()) == len(batch.tuning_log())
+    fresh.close()
     # the autotuner's log holds every timing it took; the chosen tiling is the fastest
     log = batch.tuning_log()
     for g, t in enumerate(tun):
