@@ -821,8 +821,10 @@ def study_denoise(args):
     """Denoising with one batch of three patch sizes (8, 12, 16; D p x 2p;
     error-driven stop at 1.15 sigma p, s <= p/2) on a 512x512 synthetic image
     with sigma = 20 noise, 10 iterations: PSNRs and device time of the whole
-    pipeline (patch extraction, batch set-up with autotuning and graph capture,
-    learning, coding, averaging) and of each of those phases."""
+    pipeline (patch extraction, batch set-up, learning, coding, averaging) and
+    of each of those phases.  The timed pipelines run in a context that has
+    already tuned the batch (set-up = graph capture); the first pipeline's
+    set-up, with the autotuning, is reported on its own."""
     import torch
 
     from paper_2007_03800_gb300 import denoise as dn
@@ -834,7 +836,9 @@ def study_denoise(args):
     cg = torch.tensor(clean, dtype=torch.float32, device=dev)
     ng = torch.tensor(noisy, dtype=torch.float32, device=dev)
     ctx = sdl.Context(0)
-    for _ in range(args.warmup):
+    # the first pipeline of a context tunes the batch; later ones reuse it
+    cold = dn.denoise(ctx, ng, sigma, iterations=1, clean=cg, timing=True)
+    for _ in range(args.warmup - 1):
         dn.denoise(ctx, ng, sigma, iterations=1, clean=cg)
     ms, phases = [], []
     r = None
@@ -853,6 +857,7 @@ def study_denoise(args):
            "ms_pipeline": statistics.median(ms), "patches": n_patches,
            "patch_iterations_per_s": 10 * n_patches / (statistics.median(ms) / 1e3),
            "ms_phases": {k: statistics.median(p[k] for p in phases) for k in phases[0]},
+           "ms_setup_first_pipeline": cold["ms_phases"]["setup"],
            "ms_per_learning_iteration": statistics.median(p["iterations"] for p in phases) / 10,
            "tuning": r["tuning"],
            "tuning_log": [dict(group=t["group"], shape_id=t["shape_id"], ctas_per_sm=t["ctas_per_sm"],

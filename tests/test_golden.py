@@ -1,0 +1,206 @@
+"""Hand-worked examples (tests/golden/*.json): tiny problems whose codes,
+dictionaries and energies follow from the definitions by hand, each fixture
+citing the passage it works through and giving its derivation.  Numbers may
+be written as closed forms ("sqrt(2)", "1/sqrt(5)").
+
+The CPU tests pin the FP64 oracle to them; the GPU tests run the same
+examples through the C ABI (FP32, so within a few ulps).
+"""
+import glob
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import denoise as odn
+from oracle import ortho, tmod3
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+_NS = {"__builtins__": {}, "sqrt": math.sqrt, "log10": math.log10}
+
+
+def num(v):
+    """A fixture number: a JSON number or a closed-form string."""
+    if isinstance(v, str):
+        return float(eval(v, _NS))   # fixture text only: sqrt, log10, arithmetic
+    if isinstance(v, list):
+        return [num(x) for x in v]
+    return v
+
+
+def arr(v, dtype=np.float64):
+    return np.asarray(num(v), dtype=dtype)
+
+
+def load(name):
+    with open(os.path.join(HERE, name)) as f:
+        return json.load(f)
+
+
+def test_every_fixture_cites_and_derives():
+    files = sorted(glob.glob(os.path.join(HERE, "*.json")))
+    assert len(files) >= 8
+    for f in files:
+        d = json.load(open(f))
+        assert d["citation"] and d["derivation"], f
+
+
+OMP_FIXTURES = ["omp2d_identity_2x2.json", "omp2d_coherent_atoms.json", "omp2d_tie_2x2.json"]
+
+
+def omp_cases():
+    for name in OMP_FIXTURES:
+        for i, c in enumerate(load(name)["cases"]):
+            yield pytest.param(name, c, id=f"{name[:-5]}-{i}")
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+@pytest.mark.parametrize("name,case", list(omp_cases()))
+def test_oracle_omp2d_golden(name, case):
+    d = load(name)
+    Y, D1, D2 = arr(d["Y"]), arr(d["D1"]), arr(d["D2"])
+    r = oracle.omp2d(Y, D1, D2, case["s"], eps=case["eps"])
+    assert np.array_equal(r.support, np.asarray(case["support"]))
+    assert np.array_equal(r.nnz, np.asarray(case["nnz"]))
+    np.testing.assert_allclose(r.coef, arr(case["coef"]), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(r.res_energy, arr(case["res_energy"]), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,fn", [("tmod_update_D1_2x2.json", oracle.update_D1),
+                                     ("tmod_update_D2_2x2.json", oracle.update_D2)])
+def test_oracle_tmod_update_golden(name, fn):
+    d = load(name)
+    e = d["expected"]
+    r = fn(arr(d["Y"]), arr(d["D1"]), arr(d["D2"]), np.asarray(d["support"]), arr(d["coef"]))
+    for key in ("P", "B", "Dstar", "D", "norms", "coef"):
+        np.testing.assert_allclose(getattr(r, key), arr(e[key]), rtol=1e-12, atol=1e-12, err_msg=key)
+    assert r.obj_before == pytest.approx(e["obj_before"], abs=1e-12)
+    assert r.obj_after == pytest.approx(e["obj_after"], abs=1e-12)
+
+
+def test_oracle_threshold_and_procrustes_golden():
+    d = load("ortho_threshold_procrustes_2x2.json")
+    t = d["threshold"]
+    sup, coef, res = ortho.threshold_code(arr(t["Y"]), arr(t["D1"]), arr(t["D2"]), t["s"])
+    assert np.array_equal(sup, np.asarray(t["support"]))
+    np.testing.assert_allclose(coef, arr(t["coef"]), atol=1e-12)
+    np.testing.assert_allclose(res, arr(t["res_energy"]), atol=1e-12)
+    for key, fn in (("procrustes_D1", ortho.procrustes_D1), ("procrustes_D2", ortho.procrustes_D2)):
+        c = d[key]
+        r = fn(arr(c["Y"]), arr(c["D1"]), arr(c["D2"]), np.asarray(c["support"]), arr(c["coef"]))
+        np.testing.assert_allclose(r.B, arr(c["B"]), atol=1e-12, err_msg=key)
+        np.testing.assert_allclose(r.D, arr(c["D"]), atol=1e-12, err_msg=key)
+        np.testing.assert_allclose(r.sigma, arr(c["sigma"]), atol=1e-12, err_msg=key)
+
+
+def test_oracle_omp3d_golden():
+    d = load("omp3d_identity_2x2x2.json")
+    r = tmod3.omp3d(arr(d["Y"]), arr(d["D1"]), arr(d["D2"]), arr(d["D3"]), d["s"])
+    assert np.array_equal(r.support, np.asarray(d["support"]))
+    assert np.array_equal(r.nnz, np.asarray(d["nnz"]))
+    np.testing.assert_allclose(r.coef, arr(d["coef"]), atol=1e-12)
+    np.testing.assert_allclose(r.res_energy, arr(d["res_energy"]), atol=1e-12)
+
+
+def test_oracle_denoise_golden():
+    d = load("denoise_mean_only_3x3.json")
+    img, p = arr(d["image"]), d["p"]
+    Yc, means = odn.extract_patches(img, p)
+    np.testing.assert_allclose(means, arr(d["means"]), atol=1e-12)
+    for k in range(len(means)):
+        np.testing.assert_allclose(Yc[k], arr(d["centred"]), atol=1e-12)
+    rebuilt = odn.patch_average(np.broadcast_to(means[:, None, None], Yc.shape), *img.shape)
+    np.testing.assert_allclose(rebuilt, arr(d["mean_only_average"]), atol=1e-12)
+    assert odn.psnr(rebuilt, img) == pytest.approx(num(d["psnr_mean_only"]), abs=1e-10)
+
+
+# ------------------------------------------------------------- CUDA path (GPU)
+FP32_TOL = 2e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,case", list(omp_cases()))
+def test_gpu_omp2d_golden(gpu_ctx, name, case):
+    from parity import to_gpu_problem
+    d = load(name)
+    Yg, D1g, D2g = to_gpu_problem(arr(d["Y"]), arr(d["D1"]), arr(d["D2"]))
+    out = gpu_ctx.sparse_code(Yg, D1g, D2g, case["s"], eps=case["eps"] or 0.0)
+    assert gpu_ctx.status() == 0
+    assert np.array_equal(out.support.cpu().numpy(), np.asarray(case["support"]))
+    assert np.array_equal(out.nnz.cpu().numpy(), np.asarray(case["nnz"]))
+    ynorm = float(np.sum(arr(d["Y"]) ** 2))
+    np.testing.assert_allclose(out.coef.cpu().numpy(), arr(case["coef"]), rtol=FP32_TOL, atol=FP32_TOL)
+    np.testing.assert_allclose(out.res_energy.cpu().numpy(), arr(case["res_energy"]),
+                               atol=FP32_TOL * ynorm)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,side", [("tmod_update_D1_2x2.json", 1), ("tmod_update_D2_2x2.json", 2)])
+def test_gpu_tmod_update_golden(gpu_ctx, name, side):
+    import torch
+    from parity import codes_from_oracle, to_gpu_problem
+    d = load(name)
+    e = d["expected"]
+    Yg, D1g, D2g = to_gpu_problem(arr(d["Y"]), arr(d["D1"]), arr(d["D2"]))
+    codes = codes_from_oracle(np.asarray(d["support"]), arr(d["coef"]))
+    obj = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    (gpu_ctx.update_D1 if side == 1 else gpu_ctx.update_D2)(Yg, D1g, D2g, codes, objective_out=obj)
+    assert gpu_ctx.status() == 0
+    D = (D1g if side == 1 else D2g).cpu().numpy()
+    np.testing.assert_allclose(D, arr(e["D"]), rtol=FP32_TOL, atol=FP32_TOL)
+    np.testing.assert_allclose(codes.coef.cpu().numpy(), arr(e["coef"]), rtol=FP32_TOL)
+    o = obj.cpu().numpy()
+    assert o[0] == pytest.approx(e["obj_before"], rel=FP32_TOL)
+    assert abs(o[1] - e["obj_after"]) <= FP32_TOL * e["obj_before"]
+
+
+@pytest.mark.gpu
+def test_gpu_threshold_golden(gpu_ctx):
+    from parity import to_gpu_problem
+    t = load("ortho_threshold_procrustes_2x2.json")["threshold"]
+    Yg, D1g, D2g = to_gpu_problem(arr(t["Y"]), arr(t["D1"]), arr(t["D2"]))
+    out = gpu_ctx.ortho_sparse_code(Yg, D1g, D2g, t["s"])
+    assert gpu_ctx.status() == 0
+    assert np.array_equal(out.support.cpu().numpy(), np.asarray(t["support"]))
+    np.testing.assert_allclose(out.coef.cpu().numpy(), arr(t["coef"]), atol=FP32_TOL)
+    np.testing.assert_allclose(out.res_energy.cpu().numpy(), arr(t["res_energy"]), atol=FP32_TOL * 26)
+
+
+@pytest.mark.gpu
+def test_gpu_omp3d_golden(gpu_ctx):
+    import torch
+    from paper_2007_03800_gb300 import sdl
+    d = load("omp3d_identity_2x2x2.json")
+    Yg = sdl.signals3(torch.tensor(arr(d["Y"]), dtype=torch.float32, device="cuda:0"))
+    Dg = [sdl.dictionary(torch.tensor(arr(d[k]), dtype=torch.float32, device="cuda:0"))
+          for k in ("D1", "D2", "D3")]
+    out = gpu_ctx.sparse_code3(Yg, *Dg, d["s"])
+    assert gpu_ctx.status() == 0
+    assert np.array_equal(out.support.cpu().numpy(), np.asarray(d["support"]))
+    assert np.array_equal(out.nnz.cpu().numpy(), np.asarray(d["nnz"]))
+    np.testing.assert_allclose(out.coef.cpu().numpy(), arr(d["coef"]), atol=FP32_TOL * 5)
+    np.testing.assert_allclose(out.res_energy.cpu().numpy(), arr(d["res_energy"]), atol=FP32_TOL * 36)
+
+
+@pytest.mark.gpu
+def test_gpu_denoise_golden(gpu_ctx):
+    import torch
+    from paper_2007_03800_gb300 import sdl
+    d = load("denoise_mean_only_3x3.json")
+    img = torch.tensor(arr(d["image"]), dtype=torch.float32, device="cuda:0")
+    p = d["p"]
+    patches, means = sdl.extract_patches(img, p)
+    np.testing.assert_allclose(means.cpu().numpy(), arr(d["means"]), atol=1e-6)
+    for k in range(len(means)):
+        np.testing.assert_allclose(patches[k].cpu().numpy(), arr(d["centred"]), atol=1e-6)
+    n = len(means)
+    codes = sdl.Codes(torch.full((n, 1), -1, dtype=torch.int32, device="cuda:0"),
+                      torch.zeros((n, 1), dtype=torch.float32, device="cuda:0"),
+                      torch.zeros((n,), dtype=torch.int32, device="cuda:0"))
+    eye = sdl.dictionary(torch.eye(p, dtype=torch.float32, device="cuda:0"))
+    rebuilt = sdl.patch_average(gpu_ctx, codes, means, eye, eye, p, *img.shape)
+    np.testing.assert_allclose(rebuilt.cpu().numpy(), arr(d["mean_only_average"]), atol=1e-6)
+    assert sdl.psnr(rebuilt, img).item() == pytest.approx(num(d["psnr_mean_only"]), abs=1e-4)
