@@ -388,6 +388,28 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
         const bool finite = isfinite(ss);
+        if (finite && a.eps2 > 0.f && ss <= a.eps2) {
+            // already within the error target: an empty code, no correlations
+            const long long ko = (a.idx && a.idx_compact) ? j : k;
+            if (a.support && lane < S) {
+                a.support[(size_t)ko * S + lane] = -1;
+                a.coef[(size_t)ko * S + lane] = 0.f;
+            }
+            if (lane == 0) {
+                if (a.nnz) a.nnz[ko] = 0;
+                if (a.res_energy) a.res_energy[ko] = ss;
+                const float ye = ss - w_energy_c;
+                const float te = w_energy + ye;
+                w_energy_c = (te - w_energy) - ye;
+                w_energy = te;
+                const float yy = ss - w_ynorm_c;
+                const float ty = w_ynorm + yy;
+                w_ynorm_c = (ty - w_ynorm) - yy;
+                w_ynorm = ty;
+            }
+            __syncwarp();
+            continue;
+        }
 
         int cnt = 0;
         float E2 = ss;
@@ -840,9 +862,11 @@ __device__ __forceinline__ void code_half_body(const PassArgs& a, int cta, int n
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
         const bool finite = act && isfinite(ss);
+        // a signal already within the error target takes no atom: skip its correlations
+        const bool work = finite && !(a.eps2 > 0.f && ss <= a.eps2);
 
         // ---- first contraction: Z = Y D2 or W = D1^T Y (packed FMAs along row pairs)
-        if (finite) {
+        if (work) {
             if constexpr (!kW) {
                 const int za = hl % Sh::ZLA, zb = hl / Sh::ZLA;
                 const int a0 = za * Sh::ZA, jz = zb * Sh::ZB;
@@ -905,7 +929,7 @@ __device__ __forceinline__ void code_half_body(const PassArgs& a, int cta, int n
         for (int m = 0; m < S; ++m) {
             si[m] = 0; sj[m] = 0; xs[m] = 0.f;
         }
-        if (__any_sync(kFull, finite)) {
+        if (__any_sync(kFull, work)) {
             // ---- C0 on the lane's RI x RJ block (flat index e = c*RI + r)
             float c0[E];
 #pragma unroll
@@ -934,7 +958,7 @@ __device__ __forceinline__ void code_half_body(const PassArgs& a, int cta, int n
 
             // ---- greedy steps: every lane of a half computes the whole Cholesky
             // update of its signal (identical values), lane 0 stores it
-            bool go = finite;
+            bool go = work;
             const int qbase = li * RI + N1 * (lj * RJ);
             static_for<0, S>([&](auto tc) {
                 constexpr int t = decltype(tc)::value;

@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
 
         int cnt = 0;
         float E = ss;
-        if (finite) {
+        // a signal already within the error target takes no atom: skip its correlations
+        if (finite && !(a.eps2 > 0.f && ss <= a.eps2)) {
             float c0[RI][RJ];
             unsigned exact = 0xffffffffu;      // bit r*RJ+c: c0 entry is an FP32 value
             const float bound = a.c0ext ? a.c0_err_rel * sqrtf(ss) : 0.f;

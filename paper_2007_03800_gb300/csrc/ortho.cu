@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kOrthoWarps * 32)
         float E2 = ss;
         int my_q = -1;
         float my_x = 0.f;
-        if (finite) {
+        // a signal already within the error target keeps no entry: skip its correlations
+        if (finite && !(eps2 > 0.f && ss <= eps2)) {
             // ---- Z = Y D2 (p1 x n2), C = D1^T Z (entry q = i + n1 j)
             for (int e = lane; e < p1 * n2; e += 32) {
                 const int a = e / n2, j = e - a * n2;
@@ -298,7 +299,8 @@ __global__ void __launch_bounds__(kOrthoWarps * 32)
         float E2 = ss;
         int my_q = -1;
         float my_x = 0.f;
-        if (finite) {
+        // a signal already within the error target keeps no entry: skip its correlations
+        if (finite && !(eps2 > 0.f && ss <= eps2)) {
             // Z block: rows i0.., cols j0.. of Y D2
             float z[R][R];
 #pragma unroll
