@@ -264,7 +264,12 @@ struct FastLayout {
     static constexpr int TZ = Sh::P1 * Sh::LD2, TW = Sh::P2 * Sh::LD1;
     static constexpr int w_z = w_y + 2 * al4(Sh::PP);
     static constexpr int w_c0 = w_z + al4(TZ > TW ? TZ : TW);
-    static constexpr int w_stride = w_c0 + 32 * EP;
+    // with s >= 8 the Cholesky state (rows of L, 1/L_tt, y) sits in shared
+    // memory rather than in every lane's registers
+    static constexpr bool kSmemChol = Sh::S >= 8;
+    static constexpr int w_chol = w_c0 + 32 * EP;
+    static constexpr int n_chol = kSmemChol ? al4(Sh::S * (Sh::S + 1) / 2) + 2 * al4(Sh::S) : 0;
+    static constexpr int w_stride = w_chol + n_chol;
     __host__ __device__ static constexpr int total(int side, int wpc) { return warp0(side) + wpc * w_stride; }
 };
 
@@ -498,17 +503,28 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
             }
             __syncwarp();
 
-            // ---- greedy steps, fully unrolled.  Every lane keeps the whole
-            // Cholesky factor (packed rows of L and 1/L_tt), so both triangular
-            // solves run without shuffles.
+            // ---- greedy steps, fully unrolled.  Every lane computes the whole
+            // Cholesky update (packed rows of L and 1/L_tt), so both triangular
+            // solves run without shuffles; the factor stays in registers, or
+            // (s >= 8) in shared memory, written by lane 0, so that it holds no
+            // registers while the scores are live.
+            constexpr bool kSC = L::kSmemChol;
+            constexpr int kR = kSC ? 1 : S, kRL = kSC ? 1 : S * (S + 1) / 2;
+            float* Lsm = wb + L::w_chol;
+            float* ivsm = Lsm + al4(S * (S + 1) / 2);
+            float* yvsm = ivsm + al4(S);
             int si[S], sj[S];
-            float xs[S], yv[S], Lf[S * (S + 1) / 2], invd[S];
+            float xs[S], yv[kR], Lf[kRL], invd[kR];
 #pragma unroll
             for (int m = 0; m < S; ++m) {
-                si[m] = 0; sj[m] = 0; xs[m] = 0.f; yv[m] = 0.f; invd[m] = 0.f;
+                si[m] = 0; sj[m] = 0; xs[m] = 0.f;
             }
 #pragma unroll
-            for (int m = 0; m < S * (S + 1) / 2; ++m) Lf[m] = 0.f;
+            for (int m = 0; m < kR; ++m) {
+                yv[m] = 0.f; invd[m] = 0.f;
+            }
+#pragma unroll
+            for (int m = 0; m < kRL; ++m) Lf[m] = 0.f;
             bool go = true;
             const int qbase = li * RI + N1 * (lj * RJ);
             static_for<0, S>([&](auto tc) {
@@ -564,35 +580,89 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
                 const float* g2t = G2s + jt * LD2;
                 const float Att = g1t[pos1<Sh>(it_)] * g2t[pos2<Sh>(jt)];
                 float ww = 0.f, wy = 0.f;
+                float yt;
+                if constexpr (kSC) {
+                    // the state of steps 0..t-1 from shared memory; the same
+                    // recurrences and FMA order as the register form below
+                    constexpr int kOld = t * (t + 1) / 2;
+                    float Lo[kOld > 0 ? kOld : 1], io[t > 0 ? t : 1], yo[t > 0 ? t : 1];
 #pragma unroll
-                for (int m = 0; m < t; ++m) {
-                    float am = g1t[pos1<Sh>(si[m])] * g2t[pos2<Sh>(sj[m])];
+                    for (int m = 0; m < kOld; ++m) Lo[m] = Lsm[m];
 #pragma unroll
-                    for (int l = 0; l < m; ++l) am = fmaf(-Lf[m * (m + 1) / 2 + l], Lf[t * (t + 1) / 2 + l], am);
-                    const float wm = am * invd[m];
-                    Lf[t * (t + 1) / 2 + m] = wm;
-                    ww = fmaf(wm, wm, ww);
-                    wy = fmaf(wm, yv[m], wy);
-                }
-                const float d = Att - ww;
-                if (!(d > kPivotRel * Att)) { go = false; return; }
-                const float inv = rsqrtf(d);
-                const float yt = (b - wy) * inv;
-                yv[t] = yt;
-                si[t] = it_;
-                sj[t] = jt;
-                invd[t] = inv;
-                if (lane == t) {
-                    myi = it_;
-                    myj = jt;
-                }
-                // ---- x = L^{-T} y (rows t..0)
+                    for (int m = 0; m < t; ++m) {
+                        io[m] = ivsm[m];
+                        yo[m] = yvsm[m];
+                    }
+                    float wr[t > 0 ? t : 1];   // row t of L
 #pragma unroll
-                for (int kk = t; kk >= 0; --kk) {
-                    float v = yv[kk];
+                    for (int m = 0; m < t; ++m) {
+                        float am = g1t[pos1<Sh>(si[m])] * g2t[pos2<Sh>(sj[m])];
 #pragma unroll
-                    for (int l = kk + 1; l <= t; ++l) v = fmaf(-Lf[l * (l + 1) / 2 + kk], xs[l], v);
-                    xs[kk] = v * invd[kk];
+                        for (int l = 0; l < m; ++l) am = fmaf(-Lo[m * (m + 1) / 2 + l], wr[l], am);
+                        wr[m] = am * io[m];
+                        ww = fmaf(wr[m], wr[m], ww);
+                        wy = fmaf(wr[m], yo[m], wy);
+                    }
+                    const float d = Att - ww;
+                    if (!(d > kPivotRel * Att)) { go = false; return; }
+                    const float inv = rsqrtf(d);
+                    yt = (b - wy) * inv;
+                    si[t] = it_;
+                    sj[t] = jt;
+                    if (lane == t) {
+                        myi = it_;
+                        myj = jt;
+                    }
+                    // ---- x = L^{-T} y (rows t..0)
+                    float xn[t + 1];
+                    xn[t] = yt * inv;
+#pragma unroll
+                    for (int kk = t - 1; kk >= 0; --kk) {
+                        float v = yo[kk];
+#pragma unroll
+                        for (int l = kk + 1; l < t; ++l) v = fmaf(-Lo[l * (l + 1) / 2 + kk], xn[l], v);
+                        v = fmaf(-wr[kk], xn[t], v);
+                        xn[kk] = v * io[kk];
+                    }
+#pragma unroll
+                    for (int kk = 0; kk <= t; ++kk) xs[kk] = xn[kk];
+                    if (lane == 0) {
+#pragma unroll
+                        for (int m = 0; m < t; ++m) Lsm[kOld + m] = wr[m];
+                        ivsm[t] = inv;
+                        yvsm[t] = yt;
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < t; ++m) {
+                        float am = g1t[pos1<Sh>(si[m])] * g2t[pos2<Sh>(sj[m])];
+#pragma unroll
+                        for (int l = 0; l < m; ++l) am = fmaf(-Lf[m * (m + 1) / 2 + l], Lf[t * (t + 1) / 2 + l], am);
+                        const float wm = am * invd[m];
+                        Lf[t * (t + 1) / 2 + m] = wm;
+                        ww = fmaf(wm, wm, ww);
+                        wy = fmaf(wm, yv[m], wy);
+                    }
+                    const float d = Att - ww;
+                    if (!(d > kPivotRel * Att)) { go = false; return; }
+                    const float inv = rsqrtf(d);
+                    yt = (b - wy) * inv;
+                    yv[t] = yt;
+                    si[t] = it_;
+                    sj[t] = jt;
+                    invd[t] = inv;
+                    if (lane == t) {
+                        myi = it_;
+                        myj = jt;
+                    }
+                    // ---- x = L^{-T} y (rows t..0)
+#pragma unroll
+                    for (int kk = t; kk >= 0; --kk) {
+                        float v = yv[kk];
+#pragma unroll
+                        for (int l = kk + 1; l <= t; ++l) v = fmaf(-Lf[l * (l + 1) / 2 + kk], xs[l], v);
+                        xs[kk] = v * invd[kk];
+                    }
                 }
                 E2 = fmaf(-yt, yt, E2);
                 cnt = t + 1;

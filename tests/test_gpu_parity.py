@@ -279,16 +279,23 @@ def test_every_tiling_gives_identical_codes_and_matches_oracle(gpu_ctx, p1, n1, 
     """Pin each compiled tiling in turn (one and two signals per warp, both lane
     grids, 1 or 2 CTAs per SM): the codes are bit-identical across tilings,
     with and without the error-driven stop, and one Algorithm-1 iteration
-    matches the oracle with each."""
+    matches the oracle with each, with and without the stop.  About 40 % of
+    the signals are halved, so that with the stop they start within the error
+    target and take no atom: neighbours (the two halves of a warp) then mix
+    signals that skip their correlations with signals that code."""
     tilings = sdl.tilings(p1, p1, n1, n1, s)
     assert len(tilings) >= 2
     rng = np.random.default_rng(77 + p1)
     Y = rng.standard_normal((N, p1, p1))
+    Y[rng.random(N) < 0.4] *= 0.5           # ||Y|| about 0.5 p: below eps
     D1, D2 = synth.init_dictionaries(p1, p1, n1, n1, seed=1)
-    eps = 0.8 * np.sqrt(p1 * p1)            # some signals stop before s picks
+    eps = 0.8 * np.sqrt(p1 * p1)            # the others stop before or at s picks
     ref = oracle.omp2d(Y, D1, D2, s)
     ref_eps = oracle.omp2d(Y, D1, D2, s, eps=eps)
+    skipped = ref_eps.nnz == 0
+    assert 0.3 * N < skipped.sum() < 0.5 * N
     it_ref = oracle.iterate(Y, D1, D2, s)
+    it_ref_eps = oracle.iterate(Y, D1, D2, s, eps=eps)
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
     first = first_eps = None
     try:
@@ -311,15 +318,16 @@ def test_every_tiling_gives_identical_codes_and_matches_oracle(gpu_ctx, p1, n1, 
                                                   eps=(e or None))
                     assert rep.bad == 0 and rep.ties <= max(2, 2e-3 * rep.n), (t, rep)
                     assert coef_rel_error(got[1].numpy(), r.coef, exact).max(initial=0) < COEF_RTOL
-            D1i, D2i = D1g.clone(), D2g.clone()
-            rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
-            gpu_ctx.iterate(Yg, D1i, D2i, s, rmse_out=rmse)
-            assert gpu_ctx.status() == 0
-            rm = rmse.cpu().numpy()
-            assert abs(rm[0] - it_ref.rmse_after_D1) / it_ref.rmse_after_D1 < RMSE_RTOL, (t, rm)
-            assert abs(rm[1] - it_ref.rmse_after_D2) / it_ref.rmse_after_D2 < RMSE_RTOL, (t, rm)
-            assert np.abs(D1i.cpu().numpy() - it_ref.D1).max() < DICT_RTOL, t
-            assert np.abs(D2i.cpu().numpy() - it_ref.D2).max() < DICT_RTOL, t
+            for e, r in ((0.0, it_ref), (eps, it_ref_eps)):
+                D1i, D2i = D1g.clone(), D2g.clone()
+                rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+                gpu_ctx.iterate(Yg, D1i, D2i, s, eps=e, rmse_out=rmse)
+                assert gpu_ctx.status() == 0
+                rm = rmse.cpu().numpy()
+                assert abs(rm[0] - r.rmse_after_D1) / r.rmse_after_D1 < RMSE_RTOL, (t, e, rm)
+                assert abs(rm[1] - r.rmse_after_D2) / r.rmse_after_D2 < RMSE_RTOL, (t, e, rm)
+                assert np.abs(D1i.cpu().numpy() - r.D1).max() < DICT_RTOL, (t, e)
+                assert np.abs(D2i.cpu().numpy() - r.D2).max() < DICT_RTOL, (t, e)
     finally:
         gpu_ctx.set_tiling(p1, p1, n1, n1, s, -1)
 
