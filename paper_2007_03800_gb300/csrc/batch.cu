@@ -111,7 +111,7 @@ bool valid_group(const sdl_group& g, int* shape_ids, int* n_ids) {
     const int n = fast_shape_variants(g.p1, g.p2, g.n1, g.n2, g.s_max, all, 16);
     *n_ids = 0;
     for (int v = 0; v < n && *n_ids < 8; ++v)
-        if (fast_variant_warps(all[v]) == kMultiWarps) shape_ids[(*n_ids)++] = all[v];
+        if (fast_variant_warps(all[v]) <= kMultiWarps) shape_ids[(*n_ids)++] = all[v];
     return *n_ids > 0;
 }
 

@@ -285,8 +285,11 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
     constexpr unsigned kBytes = PP * 4;
     extern __shared__ __align__(16) float smem[];
 
-    const int wpc = blockDim.x >> 5;
+    // the shape's warps code signals; a CTA of the multi-problem kernel may
+    // have more (warps w >= WPC only join the CTA-wide set-up and combine)
+    constexpr int wpc = Sh::WPC;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool wact = w < wpc;
     const int li = lane % LI, lj = lane / LI;
     constexpr bool kW = (SIDE == kSideD2);   // C0 = (D1^T Y) D2 rather than D1^T (Y D2)
     float* D1r = smem + L::d1r;
@@ -346,9 +349,9 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
     const long long stride = (long long)n_ctas * wpc;
     // positions j index either the signals themselves or a list of signals
     const long long count = a.idx ? (long long)*a.idx_count : a.N;
-    long long j = (long long)cta * wpc + w;
+    long long j = wact ? (long long)cta * wpc + w : count;
     long long k = (a.idx && j < count) ? (long long)a.idx[j] : j;
-    if (lane == 0) {
+    if (wact && lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
@@ -752,22 +755,21 @@ __device__ __forceinline__ void code_fast_body(const PassArgs& a, int cta, int n
     }
 
     if constexpr (SIDE != kCodeOnly) {
-        if (lane == 0) {
+        if (wact && lane == 0) {
             acce[2 * w] = w_energy - w_energy_c;
             acce[2 * w + 1] = w_ynorm - w_ynorm_c;
         }
         __syncthreads();
         // combine the warps' accumulators in warp order
-        const int wpc_all = blockDim.x >> 5;
         float* dst = a.part_f + (size_t)slot * nf;
         for (int e = threadIdx.x; e < nf; e += blockDim.x) {
             float v = 0.f;
-            for (int ww = 0; ww < wpc_all; ++ww) v += acc[ww * nfa + e];
+            for (int ww = 0; ww < wpc; ++ww) v += acc[ww * nfa + e];
             dst[e] = v;
         }
         if (threadIdx.x < 2) {
             double d = 0.0;
-            for (int ww = 0; ww < wpc_all; ++ww) d += (double)acce[2 * ww + threadIdx.x];
+            for (int ww = 0; ww < wpc; ++ww) d += (double)acce[2 * ww + threadIdx.x];
             a.part_d[(size_t)slot * 2 + threadIdx.x] = d;
         }
     }
@@ -1310,8 +1312,10 @@ using F8x16s4 = Shape<8, 8, 16, 16, 4, 4, 4, 2, 2, 2, 2, 2, 8, 3>;
 using F8x16s4b = Shape<8, 8, 16, 16, 4, 8, 2, 4, 2, 2, 2, 2, 8, 2>;
 using F12x24s6 = Shape<12, 12, 24, 24, 6, 4, 6, 3, 3, 3, 3, 3, 8, 2>;
 using F12x24s6b = Shape<12, 12, 24, 24, 6, 8, 3, 6, 3, 3, 3, 3, 8, 2>;
-using F16x32s8 = Shape<16, 16, 32, 32, 8, 4, 8, 4, 4, 4, 4, 4, 8, 2>;
-using F16x32s8b = Shape<16, 16, 32, 32, 8, 8, 4, 8, 4, 4, 4, 4, 8, 2>;
+// 16x32: 6 warps per CTA, so that two CTAs' shared memory (partial-sum copies,
+// C0 blocks, Y buffers) fits an SM
+using F16x32s8 = Shape<16, 16, 32, 32, 8, 4, 8, 4, 4, 4, 4, 4, 6, 2>;
+using F16x32s8b = Shape<16, 16, 32, 32, 8, 8, 4, 8, 4, 4, 4, 4, 6, 2>;
 // two signals per warp: <p1, p2, n1, n2, s, LI, RI, RJ, ZA, ZB, WI, WB, warps/CTA, min CTAs/SM>
 using H8x16s4 = HalfShape<8, 8, 16, 16, 4, 4, 4, 4, 2, 4, 4, 2, 8, 2>;
 using H12x24s6 = HalfShape<12, 12, 24, 24, 6, 2, 12, 3, 6, 3, 6, 3, 8, 2>;
