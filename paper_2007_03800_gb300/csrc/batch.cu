@@ -437,7 +437,7 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
                              b->norms[g]};
         maxcount = std::max(maxcount, res[g].count);
     }
-    b->rescale_blocks = (int)std::min<long long>((maxcount + 255) / 256, (long long)c->num_sms * 4);
+    b->rescale_blocks = (int)std::min<long long>((maxcount / 4 + 255) / 256 + 1, (long long)c->num_sms * 4);
     std::vector<PassArgs> all_args(3 * G);
     for (int side = 0; side < 3; ++side)
         std::copy(b->args[side].begin(), b->args[side].end(), all_args.begin() + side * G);
