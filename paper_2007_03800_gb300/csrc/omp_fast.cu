@@ -1040,30 +1040,25 @@ __device__ __forceinline__ void code_half_body(const PassArgs& a, int cta, int n
                     return;
                 }
                 // scores in two row halves of the lane's block (RH x RJ each), so
-                // that only half the block is live at once; half hh feeds argmax
-                // chains 2hh and 2hh + 1 (alternate rows), each visited in
-                // increasing q, merged by (value, q)
+                // that only half the block is live at once, in a loop that is not
+                // unrolled (half the code, for the instruction cache); C0 comes
+                // from shared memory, so no register array is indexed by the
+                // half.  Each half scans two argmax chains (alternate rows, each
+                // in increasing q), merged by (value, q) into the running best.
                 constexpr int RH = RI / 2, EH = RH * RJ;
-                float bv[4] = {0.f, 0.f, 0.f, 0.f};
-                int bqv[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
-                static_for<0, 2>([&](auto hc) {
-                    constexpr int hh = decltype(hc)::value;
+                float bv[1] = {0.f};
+                int bqv[1] = {0x7fffffff};
+#pragma unroll 1
+                for (int hh = 0; hh < 2; ++hh) {
                     float sc[EH];   // sc[c*RH + r] = score of row hh*RH + r, column c
-                    if constexpr (t == 0) {
 #pragma unroll
-                        for (int c = 0; c < RJ; ++c)
+                    for (int c = 0; c < RJ; ++c)
 #pragma unroll
-                            for (int r = 0; r < RH; ++r) sc[c * RH + r] = c0[c * RI + hh * RH + r];
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < RJ; ++c)
-#pragma unroll
-                            for (int r = 0; r < RH; r += 2) {
-                                const float2 x2 = *reinterpret_cast<const float2*>(myc0 + c * RI + hh * RH + r);
-                                sc[c * RH + r] = x2.x;
-                                sc[c * RH + r + 1] = x2.y;
-                            }
-                    }
+                        for (int r = 0; r < RH; r += 2) {
+                            const float2 x2 = *reinterpret_cast<const float2*>(myc0 + c * RI + hh * RH + r);
+                            sc[c * RH + r] = x2.x;
+                            sc[c * RH + r + 1] = x2.y;
+                        }
 #pragma unroll
                     for (int l = 0; l < t; ++l) {
                         float u[RH], v[RJ];
@@ -1074,24 +1069,28 @@ __device__ __forceinline__ void code_half_body(const PassArgs& a, int cta, int n
                         for (int c = 0; c < RJ; ++c) v[c] *= nx;
                         rank1_update<RH, RJ>(sc, u, v);
                     }
+                    float be = 0.f, bo = 0.f;
+                    int qe = 0x7fffffff, qo = 0x7fffffff;
+                    const int qh = qbase + hh * RH;
 #pragma unroll
                     for (int c = 0; c < RJ; ++c)
 #pragma unroll
                         for (int r = 0; r < RH; ++r) {
-                            const int ch = 2 * hh + (r & 1);
                             const float v = fabsf(sc[c * RH + r]);
-                            if (v > bv[ch]) { bv[ch] = v; bqv[ch] = qbase + hh * RH + r + N1 * c; }
+                            if (r & 1) {
+                                if (v > bo) { bo = v; qo = qh + r + N1 * c; }
+                            } else {
+                                if (v > be) { be = v; qe = qh + r + N1 * c; }
+                            }
                         }
-                });
-#pragma unroll
-                for (int ch = 1; ch < 4; ch += 2)
-                    if (bv[ch] > bv[ch - 1] || (bv[ch] == bv[ch - 1] && bqv[ch] < bqv[ch - 1])) {
-                        bv[ch - 1] = bv[ch];
-                        bqv[ch - 1] = bqv[ch];
+                    if (bo > be || (bo == be && qo < qe)) {
+                        be = bo;
+                        qe = qo;
                     }
-                if (bv[2] > bv[0] || (bv[2] == bv[0] && bqv[2] < bqv[0])) {
-                    bv[0] = bv[2];
-                    bqv[0] = bqv[2];
+                    if (be > bv[0] || (be == bv[0] && qe < bqv[0])) {
+                        bv[0] = be;
+                        bqv[0] = qe;
+                    }
                 }
                 // the Cholesky state of steps 0..t-1 (shared memory, so that it
                 // holds no registers while the scores are live)
