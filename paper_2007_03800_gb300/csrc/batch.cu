@@ -57,7 +57,7 @@ constexpr int kMultiWarps = 8;   // warps per CTA of the persistent multi-proble
 int code_pass(const sdl_batch* b, int side, cudaStream_t st) {
     if (b->G == 1) return launch_code_pass_grid(b->args[side][0], side, b->shape[0], b->total_ctas, st);
     return launch_code_multi(b->d_args[side], b->d_cta_begin, b->d_shape, b->G, b->total_ctas,
-                             b->smem[side], side, st);
+                             b->smem[side], side, st, b->ctx->num_sms);
 }
 
 

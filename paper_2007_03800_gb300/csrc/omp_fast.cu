@@ -1350,10 +1350,17 @@ int with_shape(int id, F&& f) {
 template <int SIDE>
 __global__ void __launch_bounds__(256, 2)
     code_multi_kernel(const PassArgs* __restrict__ groups, const int* __restrict__ cta_begin,
-                      const int* __restrict__ shape, int G) {
+                      const int* __restrict__ shape, int G, int spread) {
+    // position of this CTA: with spread = R SMs and W = gridDim / R waves, CTA
+    // b = w R + r takes position r W + w (a bijection of 0..gridDim-1)
+    int b = (int)blockIdx.x;
+    if (spread > 0 && (int)gridDim.x % spread == 0) {
+        const int waves = (int)gridDim.x / spread;
+        b = (b % spread) * waves + b / spread;
+    }
     int g = 0;
-    while (g + 1 < G && (int)blockIdx.x >= cta_begin[g + 1]) ++g;
-    const int cta = blockIdx.x - cta_begin[g];
+    while (g + 1 < G && b >= cta_begin[g + 1]) ++g;
+    const int cta = b - cta_begin[g];
     const int n = cta_begin[g + 1] - cta_begin[g];
     const PassArgs a = groups[g];
     switch (shape[g]) {
@@ -1371,12 +1378,12 @@ __global__ void __launch_bounds__(256, 2)
 
 template <int SIDE>
 int launch_multi_impl(const PassArgs* d_groups, const int* d_cta_begin, const int* d_shape, int G,
-                      int total_ctas, size_t smem, cudaStream_t st) {
+                      int total_ctas, size_t smem, cudaStream_t st, int spread) {
     auto kern = code_multi_kernel<SIDE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return SDL_ERR_CUDA;
-    kern<<<total_ctas, 256, smem, st>>>(d_groups, d_cta_begin, d_shape, G);
+    kern<<<total_ctas, 256, smem, st>>>(d_groups, d_cta_begin, d_shape, G, spread);
     return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
 }
 
@@ -1453,11 +1460,11 @@ int launch_code_pass_variant(const PassArgs& a, int side, int shape_id, int ctas
 }
 
 int launch_code_multi(const PassArgs* d_groups, const int* d_cta_begin, const int* d_shape, int G,
-                      int total_ctas, size_t smem, int side, cudaStream_t st) {
+                      int total_ctas, size_t smem, int side, cudaStream_t st, int spread) {
     switch (side) {
-        case kCodeOnly: return launch_multi_impl<kCodeOnly>(d_groups, d_cta_begin, d_shape, G, total_ctas, smem, st);
-        case kSideD1: return launch_multi_impl<kSideD1>(d_groups, d_cta_begin, d_shape, G, total_ctas, smem, st);
-        case kSideD2: return launch_multi_impl<kSideD2>(d_groups, d_cta_begin, d_shape, G, total_ctas, smem, st);
+        case kCodeOnly: return launch_multi_impl<kCodeOnly>(d_groups, d_cta_begin, d_shape, G, total_ctas, smem, st, spread);
+        case kSideD1: return launch_multi_impl<kSideD1>(d_groups, d_cta_begin, d_shape, G, total_ctas, smem, st, spread);
+        case kSideD2: return launch_multi_impl<kSideD2>(d_groups, d_cta_begin, d_shape, G, total_ctas, smem, st, spread);
         default: return SDL_ERR_ARG;
     }
 }

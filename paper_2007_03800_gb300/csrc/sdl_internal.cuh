@@ -88,9 +88,12 @@ size_t fast_smem_bytes(int shape_id, int side);
 int launch_code_pass_variant(const PassArgs& a, int side, int shape_id, int ctas_per_sm,
                              cudaStream_t st, int num_sms);
 // Several problems in one persistent launch (device arrays of G entries,
-// cta_begin has G+1); smem = the largest per-problem requirement.
+// cta_begin has G+1); smem = the largest per-problem requirement.  spread > 0
+// (the SM count, total_ctas a multiple of it): CTAs b and b + spread take
+// neighbouring positions, so that the CTAs an SM holds at once mostly run the
+// same problem's code.
 int launch_code_multi(const PassArgs* d_groups, const int* d_cta_begin, const int* d_shape, int G,
-                      int total_ctas, size_t smem, int side, cudaStream_t st);
+                      int total_ctas, size_t smem, int side, cudaStream_t st, int spread = 0);
 int multi_ctas_per_sm(size_t smem, int side);
 bool code_shape_supported(int p1, int p2, int n1, int n2, int s);
 // Upper bound of the partial-sum slots any pass may use for these sizes.
