@@ -257,7 +257,7 @@ class Context:
 
     def profile_collect(self) -> dict:
         """{kernel name: (total device ms, launches)} since the last collect."""
-        n = 18
+        n = NUM_KERNEL_KINDS
         ms = (ctypes.c_double * n)()
         cnt = (ctypes.c_int64 * n)()
         k = self._lib.sdl_profile_collect(self._h, ms, cnt, n)
@@ -423,6 +423,8 @@ class _Group(ctypes.Structure):
                 ("D2", _P), ("n2", _I), ("s_max", _I), ("eps", _F), ("support", _P),
                 ("coef", _P), ("nnz", _P), ("res_energy", _P)]
 
+
+NUM_KERNEL_KINDS = 18   # SDL_NUM_KERNEL_KINDS
 
 BATCH_AUTOTUNE = 1
 BATCH_GRAPH = 2

@@ -90,3 +90,19 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     assert lib.sdl_create(ctypes.byref(h), 0) == -2
     assert h.value is None
+
+
+def test_binding_constants_match_the_header():
+    """Error codes, batch flags and precision flags of the binding are the
+    values the header defines (parsed from the header text)."""
+    from paper_2007_03800_gb300 import sdl
+    text = open(HEADER).read()
+    errs = dict((int(v), k) for k, v in re.findall(r"^\s*(SDL_ERR_\w+)\s*=\s*(-?\d+)", text, flags=re.M))
+    assert errs == sdl.ERRORS
+    defs = dict((k, int(v)) for k, v in re.findall(r"^#define\s+(SDL_\w+)\s+(\d+)", text, flags=re.M))
+    assert sdl.NUM_KERNEL_KINDS == defs["SDL_NUM_KERNEL_KINDS"]
+    for name in ("BATCH_AUTOTUNE", "BATCH_GRAPH", "BATCH_RETUNE"):
+        assert getattr(sdl, name) == defs["SDL_" + name], name
+    ctx_cls = sdl.Context
+    for name in ("PREC_FP32", "PREC_BF16_CORR", "PREC_NO_RESCORE", "PREC_FP64_SOLVE"):
+        assert getattr(ctx_cls, name) == defs["SDL_" + name], name
