@@ -6,6 +6,7 @@ be written as closed forms ("sqrt(2)", "1/sqrt(5)").
 The CPU tests pin the FP64 oracle to them; the GPU tests run the same
 examples through the C ABI (FP32, so within a few ulps).
 """
+import ast
 import glob
 import json
 import math
@@ -19,13 +20,31 @@ from oracle import denoise as odn
 from oracle import ortho, tmod3
 
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-_NS = {"__builtins__": {}, "sqrt": math.sqrt, "log10": math.log10}
+_FUNCS = {"sqrt": math.sqrt, "log10": math.log10}
+_BINOPS = {ast.Add: lambda a, b: a + b, ast.Sub: lambda a, b: a - b, ast.Mult: lambda a, b: a * b,
+           ast.Div: lambda a, b: a / b, ast.Pow: lambda a, b: a ** b}
+
+
+def _closed_form(node):
+    """Numbers, + - * / **, unary minus, sqrt() and log10(): nothing else."""
+    if isinstance(node, ast.Expression):
+        return _closed_form(node.body)
+    if isinstance(node, ast.Constant) and isinstance(node.value, (int, float)):
+        return float(node.value)
+    if isinstance(node, ast.UnaryOp) and isinstance(node.op, ast.USub):
+        return -_closed_form(node.operand)
+    if isinstance(node, ast.BinOp) and type(node.op) in _BINOPS:
+        return _BINOPS[type(node.op)](_closed_form(node.left), _closed_form(node.right))
+    if (isinstance(node, ast.Call) and isinstance(node.func, ast.Name) and node.func.id in _FUNCS
+            and len(node.args) == 1 and not node.keywords):
+        return _FUNCS[node.func.id](_closed_form(node.args[0]))
+    raise ValueError(f"not a closed form: {ast.dump(node)}")
 
 
 def num(v):
     """A fixture number: a JSON number or a closed-form string."""
     if isinstance(v, str):
-        return float(eval(v, _NS))   # fixture text only: sqrt, log10, arithmetic
+        return _closed_form(ast.parse(v, mode="eval"))
     if isinstance(v, list):
         return [num(x) for x in v]
     return v
