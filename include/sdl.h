@@ -193,8 +193,8 @@ typedef struct sdl_group {
 #define SDL_BATCH_AUTOTUNE 1  /* time each group's compiled lane tilings and
                                  split the CTAs between groups by measured cost;
                                  the context remembers the result for batches
-                                 of the same groups (shapes, N, s_max, whether
-                                 eps > 0) and reuses it                         */
+                                 of the same groups (shapes, N, s_max, eps)
+                                 and reuses it                                  */
 #define SDL_BATCH_GRAPH 2     /* capture one iteration into a CUDA graph       */
 #define SDL_BATCH_RETUNE 4    /* with AUTOTUNE: time again even if remembered  */
 

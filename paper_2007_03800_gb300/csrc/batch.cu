@@ -257,11 +257,15 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
     // ---- tiling and CTA split
     b->shape.resize(G);
     b->cost_us.resize(G);
+    // remembered tunings are keyed by every group's shape, count and error
+    // target (its bit pattern; 0 for a fixed s), which set the groups' costs
     std::vector<long long> tkey;
     for (int g = 0; g < G; ++g) {
         const sdl_group& q = groups[g];
+        uint32_t eps_bits = 0;
+        if (q.eps > 0.f) std::memcpy(&eps_bits, &q.eps, sizeof eps_bits);
         for (long long v : {(long long)q.p1, (long long)q.p2, (long long)q.n1, (long long)q.n2,
-                            (long long)q.s_max, (long long)q.N, (long long)(q.eps > 0.f)})
+                            (long long)q.s_max, (long long)q.N, (long long)eps_bits})
             tkey.push_back(v);
     }
     const sdl_ctx::BatchTune* known = nullptr;
