@@ -61,7 +61,7 @@ def load(name):
 
 def test_every_fixture_cites_and_derives():
     files = sorted(glob.glob(os.path.join(HERE, "*.json")))
-    assert len(files) >= 8
+    assert len(files) >= 9
     for f in files:
         d = json.load(open(f))
         assert d["citation"] and d["derivation"], f
@@ -122,6 +122,17 @@ def test_oracle_omp3d_golden():
     assert np.array_equal(r.nnz, np.asarray(d["nnz"]))
     np.testing.assert_allclose(r.coef, arr(d["coef"]), atol=1e-12)
     np.testing.assert_allclose(r.res_energy, arr(d["res_energy"]), atol=1e-12)
+
+
+def test_oracle_tmod3_update_golden():
+    d = load("tmod3_update_mode3_2x2x2.json")
+    e = d["expected"]
+    Ds = [arr(d[k]) for k in ("D1", "D2", "D3")]
+    r = tmod3.update_mode(arr(d["Y"]), Ds, np.asarray(d["support"]), arr(d["coef"]), d["mode"])
+    for key in ("P", "B", "D", "norms", "coef"):
+        np.testing.assert_allclose(getattr(r, key), arr(e[key]), rtol=1e-12, atol=1e-12, err_msg=key)
+    assert r.obj_before == pytest.approx(e["obj_before"], abs=1e-12)
+    assert r.obj_after == pytest.approx(e["obj_after"], abs=1e-12)
 
 
 def test_oracle_denoise_golden():
