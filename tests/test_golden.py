@@ -20,17 +20,20 @@ from oracle import denoise as odn
 from oracle import ortho, tmod3
 
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-_FUNCS = {"sqrt": math.sqrt, "log10": math.log10}
+_FUNCS = {"sqrt": math.sqrt, "log10": math.log10, "log": math.log, "exp": math.exp, "erf": math.erf}
+_NAMES = {"pi": math.pi}
 _BINOPS = {ast.Add: lambda a, b: a + b, ast.Sub: lambda a, b: a - b, ast.Mult: lambda a, b: a * b,
            ast.Div: lambda a, b: a / b, ast.Pow: lambda a, b: a ** b}
 
 
 def _closed_form(node):
-    """Numbers, + - * / **, unary minus, sqrt() and log10(): nothing else."""
+    """Numbers, pi, + - * / **, unary minus, sqrt, log10, log, exp, erf: nothing else."""
     if isinstance(node, ast.Expression):
         return _closed_form(node.body)
     if isinstance(node, ast.Constant) and isinstance(node.value, (int, float)):
         return float(node.value)
+    if isinstance(node, ast.Name) and node.id in _NAMES:
+        return _NAMES[node.id]
     if isinstance(node, ast.UnaryOp) and isinstance(node.op, ast.USub):
         return -_closed_form(node.operand)
     if isinstance(node, ast.BinOp) and type(node.op) in _BINOPS:
@@ -61,7 +64,7 @@ def load(name):
 
 def test_every_fixture_cites_and_derives():
     files = sorted(glob.glob(os.path.join(HERE, "*.json")))
-    assert len(files) >= 9
+    assert len(files) >= 10
     for f in files:
         d = json.load(open(f))
         assert d["citation"] and d["derivation"], f
@@ -133,6 +136,30 @@ def test_oracle_tmod3_update_golden():
         np.testing.assert_allclose(getattr(r, key), arr(e[key]), rtol=1e-12, atol=1e-12, err_msg=key)
     assert r.obj_before == pytest.approx(e["obj_before"], abs=1e-12)
     assert r.obj_after == pytest.approx(e["obj_after"], abs=1e-12)
+
+
+def test_oracle_mlp_golden():
+    from oracle import mlp
+    d = load("mlp_tiny_closed_form.json")
+    e = d["expected"]
+    W1, b1, W2, b2 = (arr(d[k]) for k in ("W1", "b1", "W2", "b2"))
+    X = mlp.inputs(arr(d["Y"]))
+    np.testing.assert_allclose(X, arr(e["x"]), atol=1e-15)
+    pre, H, Z = mlp.forward(X, W1, b1, W2, b2)
+    np.testing.assert_allclose(H, arr(e["h"]), atol=1e-15)
+    np.testing.assert_allclose(Z, arr(e["z"]), atol=1e-15)
+    T = mlp.targets(np.asarray(d["support"]), 1)
+    loss, g = mlp.loss_and_grads(X, T, W1, b1, W2, b2)
+    assert loss == pytest.approx(num(e["loss"]), abs=1e-14)
+    gz, gp = num(e["gz"]), num(e["gz"]) * 2.0 * num(e["gelu_grad_1"])
+    np.testing.assert_allclose(g["b2"], [gz], atol=1e-14)
+    np.testing.assert_allclose(g["W2"], [[gz * num(e["h"][0][0])]], atol=1e-14)
+    np.testing.assert_allclose(g["b1"], [gp], atol=1e-14)
+    np.testing.assert_allclose(g["W1"], [[gp * 0.6, gp * 0.8]], atol=1e-14)
+    lr = d["lr"]
+    for key, p0 in (("W1", W1), ("b1", b1), ("W2", W2), ("b2", b2)):
+        p1, m, v = mlp.adam_step(p0, g[key], np.zeros_like(p0), np.zeros_like(p0), 1, lr)
+        np.testing.assert_allclose(p1, p0 - lr * g[key] / (np.abs(g[key]) + 1e-8), atol=1e-15, err_msg=key)
 
 
 def test_oracle_denoise_golden():
