@@ -64,7 +64,7 @@ def load(name):
 
 def test_every_fixture_cites_and_derives():
     files = sorted(glob.glob(os.path.join(HERE, "*.json")))
-    assert len(files) >= 10
+    assert len(files) >= 11
     for f in files:
         d = json.load(open(f))
         assert d["citation"] and d["derivation"], f
@@ -92,6 +92,7 @@ def test_oracle_omp2d_golden(name, case):
 
 
 @pytest.mark.parametrize("name,fn", [("tmod_update_D1_2x2.json", oracle.update_D1),
+                                     ("tmod_update_D1_offdiag_2x2.json", oracle.update_D1),
                                      ("tmod_update_D2_2x2.json", oracle.update_D2)])
 def test_oracle_tmod_update_golden(name, fn):
     d = load(name)
