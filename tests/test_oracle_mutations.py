@@ -96,3 +96,84 @@ def test_every_mutant_is_caught(monkeypatch, name):
         monkeypatch.setattr(oracle, attr, fn)
     failed = caught()
     assert failed, f"no pin caught the mutant {name}"
+
+
+# ------------------------------------------------- the extensions' oracles
+import test_oracle_denoise as pins_dn  # noqa: E402
+import test_oracle_mlp as pins_mlp  # noqa: E402
+import test_oracle_ortho as pins_or  # noqa: E402
+import test_oracle_tmod3 as pins_t3  # noqa: E402
+from oracle import denoise as o_dn  # noqa: E402
+from oracle import mlp as o_mlp  # noqa: E402
+from oracle import ortho as o_or  # noqa: E402
+from oracle import tmod3 as o_t3  # noqa: E402
+
+_orig_polar = o_or._polar
+_orig_unfold = o_t3.unfold
+_orig_gelu_grad = o_mlp.gelu_grad
+
+
+def _polar_without_vt(B):                         # U alone instead of U V^T
+    U, S, Vt = np.linalg.svd(B)
+    return U, S
+
+
+def _unfold_row_major(T, k):                      # the other column order
+    return np.moveaxis(T, k, 0).reshape(T.shape[k], -1, order="C")
+
+
+def _gelu_grad_no_density_term(u):               # Phi(u) only, the u phi(u) term dropped
+    import math
+    from scipy.special import erf
+    return 0.5 * (1.0 + erf(u / math.sqrt(2.0)))
+
+
+def _average_without_counts(patches, H, W):      # sums instead of averages
+    N, p, _ = patches.shape
+    acc = np.zeros((H, W))
+    k = 0
+    for r in range(H - p + 1):
+        for c in range(W - p + 1):
+            acc[r:r + p, c:c + p] += patches[k]
+            k += 1
+    return acc
+
+
+EXT_MUTANTS = {
+    "procrustes_without_vt": (o_or, "_polar", _polar_without_vt, [
+        lambda: pins_or.test_procrustes_beats_every_other_orthonormal_dictionary(1),
+        lambda: pins_or.test_procrustes_beats_every_other_orthonormal_dictionary(2),
+        lambda: pins_or.test_procrustes_recovers_a_planted_dictionary(1),
+        pins_or.test_ortho_iteration_is_monotone_and_orthonormal,
+        golden.test_oracle_threshold_and_procrustes_golden]),
+    "unfolding_row_major": (o_t3, "unfold", _unfold_row_major, [
+        pins_t3.test_unfolding_identity,
+        lambda: pins_t3.test_mode_update_is_least_squares_optimum(0),
+        lambda: pins_t3.test_mode_update_is_least_squares_optimum(2),
+        golden.test_oracle_tmod3_update_golden]),
+    "gelu_grad_without_density": (o_mlp, "gelu_grad", _gelu_grad_no_density_term, [
+        lambda: pins_mlp.test_gradients_match_central_differences("W1"),
+        pins_mlp.test_gelu_definition_and_derivative,
+        golden.test_oracle_mlp_golden]),
+    "average_without_counts": (o_dn, "patch_average", _average_without_counts, [
+        pins_dn.test_average_of_exact_patches_is_the_image,
+        pins_dn.test_average_weights_by_brute_force,
+        golden.test_oracle_denoise_golden]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EXT_MUTANTS))
+def test_every_extension_mutant_is_caught(monkeypatch, name):
+    mod, attr, fn, pin_list = EXT_MUTANTS[name]
+    with np.errstate(all="ignore"):
+        for p in pin_list:                         # every pin passes on the real oracle
+            p()
+    monkeypatch.setattr(mod, attr, fn)
+    failed = 0
+    with np.errstate(all="ignore"):
+        for p in pin_list:
+            try:
+                p()
+            except Exception:
+                failed += 1
+    assert failed, f"no pin caught the mutant {name}"
