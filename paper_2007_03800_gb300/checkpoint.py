@@ -85,6 +85,8 @@ def learn(ctx, Y, D1, D2, s: int, iterations: int, eps: float = 0.0, *, config: 
     iteration."""
     import torch
 
+    if every < 1:
+        raise ValueError("every must be at least 1")
     N = Y.shape[0]
     config = dict(config or {})
     rmse = torch.zeros(2, dtype=torch.float32, device=Y.device)

@@ -43,6 +43,11 @@ def test_metrics_log_is_json_lines(tmp_path):
         json.loads(line)
 
 
+def test_learn_rejects_a_zero_checkpoint_interval():
+    with pytest.raises(ValueError):
+        ck.learn(None, np.zeros((1, 2, 2)), None, None, 1, 1, every=0)
+
+
 @pytest.mark.gpu
 def test_resume_follows_the_uninterrupted_run(gpu_ctx, tmp_path):
     import torch
