@@ -59,3 +59,15 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""                    # no line, no oracle work
+
+
+def test_algorithmic_work_of_the_c2_pass_by_hand():
+    """12x12 signals, D 12x24, s = 6: C0 in the cheaper association
+    2 (12*12*24 + 24*12*24) = 20 736; correlation updates 2*576*(0+1+...+5) =
+    17 280; Cholesky and solves sum_t (2t^2 + 4t + 4) = 194; D1-side epilogue
+    2*12*6 + 3*36 = 252: 38 462 FLOP per signal, 7.69e9 per 200k-signal pass.
+    Bytes: the signal (576) and, in the second pass, the code (8 s + 4)."""
+    assert bench.flops_per_signal_pass(12, 12, 24, 24, 6, 1) == 20736 + 17280 + 194 + 252
+    assert bench.flops_per_signal_pass(12, 12, 24, 24, 6, 1) * 200_000 == pytest.approx(7.69e9, rel=1e-3)
+    assert bench.bytes_per_signal_pass(12, 12, 6, 1) == 576
+    assert bench.bytes_per_signal_pass(12, 12, 6, 2) == 576 + 52
