@@ -18,6 +18,9 @@ What each routine follows:
   omp2d             : the 2D-OMP sparse coder of Sec. III step 1), i.e. greedy
                       pursuit over Kronecker atom pairs, equivalent to 1D OMP on
                       D2 (x) D1 (Sec. II); full least-squares re-fit per pick
+  omp2d_replay      : the same pursuit forced along a given pick sequence
+                      (every step's scores, pivots and residual energies on
+                      that path, and the least-squares fit on its support)
   update_D1         : Corollary 1 (optimal D1, then the W1 normalisation)
   update_D2         : Result 1 (optimal D2, then the W2 normalisation)
   iterate           : one pass of the main loop of Algorithm 1 (steps 1-4)
@@ -44,8 +47,8 @@ import scipy.linalg
 
 __all__ = [
     "PIVOT_REL", "grams", "reconstruct", "residual", "objective", "rmse",
-    "densify", "omp2d", "update_D1", "update_D2", "iterate", "OMPResult",
-    "UpdateResult", "IterResult", "SingularError",
+    "densify", "omp2d", "omp2d_replay", "ReplayResult", "update_D1", "update_D2", "iterate",
+    "OMPResult", "UpdateResult", "IterResult", "SingularError",
 ]
 
 PIVOT_REL = 1e-6          # degenerate-pick threshold on pivot^2 / A_tt
@@ -209,6 +212,104 @@ def omp2d(Y, D1, D2, s: int, eps: float | None = None, top_k: int = 4) -> OMPRes
         active[idx[~accept]] = False
     res_energy = np.sum(R * R, axis=(1, 2))
     return OMPResult(support, coef, nnz, res_energy, top_q, top_val)
+
+
+class ReplayResult:
+    """Quantities of 2D-OMP along a forced pick sequence, per signal k and
+    step t (t picks already made):
+      energy (N, s+1)     ||R_k||^2 after t picks (R = Y - D1 X D2^T, explicit)
+      best (N, s)         max |C_q| over unselected pairs at step t (NaN once
+                          the sequence has ended before step t)
+      best_q (N, s)       the pair the greedy rule would take there (ties ->
+                          smallest q), -1 where best is NaN
+      best_piv2 (N, s)    pivot^2 of best_q against the selected pairs, and
+      best_Att (N, s)     its A_tt = G1[i,i] G2[j,j]
+      pick (N, s)         |C_q| of the given pick at step t (-1 if that pair
+                          was already selected; NaN past the sequence)
+      pick_piv2, pick_Att (N, s)  the same two for the given pick
+      coef (N, s)         least-squares coefficients on the whole given support
+      res_energy (N,)     ||R_k||^2 after the whole sequence"""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def _pivot2(G1, G2, sup_prev, q, n1):
+    """pivot^2 of pair q against the selected pairs sup_prev (rows of the
+    fresh Cholesky of A over sup_prev + [q]) and A_qq = G1[i,i] G2[j,j]."""
+    sup = np.concatenate([sup_prev, q[:, None]], axis=1)
+    ii, jj = sup % n1, sup // n1
+    A = G1[ii[:, :, None], ii[:, None, :]] * G2[jj[:, :, None], jj[:, None, :]]
+    _, piv2 = _cholesky_rows(A)
+    t = sup.shape[1] - 1
+    return piv2, A[:, t, t]
+
+
+def omp2d_replay(Y, D1, D2, support, nnz, s: int) -> ReplayResult:
+    """2D-OMP (Sec. III step 1, 1D OMP on D2 (x) D1 by Sec. II) forced to take
+    the picks support[k, :nnz[k]] in that order instead of its own argmax.
+
+    At each step t of signal k (t = 0..nnz[k], and t < s) the residual of the
+    previous least-squares fit gives the correlations C = D1^T R D2; recorded
+    are the greedy rule's choice there (max |C_q| over unselected pairs, ties
+    to the smallest q, with its Cholesky pivot) and, for t < nnz[k], the score
+    and pivot of the forced pick, after which all coefficients are re-fitted
+    on the forced support exactly as omp2d does (fresh Cholesky of A with
+    b_l = (D1^T Y D2)[i_l, j_l]) and R is formed explicitly.  Used to judge a
+    pick sequence that left the oracle's own path (at an argmax tie, or at
+    the stop threshold): every step of it can be checked against the rule,
+    and its coefficients and residual energies against this fit."""
+    Y = np.asarray(Y, dtype=np.float64)
+    D1 = np.asarray(D1, dtype=np.float64)
+    D2 = np.asarray(D2, dtype=np.float64)
+    support = np.asarray(support, dtype=np.int64)
+    nnz = np.asarray(nnz, dtype=np.int64)
+    N, p1, p2 = Y.shape
+    n1, n2 = D1.shape[1], D2.shape[1]
+    nq = n1 * n2
+    G1, G2 = grams(D1, D2)
+    C0 = np.einsum("ai,kab,bj->kij", D1, Y, D2, optimize=True)
+    nan = lambda: np.full((N, s), np.nan)
+    energy = np.full((N, s + 1), np.nan)
+    best, best_piv2, best_Att = nan(), nan(), nan()
+    pick, pick_piv2, pick_Att = nan(), nan(), nan()
+    best_q = np.full((N, s), -1, dtype=np.int64)
+    coef = np.zeros((N, s))
+    R = Y.copy()
+    for t in range(s + 1):
+        live = np.nonzero(nnz >= t)[0]                 # signals that reach step t
+        energy[live, t] = np.sum(R[live] ** 2, axis=(1, 2))
+        if t == s or live.size == 0:
+            continue
+        C = np.einsum("ai,kab,bj->kij", D1, R[live], D2, optimize=True)
+        score = np.abs(C).transpose(0, 2, 1).reshape(live.size, nq)   # column q = i + n1*j
+        rows = np.arange(live.size)
+        prev = support[live, :t]
+        for l in range(t):
+            score[rows, prev[:, l]] = -1.0                             # mask selected pairs
+        order = np.lexsort((np.broadcast_to(np.arange(nq), score.shape), -score), axis=1)
+        bq = order[:, 0]
+        best_q[live, t] = bq
+        best[live, t] = score[rows, bq]
+        best_piv2[live, t], best_Att[live, t] = _pivot2(G1, G2, prev, bq, n1)
+        go = nnz[live] > t                                           # a forced pick at step t
+        idx = live[go]
+        if idx.size == 0:
+            continue
+        q = support[idx, t]
+        pick[idx, t] = score[rows[go], q]
+        pick_piv2[idx, t], pick_Att[idx, t] = _pivot2(G1, G2, support[idx, :t], q, n1)
+        sup = support[idx, :t + 1]
+        ii, jj = sup % n1, sup // n1
+        A = G1[ii[:, :, None], ii[:, None, :]] * G2[jj[:, :, None], jj[:, None, :]]
+        L, _ = _cholesky_rows(A)
+        x = _cholesky_solve(L, C0[idx[:, None], ii, jj])
+        coef[idx, :t + 1] = x
+        R[idx] = Y[idx] - reconstruct(D1, D2, sup, x)
+    res_energy = energy[np.arange(N), np.minimum(nnz, s)]
+    return ReplayResult(energy=energy, best=best, best_q=best_q, best_piv2=best_piv2,
+                        best_Att=best_Att, pick=pick, pick_piv2=pick_piv2, pick_Att=pick_Att,
+                        coef=coef, res_energy=res_energy)
 
 
 # --------------------------------------------------------------------------

@@ -352,3 +352,66 @@ def test_selected_pairs_never_reselected():
         # an early stop is only allowed when every remaining score is exactly 0
         assert t == 4 or (t >= 2 and res.top_val[k, t, 0] == 0.0)
         assert len(set(res.support[k][:t])) == t
+
+
+# ------------------------------------------- forced-support replay (Sec. III step 1)
+def test_replay_of_own_sequence_reproduces_omp():
+    """Forced along the oracle's own picks, the replay takes the greedy rule's
+    choice at every step (pick score = best score, best_q = the pick) and
+    returns omp2d's coefficients and residual energies."""
+    Y, _, _, _, _ = synth.kron_model(200, 8, 8, 16, 16, 4, 20.0, seed=11)
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    res = oracle.omp2d(Y, D1, D2, 4)
+    rp = oracle.omp2d_replay(Y, D1, D2, res.support, res.nnz, 4)
+    assert np.array_equal(rp.best_q, res.support)
+    assert np.array_equal(rp.pick, rp.best)
+    assert np.allclose(rp.coef, res.coef, rtol=1e-12, atol=1e-14)
+    assert np.allclose(rp.res_energy, res.res_energy, rtol=1e-12)
+    assert np.all(rp.pick_piv2 > oracle.PIVOT_REL * rp.pick_Att)
+
+
+@pytest.mark.parametrize("n1,n2,s", [(4, 4, 3), (6, 4, 4), (8, 8, 5)])
+def test_replay_forced_sequence_against_explicit_kronecker(n1, n2, s):
+    """Arbitrary forced pick sequences (not the greedy ones, some ending
+    early) on 4x4 signals, checked step by step against the explicit
+    D2 (x) D1 (Sec. I): correlations of the explicit residual, the least-squares
+    fit by lstsq on the explicit columns, pivot^2 as the squared distance of an
+    atom from the span of the selected ones, and the residual energies."""
+    rng = np.random.default_rng(400 + n1 + 10 * n2 + s)
+    p1 = p2 = 4
+    D1 = synth.random_dictionary(p1, n1, rng)
+    D2 = synth.random_dictionary(p2, n2, rng)
+    N = 25
+    Y = rng.standard_normal((N, p1, p2))
+    sup = np.stack([rng.choice(n1 * n2, s, replace=False) for _ in range(N)]).astype(np.int64)
+    nnz = rng.integers(0, s + 1, N)
+    sup[np.arange(s)[None, :] >= nnz[:, None]] = -1
+    rp = oracle.omp2d_replay(Y, D1, D2, sup, nnz, s)
+    Dk = np.kron(D2, D1)
+    for k in range(N):
+        y = Y[k].flatten(order="F")
+        S = []
+        r = y.copy()
+        for t in range(min(nnz[k] + 1, s)):
+            c = np.abs(Dk.T @ r)
+            c[S] = -1.0
+            assert np.isclose(rp.energy[k, t], r @ r, rtol=1e-10)
+            assert np.isclose(rp.best[k, t], c.max(), rtol=1e-10, atol=1e-13)
+            assert c[rp.best_q[k, t]] >= c.max() * (1 - 1e-12)
+            # pivot^2 of the greedy choice: squared distance from span(S)
+            a = Dk[:, rp.best_q[k, t]]
+            proj = Dk[:, S] @ np.linalg.lstsq(Dk[:, S], a, rcond=None)[0] if S else 0.0
+            assert np.isclose(rp.best_piv2[k, t], np.sum((a - proj) ** 2), rtol=1e-8, atol=1e-12)
+            if t == nnz[k]:
+                break
+            q = int(sup[k, t])
+            assert np.isclose(rp.pick[k, t], c[q], rtol=1e-10, atol=1e-13)
+            S.append(q)
+            x, *_ = np.linalg.lstsq(Dk[:, S], y, rcond=None)
+            r = y - Dk[:, S] @ x
+        # the final fit on the whole forced support
+        if S:
+            assert np.allclose(rp.coef[k, :len(S)], x, rtol=1e-9, atol=1e-11)
+        assert np.all(rp.coef[k, len(S):] == 0.0)
+        assert np.isclose(rp.res_energy[k], r @ r, rtol=1e-10)
+        assert np.all(np.isnan(rp.energy[k, nnz[k] + 1:]))
