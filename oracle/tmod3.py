@@ -13,6 +13,8 @@ What each routine follows:
                     as 2D-OMP is on D2 (x) D1, Sec. II), full least-squares re-fit
                     after each pick, ties to the smallest q, the same degenerate-
                     pick rule as the 2-D oracle
+  omp3d_replay    : the same pursuit forced along a given pick sequence (the
+                    quantities of sdl_oracle.omp2d_replay, for atom triples)
   update_mode     : Remark 3 with X fixed: Y_(k) = D_k X_(k) T_k^T, T_k the
                     Kronecker product of the other dictionaries, so Corollary 1
                     gives D_k* = (sum Y_(k) T X_(k)^T)(sum X_(k) T^T T X_(k)^T)^{-1};
@@ -28,10 +30,11 @@ from __future__ import annotations
 
 import numpy as np
 
-from .sdl_oracle import PIVOT_REL, SingularError, _cholesky_rows, _cholesky_solve, _solve_normal
+from .sdl_oracle import (PIVOT_REL, ReplayResult, SingularError, _cholesky_rows, _cholesky_solve,
+                         _solve_normal)
 
-__all__ = ["kron3", "densify3", "reconstruct3", "objective3", "omp3d", "update_mode",
-           "iterate3", "unfold"]
+__all__ = ["kron3", "densify3", "reconstruct3", "objective3", "omp3d", "omp3d_replay",
+           "update_mode", "iterate3", "unfold"]
 
 
 def kron3(D1, D2, D3):
@@ -125,6 +128,71 @@ def omp3d(Y, D1, D2, D3, s: int, top_k: int = 4) -> OMP3Result:
             break
     R = Y - reconstruct3(D1, D2, D3, support, coef)
     return OMP3Result(support, coef, nnz, np.einsum("kabc,kabc->k", R, R), top_q, top_val)
+
+
+def _gram3(G1, G2, G3, sup, n1, n2):
+    ii, jj, ll = sup % n1, (sup // n1) % n2, sup // (n1 * n2)
+    return (G1[ii[:, :, None], ii[:, None, :]] * G2[jj[:, :, None], jj[:, None, :]] *
+            G3[ll[:, :, None], ll[:, None, :]])
+
+
+def omp3d_replay(Y, D1, D2, D3, support, nnz, s: int) -> ReplayResult:
+    """The pursuit of omp3d forced to take support[k, :nnz[k]] in that order
+    (Remark 3's pursuit is 1D OMP on D3 (x) D2 (x) D1, Sec. II): at every step
+    the residual of the previous fit gives the correlations, and the rule's
+    own choice (max |C| over unselected triples, ties to the smallest q, with
+    its pivot), the forced pick's score and pivot, and the residual energy are
+    recorded; the coefficients are fitted on the forced support as omp3d does.
+    Fields as sdl_oracle.ReplayResult."""
+    Y = np.asarray(Y, dtype=np.float64)
+    support = np.asarray(support, dtype=np.int64)
+    nnz = np.asarray(nnz, dtype=np.int64)
+    N = Y.shape[0]
+    n1, n2, n3 = D1.shape[1], D2.shape[1], D3.shape[1]
+    Q = n1 * n2 * n3
+    G1, G2, G3 = D1.T @ D1, D2.T @ D2, D3.T @ D3
+    C0 = np.einsum("ai,bj,cl,kabc->klji", D1, D2, D3, Y, optimize=True).reshape(N, Q)
+    nan = lambda: np.full((N, s), np.nan)
+    energy = np.full((N, s + 1), np.nan)
+    best, best_piv2, best_Att = nan(), nan(), nan()
+    pick, pick_piv2, pick_Att = nan(), nan(), nan()
+    best_q = np.full((N, s), -1, dtype=np.int64)
+    coef = np.zeros((N, s))
+    R = Y.copy()
+    for t in range(s + 1):
+        live = np.nonzero(nnz >= t)[0]
+        energy[live, t] = np.einsum("kabc,kabc->k", R[live], R[live])
+        if t == s or live.size == 0:
+            continue
+        C = np.einsum("ai,bj,cl,kabc->klji", D1, D2, D3, R[live], optimize=True).reshape(live.size, Q)
+        score = np.abs(C)
+        rows = np.arange(live.size)
+        prev = support[live, :t]
+        for m in range(t):
+            score[rows, prev[:, m]] = -1.0
+        order = np.argsort(-score, axis=1, kind="stable")
+        bq = order[:, 0]
+        best_q[live, t] = bq
+        best[live, t] = score[rows, bq]
+        A = _gram3(G1, G2, G3, np.concatenate([prev, bq[:, None]], axis=1), n1, n2)
+        _, best_piv2[live, t] = _cholesky_rows(A)
+        best_Att[live, t] = A[:, t, t]
+        go = nnz[live] > t
+        idx = live[go]
+        if idx.size == 0:
+            continue
+        sel = support[idx, :t + 1]
+        pick[idx, t] = score[rows[go], sel[:, t]]
+        A = _gram3(G1, G2, G3, sel, n1, n2)
+        Lc, pick_piv2[idx, t] = _cholesky_rows(A)
+        pick_Att[idx, t] = A[:, t, t]
+        x = _cholesky_solve(Lc, np.take_along_axis(C0[idx], sel, axis=1))
+        coef[idx, :t + 1] = x
+        R[idx] = Y[idx] - reconstruct3(D1, D2, D3, sel, x)
+    res_energy = energy[np.arange(N), np.minimum(nnz, s)]
+    return ReplayResult(energy=energy, best=best, best_q=best_q, best_piv2=best_piv2,
+                        best_Att=best_Att, pick=pick, pick_piv2=pick_piv2, pick_Att=pick_Att,
+                        coef=coef, res_energy=res_energy)
 
 
 class Update3Result:

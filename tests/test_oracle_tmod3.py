@@ -121,3 +121,51 @@ def test_three_mode_updates_are_monotone():
         first = it.rmse[0] if first is None else first
         Ds = it.D
     assert it.rmse[2] < first          # learning fits the planted model better
+
+
+def test_replay3_of_own_sequence_reproduces_pursuit():
+    Y, _, _, _ = synth.kron_model3(150, (4, 4, 4), (8, 8, 8), 4, 20.0, seed=81)
+    rng = np.random.default_rng(1)
+    Ds = [synth.random_dictionary(4, 8, rng) for _ in range(3)]
+    ref = tmod3.omp3d(Y, *Ds, 4)
+    rp = tmod3.omp3d_replay(Y, *Ds, ref.support, ref.nnz, 4)
+    assert np.array_equal(rp.best_q, ref.support)
+    assert np.array_equal(rp.pick, rp.best)
+    assert np.allclose(rp.coef, ref.coef, rtol=1e-12, atol=1e-14)
+    assert np.allclose(rp.res_energy, ref.res_energy, rtol=1e-12)
+
+
+def test_replay3_forced_sequence_against_explicit_kronecker():
+    """Forced triple sequences on 2x3x2 cubes against D3 (x) D2 (x) D1 written
+    out: correlations of the explicit residual, lstsq fit, pivot^2 as the
+    squared distance from the span of the selected atoms."""
+    rng = np.random.default_rng(7)
+    p, n, s, N = (2, 3, 2), (3, 4, 2), 4, 20
+    Ds = [synth.random_dictionary(p[m], n[m], rng) for m in range(3)]
+    Y = rng.standard_normal((N,) + p)
+    Q = n[0] * n[1] * n[2]
+    sup = np.stack([rng.choice(Q, s, replace=False) for _ in range(N)]).astype(np.int64)
+    nnz = rng.integers(0, s + 1, N)
+    sup[np.arange(s)[None, :] >= nnz[:, None]] = -1
+    rp = tmod3.omp3d_replay(Y, *Ds, sup, nnz, s)
+    K = tmod3.kron3(*Ds)
+    for k in range(N):
+        y = Y[k].flatten(order="F")
+        S, r = [], y.copy()
+        for t in range(min(nnz[k] + 1, s)):
+            c = np.abs(K.T @ r)
+            c[S] = -1.0
+            assert np.isclose(rp.energy[k, t], r @ r, rtol=1e-10)
+            assert np.isclose(rp.best[k, t], c.max(), rtol=1e-10, atol=1e-13)
+            a = K[:, rp.best_q[k, t]]
+            proj = K[:, S] @ np.linalg.lstsq(K[:, S], a, rcond=None)[0] if S else 0.0
+            assert np.isclose(rp.best_piv2[k, t], np.sum((a - proj) ** 2), rtol=1e-8, atol=1e-12)
+            if t == nnz[k]:
+                break
+            assert np.isclose(rp.pick[k, t], c[sup[k, t]], rtol=1e-10, atol=1e-13)
+            S.append(int(sup[k, t]))
+            x, *_ = np.linalg.lstsq(K[:, S], y, rcond=None)
+            r = y - K[:, S] @ x
+        if S:
+            assert np.allclose(rp.coef[k, :len(S)], x, rtol=1e-9, atol=1e-11)
+        assert np.isclose(rp.res_energy[k], r @ r, rtol=1e-10)
