@@ -12,4 +12,5 @@ from .sdl_oracle import *  # noqa: F401,F403
 from . import denoise  # noqa: F401
 from . import mlp  # noqa: F401
 from . import ortho  # noqa: F401
+from . import shortlist  # noqa: F401
 from . import tmod3  # noqa: F401
