@@ -45,7 +45,7 @@ W = dict(N=200_000, p1=12, p2=12, n1=24, n2=24, s=6, n_images=64, image_seed=100
 WORKLOAD = ("image-patch learning: N=200000 mean-removed 12x12 FP32 patches from 64 seeded "
             "synthetic 512x512 images, D1,D2 12x24, s=6, one Algorithm-1 iteration per step")
 CPU_SAMPLE = 32768          # signals in the timed oracle sample (cpu_baseline)
-REF_SAMPLE = 4096           # signals per step of the reference arm
+REF_SAMPLE = 8192           # signals per step of the reference arm
 FLUSH_BYTES = 256 << 20     # > 129 MB L2
 
 
@@ -154,32 +154,83 @@ class ClockSampler:
 
 # ------------------------------------------------------------- CPU oracle
 _ORACLE_SNIPPET = r"""
-import sys, time, json
+import sys, time, json, os
 import numpy as np
 sys.path.insert(0, sys.argv[1])
 import oracle
-d = np.load(sys.argv[2])
-Y, D1, D2, s, reps = d["Y"], d["D1"], d["D2"], int(d["s"]), int(d["reps"])
-times = []
-for _ in range(reps):
-    t = time.perf_counter()
-    oracle.iterate(Y, D1, D2, s)
-    times.append(time.perf_counter() - t)
-print(json.dumps(times))
+
+
+def code_chunk(args):
+    Y, D1, D2, s = args
+    r = oracle.omp2d(Y, D1, D2, s)
+    return r.support, r.coef
+
+
+def iterate_pool(pool, nchunks, Y, D1, D2, s):
+    # Algorithm 1 with the two coding passes spread over worker processes by
+    # signal chunks (each signal's pursuit is independent); the dictionary
+    # updates, which sum over all signals, run here
+    parts = np.array_split(np.arange(Y.shape[0]), nchunks)
+
+    def code(Da, Db):
+        out = pool.map(code_chunk, [(Y[c], Da, Db, s) for c in parts])
+        return np.concatenate([o[0] for o in out]), np.concatenate([o[1] for o in out])
+
+    sa, ca = code(D1, D2)
+    upd_a = oracle.update_D1(Y, D1, D2, sa, ca)
+    sb, cb = code(upd_a.D, D2)
+    return oracle.update_D2(Y, upd_a.D, D2, sb, cb)
+
+
+if __name__ == "__main__":
+    d = np.load(sys.argv[2])
+    Y, D1, D2, s, reps, cores = d["Y"], d["D1"], d["D2"], int(d["s"]), int(d["reps"]), int(d["cores"])
+    times = []
+    if cores <= 1:
+        for _ in range(reps):
+            t = time.perf_counter()
+            r = oracle.iterate(Y, D1, D2, s)
+            times.append(time.perf_counter() - t)
+        if len(sys.argv) > 3:
+            N, p1, p2 = Y.shape
+            np.savez(sys.argv[3], D1=r.D1, D2=r.D2, support=r.support, nnz=r.nnz,
+                     rmse=np.array([r.rmse_after_D1, r.rmse_after_D2]))
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(code_chunk, [(Y[:8], D1, D2, s)] * cores)      # workers started and warm
+            for _ in range(reps):
+                t = time.perf_counter()
+                iterate_pool(pool, 4 * cores, Y, D1, D2, s)
+                times.append(time.perf_counter() - t)
+    print(json.dumps(times))
 """
 
 
-def time_oracle(Y, D1, D2, s, reps):
-    """Run the FP64 oracle (unmodified) on one host core in a child process;
-    returns the per-iteration wall times."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle(Y, D1, D2, s, reps, cores=1, result_path=None):
+    """Run the FP64 oracle (unmodified) in a child process: one iteration of
+    Algorithm 1 per rep, on one host thread (cores = 1; `result_path` then
+    receives its dictionaries, codes and RMSEs) or with its coding passes
+    spread over `cores` single-threaded worker processes.  Returns the wall
+    time of every rep."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     with tempfile.TemporaryDirectory() as td:
         path = os.path.join(td, "sample.npz")
-        np.savez(path, Y=Y, D1=D1, D2=D2, s=s, reps=reps)
-        out = subprocess.run([sys.executable, "-c", _ORACLE_SNIPPET, ROOT, path], env=env,
-                             capture_output=True, text=True, check=True)
+        script = os.path.join(td, "oracle_run.py")
+        with open(script, "w") as f:
+            f.write(_ORACLE_SNIPPET)
+        np.savez(path, Y=Y, D1=D1, D2=D2, s=s, reps=reps, cores=cores)
+        cmd = [sys.executable, script, ROOT, path] + ([result_path] if result_path else [])
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
@@ -215,7 +266,8 @@ def run_reference(args):
         return 0
     Y, D1, D2 = make_inputs()
     sample = Y[:REF_SAMPLE]
-    times = time_oracle(sample, D1, D2, W["s"], args.warmup + args.steps)[args.warmup:]
+    cores = host_cores()
+    times = time_oracle(sample, D1, D2, W["s"], args.warmup + args.steps, cores=cores)[args.warmup:]
     per_step = sum(times) / len(times)
     value = REF_SAMPLE / per_step
     line = {
@@ -224,9 +276,10 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_signals_per_step": REF_SAMPLE},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"first {REF_SAMPLE} of the 200000 patches, one full "
-                                   "Algorithm-1 iteration per step, FP64 numpy, 1 thread"},
+                                   "Algorithm-1 iteration per step, FP64 numpy, the coding passes "
+                                   f"over {cores} single-threaded worker processes"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -258,7 +311,7 @@ def run_ours(args):
     D2_0 = sdl.dictionary(torch.tensor(D2, dtype=torch.float32, device=dev))
     D1g, D2g = sdl.dictionary(D1_0.clone()), sdl.dictionary(D2_0.clone())
     codes = sdl.Codes.empty(N, s, dev)
-    rmse = torch.zeros(2, dtype=torch.float32, device=dev)
+    rmse = torch.zeros(2, dtype=torch.float64, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -301,7 +354,7 @@ def run_ours(args):
 
     batch = sdl.Batch(ctx, [dict(Y=Yg, D1=D1g, D2=D2g, s=s, codes=codes)], autotune=True,
                       graph=True)
-    rmse_b = torch.zeros(2, dtype=torch.float32, device=dev)
+    rmse_b = torch.zeros(2, dtype=torch.float64, device=dev)
     for _ in range(args.warmup):
         batch.iterate(rmse_out=rmse_b)
     ctx.check()
@@ -357,13 +410,13 @@ def run_ours(args):
              "D1": torch.empty((n1, p1), dtype=torch.float32, device=dev),
              "D2": torch.empty((n2, p2), dtype=torch.float32, device=dev),
              "codes": sdl.Codes.empty(N, s, dev),
-             "rmse": torch.zeros(2, dtype=torch.float32, device=dev),
+             "rmse": torch.zeros(2, dtype=torch.float64, device=dev),
              "in": torch.cuda.Event(), "done": torch.cuda.Event(), "out": torch.cuda.Event()}
         S["host"] = {"D1": torch.empty_like(D1h).pin_memory(), "D2": torch.empty_like(D2h).pin_memory(),
                      "support": torch.empty((N, s), dtype=torch.int32).pin_memory(),
                      "coef": torch.empty((N, s), dtype=torch.float32).pin_memory(),
                      "nnz": torch.empty((N,), dtype=torch.int32).pin_memory(),
-                     "rmse": torch.empty(2, dtype=torch.float32).pin_memory()}
+                     "rmse": torch.empty(2, dtype=torch.float64).pin_memory()}
         S["batch"] = sdl.Batch(ctx, [dict(Y=S["Y"].transpose(1, 2), D1=S["D1"].t(), D2=S["D2"].t(),
                                           s=s, codes=S["codes"])], autotune=True, graph=True)
         sets.append(S)
@@ -428,22 +481,57 @@ def run_ours(args):
         peaks = measured_peaks()
         props = torch.cuda.get_device_properties(dev)
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+        fp32_derived = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+        # the FP32 FMA peak, measured on this GPU (packed fma.rn.f32x2, as the coders issue)
+        fp32_peak, _ = sdl.fp32_fma_peak(packed=True)
+        fp32_scalar, _ = sdl.fp32_fma_peak(packed=False)
         kinds = {k: v for k, v in prof.items() if v[1] > 0}
         dom = max(kinds, key=lambda k: kinds[k][0])
         dom_ms, dom_n = kinds[dom]
         side = {"code_D1": 1, "code_D2": 2}.get(dom, 2)
         flops = N * flops_per_signal_pass(p1, p2, n1, n2, s, side)
         achieved = flops / (dom_ms / dom_n / 1e3) / 1e12
-        traffic = None
+        traffic = issue = None
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
+        clk = clk.summary()
         if os.path.exists(tpath):
             t = json.load(open(tpath))
             ent = t.get(f"{dom}/tiling{tiling}")
             if ent and ent.get("source_hash") == source_hash() and ent.get("N") == N:
                 traffic = ent["dram_bytes_per_launch"]
-        cpu_times = time_oracle(Y[:CPU_SAMPLE], D1, D2, s, 1)
-        clk = clk.summary()
+                inst = ent.get("warp_instructions_per_launch")
+                if inst:
+                    # instruction-issue bound: every SM sub-partition issues at
+                    # most one warp instruction per cycle
+                    mhz = (clk or {}).get("sm_mhz") or sm_max
+                    bound_ms = inst / (props.multi_processor_count * 4 * mhz * 1e6) * 1e3
+                    issue = {"warp_instructions_per_signal": inst / N,
+                             "bound_ms": bound_ms, "kernel_ms": dom_ms / dom_n,
+                             "frac": bound_ms / (dom_ms / dom_n), "sm_mhz": mhz}
+        # the oracle on a bounded sample: one thread (its results also judge
+        # the GPU below), and its coding passes spread over every host core
+        with tempfile.TemporaryDirectory() as td:
+            res_path = os.path.join(td, "oracle.npz")
+            cpu_times = time_oracle(Y[:CPU_SAMPLE], D1, D2, s, 1, cores=1, result_path=res_path)
+            ores = dict(np.load(res_path))
+        cores = host_cores()
+        cpu_all = time_oracle(Y[:CPU_SAMPLE], D1, D2, s, 1, cores=cores) if cores > 1 else cpu_times
+        # matched RMSE: the same iteration on the GPU over the oracle's sample
+        Ys = sdl.signals(torch.from_numpy(Y32[:CPU_SAMPLE]).to(dev))
+        D1s, D2s = sdl.dictionary(D1_0.clone()), sdl.dictionary(D2_0.clone())
+        rm = torch.zeros(2, dtype=torch.float64, device=dev)
+        cs = ctx.iterate(Ys, D1s, D2s, s, rmse_out=rm)
+        ctx.check()
+        rm = rm.cpu().numpy()
+        same = ((cs.support.cpu().numpy() == ores["support"]).all(axis=1) &
+                (cs.nnz.cpu().numpy() == ores["nnz"]))
+        parity = {"sample": f"first {CPU_SAMPLE} patches, one Algorithm-1 iteration from the same "
+                            "start, GPU sdl_iterate (FP32) against the FP64 oracle",
+                  "rmse_rel_err": [float(abs(rm[i] - ores["rmse"][i]) / ores["rmse"][i]) for i in range(2)],
+                  "dict_max_abs_err": [float(np.abs(D1s.cpu().numpy() - ores["D1"]).max()),
+                                       float(np.abs(D2s.cpu().numpy() - ores["D2"]).max())],
+                  "supports_identical": float(same.mean()),
+                  "tolerance": 1e-4}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -465,15 +553,21 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": f"{dom} (tiling {tiling})", "achieved": achieved,
                          "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                         "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes "
-                                       f"x 2 x {sm_max:.0f} MHz",
+                         "peak_basis": "measured: FP32 FMA microbenchmark (sdl_fp32_fma_peak, packed "
+                                       f"fma.rn.f32x2; scalar fma.rn.f32 {fp32_scalar:.1f}); derived "
+                                       f"{props.multi_processor_count} SMs x 128 lanes x 2 x "
+                                       f"{sm_max:.0f} MHz = {fp32_derived:.1f}",
                          "algorithmic_flops_per_launch": flops,
+                         "issue": issue,
                          "hbm_gbs": N * bytes_per_signal_pass(p1, p2, s, side) /
                                     (dom_ms / dom_n / 1e3) / 1e9},
-            "cpu_baseline": {"value": CPU_SAMPLE / cpu_times[0], "unit": UNIT, "cores": 1,
+            "parity": parity,
+            "cpu_baseline": {"value": CPU_SAMPLE / cpu_all[0], "unit": UNIT, "cores": cores,
                              "kind": "oracle",
                              "sample": f"first {CPU_SAMPLE} of the 200000 patches, one full "
-                                       "Algorithm-1 iteration, FP64 numpy, 1 thread"},
+                                       "Algorithm-1 iteration, FP64 numpy, the coding passes over "
+                                       f"{cores} single-threaded worker processes",
+                             "single_thread": {"value": CPU_SAMPLE / cpu_times[0], "cores": 1}},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / args.steps,
                     "path": "sdl_batch_iterate (graph replay) per step from pinned host buffers; copies "
@@ -520,7 +614,7 @@ def study_precision(args):
     ctx = sdl.Context(0)
     Yg = sdl.signals(torch.tensor(Y, dtype=torch.float32, device=dev))
     codes = sdl.Codes.empty(N, s, dev)
-    rmse = torch.zeros(2, dtype=torch.float32, device=dev)
+    rmse = torch.zeros(2, dtype=torch.float64, device=dev)
     C = sdl.Context
     modes = {"fp32": C.PREC_FP32, "bf16_rescored": C.PREC_BF16_CORR,
              "fp64_solve": C.PREC_FP64_SOLVE, "bf16_fp64": C.PREC_BF16_CORR | C.PREC_FP64_SOLVE}
@@ -639,7 +733,7 @@ def study_ortho(args):
     ctx = sdl.Context(0)
     Yg = sdl.signals(torch.tensor(Y, dtype=torch.float32, device=dev))
     codes = sdl.Codes.empty(N, s, dev)
-    rmse = torch.zeros(2, dtype=torch.float32, device=dev)
+    rmse = torch.zeros(2, dtype=torch.float64, device=dev)
     D1w, D2w = _device_dict(Qs[0], dev), _device_dict(Qs[1], dev)
     for _ in range(args.warmup):
         ctx.ortho_iterate(Yg, D1w, D2w, s, out=codes, rmse_out=rmse)
@@ -797,7 +891,7 @@ def study_tmod3(args):
         return [sdl.dictionary(torch.tensor(D, dtype=torch.float32, device=dev)) for D in Ds]
 
     codes = sdl.Codes.empty(N, s, dev)
-    rmse = torch.zeros(3, dtype=torch.float32, device=dev)
+    rmse = torch.zeros(3, dtype=torch.float64, device=dev)
     Dw = dicts()
     for _ in range(args.warmup):
         ctx.iterate3(Yg, *Dw, s, out=codes, rmse_out=rmse)

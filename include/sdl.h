@@ -120,15 +120,18 @@ int sdl_sparse_code(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
  *   D1   in/out: replaced by the normalised optimum on success; left
  *        unchanged if the update fails on the device (see sdl_status).
  *   coef in/out: rescaled by W1^{-1} (slot l times ||d1*_{i_l}||).
- *   objective_out: NULL or device float[2] = {objective of Eq. (1) before,
- *        after} the update, FP32.
+ *   objective_out: NULL or device double[2] = {objective of Eq. (1) before,
+ *        after} the update: sums over all signals kept in FP64 (the FP32
+ *        per-signal energies are added in compensated FP32 per warp and in
+ *        FP64 across warps; "after" uses the exact change identity of the
+ *        update, so the solve error enters only to second order).
  * Atoms used by no signal (zero row/column of P) are kept unchanged and the
  * normal equations are solved on the used atoms.
  */
 int sdl_update_D1(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
                   float* D1, int n1, const float* D2, int n2, int s_max,
                   const int32_t* support, float* coef,
-                  float* objective_out, void* stream);
+                  double* objective_out, void* stream);
 
 /*
  * sdl_update_D2 - optimal right dictionary for fixed codes (Result 1):
@@ -140,7 +143,7 @@ int sdl_update_D1(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
 int sdl_update_D2(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
                   const float* D1, int n1, float* D2, int n2, int s_max,
                   const int32_t* support, float* coef,
-                  float* objective_out, void* stream);
+                  double* objective_out, void* stream);
 
 /*
  * sdl_iterate - one iteration of Algorithm 1 on one GPU:
@@ -150,13 +153,13 @@ int sdl_update_D2(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
  *   4. D2 update (Result 1), and X_k <- X_k W2^{-1}.
  * D1, D2 in/out.  support/coef/nnz receive the codes of step 3 rescaled as
  * in step 4, consistent with the returned dictionaries.  rmse_out: NULL or
- * device float[2] = RMSE ||Y - D1 X D2^T||_F / sqrt(p1 p2 N) right after step
+ * device double[2] = RMSE ||Y - D1 X D2^T||_F / sqrt(p1 p2 N) right after step
  * 2 and right after step 4.  eps as in sdl_sparse_code.
  */
 int sdl_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
                 float* D1, int n1, float* D2, int n2, int s_max, float eps,
                 int32_t* support, float* coef, int32_t* nnz,
-                float* rmse_out, void* stream);
+                double* rmse_out, void* stream);
 
 /*
  * Batching: several independent dictionary-learning problems ("groups") that
@@ -210,9 +213,9 @@ int sdl_batch_create(sdl_ctx* ctx, const sdl_group* groups, int n_groups, int fl
 int sdl_batch_sparse_code(sdl_batch* batch, void* stream);
 
 /* One Algorithm-1 iteration of every group (graph replay when captured).
- * rmse_out: NULL or device float[2 * n_groups], for group g the RMSE after
+ * rmse_out: NULL or device double[2 * n_groups], for group g the RMSE after
  * its D1 update (2g) and after its D2 update (2g + 1). */
-int sdl_batch_iterate(sdl_batch* batch, float* rmse_out, void* stream);
+int sdl_batch_iterate(sdl_batch* batch, double* rmse_out, void* stream);
 
 /* Host arrays of n_groups (each may be NULL): chosen tiling id, CTAs given to
  * the group, and the measured (autotune) or modelled cost of one of its
@@ -416,6 +419,38 @@ int sdl_sparse_code_learned(sdl_ctx* ctx, sdl_mlp* mlp, const float* Y, int p1, 
                             float* guard_out, void* stream);
 
 /*
+ * The first two steps of sdl_sparse_code_learned on their own (no fallback),
+ * for callers that bring their own scores and for checking each step.
+ *
+ * sdl_learned_shortlists - per signal, rank the N x Q device FP32 scores
+ * (row k at scores + k*Q) by the order-preserving 16-bit key of each score
+ * (its upper 16 bits after flipping negative values, so that a larger float
+ * never has a smaller key), ties to the smaller pair index q; NaN scores never
+ * rank.  cand (device int32, N x k2): the k1 best pairs, then the next k2 - k1
+ * (the check set), -1 where fewer than k2 scores are valid.
+ * 1 <= k1 <= k2 <= Q <= 1024.
+ */
+int sdl_learned_shortlists(sdl_ctx* ctx, const float* scores, int64_t N, int Q, int k1, int k2,
+                           int32_t* cand, void* stream);
+
+/*
+ * sdl_sparse_code_shortlist - 2D-OMP whose greedy step looks only at the
+ * first k1 pairs of cand[k] (k2 entries per signal, -1 = none): the largest
+ * |correlation| over unselected candidates, ties to the smallest q, with the
+ * re-fit, energy identity and stopping rules of sdl_sparse_code (fixed
+ * s_max).  flag[k] = 1 when the signal's data is not finite, or when it took
+ * s_max picks and some check-set pair (cand[k][k1 .. k2-1]) correlates with
+ * its final residual more strongly than 0.7 x the smallest best-score among
+ * its picks (the learned coder's fallback test); else 0.  res_energy may be
+ * NULL.  1 <= k1 <= 32, k1 <= k2 <= k1 + 64.  Compiled for (p1,p2,n1,n2,s_max)
+ * = (12,12,24,24,6) and (8,8,16,16,4).
+ */
+int sdl_sparse_code_shortlist(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
+                              const float* D1, int n1, const float* D2, int n2, int s_max,
+                              const int32_t* cand, int k1, int k2, int32_t* support, float* coef,
+                              int32_t* nnz, float* res_energy, int32_t* flag, void* stream);
+
+/*
  * Orthonormal variant (Remark 1): square orthonormal dictionaries
  * (n1 = p1, n2 = p2, D^T D = I), codes X_k = T_s(D1^T Y_k D2) (the s largest
  * |entries|, ties to the smallest q = i + p1 j; a signal keeps fewer when the
@@ -441,14 +476,14 @@ int sdl_ortho_sparse_code(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t 
  * (D1, D2), D1 by Procrustes (a one-sided Jacobi SVD of the FP32 sum B, in
  * FP32), codes again with the new D1, D2 by Procrustes.  D1, D2 in/out (must
  * be orthonormal on entry); support/coef/nnz receive the second codes.
- * rmse_out: NULL or device float[2], the RMSE right after each update (with
+ * rmse_out: NULL or device double[2], the RMSE right after each update (with
  * the codes of the preceding coding pass).  A numerically rank-deficient B
  * (smallest singular value <= 1e-6 of the largest) records SDL_ERR_SINGULAR
  * and leaves that dictionary unchanged.  N >= 1.
  */
 int sdl_ortho_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N, float* D1,
                       float* D2, int s, float eps, int32_t* support, float* coef, int32_t* nnz,
-                      float* rmse_out, void* stream);
+                      double* rmse_out, void* stream);
 
 /*
  * Three-mode generalisation (Remark 3): signals Y_k of shape p1 x p2 x p3
@@ -474,12 +509,12 @@ int sdl_sparse_code3(sdl_ctx* ctx, const float* Y, int p1, int p2, int p3, int64
  * Y_(k) = D_k X_(k) T_k^T (T_k the Kronecker product of the other two
  * dictionaries), with the column normalisation.  D1, D2, D3 in/out;
  * support/coef/nnz receive the codes of the third pass rescaled by W3^{-1};
- * rmse_out: NULL or device float[3], the RMSE right after each update.
+ * rmse_out: NULL or device double[3], the RMSE right after each update.
  * Singular normal matrices follow sdl_update_D1.  N >= 1.
  */
 int sdl_iterate3(sdl_ctx* ctx, const float* Y, int p1, int p2, int p3, int64_t N, float* D1,
                  int n1, float* D2, int n2, float* D3, int n3, int s, int32_t* support,
-                 float* coef, int32_t* nnz, float* rmse_out, void* stream);
+                 float* coef, int32_t* nnz, double* rmse_out, void* stream);
 
 /*
  * sdl_sparse_code_static - the sparse coder of sdl_sparse_code with no
@@ -502,14 +537,36 @@ int sdl_iterate3(sdl_ctx* ctx, const float* Y, int p1, int p2, int p3, int64_t N
  *    of the last call (each call rewrites both Gram matrices before reading
  *    them).  Calls whose work overlaps on the GPU (different streams, no
  *    ordering between them) race on the array and give wrong codes.
- *  - Device-side errors are not recorded (no context): a signal with NaN/Inf
- *    gets nnz = 0.
+ *  - Device-side errors (a signal with NaN/Inf, which also gets nnz = 0; a
+ *    bounded wait for a signal copy that gave up, after which the remaining
+ *    signals of that warp are not coded) go to a second file-scope device
+ *    word shared by every allocation-free call on the device, kept until
+ *    sdl_static_status reads it.
+ *  - The device addresses of both arrays are cached per device ordinal; a
+ *    cudaDeviceReset of that device invalidates them (reload the library).
  */
 int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
                            const float* D1, int n1, const float* D2, int n2,
                            int s_max, float eps,
                            int32_t* support, float* coef, int32_t* nnz,
                            float* res_energy, void* stream);
+
+/* Synchronise `stream`, then return the first device-side error recorded by
+ * allocation-free calls on the current device since the previous
+ * sdl_static_status (SDL_OK if none) and clear it.  Allocates nothing. */
+int sdl_static_status(void* stream);
+
+/*
+ * sdl_fp32_fma_peak - FP32 fused multiply-add throughput of the current
+ * device, the denominator of the coding passes' roofline (those passes are
+ * bound by FP32 FMAs; the paper has no counterpart).  Times 12 launches of a
+ * kernel in which every thread runs 8 independent chains of packed
+ * fma.rn.f32x2 (packed = 1) or 16 chains of scalar fma.rn.f32 (packed = 0),
+ * 64 warps per SM, with CUDA events on `stream`, and returns the best of the
+ * last 10 in TFLOP/s (2 FLOP per multiply-add) and, if ms_out != NULL, its
+ * duration.  Changes no clock or other GPU setting.  Synchronous.
+ */
+int sdl_fp32_fma_peak(int packed, double* tflops_out, double* ms_out, void* stream);
 
 /*
  * Tracing: per-kernel device time and launch counts.  The paper reports only

@@ -17,8 +17,11 @@ from __future__ import annotations
 import hashlib
 import json
 import os
+import time
 
 import numpy as np
+
+from . import sdl
 
 __all__ = ["config_hash", "save", "load", "MetricsLog", "learn"]
 
@@ -89,15 +92,26 @@ def learn(ctx, Y, D1, D2, s: int, iterations: int, eps: float = 0.0, *, config: 
         raise ValueError("every must be at least 1")
     N = Y.shape[0]
     config = dict(config or {})
-    rmse = torch.zeros(2, dtype=torch.float32, device=Y.device)
+    rmse = torch.zeros(2, dtype=torch.float64, device=Y.device)
     codes = None
     for it in range(start + 1, iterations + 1):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        codes = ctx.iterate(Y, D1, D2, s, eps=eps, out=codes, rmse_out=rmse)
-        b.record()
-        b.synchronize()
-        ms = a.elapsed_time(b)
+        if Y.is_cuda:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            codes = ctx.iterate(Y, D1, D2, s, eps=eps, out=codes, rmse_out=rmse)
+            b.record()
+            b.synchronize()
+            ms = a.elapsed_time(b)
+        else:   # a stand-in context (host tests)
+            t0 = time.perf_counter()
+            codes = ctx.iterate(Y, D1, D2, s, eps=eps, out=codes, rmse_out=rmse)
+            ms = (time.perf_counter() - t0) * 1e3
+        # a device-side error (non-finite data, a singular normal matrix, a
+        # timed-out wait) leaves the dictionaries unusable: stop before this
+        # iteration is logged or checkpointed
+        code = ctx.status()
+        if code != 0:
+            raise sdl.SDLError(code, f"iteration {it}")
         if log is not None:
             hist = torch.bincount(codes.nnz.long(), minlength=s + 1).cpu().tolist()
             r = rmse.cpu().tolist()

@@ -131,7 +131,7 @@ int prepare_tc_pass(sdl_ctx* c, PassArgs& a, bool fill_y, cudaStream_t st) {
 
 // reduce -> solve for one dictionary side, using the partial sums in slots.
 int finish_update(sdl_ctx* c, int slots, int side, float* D, int p1, int p2, int64_t N, int n1,
-                  int n2, float* objective_out, float* rmse_out, cudaStream_t st,
+                  int n2, double* objective_out, double* rmse_out, cudaStream_t st,
                   float* G_out = nullptr) {
     const int p = side == kSideD1 ? p1 : p2;
     const int n = side == kSideD1 ? n1 : n2;
@@ -283,7 +283,7 @@ int sdl_sparse_code(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const
 
 static int update_common(sdl_ctx* c, int side, const float* Y, int p1, int p2, int64_t N,
                          const float* D1, float* D1w, int n1, const float* D2, float* D2w, int n2,
-                         int s, const int32_t* support, float* coef, float* objective_out,
+                         int s, const int32_t* support, float* coef, double* objective_out,
                          void* stream) {
     if (!valid_common(c, Y, p1, p2, N, n1, n2, s) || !D1 || !D2) return SDL_ERR_ARG;
     if (N > 0 && (!support || !coef)) return SDL_ERR_ARG;
@@ -314,21 +314,21 @@ static int update_common(sdl_ctx* c, int side, const float* Y, int p1, int p2, i
 
 int sdl_update_D1(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1, int n1,
                   const float* D2, int n2, int s, const int32_t* support, float* coef,
-                  float* objective_out, void* stream) {
+                  double* objective_out, void* stream) {
     return update_common(c, kSideD1, Y, p1, p2, N, D1, D1, n1, D2, nullptr, n2, s, support, coef,
                          objective_out, stream);
 }
 
 int sdl_update_D2(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, const float* D1, int n1,
                   float* D2, int n2, int s, const int32_t* support, float* coef,
-                  float* objective_out, void* stream) {
+                  double* objective_out, void* stream) {
     return update_common(c, kSideD2, Y, p1, p2, N, D1, nullptr, n1, D2, D2, n2, s, support, coef,
                          objective_out, stream);
 }
 
 int sdl_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1, int n1, float* D2,
                 int n2, int s, float eps, int32_t* support, float* coef, int32_t* nnz,
-                float* rmse_out, void* stream) {
+                double* rmse_out, void* stream) {
     if (!valid_common(c, Y, p1, p2, N, n1, n2, s) || !D1 || !D2) return SDL_ERR_ARG;
     if (N > 0 && (!support || !coef || !nnz)) return SDL_ERR_ARG;
     int rc = check_shape(p1, p2, n1, n2, s);

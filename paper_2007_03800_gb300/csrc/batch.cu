@@ -38,7 +38,7 @@ struct sdl_batch {
     ReduceDesc* d_red[2] = {nullptr, nullptr};
     SolveDesc* d_solve[2] = {nullptr, nullptr};
     RescaleDesc* d_rescale = nullptr;
-    float* rmse_stage = nullptr;
+    double* rmse_stage = nullptr;
     std::vector<PassArgs> args[3];
     std::vector<float*> G1, G2, red_f, norms;
     std::vector<double*> red_d, part_d;
@@ -177,7 +177,7 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
     const size_t o_red = take(sizeof(ReduceDesc) * 2 * G);
     const size_t o_sol = take(sizeof(SolveDesc) * 2 * G);
     const size_t o_res = take(sizeof(RescaleDesc) * G);
-    const size_t o_rmse = take(sizeof(float) * 2 * G);
+    const size_t o_rmse = take(sizeof(double) * 2 * G);
     if (cudaMalloc(&b->dmem, bytes) != cudaSuccess) {
         cudaGetLastError();
         destroy(b);
@@ -202,7 +202,7 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
     b->d_solve[0] = reinterpret_cast<SolveDesc*>(b->dmem + o_sol);
     b->d_solve[1] = b->d_solve[0] + G;
     b->d_rescale = reinterpret_cast<RescaleDesc*>(b->dmem + o_res);
-    b->rmse_stage = reinterpret_cast<float*>(b->dmem + o_rmse);
+    b->rmse_stage = reinterpret_cast<double*>(b->dmem + o_rmse);
 
     // ---- per-group pass arguments
     for (int side = 0; side < 3; ++side) b->args[side].resize(G);
@@ -514,7 +514,7 @@ int sdl_batch_sparse_code(sdl_batch* b, void* stream) {
     return code_pass(b, kCodeOnly, st);
 }
 
-int sdl_batch_iterate(sdl_batch* b, float* rmse_out, void* stream) {
+int sdl_batch_iterate(sdl_batch* b, double* rmse_out, void* stream) {
     if (!b) return SDL_ERR_ARG;
     sdl_ctx* c = b->ctx;
     DeviceGuard guard(c->device);
@@ -535,7 +535,7 @@ int sdl_batch_iterate(sdl_batch* b, float* rmse_out, void* stream) {
         rc = enqueue_iteration(b, st, true);
     }
     if (rc != SDL_OK) return rc;
-    if (rmse_out && cudaMemcpyAsync(rmse_out, b->rmse_stage, sizeof(float) * 2 * b->G,
+    if (rmse_out && cudaMemcpyAsync(rmse_out, b->rmse_stage, sizeof(double) * 2 * b->G,
                                     cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return SDL_ERR_CUDA;
     return SDL_OK;

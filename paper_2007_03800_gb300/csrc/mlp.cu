@@ -878,3 +878,54 @@ extern "C" int sdl_sparse_code_learned(sdl_ctx* c, sdl_mlp* m, const float* Y, i
     }
     return rc < 0 ? rc : SDL_OK;
 }
+
+// The two shortlist steps of sdl_sparse_code_learned on their own (before
+// any fallback), so that each can be checked against a reference.
+extern "C" int sdl_learned_shortlists(sdl_ctx* c, const float* scores, int64_t N, int Q, int k1,
+                                      int k2, int32_t* cand, void* stream) {
+    if (!c || N < 0 || N > 0x7fffffffLL || Q < 1 || Q > 1024 || k1 < 1 || k2 < k1 || k2 > Q)
+        return SDL_ERR_ARG;
+    if (N == 0) return SDL_OK;
+    if (!scores || !cand) return SDL_ERR_ARG;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Trace tr(c, kTopk, st);
+    const int blocks = blocks_for(N * 32, 256);
+    if (Q <= 256)
+        topk_kernel<8><<<blocks, 256, 0, st>>>(scores, Q, N, Q, k1, k2, cand);
+    else if (Q <= 576)
+        topk_kernel<18><<<blocks, 256, 0, st>>>(scores, Q, N, Q, k1, k2, cand);
+    else
+        topk_kernel<32><<<blocks, 256, 0, st>>>(scores, Q, N, Q, k1, k2, cand);
+    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+}
+
+extern "C" int sdl_sparse_code_shortlist(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N,
+                                         const float* D1, int n1, const float* D2, int n2,
+                                         int s_max, const int32_t* cand, int k1, int k2,
+                                         int32_t* support, float* coef, int32_t* nnz,
+                                         float* res_energy, int32_t* flag, void* stream) {
+    if (!c || !D1 || !D2 || N < 0 || N > 0x7fffffffLL || k1 < 1 || k1 > 32 || k2 < k1 ||
+        k2 > k1 + 32 * kCheck)
+        return SDL_ERR_ARG;
+    const bool shape_a = p1 == 12 && p2 == 12 && n1 == 24 && n2 == 24 && s_max == 6;
+    const bool shape_b = p1 == 8 && p2 == 8 && n1 == 16 && n2 == 16 && s_max == 4;
+    if (!shape_a && !shape_b) return SDL_ERR_UNSUPPORTED;
+    if (N == 0) return SDL_OK;
+    if (!Y || !cand || !support || !coef || !nnz || !flag) return SDL_ERR_ARG;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ctx_workspace(c, p1, p2, n1, n2);
+    if (rc) return rc;
+    {
+        Trace tr(c, kGram, st);
+        launch_gram2(D1, p1, n1, c->G1, D2, p2, n2, c->G2, st);
+    }
+    Trace tr(c, kShortlist, st);
+    return shape_a ? launch_shortlist<12, 12, 24, 24, 6>(Y, N, D1, D2, c->G1, c->G2, cand, k1, k2,
+                                                         support, coef, nnz, res_energy, flag,
+                                                         c->num_sms, st)
+                   : launch_shortlist<8, 8, 16, 16, 4>(Y, N, D1, D2, c->G1, c->G2, cand, k1, k2,
+                                                       support, coef, nnz, res_energy, flag,
+                                                       c->num_sms, st);
+}

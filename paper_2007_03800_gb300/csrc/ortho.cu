@@ -491,8 +491,8 @@ int launch_sq_side(const float* Y, long long N, const float* D1, const float* D2
 //   f(D) = sum ||Y||^2 - 2 tr(D^T B) + sum ||X||^2, and the change is
 //   -2 (sum sigma - tr(D_old^T B)) (accumulated in FP64).
 __global__ void procrustes_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d,
-                                  float* D, int n, double inv_count, float* objective_out,
-                                  float* rmse_out, int* err) {
+                                  float* D, int n, double inv_count, double* objective_out,
+                                  double* rmse_out, int* err) {
     extern __shared__ __align__(16) float smf[];
     const int m = (n + 1) & ~1;             // even number of columns (a zero column pads)
     float* A = smf;                          // m columns of length n (column-major)
@@ -637,10 +637,10 @@ __global__ void procrustes_kernel(const float* __restrict__ red_f, const double*
         const double before = red_d[0];
         const double after = ok ? before - 2.0 * (s_sig - s_tr) : before;
         if (objective_out) {
-            objective_out[0] = (float)before;
-            objective_out[1] = (float)after;
+            objective_out[0] = before;
+            objective_out[1] = after;
         }
-        if (rmse_out) rmse_out[0] = (float)sqrt(fmax(after, 0.0) * inv_count);
+        if (rmse_out) rmse_out[0] = sqrt(fmax(after, 0.0) * inv_count);
     }
 }
 
@@ -712,7 +712,7 @@ int launch_ortho_code(const float* Y, int p1, int p2, long long N, const float* 
 }
 
 int launch_procrustes(const float* red_f, const double* red_d, float* D, int n, double inv_count,
-                      float* objective_out, float* rmse_out, int* err, cudaStream_t st) {
+                      double* objective_out, double* rmse_out, int* err, cudaStream_t st) {
     const int m = (n + 1) & ~1;
     const size_t bytes = sizeof(float) * ((size_t)m * n + (size_t)m * m + m) +
                          sizeof(int) * (size_t)(m - 1) * (m / 2);
@@ -747,7 +747,7 @@ int sdl_ortho_sparse_code(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N,
 
 int sdl_ortho_iterate(sdl_ctx* c, const float* Y, int p1, int p2, int64_t N, float* D1, float* D2,
                       int s, float eps, int32_t* support, float* coef, int32_t* nnz,
-                      float* rmse_out, void* stream) {
+                      double* rmse_out, void* stream) {
     if (!c || N < 1 || !Y || !D1 || !D2 || !support || !coef || !nnz) return SDL_ERR_ARG;
     if (!ortho_shape_supported(p1, p2, s)) return SDL_ERR_ARG;
     DeviceGuard g(c->device);

@@ -115,7 +115,7 @@ void launch_gram2(const float* D1, int p1, int n1, float* G1, const float* D2, i
                   float* G2, cudaStream_t st);
 // G_out (may be NULL): receives the Gram matrix of D after the update.
 int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n,
-                 float* norms, double inv_count, float* objective_out, float* rmse_out,
+                 float* norms, double inv_count, double* objective_out, double* rmse_out,
                  int* err, cudaStream_t st, float* G_out = nullptr);
 
 void launch_rescale(const int32_t* support, float* coef, long long count, int n1, int n2,
@@ -143,8 +143,8 @@ struct SolveDesc {
     int p, n;
     float* norms;
     double inv_count;
-    float* objective_out;
-    float* rmse_out;
+    double* objective_out;
+    double* rmse_out;
     float* G_out;
     int keep_p;
 };
@@ -160,7 +160,7 @@ int launch_multi_update_kernels(int which, const void* d_desc, int G, int blocks
                                 int* err, cudaStream_t st);
 size_t solve_smem_bytes(int p, int n, int* keep_p);
 int launch_solve64(const float* red_f, const double* red_d, float* D, int p, int n, float* norms,
-                   double inv_count, float* objective_out, float* rmse_out, int* err,
+                   double inv_count, double* objective_out, double* rmse_out, int* err,
                    cudaStream_t st, float* G_out);
 }  // namespace sdl
 #include <cuda_bf16.h>

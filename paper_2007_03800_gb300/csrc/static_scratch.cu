@@ -24,25 +24,37 @@ namespace {
 constexpr int kStaticGramFloats = 8192;
 
 static __device__ __align__(256) float g_static_gram[kStaticGramFloats];
+// Error word of the allocation-free calls on this device (SDL_OK or the first
+// device-side error since it was last read by sdl_static_status).
+static __device__ int g_static_err;
 
 constexpr int kMaxDevices = 64;
-// Device address of g_static_gram per device ordinal, looked up once per
-// device (with that device current) on its first call.
+// Device addresses of g_static_gram and g_static_err per device ordinal,
+// looked up once per device (with that device current) on its first call.
+// They stay valid for the life of the device's primary context: after a
+// cudaDeviceReset of that device the library must be reloaded.
 std::atomic<float*> g_static_addr[kMaxDevices];
+std::atomic<int*> g_static_err_addr[kMaxDevices];
 
-int static_scratch(int device, float** out) {
+int static_scratch(int device, float** out, int** err) {
     if (device < 0 || device >= kMaxDevices) return SDL_ERR_ARG;
     float* p = g_static_addr[device].load(std::memory_order_acquire);
-    if (!p) {
+    int* e = g_static_err_addr[device].load(std::memory_order_acquire);
+    if (!p || !e) {
         void* addr = nullptr;
-        if (cudaGetSymbolAddress(&addr, g_static_gram) != cudaSuccess || !addr) {
+        void* eaddr = nullptr;
+        if (cudaGetSymbolAddress(&addr, g_static_gram) != cudaSuccess || !addr ||
+            cudaGetSymbolAddress(&eaddr, g_static_err) != cudaSuccess || !eaddr) {
             cudaGetLastError();
             return SDL_ERR_CUDA;
         }
         p = static_cast<float*>(addr);
+        e = static_cast<int*>(eaddr);
         g_static_addr[device].store(p, std::memory_order_release);
+        g_static_err_addr[device].store(e, std::memory_order_release);
     }
     *out = p;
+    *err = e;
     return SDL_OK;
 }
 
@@ -67,7 +79,8 @@ extern "C" int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
         return SDL_ERR_CUDA;
     }
     float* scratch = nullptr;
-    int rc = static_scratch(device, &scratch);
+    int* err = nullptr;
+    int rc = static_scratch(device, &scratch, &err);
     if (rc != SDL_OK) return rc;
     int num_sms = 0;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
@@ -80,7 +93,9 @@ extern "C" int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
     // Both Grams are fully rewritten before the coding pass reads them, so
     // nothing left over from an earlier call is used.
     launch_gram(D1, p1, n1, G1, st);
+    if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
     launch_gram(D2, p2, n2, G2, st);
+    if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
 
     PassArgs a{};
     a.Y = Y;
@@ -100,8 +115,28 @@ extern "C" int sdl_sparse_code_static(const float* Y, int p1, int p2, int64_t N,
     a.nnz = nnz;
     a.res_energy = res_energy;
     a.n_slots = 1;
-    a.err = nullptr;   // no context: a non-finite signal shows up only as nnz = 0
+    a.err = err;       // read by sdl_static_status
     rc = launch_code_pass(a, kCodeOnly, st, num_sms);
-    if (rc < 0) return rc;
-    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+    return rc < 0 ? rc : SDL_OK;
+}
+
+extern "C" int sdl_static_status(void* stream) {
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return SDL_ERR_CUDA;
+    }
+    float* scratch = nullptr;
+    int* err = nullptr;
+    int rc = static_scratch(device, &scratch, &err);
+    if (rc != SDL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = SDL_OK;
+    if (cudaMemcpyAsync(&v, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return SDL_ERR_CUDA;
+    }
+    return v;
 }

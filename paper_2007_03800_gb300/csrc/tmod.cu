@@ -157,7 +157,7 @@ constexpr int kSolveThreads = 512;
 __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
                                            const double* __restrict__ red_d, float* D, int p,
                                            int n, float* __restrict__ norms, double inv_count,
-                                           float* objective_out, float* rmse_out, int* err,
+                                           double* objective_out, double* rmse_out, int* err,
                                            float* G_out, int keep_p) {
     extern __shared__ __align__(16) float sm[];
     // keep_p bit 0: a copy of P_u stays in shared memory; bit 1: the inverse
@@ -338,17 +338,17 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
         const double before = red_d[0];
         const double after = ok ? before + change : before;
         if (objective_out) {
-            objective_out[0] = (float)before;
-            objective_out[1] = (float)after;
+            objective_out[0] = before;
+            objective_out[1] = after;
         }
-        if (rmse_out) rmse_out[0] = (float)sqrt(fmax(after, 0.0) * inv_count);
+        if (rmse_out) rmse_out[0] = sqrt(fmax(after, 0.0) * inv_count);
     }
 }
 
 __global__ void __launch_bounds__(kSolveThreads)
     solve_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D, int p,
-                 int n, float* __restrict__ norms, double inv_count, float* objective_out,
-                 float* rmse_out, int* err, float* G_out, int keep_p) {
+                 int n, float* __restrict__ norms, double inv_count, double* objective_out,
+                 double* rmse_out, int* err, float* G_out, int keep_p) {
     solve_body(red_f, red_d, D, p, n, norms, inv_count, objective_out, rmse_out, err, G_out,
                keep_p);
 }
@@ -373,7 +373,7 @@ constexpr double kSolvePivotRel64 = 1e-12;
 __global__ void __launch_bounds__(kSolve64Threads)
     solve64_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D,
                    int p, int n, float* __restrict__ norms, double inv_count,
-                   float* objective_out, float* rmse_out, int* err, float* G_out) {
+                   double* objective_out, double* rmse_out, int* err, float* G_out) {
     extern __shared__ __align__(16) double smd[];
     const int lda = n | 1;
     double* A = smd;                        // nu x nu (stride lda)
@@ -505,10 +505,10 @@ __global__ void __launch_bounds__(kSolve64Threads)
         const double before = red_d[0];
         const double after = ok ? before + change : before;
         if (objective_out) {
-            objective_out[0] = (float)before;
-            objective_out[1] = (float)after;
+            objective_out[0] = before;
+            objective_out[1] = after;
         }
-        if (rmse_out) rmse_out[0] = (float)sqrt(fmax(after, 0.0) * inv_count);
+        if (rmse_out) rmse_out[0] = sqrt(fmax(after, 0.0) * inv_count);
     }
 }
 
@@ -630,7 +630,7 @@ void launch_reduce_partials(const float* part_f, const double* part_d, int n_slo
 }
 
 int launch_solve64(const float* red_f, const double* red_d, float* D, int p, int n, float* norms,
-                   double inv_count, float* objective_out, float* rmse_out, int* err,
+                   double inv_count, double* objective_out, double* rmse_out, int* err,
                    cudaStream_t st, float* G_out) {
     const size_t lda = (size_t)(n | 1);
     const size_t bytes = sizeof(double) * ((size_t)n * lda + (size_t)p * lda +
@@ -646,7 +646,7 @@ int launch_solve64(const float* red_f, const double* red_d, float* D, int p, int
 }
 
 int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n, float* norms,
-                 double inv_count, float* objective_out, float* rmse_out, int* err,
+                 double inv_count, double* objective_out, double* rmse_out, int* err,
                  cudaStream_t st, float* G_out) {
     // keep a copy of P in shared memory for the objective term when it fits
     int keep_p = 0;

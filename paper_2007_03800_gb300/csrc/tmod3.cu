@@ -428,7 +428,7 @@ int sdl_sparse_code3(sdl_ctx* c, const float* Y, int p1, int p2, int p3, int64_t
 
 int sdl_iterate3(sdl_ctx* c, const float* Y, int p1, int p2, int p3, int64_t N, float* D1, int n1,
                  float* D2, int n2, float* D3, int n3, int s, int32_t* support, float* coef,
-                 int32_t* nnz, float* rmse_out, void* stream) {
+                 int32_t* nnz, double* rmse_out, void* stream) {
     const Shape3 h{p1, p2, p3, n1, n2, n3};
     if (!c || N < 1 || !Y || !D1 || !D2 || !D3 || !support || !coef || !nnz || !shape3_ok(h, s))
         return SDL_ERR_ARG;

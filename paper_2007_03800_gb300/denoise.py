@@ -43,7 +43,7 @@ def denoise(ctx: sdl.Context, noisy: torch.Tensor, sigma: float, groups=DEFAULT_
         meta.append(dict(p=p, n=n, s=s, means=means))
     mark()
     batch = sdl.Batch(ctx, specs, autotune=autotune, graph=graph, stream=stream)
-    rmse = torch.zeros(2 * len(specs), dtype=torch.float32, device=noisy.device)
+    rmse = torch.zeros(2 * len(specs), dtype=torch.float64, device=noisy.device)
     mark()
     traj = []
     for _ in range(iterations):

@@ -44,6 +44,8 @@ SIGNATURES = {
     "sdl_update_D2": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _P, _P, _P],
     "sdl_iterate": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
     "sdl_sparse_code_static": [_P, _I, _I, _L, _P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
+    "sdl_static_status": [_P],
+    "sdl_fp32_fma_peak": [_I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
     "sdl_batch_create": [_P, _P, _I, _I, _P, ctypes.POINTER(_P)],
     "sdl_batch_sparse_code": [_P, _P],
     "sdl_batch_iterate": [_P, _P, _P],
@@ -64,6 +66,9 @@ SIGNATURES = {
     "sdl_mlp_forward": [_P, _P, _L, _P, _P],
     "sdl_sparse_code_learned": [_P, _P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P,
                                 _P, _P, _P, _P],
+    "sdl_learned_shortlists": [_P, _P, _L, _I, _I, _I, _P, _P],
+    "sdl_sparse_code_shortlist": [_P, _P, _I, _I, _L, _P, _I, _P, _I, _I, _P, _I, _I, _P, _P, _P, _P,
+                                  _P, _P],
     "sdl_ortho_sparse_code": [_P, _P, _I, _I, _L, _P, _P, _I, _F, _P, _P, _P, _P, _P],
     "sdl_ortho_iterate": [_P, _P, _I, _I, _L, _P, _P, _I, _F, _P, _P, _P, _P, _P],
     "sdl_selftest_timeout": [_P, ctypes.c_longlong, _P],
@@ -203,6 +208,22 @@ def sparse_code_static(Y, D1, D2, s, eps=0.0, out: "Codes | None" = None, stream
     return out
 
 
+def static_status(stream=None) -> int:
+    """``sdl_static_status``: the first device-side error of the
+    allocation-free calls on the current device since the last query (0 if
+    none), cleared by the query."""
+    return lib().sdl_static_status(_stream(stream))
+
+
+def fp32_fma_peak(packed=True, stream=None):
+    """``sdl_fp32_fma_peak``: measured FP32 FMA throughput of the current
+    device in TFLOP/s, and the duration (ms) of the timed launch."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().sdl_fp32_fma_peak(1 if packed else 0, ctypes.byref(tf), ctypes.byref(ms),
+                                   _stream(stream)), "sdl_fp32_fma_peak")
+    return tf.value, ms.value
+
+
 class Codes:
     """Sparse codes of N signals: support (N, s) int32 pair indices q = i + n1*j
     (-1 unused), coef (N, s) float32, nnz (N,) int32."""
@@ -301,7 +322,7 @@ class Context:
         _need(codes.support, torch.int32, (N, s), None, "support")
         _need(codes.coef, torch.float32, (N, s), None, "coef")
         if objective_out is not None:
-            _need(objective_out, torch.float32, (2,), None, "objective_out")
+            _need(objective_out, torch.float64, (2,), None, "objective_out")
         rc = fn(self._h, _ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2, s,
                 _ptr(codes.support), _ptr(codes.coef), _ptr(objective_out), _stream(stream))
         return rc
@@ -327,12 +348,38 @@ class Context:
         _need(out.coef, torch.float32, (N, s), None, "coef")
         _need(out.nnz, torch.int32, (N,), None, "nnz")
         if rmse_out is not None:
-            _need(rmse_out, torch.float32, (2,), None, "rmse_out")
+            _need(rmse_out, torch.float64, (2,), None, "rmse_out")
         rc = self._lib.sdl_iterate(self._h, _ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2, s,
                                    float(eps), _ptr(out.support), _ptr(out.coef), _ptr(out.nnz),
                                    _ptr(rmse_out), _stream(stream))
         _check(rc, "sdl_iterate")
         return out
+
+    # ---- the learned coder's shortlist steps on their own
+    def learned_shortlists(self, scores, k1, k2, stream=None):
+        """``sdl_learned_shortlists``: (N, k2) int32 candidate lists from
+        (N, Q) FP32 scores (the k1-best shortlist, then the check set)."""
+        N, Q = scores.shape
+        _need(scores, torch.float32, (N, Q), (Q, 1), "scores")
+        cand = torch.empty((N, k2), dtype=torch.int32, device=scores.device)
+        _check(self._lib.sdl_learned_shortlists(self._h, _ptr(scores), N, Q, int(k1), int(k2),
+                                                _ptr(cand), _stream(stream)), "sdl_learned_shortlists")
+        return cand
+
+    def sparse_code_shortlist(self, Y, D1, D2, s, cand, k1, stream=None):
+        """``sdl_sparse_code_shortlist``: 2D-OMP over the first k1 pairs of
+        each candidate list, without fallback; returns (codes, flags)."""
+        N, p1, p2 = _check_Y(Y)
+        n1, n2 = _check_D(D1, p1, "D1"), _check_D(D2, p2, "D2")
+        k2 = cand.shape[1]
+        _need(cand, torch.int32, (N, k2), (k2, 1), "cand")
+        out = Codes.empty(N, s, Y.device, with_energy=True)
+        flag = torch.empty((N,), dtype=torch.int32, device=Y.device)
+        _check(self._lib.sdl_sparse_code_shortlist(
+            self._h, _ptr(Y), p1, p2, N, _ptr(D1), n1, _ptr(D2), n2, s, _ptr(cand), int(k1), int(k2),
+            _ptr(out.support), _ptr(out.coef), _ptr(out.nnz), _ptr(out.res_energy), _ptr(flag),
+            _stream(stream)), "sdl_sparse_code_shortlist")
+        return out, flag
 
     # ---- coder tilings
     def set_tiling(self, p1, p2, n1, n2, s, tiling, ctas_per_sm=0) -> None:
@@ -375,7 +422,7 @@ class Context:
         if out is None:
             out = Codes.empty(N, s, Y.device)
         if rmse_out is not None:
-            _need(rmse_out, torch.float32, (3,), None, "rmse_out")
+            _need(rmse_out, torch.float64, (3,), None, "rmse_out")
         _check(self._lib.sdl_iterate3(
             self._h, _ptr(Y), p1, p2, p3, N, _ptr(D1), n1, _ptr(D2), n2, _ptr(D3), n3, s,
             _ptr(out.support), _ptr(out.coef), _ptr(out.nnz), _ptr(rmse_out), _stream(stream)),
@@ -410,7 +457,7 @@ class Context:
         _need(out.coef, torch.float32, (N, s), None, "coef")
         _need(out.nnz, torch.int32, (N,), None, "nnz")
         if rmse_out is not None:
-            _need(rmse_out, torch.float32, (2,), None, "rmse_out")
+            _need(rmse_out, torch.float64, (2,), None, "rmse_out")
         _check(self._lib.sdl_ortho_iterate(
             self._h, _ptr(Y), p1, p2, N, _ptr(D1), _ptr(D2), s, float(eps), _ptr(out.support),
             _ptr(out.coef), _ptr(out.nnz), _ptr(rmse_out), _stream(stream)), "sdl_ortho_iterate")
@@ -468,7 +515,7 @@ class Batch:
 
     def iterate(self, rmse_out=None, stream=None):
         if rmse_out is not None:
-            _need(rmse_out, torch.float32, (2 * len(self.groups),), None, "rmse_out")
+            _need(rmse_out, torch.float64, (2 * len(self.groups),), None, "rmse_out")
         _check(self._lib.sdl_batch_iterate(self._h, _ptr(rmse_out), _stream(stream)),
                "sdl_batch_iterate")
 

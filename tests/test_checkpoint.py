@@ -2,6 +2,7 @@
 CPU; on the GPU, a run resumed from a checkpoint follows the uninterrupted
 run."""
 import json
+import os
 
 import numpy as np
 import pytest
@@ -46,6 +47,64 @@ def test_metrics_log_is_json_lines(tmp_path):
 def test_learn_rejects_a_zero_checkpoint_interval():
     with pytest.raises(ValueError):
         ck.learn(None, np.zeros((1, 2, 2)), None, None, 1, 1, every=0)
+
+
+class _FailingContext:
+    """Stand-in context: iterations run, the device error word reports
+    SDL_ERR_NONFINITE from iteration `bad` on."""
+
+    def __init__(self, bad):
+        self.bad, self.calls = bad, 0
+
+    def iterate(self, Y, D1, D2, s, eps=0.0, out=None, rmse_out=None):
+        import torch
+
+        from paper_2007_03800_gb300 import sdl
+        self.calls += 1
+        N = Y.shape[0]
+        return sdl.Codes(torch.zeros((N, s), dtype=torch.int32), torch.zeros((N, s)),
+                         torch.full((N,), s, dtype=torch.int32))
+
+    def status(self):
+        return -3 if self.calls >= self.bad else 0
+
+
+def test_learn_stops_on_a_device_error_without_checkpointing(tmp_path):
+    """A device-side error reported after an iteration stops learn() before
+    that iteration is logged or checkpointed; earlier iterations stand."""
+    import torch
+
+    from paper_2007_03800_gb300 import sdl
+    Y = torch.zeros((4, 2, 2))
+    D1, D2 = torch.zeros((2, 3)), torch.zeros((2, 3))
+    path = str(tmp_path / "ck.npz")
+    log = ck.MetricsLog(str(tmp_path / "m.jsonl"))
+    with pytest.raises(sdl.SDLError) as e:
+        ck.learn(_FailingContext(bad=1), Y, D1, D2, 2, 3, checkpoint=path, log=log)
+    assert e.value.code == -3
+    assert not os.path.exists(path) and log.read() == []
+    with pytest.raises(sdl.SDLError):
+        ck.learn(_FailingContext(bad=3), Y, D1, D2, 2, 5, checkpoint=path, log=log)
+    assert [r["iteration"] for r in log.read()] == [1, 2]
+    assert ck.load(path)["iteration"] == 2
+
+
+@pytest.mark.gpu
+def test_learn_refuses_to_checkpoint_non_finite_data(gpu_ctx, tmp_path):
+    import torch
+
+    from paper_2007_03800_gb300 import sdl, synth
+    Y, _, _, _, _ = synth.kron_model(512, 8, 8, 16, 16, 4, 20.0, seed=11)
+    Y[5, 1, 1] = np.nan
+    D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
+    Yg = sdl.signals(torch.tensor(Y, dtype=torch.float32, device="cuda:0"))
+    D1g = sdl.dictionary(torch.tensor(D1, dtype=torch.float32, device="cuda:0"))
+    D2g = sdl.dictionary(torch.tensor(D2, dtype=torch.float32, device="cuda:0"))
+    path = str(tmp_path / "ck.npz")
+    with pytest.raises(sdl.SDLError) as e:
+        ck.learn(gpu_ctx, Yg, D1g, D2g, 4, 2, checkpoint=path)
+    assert sdl.ERRORS[e.value.code] == "SDL_ERR_NONFINITE"
+    assert not os.path.exists(path)
 
 
 @pytest.mark.gpu

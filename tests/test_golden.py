@@ -204,7 +204,7 @@ def test_gpu_tmod_update_golden(gpu_ctx, name, side):
     e = d["expected"]
     Yg, D1g, D2g = to_gpu_problem(arr(d["Y"]), arr(d["D1"]), arr(d["D2"]))
     codes = codes_from_oracle(np.asarray(d["support"]), arr(d["coef"]))
-    obj = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    obj = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     (gpu_ctx.update_D1 if side == 1 else gpu_ctx.update_D2)(Yg, D1g, D2g, codes, objective_out=obj)
     assert gpu_ctx.status() == 0
     D = (D1g if side == 1 else D2g).cpu().numpy()

@@ -8,8 +8,7 @@ import torch
 
 import oracle
 from paper_2007_03800_gb300 import sdl, synth
-from parity import (COEF_RTOL, DICT_RTOL, RMSE_RTOL, coef_rel_error, compare_supports,
-                    to_gpu_problem)
+from parity import check_codes, check_iteration, to_gpu_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -50,10 +49,8 @@ def test_batch_sparse_code_matches_oracle_and_single_calls(gpu_ctx):
         eps = g["eps"] or None
         ref = oracle.omp2d(g["Y"], g["D1"], g["D2"], g["s"], eps=eps)
         codes = spec["codes"]
-        rep, exact = compare_supports(codes.support.cpu().numpy(), codes.nnz.cpu().numpy(), ref,
-                                      eps=eps)
-        assert rep.bad == 0 and rep.ties <= max(2, 2e-3 * rep.n), rep
-        assert coef_rel_error(codes.coef.cpu().numpy(), ref.coef, exact).max(initial=0) < COEF_RTOL
+        check_codes(g["Y"], g["D1"], g["D2"], g["s"], codes.support.cpu().numpy(), codes.nnz.cpu().numpy(),
+                    codes.coef.cpu().numpy(), eps=eps, ref=ref).assert_ok()
         # every lane tiling performs the same per-entry arithmetic: identical codes
         single = gpu_ctx.sparse_code(spec["Y"], spec["D1"], spec["D2"], spec["s"], eps=spec["eps"])
         assert torch.equal(single.support, codes.support)
@@ -80,21 +77,15 @@ def test_batch_iterate_matches_oracle(gpu_ctx):
     groups = make_groups(seed=1)
     specs = to_specs(groups)
     batch = sdl.Batch(gpu_ctx, specs, autotune=True, graph=True)
-    rmse = torch.zeros(6, dtype=torch.float32, device="cuda:0")
+    rmse = torch.zeros(6, dtype=torch.float64, device="cuda:0")
     batch.iterate(rmse_out=rmse)
     assert gpu_ctx.status() == 0
     r = rmse.cpu().numpy()
     for g, (grp, spec) in enumerate(zip(groups, batch.groups)):
-        ref = oracle.iterate(grp["Y"], grp["D1"], grp["D2"], grp["s"], eps=grp["eps"] or None)
-        assert abs(r[2 * g] - ref.rmse_after_D1) / ref.rmse_after_D1 < RMSE_RTOL, (g, r, ref.rmse_after_D1)
-        assert abs(r[2 * g + 1] - ref.rmse_after_D2) / ref.rmse_after_D2 < RMSE_RTOL
-        assert np.abs(spec["D1"].cpu().numpy() - ref.D1).max() < DICT_RTOL
-        assert np.abs(spec["D2"].cpu().numpy() - ref.D2).max() < DICT_RTOL
         codes = spec["codes"]
-        rep, exact = compare_supports(codes.support.cpu().numpy(), codes.nnz.cpu().numpy(),
-                                      ref.omp_b, eps=grp["eps"] or None)
-        assert rep.bad == 0, rep
-        assert coef_rel_error(codes.coef.cpu().numpy(), ref.coef, exact).max(initial=0) < COEF_RTOL
+        check_iteration(grp["Y"], grp["D1"], grp["D2"], grp["s"], codes.support.cpu().numpy(),
+                        codes.nnz.cpu().numpy(), codes.coef.cpu().numpy(), spec["D1"].cpu().numpy(),
+                        spec["D2"].cpu().numpy(), r[2 * g:2 * g + 2], eps=grp["eps"] or None)
     batch.close()
 
 
@@ -106,7 +97,7 @@ def test_graph_replay_equals_direct_launches(gpu_ctx):
     for graph in (False, True):
         specs = to_specs(groups)
         batch = sdl.Batch(gpu_ctx, specs, autotune=False, graph=graph)
-        rmse = torch.zeros(6, dtype=torch.float32, device="cuda:0")
+        rmse = torch.zeros(6, dtype=torch.float64, device="cuda:0")
         for _ in range(3):
             batch.iterate(rmse_out=rmse)
         assert gpu_ctx.status() == 0
@@ -137,18 +128,13 @@ def test_one_group_batch_runs_its_tiling_kernel_and_matches_oracle(gpu_ctx, grap
     for gr in (False, graph):
         spec = to_specs([g])
         batch = sdl.Batch(gpu_ctx, spec, autotune=False, graph=gr)
-        rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+        rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
         batch.iterate(rmse_out=rmse)
         assert gpu_ctx.status() == 0
         s = batch.groups[0]
-        r = rmse.cpu().numpy()
-        assert abs(r[0] - ref.rmse_after_D1) / ref.rmse_after_D1 < RMSE_RTOL
-        assert abs(r[1] - ref.rmse_after_D2) / ref.rmse_after_D2 < RMSE_RTOL
-        assert np.abs(s["D1"].cpu().numpy() - ref.D1).max() < DICT_RTOL
-        assert np.abs(s["D2"].cpu().numpy() - ref.D2).max() < DICT_RTOL
-        rep, exact = compare_supports(s["codes"].support.cpu().numpy(), s["codes"].nnz.cpu().numpy(),
-                                      ref.omp_b, eps=g["eps"] or None)
-        assert rep.bad == 0, rep
+        check_iteration(g["Y"], g["D1"], g["D2"], g["s"], s["codes"].support.cpu().numpy(),
+                        s["codes"].nnz.cpu().numpy(), s["codes"].coef.cpu().numpy(), s["D1"].cpu().numpy(),
+                        s["D2"].cpu().numpy(), rmse.cpu().numpy(), eps=g["eps"] or None, ref=ref)
         results.append((s["D1"].clone(), s["D2"].clone(), s["codes"].coef.clone(), rmse.clone()))
         batch.close()
     for x, y in zip(*results):
@@ -167,7 +153,7 @@ def test_one_group_batch_equals_the_per_call_path_at_full_size(gpu_ctx):
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
     D1b, D2b = D1g.clone(), D2g.clone()
     batch = sdl.Batch(gpu_ctx, [dict(Y=Yg, D1=D1b, D2=D2b, s=6, eps=0.0)], autotune=True, graph=True)
-    rmse_b = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    rmse_b = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     batch.iterate(rmse_out=rmse_b)
     assert gpu_ctx.status() == 0
     t = batch.tuning()[0]
@@ -175,7 +161,7 @@ def test_one_group_batch_equals_the_per_call_path_at_full_size(gpu_ctx):
     assert t["ctas"] % sms == 0
     try:
         gpu_ctx.set_tiling(12, 12, 24, 24, 6, t["shape_id"], t["ctas"] // sms)
-        rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+        rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
         out = gpu_ctx.iterate(Yg, D1g, D2g, 6, rmse_out=rmse)
         assert gpu_ctx.status() == 0
     finally:
@@ -184,6 +170,6 @@ def test_one_group_batch_equals_the_per_call_path_at_full_size(gpu_ctx):
     assert torch.equal(D1g, batch.groups[0]["D1"]) and torch.equal(D2g, batch.groups[0]["D2"])
     assert torch.equal(out.support, codes.support) and torch.equal(out.coef, codes.coef)
     # the objective change is an FP64 sum split over a different number of solve
-    # threads: equal up to its last bit
-    assert torch.allclose(rmse, rmse_b, rtol=1e-6, atol=0)
+    # threads: equal up to rounding
+    assert torch.allclose(rmse, rmse_b, rtol=1e-9, atol=0)
     batch.close()

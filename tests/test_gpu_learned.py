@@ -105,3 +105,76 @@ def test_rmse_guard_recodes_everything_when_the_shortlists_miss(gpu_ctx):
     e = plain.res_energy.double().cpu().numpy()[rows]
     assert abs(g[1] - np.sqrt(e.sum() / (m * p * p))) < 1e-5 * g[1]
     net.close()
+
+
+# ---------------------------------------------- the shortlist steps, element by element
+def test_shortlists_equal_the_oracle_ranking(gpu_ctx):
+    """Top-k (k1 = 32) and check set (k2 = 96) of 100 000 signals x 576 pair
+    scores, bit for bit against the oracle's stable sort on a strided sample
+    of 5000 signals: planted exact ties, scores that differ only below the
+    16-bit key (ranked by pair index), NaN scores and rows with fewer valid
+    scores than k2."""
+    from oracle import shortlist as osl
+    rng = np.random.default_rng(91)
+    N, Q, k1, k2 = 100_000, 576, 32, 96
+    S = rng.standard_normal((N, Q)).astype(np.float32)
+    S[:, 100] = S[:, 7]                                             # exact ties
+    S[:, 300] = np.nextafter(S[:, 301], np.float32(np.inf))         # equal keys
+    S[::997, :500] = np.nan                                         # 76 valid scores only
+    S[5::1013, 200:260] = np.nan
+    Sg = torch.tensor(S, device="cuda:0")
+    cand = gpu_ctx.learned_shortlists(Sg, k1, k2).cpu().numpy()
+    assert gpu_ctx.status() == 0
+    rows = np.arange(0, N, 20)
+    ref = osl.shortlists(S[rows], k1, k2)
+    assert np.array_equal(cand[rows], ref)
+
+
+def test_shortlist_coder_matches_restricted_oracle(gpu_ctx):
+    """2D-OMP restricted to given candidate lists, at the learned coder's
+    shapes (12x12 signals, 24x24 atom pairs, s = 6, k1 = 32, k2 = 96) on
+    100 000 signals of the separable model: on a strided sample of 3000 the
+    picks equal the restricted oracle's (ties at the first difference
+    counted and bounded), coefficients and energies within 1e-4, and the
+    fallback flags equal the oracle's rule except where the check score sits
+    within 1e-4 of its threshold."""
+    from oracle import shortlist as osl
+    p, n, s, k1, k2, N = 12, 24, 6, 32, 96, 100_000
+    Y, D1, D2, sup_true, _ = synth.kron_model(N, p, p, n, n, s, 20.0, seed=93)
+    rng = np.random.default_rng(94)
+    cand = np.empty((N, k2), dtype=np.int64)
+    for k in range(N):
+        others = rng.choice(np.setdiff1d(np.arange(n * n), sup_true[k]), k2 - s, replace=False)
+        first = rng.permutation(np.concatenate([sup_true[k], others[:k1 - s]]))
+        cand[k] = np.concatenate([first, others[k1 - s:]])
+    cand[::50, k1 - 5:k1] = -1                                      # shorter shortlists
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    cg = torch.tensor(cand, dtype=torch.int32, device="cuda:0")
+    codes, flag = gpu_ctx.sparse_code_shortlist(Yg, D1g, D2g, s, cg, k1)
+    assert gpu_ctx.status() == 0
+    rows = np.arange(0, N, N // 3000)
+    ref = osl.omp2d_restricted(Y[rows], D1, D2, s, cand[rows, :k1])
+    sup = codes.support.cpu().numpy()[rows]
+    nnz = codes.nnz.cpu().numpy()[rows]
+    same = np.all(sup == ref.support, axis=1) & (nnz == ref.nnz)
+    ties = 0
+    for r in np.nonzero(~same)[0]:
+        t = int(np.nonzero(sup[r] != ref.support[r])[0][0])
+        hit = np.nonzero(ref.top_q[r, t] == sup[r, t])[0]
+        assert hit.size and ref.top_val[r, t, hit[0]] >= (1 - 1e-6) * ref.top_val[r, t, 0], (r, t)
+        ties += 1
+    assert ties <= max(2, 2e-3 * rows.size), ties
+    coef = codes.coef.cpu().numpy()[rows].astype(np.float64)
+    err = np.linalg.norm(coef - ref.coef, axis=1) / np.maximum(np.linalg.norm(ref.coef, axis=1), 1e-30)
+    assert err[same].max() < 1e-4
+    e = codes.res_energy.cpu().numpy()[rows].astype(np.float64)
+    yy = np.sum(Y[rows] ** 2, axis=(1, 2))
+    assert np.max(np.abs(e - ref.res_energy)[same] / (ref.res_energy + 1e-5 * yy)[same]) < 1e-3
+    maxe, worst = osl.check_scores(Y[rows], D1, D2, ref, cand[rows, k1:])
+    want = (ref.nnz == s) & (maxe > osl.CHECK_MARGIN * worst)
+    got = flag.cpu().numpy()[rows] == 1
+    near = np.abs(maxe - osl.CHECK_MARGIN * worst) <= 1e-4 * worst
+    bad = (got != want) & same & ~near
+    assert not bad.any(), np.nonzero(bad)[0][:5]
+    print(f"shortlist coder: {same.mean():.4f} identical, {ties} ties, "
+          f"{want.mean():.3f} flagged, {(got != want).sum()} flag differences near the threshold")

@@ -71,7 +71,7 @@ def test_ortho_iteration_matches_oracle(gpu_ctx, p, s):
     D1, D2 = orth(1, p), orth(2, p)
     ref = ortho.ortho_iterate(Y, D1, D2, s)
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
-    rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     out = gpu_ctx.ortho_iterate(Yg, D1g, D2g, s, rmse_out=rmse)
     assert gpu_ctx.status() == 0
     r = rmse.cpu().numpy()
@@ -90,7 +90,7 @@ def test_ortho_ten_iterations_rmse_trajectory(gpu_ctx):
     Y = ortho_model(4096, p, s, seed=70)
     D1, D2 = orth(1, p), orth(2, p)
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
-    rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     out = None
     for it in range(10):
         ref = ortho.ortho_iterate(Y, D1, D2, s)

@@ -1,9 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Inputs come from the seeded generators only; expected values come from the
-oracle only.  Supports must match pick for pick except at argmax ties the
-oracle itself shows (counted); coefficients, dictionaries and RMSE must match
-within 1e-4 relative.
+oracle only.  Supports must match pick for pick except at argmax ties and
+stop thresholds the oracle itself shows (counted, bounded, and every step of
+such a signal checked by the oracle's replay of its picks); coefficients,
+residual energies, dictionaries and RMSE must match within 1e-4 relative.
 """
 import numpy as np
 import pytest
@@ -11,8 +12,8 @@ import torch
 
 import oracle
 from paper_2007_03800_gb300 import sdl, synth
-from parity import (COEF_RTOL, DICT_RTOL, RMSE_RTOL, codes_from_oracle, coef_rel_error,
-                    compare_supports, to_gpu_problem)
+from parity import (COEF_RTOL, DICT_RTOL, RMSE_RTOL, check_codes, check_iteration,
+                    codes_from_oracle, coef_rel_error, to_gpu_problem)
 
 pytestmark = pytest.mark.gpu
 
@@ -25,18 +26,23 @@ def run_code(ctx, Y, D1, D2, s, eps=0.0):
             out.res_energy.cpu().numpy())
 
 
-def check_code(ctx, Y, D1, D2, s, eps=None, max_tie_frac=2e-3):
-    ref = oracle.omp2d(Y, D1, D2, s, eps=eps)
+def check_code(ctx, Y, D1, D2, s, eps=None, ref=None):
     sup, coef, nnz, energy = run_code(ctx, Y, D1, D2, s, eps=eps or 0.0)
-    rep, exact = compare_supports(sup, nnz, ref, eps=eps)
-    assert rep.bad == 0, rep
-    assert rep.ties <= max(2, max_tie_frac * rep.n), rep
-    err = coef_rel_error(coef, ref.coef, exact)
-    assert err.max(initial=0.0) < COEF_RTOL, (err.max(), rep)
-    ynorm = np.sum(np.asarray(Y) ** 2, axis=(1, 2))
-    e_err = np.abs(energy[exact] - ref.res_energy[exact]) / (ref.res_energy[exact] + 1e-5 * ynorm[exact])
-    assert e_err.max(initial=0.0) < 1e-3
+    rep = check_codes(Y, D1, D2, s, sup, nnz, coef, energy, eps=eps, ref=ref)
+    rep.assert_ok()
     return rep
+
+
+def iterate_and_check(ctx, Y, D1, D2, s, eps=None, ref=None, out=None, Ygpu=None):
+    """One sdl_iterate on copies of (D1, D2), judged by check_iteration."""
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2) if Ygpu is None else Ygpu
+    D1i, D2i = sdl.dictionary(D1g.clone()), sdl.dictionary(D2g.clone())
+    rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+    got = ctx.iterate(Yg, D1i, D2i, s, eps=eps or 0.0, out=out, rmse_out=rmse)
+    assert ctx.status() == 0
+    return check_iteration(Y, D1, D2, s, got.support.cpu().numpy(), got.nnz.cpu().numpy(),
+                           got.coef.cpu().numpy(), D1i.cpu().numpy(), D2i.cpu().numpy(),
+                           rmse.cpu().numpy(), eps=eps, ref=ref)
 
 
 # ----------------------------------------------------------------- sparse coding
@@ -116,7 +122,7 @@ def test_update_matches_oracle(gpu_ctx, p1, p2, n1, n2, s, N, side):
                                                                 ref_code.coef)
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
     codes = codes_from_oracle(ref_code.support, ref_code.coef)
-    obj = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    obj = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     (gpu_ctx.update_D1 if side == 1 else gpu_ctx.update_D2)(Yg, D1g, D2g, codes, objective_out=obj)
     assert gpu_ctx.status() == 0
     D = (D1g if side == 1 else D2g).cpu().numpy()
@@ -152,20 +158,7 @@ def test_update_keeps_unused_atom(gpu_ctx):
 def test_iterate_one_step(gpu_ctx):
     Y, _, _, _, _ = synth.kron_model(4096, 8, 8, 16, 16, 4, 20.0, seed=11)
     D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
-    ref = oracle.iterate(Y, D1, D2, 4)
-    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
-    rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
-    out = gpu_ctx.iterate(Yg, D1g, D2g, 4, rmse_out=rmse)
-    assert gpu_ctx.status() == 0
-    r = rmse.cpu().numpy()
-    assert abs(r[0] - ref.rmse_after_D1) / ref.rmse_after_D1 < RMSE_RTOL
-    assert abs(r[1] - ref.rmse_after_D2) / ref.rmse_after_D2 < RMSE_RTOL
-    assert np.abs(D1g.cpu().numpy() - ref.D1).max() < DICT_RTOL
-    assert np.abs(D2g.cpu().numpy() - ref.D2).max() < DICT_RTOL
-    rep, exact = compare_supports(out.support.cpu().numpy(), out.nnz.cpu().numpy(), ref.omp_b)
-    assert rep.bad == 0 and rep.ties <= 4, rep
-    err = coef_rel_error(out.coef.cpu().numpy(), ref.coef, exact)
-    assert err.max() < COEF_RTOL
+    iterate_and_check(gpu_ctx, Y, D1, D2, 4)
 
 
 def test_iterate_ten_steps_rmse_trajectory(gpu_ctx):
@@ -174,7 +167,7 @@ def test_iterate_ten_steps_rmse_trajectory(gpu_ctx):
     Y, _, _, _, _ = synth.kron_model(4096, 8, 8, 16, 16, 4, 20.0, seed=11)
     D1, D2 = synth.init_dictionaries(8, 8, 16, 16, seed=1)
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
-    rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     out = None
     for it in range(10):
         ref = oracle.iterate(Y, D1, D2, 4)
@@ -197,12 +190,11 @@ def test_iterate_full_size_properties(gpu_ctx):
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
     codes = gpu_ctx.sparse_code(Yg, D1g, D2g, 6)
     rows = np.random.default_rng(0).choice(200_000, 1500, replace=False)
-    ref = oracle.omp2d(Y[rows], D1, D2, 6)
-    rep, exact = compare_supports(codes.support.cpu().numpy()[rows], codes.nnz.cpu().numpy()[rows], ref)
-    assert rep.bad == 0 and rep.ties <= 3, rep
-    assert coef_rel_error(codes.coef.cpu().numpy()[rows], ref.coef, exact).max() < COEF_RTOL
+    rep = check_codes(Y[rows], D1, D2, 6, codes.support.cpu().numpy()[rows], codes.nnz.cpu().numpy()[rows],
+                      codes.coef.cpu().numpy()[rows], codes.res_energy.cpu().numpy()[rows])
+    rep.assert_ok()
 
-    rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     out = gpu_ctx.iterate(Yg, D1g, D2g, 6, rmse_out=rmse)
     assert gpu_ctx.status() == 0
     D1n, D2n = D1g.cpu().numpy().astype(np.float64), D2g.cpu().numpy().astype(np.float64)
@@ -314,20 +306,12 @@ def test_every_tiling_gives_identical_codes_and_matches_oracle(gpu_ctx, p1, n1, 
                         base = first_eps
                     for x, y in zip(got, base):
                         assert torch.equal(x, y), (t, cps, e)
-                    rep, exact = compare_supports(got[0].numpy(), got[2].numpy(), r,
-                                                  eps=(e or None))
-                    assert rep.bad == 0 and rep.ties <= max(2, 2e-3 * rep.n), (t, rep)
-                    assert coef_rel_error(got[1].numpy(), r.coef, exact).max(initial=0) < COEF_RTOL
+                    if got is base:   # identical codes: the oracle judges them once
+                        check_codes(Y, D1, D2, s, *(v.numpy() for v in got), eps=(e or None),
+                                    ref=r).assert_ok()
             for e, r in ((0.0, it_ref), (eps, it_ref_eps)):
-                D1i, D2i = D1g.clone(), D2g.clone()
-                rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
-                gpu_ctx.iterate(Yg, D1i, D2i, s, eps=e, rmse_out=rmse)
-                assert gpu_ctx.status() == 0
-                rm = rmse.cpu().numpy()
-                assert abs(rm[0] - r.rmse_after_D1) / r.rmse_after_D1 < RMSE_RTOL, (t, e, rm)
-                assert abs(rm[1] - r.rmse_after_D2) / r.rmse_after_D2 < RMSE_RTOL, (t, e, rm)
-                assert np.abs(D1i.cpu().numpy() - r.D1).max() < DICT_RTOL, (t, e)
-                assert np.abs(D2i.cpu().numpy() - r.D2).max() < DICT_RTOL, (t, e)
+                iterate_and_check(gpu_ctx, Y, D1, D2, s, eps=(e or None), ref=r,
+                                  Ygpu=(Yg, D1g, D2g))
     finally:
         gpu_ctx.set_tiling(p1, p1, n1, n1, s, -1)
 
@@ -344,9 +328,8 @@ def test_tune_tiling_pins_the_fastest(gpu_ctx):
         assert min(log, key=lambda e: e["us"])["tiling"] == tid
         codes = gpu_ctx.sparse_code(Yg, D1g, D2g, 6)
         rows = np.arange(0, 20_000, 17)
-        ref = oracle.omp2d(Y[rows], D1, D2, 6)
-        rep, exact = compare_supports(codes.support.cpu().numpy()[rows], codes.nnz.cpu().numpy()[rows], ref)
-        assert rep.bad == 0, rep
+        check_codes(Y[rows], D1, D2, 6, codes.support.cpu().numpy()[rows], codes.nnz.cpu().numpy()[rows],
+                    codes.coef.cpu().numpy()[rows], codes.res_energy.cpu().numpy()[rows]).assert_ok()
     finally:
         gpu_ctx.set_tiling(12, 12, 24, 24, 6, -1)
     with pytest.raises(sdl.SDLError):
@@ -377,7 +360,8 @@ def test_exact_tie_picks_the_smallest_pair_index_in_every_tiling(gpu_ctx, p1, n1
             sup = out.support.cpu().numpy()
             assert np.all(sup[:, 0] == 3 + n1 * j), t
             assert not np.any(sup == (5 + n1 * j)[:, None]), t     # the duplicate never joins
-            rep, exact = compare_supports(sup, out.nnz.cpu().numpy(), ref)
-            assert rep.bad == 0, (t, rep)
+            rep = check_codes(Y, D1, D2, s, sup, out.nnz.cpu().numpy(), out.coef.cpu().numpy(),
+                              out.res_energy.cpu().numpy(), ref=ref)
+            rep.assert_ok()   # both sides resolve the planted exact ties to the smaller q
     finally:
         gpu_ctx.set_tiling(p1, p1, n1, n1, s, -1)

@@ -6,8 +6,8 @@ import torch
 
 import oracle
 from paper_2007_03800_gb300 import sdl, synth
-from parity import (COEF_RTOL, DICT_RTOL, RMSE_RTOL, codes_from_oracle, coef_rel_error,
-                    compare_supports, to_gpu_problem)
+from parity import (DICT_RTOL, RMSE_RTOL, check_codes, check_iteration, codes_from_oracle,
+                    coef_rel_error, to_gpu_problem)
 
 pytestmark = pytest.mark.gpu
 
@@ -77,15 +77,14 @@ def test_bf16_rescored_picks_match_oracle(prec_ctx):
     out = prec_ctx.sparse_code(Yg, D1g, D2g, 10)
     assert prec_ctx.status() == 0
     assert prec_ctx.precision_stats() > 0
-    rep, exact = compare_supports(out.support.cpu().numpy(), out.nnz.cpu().numpy(), ref)
-    assert rep.bad == 0 and rep.ties <= 2, rep
-    assert coef_rel_error(out.coef.cpu().numpy(), ref.coef, exact).max() < COEF_RTOL
+    check_codes(Y, D1, D2, 10, out.support.cpu().numpy(), out.nnz.cpu().numpy(),
+                out.coef.cpu().numpy(), ref=ref).assert_ok()
     # without re-scoring (a diagnostic mode) the split-BF16 picks carry no
     # guarantee, but the split keeps C0 within ~1e-4 ||Y||: nearly all agree
     prec_ctx.set_precision(sdl.Context.PREC_BF16_CORR | sdl.Context.PREC_NO_RESCORE)
     raw = prec_ctx.sparse_code(Yg, D1g, D2g, 10)
     assert prec_ctx.status() == 0
-    rep_raw, _ = compare_supports(raw.support.cpu().numpy(), raw.nnz.cpu().numpy(), ref)
+    rep_raw = check_codes(Y, D1, D2, 10, raw.support.cpu().numpy(), raw.nnz.cpu().numpy(), ref=ref)
     assert rep_raw.exact >= 0.9 * rep_raw.n, rep_raw
 
 
@@ -98,7 +97,7 @@ def test_fp64_solve_matches_oracle(prec_ctx, side):
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
     codes = codes_from_oracle(ref_code.support, ref_code.coef)
     prec_ctx.set_precision(sdl.Context.PREC_FP64_SOLVE)
-    obj = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    obj = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     (prec_ctx.update_D1 if side == 1 else prec_ctx.update_D2)(Yg, D1g, D2g, codes, objective_out=obj)
     assert prec_ctx.status() == 0
     D = (D1g if side == 1 else D2g).cpu().numpy()
@@ -120,17 +119,12 @@ def test_bf16_fp64_iteration_matches_oracle(prec_ctx):
     ref = oracle.iterate(Y, D1, D2, 10)
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
     prec_ctx.set_precision(sdl.Context.PREC_BF16_CORR | sdl.Context.PREC_FP64_SOLVE)
-    rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+    rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     out = prec_ctx.iterate(Yg, D1g, D2g, 10, rmse_out=rmse)
     assert prec_ctx.status() == 0
-    r = rmse.cpu().numpy()
-    assert abs(r[0] - ref.rmse_after_D1) / ref.rmse_after_D1 < RMSE_RTOL
-    assert abs(r[1] - ref.rmse_after_D2) / ref.rmse_after_D2 < RMSE_RTOL
-    assert np.abs(D1g.cpu().numpy() - ref.D1).max() < DICT_RTOL
-    assert np.abs(D2g.cpu().numpy() - ref.D2).max() < DICT_RTOL
-    rep, exact = compare_supports(out.support.cpu().numpy(), out.nnz.cpu().numpy(), ref.omp_b)
-    assert rep.bad == 0 and rep.ties <= 2, rep
-    assert coef_rel_error(out.coef.cpu().numpy(), ref.coef, exact).max() < COEF_RTOL
+    check_iteration(Y, D1, D2, 10, out.support.cpu().numpy(), out.nnz.cpu().numpy(),
+                    out.coef.cpu().numpy(), D1g.cpu().numpy(), D2g.cpu().numpy(), rmse.cpu().numpy(),
+                    ref=ref)
 
 
 MODES = {
@@ -143,20 +137,29 @@ MODES = {
 
 
 def study_errors(ctx, Y, D1, D2, s, ref):
+    """Every mode's error after one iteration.  The second pass is judged by
+    check_codes with the oracle's new D1; D2, the coefficients and the final
+    RMSE are compared with the oracle's D2 update replayed on each mode's own
+    supports (so a tie resolved the other way does not hide the comparison)."""
     rows = {}
+    N, p1, p2 = Y.shape
     for name, flags in MODES.items():
         Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
         ctx.set_precision(flags)
-        rmse = torch.zeros(2, dtype=torch.float32, device="cuda:0")
+        rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
         out = ctx.iterate(Yg, D1g, D2g, s, rmse_out=rmse)
         assert ctx.status() == 0
         r = rmse.cpu().numpy()
-        rep, exact = compare_supports(out.support.cpu().numpy(), out.nnz.cpu().numpy(), ref.omp_b)
+        sup = out.support.cpu().numpy().astype(np.int64)
+        rep = check_codes(Y, ref.upd_a.D, D2, s, sup, out.nnz.cpu().numpy(), ref=ref.omp_b)
+        upd = oracle.update_D2(Y, ref.upd_a.D, D2, np.where(rep.ok_rows[:, None], sup, -1), rep.ref_coef)
+        want = float(np.sqrt(upd.obj_after / (p1 * p2 * N)))
         rows[name] = dict(
-            rmse_rel=float(abs(r[1] - ref.rmse_after_D2) / ref.rmse_after_D2),
+            rmse_rel=float(abs(r[1] - want) / want),
             D1_abs=float(np.abs(D1g.cpu().numpy() - ref.D1).max()),
-            D2_abs=float(np.abs(D2g.cpu().numpy() - ref.D2).max()),
-            exact=rep.exact / rep.n, ties=rep.ties, bad=rep.bad,
+            D2_abs=float(np.abs(D2g.cpu().numpy() - upd.D).max()),
+            coef_err=float(coef_rel_error(out.coef.cpu().numpy(), upd.coef, rep.ok_rows).max(initial=0)),
+            exact=rep.exact / rep.n, ties=rep.ties, threshold=rep.threshold, bad=rep.bad,
             rescored=ctx.precision_stats())
     ctx.set_precision(0)
     return rows
@@ -176,18 +179,16 @@ def test_hsi_precision_study(prec_ctx):
     Y, D1, D2 = hsi_problem(800, seed=35)
     ref = oracle.iterate(Y, D1, D2, 10)
     rows = study_errors(prec_ctx, Y, D1, D2, 10, ref)
-    print("\nmode            rmse_rel   D1_abs     D2_abs     exact  ties bad rescored")
+    print("\nmode            rmse_rel   D1_abs     D2_abs     coef_err   exact  ties thr bad rescored")
     for name, e in rows.items():
-        print(f"{name:15s} {e['rmse_rel']:.2e}  {e['D1_abs']:.2e}  {e['D2_abs']:.2e}  "
-              f"{e['exact']:.3f} {e['ties']:4d} {e['bad']:3d} {e['rescored']}")
+        print(f"{name:15s} {e['rmse_rel']:.2e}  {e['D1_abs']:.2e}  {e['D2_abs']:.2e}  {e['coef_err']:.2e}  "
+              f"{e['exact']:.3f} {e['ties']:4d} {e['threshold']:3d} {e['bad']:3d} {e['rescored']}")
+    n = Y.shape[0]
     for name in ("fp32", "bf16", "fp64_solve", "bf16_fp64"):
         e = rows[name]
         assert e["rmse_rel"] < RMSE_RTOL, (name, e)
         assert e["bad"] == 0, (name, e)
+        assert e["ties"] + e["threshold"] <= max(2, 2e-3 * n), (name, e)
         assert e["D1_abs"] < 1e-3, (name, e)
-        # one tie resolved the other way in the second pass changes M by that
-        # signal's terms, which cond(M) ~ 6e4 amplifies: D2 is compared only
-        # when every pick of the second pass agrees
-        if e["ties"] == 0:
-            assert e["D2_abs"] < 1e-3, (name, e)
+        assert e["D2_abs"] < 1e-3, (name, e)
 

@@ -42,6 +42,38 @@ def test_static_matches_context_entry_point_two_calls(gpu_ctx):
         assert rel.max() < COEF_RTOL
         e_ref, e_got = ref.res_energy.cpu().numpy(), got.res_energy.cpu().numpy()
         assert np.allclose(e_got, e_ref, rtol=1e-5, atol=1e-6)
+        assert sdl.static_status() == 0
+
+
+def test_static_generic_path_and_no_energy_output(gpu_ctx):
+    """A signal array that is not 16-byte aligned (a view one float in) runs
+    the generic coder instead of the bulk-copy one, and res_energy may be
+    omitted: both still equal the context-based coder."""
+    Yg, D1g, D2g = _problem(5, 12, 24, 6, 2001)
+    flat = torch.empty(Yg.numel() + 1, dtype=torch.float32, device="cuda:0")
+    Yv = flat[1:].view(Yg.shape[0], Yg.shape[2], Yg.shape[1]).transpose(1, 2)   # column-major signals
+    Yv.copy_(Yg)
+    assert Yv.data_ptr() % 16 != 0
+    ref = gpu_ctx.sparse_code(Yg, D1g, D2g, 6)
+    out = sdl.Codes.empty(Yg.shape[0], 6, "cuda:0", with_energy=False)
+    got = sdl.sparse_code_static(Yv, D1g, D2g, 6, out=out)
+    torch.cuda.synchronize()
+    assert torch.equal(got.support, ref.support) and torch.equal(got.nnz, ref.nnz)
+    rel = (np.linalg.norm(got.coef.cpu().numpy() - ref.coef.cpu().numpy(), axis=1) /
+           np.maximum(np.linalg.norm(ref.coef.cpu().numpy(), axis=1), 1e-30))
+    assert rel.max() < COEF_RTOL
+    assert sdl.static_status() == 0
+
+
+def test_static_records_nonfinite_signals(gpu_ctx):
+    """A NaN signal gets nnz = 0 and is reported by sdl_static_status, once."""
+    Yg, D1g, D2g = _problem(6, 8, 16, 4, 300)
+    Yg[17, 2, 3] = float("nan")
+    got = sdl.sparse_code_static(Yg, D1g, D2g, 4)
+    assert sdl.ERRORS[sdl.static_status()] == "SDL_ERR_NONFINITE"
+    assert sdl.static_status() == 0
+    nnz = got.nnz.cpu().numpy()
+    assert nnz[17] == 0 and np.all(np.delete(nnz, 17) == 4)
 
 
 def test_static_rejects_sizes_beyond_its_scratch(gpu_ctx):
