@@ -104,6 +104,26 @@ def test_oracle_tmod_update_golden(name, fn):
     assert r.obj_after == pytest.approx(e["obj_after"], abs=1e-12)
 
 
+def test_oracle_iterate_golden():
+    """One Algorithm-1 iteration worked by hand: the second coding pass must
+    use the new D1 (with the old one its first pick differs)."""
+    d = load("iterate_one_step_2x2.json")
+    e = d["expected"]
+    Y, D1, D2 = arr(d["Y"]), arr(d["D1"]), arr(d["D2"])
+    r = oracle.iterate(Y, D1, D2, d["s"])
+    assert np.array_equal(r.omp_a.support, np.asarray(d["pass1_support"]))
+    np.testing.assert_allclose(r.omp_a.coef, arr(d["pass1_coef"]), atol=1e-14)
+    np.testing.assert_allclose(r.D1, arr(e["D1"]), atol=1e-14)
+    np.testing.assert_allclose(r.D2, arr(e["D2"]), atol=1e-14)
+    assert np.array_equal(r.support, np.asarray(e["support"]))
+    np.testing.assert_allclose(r.coef, arr(e["coef"]), atol=1e-14)
+    assert r.rmse_after_D1 == pytest.approx(num(e["rmse_after_D1"]), rel=1e-14)
+    assert r.rmse_after_D2 == pytest.approx(num(e["rmse_after_D2"]), rel=1e-14)
+    stale = oracle.omp2d(Y, D1, D2, d["s"])
+    assert np.array_equal(stale.support, np.asarray(e["pass2_support_with_old_D1"]))
+    assert not np.array_equal(stale.support, r.support)
+
+
 def test_oracle_threshold_and_procrustes_golden():
     d = load("ortho_threshold_procrustes_2x2.json")
     t = d["threshold"]
@@ -213,6 +233,25 @@ def test_gpu_tmod_update_golden(gpu_ctx, name, side):
     o = obj.cpu().numpy()
     assert o[0] == pytest.approx(e["obj_before"], rel=FP32_TOL)
     assert abs(o[1] - e["obj_after"]) <= FP32_TOL * e["obj_before"]
+
+
+@pytest.mark.gpu
+def test_gpu_iterate_golden(gpu_ctx):
+    import torch
+    from parity import to_gpu_problem
+    d = load("iterate_one_step_2x2.json")
+    e = d["expected"]
+    Yg, D1g, D2g = to_gpu_problem(arr(d["Y"]), arr(d["D1"]), arr(d["D2"]))
+    rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+    out = gpu_ctx.iterate(Yg, D1g, D2g, d["s"], rmse_out=rmse)
+    assert gpu_ctx.status() == 0
+    assert np.array_equal(out.support.cpu().numpy(), np.asarray(e["support"]))
+    np.testing.assert_allclose(D1g.cpu().numpy(), arr(e["D1"]), atol=FP32_TOL)
+    np.testing.assert_allclose(D2g.cpu().numpy(), arr(e["D2"]), atol=FP32_TOL)
+    np.testing.assert_allclose(out.coef.cpu().numpy(), arr(e["coef"]), rtol=FP32_TOL)
+    r = rmse.cpu().numpy()
+    assert r[0] == pytest.approx(num(e["rmse_after_D1"]), rel=FP32_TOL)
+    assert r[1] == pytest.approx(num(e["rmse_after_D2"]), rel=FP32_TOL)
 
 
 @pytest.mark.gpu
