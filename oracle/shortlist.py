@@ -8,9 +8,10 @@ rules define the extension's behaviour before its fallback to the full coder
                       score (its upper 16 bits after flipping negative values,
                       so that a larger float has a larger key), ties to the
                       smaller pair index q; the first k1 form the shortlist and
-                      the next k2 - k1 the check set (-1 where fewer scores
-                      exist).  Written as a stable sort, not as the bisection
-                      the CUDA top-k uses.
+                      the next k2 - k1 the check set, each set listed in
+                      increasing q (-1 where fewer scores exist; NaN scores
+                      never rank).  Written as a stable sort, not as the
+                      bisection the CUDA top-k uses.
   omp2d_restricted  : 2D-OMP whose greedy step only looks at the signal's
                       candidate pairs: argmax |C_q| over unselected candidates
                       (ties to the smallest q), the same full least-squares
@@ -43,8 +44,9 @@ def key16(scores) -> np.ndarray:
 
 
 def shortlists(scores, k1: int, k2: int) -> np.ndarray:
-    """(N, k2) candidate lists: the k1 best pairs then the next k2 - k1, by
-    (key16 descending, q ascending); NaN scores never rank."""
+    """(N, k2) candidate lists: the k1 best pairs by (key16 descending, q
+    ascending), then the next k2 - k1; each of the two sets in increasing q;
+    NaN scores never rank."""
     scores = np.asarray(scores, dtype=np.float32)
     N, Q = scores.shape
     key = key16(scores)
@@ -54,7 +56,9 @@ def shortlists(scores, k1: int, k2: int) -> np.ndarray:
     for k in range(N):
         order = np.lexsort((q, -key[k]))          # last key primary: key desc, then q asc
         order = order[key[k][order] >= 0][:k2]
-        out[k, :order.size] = order
+        first, rest = np.sort(order[:k1]), np.sort(order[k1:])
+        out[k, :first.size] = first
+        out[k, k1:k1 + rest.size] = rest
     return out
 
 

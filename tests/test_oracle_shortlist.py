@@ -84,24 +84,27 @@ def test_key16_preserves_order():
 
 
 def test_shortlists_match_the_pairwise_rank():
-    """Pair q is in position r of the list iff exactly r pairs beat it, where
-    p beats q when key16(p) > key16(q), or the keys are equal and p < q."""
+    """The shortlist is the set of pairs that fewer than k1 pairs beat, the
+    check set those beaten by k1 .. k2-1 pairs (p beats q when key16(p) >
+    key16(q), or the keys are equal and p < q; NaN scores never rank), each
+    set listed in increasing q and padded with -1."""
     rng = np.random.default_rng(4)
     N, Q, k1, k2 = 40, 96, 8, 24
     S = rng.standard_normal((N, Q)).astype(np.float32)
     S[:, 10] = S[:, 50]                                  # exact ties
     S[:, 20] = np.nextafter(S[:, 21], np.float32(np.inf))   # equal 16-bit keys, unequal floats
     S[0, :90] = np.nan                                   # fewer valid scores than k2
+    S[1, 3:70] = np.nan                                  # fewer valid scores than k2, more than k1
     L = sl.shortlists(S, k1, k2)
     key = sl.key16(S)
     for n in range(N):
         valid = ~np.isnan(S[n])
-        for r, q in enumerate(L[n]):
-            if q < 0:
-                assert r >= valid.sum()
-                continue
-            beats = valid & ((key[n] > key[n, q]) | ((key[n] == key[n, q]) & (np.arange(Q) < q)))
-            assert beats.sum() == r
+        rank = np.array([(valid & ((key[n] > key[n, q]) | ((key[n] == key[n, q]) & (np.arange(Q) < q)))).sum()
+                         for q in range(Q)])
+        want1 = np.nonzero(valid & (rank < k1))[0]
+        want2 = np.nonzero(valid & (rank >= k1) & (rank < k2))[0]
+        assert list(L[n, :want1.size]) == list(want1) and np.all(L[n, want1.size:k1] == -1)
+        assert list(L[n, k1:k1 + want2.size]) == list(want2) and np.all(L[n, k1 + want2.size:] == -1)
     assert np.all(L[0, 6:] == -1) and np.all(L[0, :6] >= 90)
 
 
