@@ -427,7 +427,8 @@ int sdl_sparse_code_learned(sdl_ctx* ctx, sdl_mlp* mlp, const float* Y, int p1, 
  * (its upper 16 bits after flipping negative values, so that a larger float
  * never has a smaller key), ties to the smaller pair index q; NaN scores never
  * rank.  cand (device int32, N x k2): the k1 best pairs, then the next k2 - k1
- * (the check set), -1 where fewer than k2 scores are valid.
+ * (the check set), each of the two sets in increasing q and padded with -1
+ * where fewer scores are valid.
  * 1 <= k1 <= k2 <= Q <= 1024.
  */
 int sdl_learned_shortlists(sdl_ctx* ctx, const float* scores, int64_t N, int Q, int k1, int k2,

@@ -147,7 +147,8 @@ __device__ __forceinline__ unsigned key16(float f) {
 }
 
 // Per signal: the k1 best scores (the shortlist) and the next k2 - k1 (the
-// fallback check set), ranked by 16-bit key then by smaller pair index.
+// fallback check set), ranked by 16-bit key then by smaller pair index; each
+// of the two sets is written in increasing pair index.
 // One warp per signal; lane holds scores q = lane + 32 e.
 template <int EQ>
 __global__ void topk_kernel(const float* __restrict__ Z, int ldz, long long N, int Q, int k1,
@@ -159,7 +160,8 @@ __global__ void topk_kernel(const float* __restrict__ Z, int ldz, long long N, i
 #pragma unroll
     for (int e = 0; e < EQ; ++e) {
         const int q = lane + 32 * e;
-        key[e] = (q < Q) ? key16(Z[(size_t)k * ldz + q]) + 1u : 0u;   // 0 = no entry
+        const float z = (q < Q) ? Z[(size_t)k * ldz + q] : 0.f;
+        key[e] = (q < Q && z == z) ? key16(z) + 1u : 0u;   // 0 = no entry (past Q, or NaN)
     }
     auto count_ge = [&](unsigned t) {
         int c = 0;

@@ -41,6 +41,77 @@ def test_gradients_match_oracle(gpu_ctx):
     net.close()
 
 
+U_BF16 = 2.0 ** -8      # unit roundoff of bfloat16 (8 significand bits)
+
+
+def bf16_gradient_bounds(X, T, W1, b1, W2, b2):
+    """First-order elementwise bound on |GPU - oracle| for the loss and every
+    gradient, given the oracle's FP64 values on the same BF16 inputs and
+    weights.  The GPU rounds to BF16: its own input rows (FP32 normalisation,
+    at most one BF16 step from the oracle's: 2u|X|), the hidden activations
+    H (u|H|), the output gradient dZ (u|dZ|) and the pre-activation gradient
+    dPre (u|dPre|); every product is accumulated in FP32 (K 2^-24 of the
+    absolute sums, K <= 576, added as 3e-4 u of them).  Each error is carried
+    through the next stage by absolute values: |sigma'| <= 1/4 and
+    |GELU''| <= 2 phi(0) < 0.8."""
+    u = U_BF16
+    B = X.shape[0]
+    pre, H, Z = omlp.forward(X, W1, b1, W2, b2)
+    sig = 1.0 / (1.0 + np.exp(-Z))
+    dZ = (sig - T) / B
+    gp = omlp.gelu_grad(pre)
+    lin = dZ @ W2
+    dPre = lin * gp
+    aX, aH, aW1, aW2 = np.abs(X), np.abs(H), np.abs(W1), np.abs(W2)
+    acc = 1.0 + 3e-4                                   # FP32 accumulation on top of each bound
+    e_X = 2 * u * aX
+    e_pre = acc * (e_X @ aW1.T)
+    e_H = u * aH + np.abs(gp) * e_pre
+    e_Z = acc * (e_H @ aW2.T) + 3e-4 * u * (aH @ aW2.T)
+    e_dZ = 0.25 * e_Z / B + u * np.abs(dZ)
+    e_lin = acc * (e_dZ @ aW2) + 3e-4 * u * (np.abs(dZ) @ aW2)
+    e_dPre = e_lin * np.abs(gp) + 0.8 * np.abs(lin) * e_pre + u * np.abs(dPre)
+    bounds = dict(
+        W2=acc * (e_dZ.T @ aH + np.abs(dZ).T @ e_H),
+        b2=acc * e_dZ.sum(axis=0),
+        W1=acc * (e_dPre.T @ aX + np.abs(dPre).T @ e_X),
+        b1=acc * e_dPre.sum(axis=0))
+    loss_bound = float(np.sum(np.abs(sig - T) * e_Z) / B)
+    return loss_bound, bounds
+
+
+def test_gradients_of_the_full_network_within_the_bf16_bound(gpu_ctx):
+    """The learned coder's network at its real size (144 -> 512 GELU -> 576,
+    12x12 signals, 24x24 atom pairs), one batch of 256 OMP-labelled signals:
+    the GPU's loss and gradients differ from the FP64 oracle's (same BF16
+    inputs and weights) by no more than twice the first-order BF16 bound of
+    bf16_gradient_bounds, entry by entry."""
+    p, n, s, H, B = 12, 24, 6, 512, 256
+    Y, D1, D2, _, _ = synth.kron_model(B, p, p, n, n, s, 20.0, seed=75)
+    labels = oracle.omp2d(Y, D1, D2, s).support
+    rng = np.random.default_rng(76)
+    W1 = rng.standard_normal((H, p * p)) * np.sqrt(2.0 / (p * p))
+    b1 = rng.standard_normal(H) * 0.1
+    W2 = rng.standard_normal((n * n, H)) * np.sqrt(1.0 / H)
+    b2 = rng.standard_normal(n * n) * 0.1 - 2.0
+    net = sdl.MLP(gpu_ctx, p, p, n, n, hidden=H, max_batch=B)
+    net.set_weights(W1, b1, W2, b2)
+    Yg, _, _ = to_gpu_problem(Y, D1, D2)
+    loss, g = net.gradients(Yg, torch.tensor(labels, dtype=torch.int32, device="cuda:0"))
+    X, W1b, W2b = bf16(omlp.inputs(Y)), bf16(W1), bf16(W2)
+    T = omlp.targets(labels, n * n)
+    ref_loss, ref = omlp.loss_and_grads(X, T, W1b, b1, W2b, b2)
+    loss_bound, bounds = bf16_gradient_bounds(X, T, W1b, b1, W2b, b2)
+    assert abs(loss - ref_loss) <= 2 * loss_bound + 1e-6 * abs(ref_loss), (loss, ref_loss, loss_bound)
+    for name in ("W1", "b1", "W2", "b2"):
+        err = np.abs(np.asarray(g[name], dtype=np.float64) - ref[name])
+        worst = float(np.max(err / (2 * bounds[name] + 1e-12)))
+        rel = np.linalg.norm(err) / np.linalg.norm(ref[name])
+        print(f"{name}: max |err| / (2 bound) = {worst:.3f}, norm-wise relative error {rel:.2e}")
+        assert worst <= 1.0, (name, worst)
+    net.close()
+
+
 def support_recall(net, Y, plain, k=32):
     """Share of the plain coder's picks that fall inside the network's top-k."""
     top = torch.topk(net.forward(Y), k, dim=1).indices

@@ -307,8 +307,8 @@ def test_every_tiling_gives_identical_codes_and_matches_oracle(gpu_ctx, p1, n1, 
                     for x, y in zip(got, base):
                         assert torch.equal(x, y), (t, cps, e)
                     if got is base:   # identical codes: the oracle judges them once
-                        check_codes(Y, D1, D2, s, *(v.numpy() for v in got), eps=(e or None),
-                                    ref=r).assert_ok()
+                        check_codes(Y, D1, D2, s, got[0].numpy(), got[2].numpy(), got[1].numpy(),
+                                    got[3].numpy(), eps=(e or None), ref=r).assert_ok()
             for e, r in ((0.0, it_ref), (eps, it_ref_eps)):
                 iterate_and_check(gpu_ctx, Y, D1, D2, s, eps=(e or None), ref=r,
                                   Ygpu=(Yg, D1g, D2g))
