@@ -76,6 +76,58 @@ def bytes_per_signal_pass(p1, p2, s, side):
     return 4 * p1 * p2 + (8 * s + 4 if side == 2 else 0)
 
 
+def flops_pass_hist(p1, p2, n1, n2, s, side, nnz_hist):
+    """Algorithmic FLOPs of one coding pass of signals whose code sizes have
+    the histogram nnz_hist (error-driven stop): a signal with no atom skips
+    its correlations; one with m atoms pays C0, the score updates of steps
+    1..m-1, m Cholesky steps and its epilogue sums."""
+    c0 = 2 * min(p1 * p2 * n2 + n1 * p1 * n2, n1 * p1 * p2 + n1 * p2 * n2)
+    tot = 0
+    for m, count in enumerate(nnz_hist):
+        if m == 0 or count == 0:
+            continue
+        upd = sum(2 * t * n1 * n2 for t in range(m))
+        chol = sum(2 * t * t + 4 * t + 4 for t in range(m))
+        epi = 2 * (p1 if side == 1 else p2) * m + 3 * m * m if side else 0
+        tot += count * (c0 + upd + chol + epi)
+    return tot
+
+
+def flops_ortho_pass(p1, p2, s):
+    """Thresholded coding (Remark 1, square dictionaries): C0 = D1^T Y D2 and
+    the epilogue sums; no pursuit."""
+    return 2 * (p1 * p2 * p2 + p1 * p1 * p2) + 2 * max(p1, p2) * s
+
+
+def flops_pass3(p, n, s):
+    """Three-mode pursuit (Remark 3) of one signal: C0 by three mode
+    contractions in the cheapest order, the score updates sum_t 2 t Q over
+    Q = n1 n2 n3 triples, the Cholesky steps and the mode-k epilogue."""
+    import itertools
+    best = None
+    for order in itertools.permutations(range(3)):
+        dims, cost = list(p), 0
+        for m in order:       # mode-m product: every fibre of length p_m becomes one of length n_m
+            others = dims[0] * dims[1] * dims[2] // dims[m]
+            cost += 2 * others * p[m] * n[m]
+            dims[m] = n[m]
+        best = cost if best is None else min(best, cost)
+    Q = n[0] * n[1] * n[2]
+    upd = sum(2 * t * Q for t in range(s))
+    chol = sum(2 * t * t + 4 * t + 4 for t in range(s))
+    return best + upd + chol + 2 * max(p) * s + 3 * s * s
+
+
+def alu_roofline(kernel, flops_per_launch, ms_per_launch, peak, basis):
+    achieved = flops_per_launch / (ms_per_launch / 1e3) / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "algorithmic_flops_per_launch": flops_per_launch,
+            "ms_per_launch": ms_per_launch, "peak_basis": basis}
+
+
+PEAK_BASIS = "measured FP32 FMA rate (sdl_fp32_fma_peak, packed fma.rn.f32x2)"
+
+
 # sources of the coding-pass kernels timed by the roofline (the specialised
 # kernel and its shared header): stored DRAM counters are only used while
 # these files are unchanged
@@ -618,6 +670,7 @@ def study_precision(args):
     C = sdl.Context
     modes = {"fp32": C.PREC_FP32, "bf16_rescored": C.PREC_BF16_CORR,
              "fp64_solve": C.PREC_FP64_SOLVE, "bf16_fp64": C.PREC_BF16_CORR | C.PREC_FP64_SOLVE}
+    peak, _ = sdl.fp32_fma_peak(packed=True)
     out = {}
     for name, flags in modes.items():
         ctx.set_precision(flags)
@@ -645,9 +698,16 @@ def study_precision(args):
         ctx.profile(True)
         ctx.iterate(Yg, D1w, D2w, s, out=codes, rmse_out=rmse)
         ctx.profile(False)
-        split = {k: round(v[0], 4) for k, v in ctx.profile_collect().items() if v[1] > 0}
+        prof = {k: v for k, v in ctx.profile_collect().items() if v[1] > 0}
+        split = {k: round(v[0], 4) for k, v in prof.items()}
         ctx.status()
-        out[name] = {"ms_per_iteration": statistics.median(ms), "signals_per_s":
+        roof = None
+        if not flags & C.PREC_BF16_CORR and "code_D1" in prof:
+            # the FP32 coding pass (D1 side) against the FP32 FMA peak
+            roof = alu_roofline("code_D1 (generic coder, 16x64 signals, 32x128 pairs, s=10)",
+                                N * flops_per_signal_pass(16, 64, 32, 128, s, 1),
+                                prof["code_D1"][0] / prof["code_D1"][1], peak, PEAK_BASIS)
+        out[name] = {"roofline": roof, "ms_per_iteration": statistics.median(ms), "signals_per_s":
                      N / (statistics.median(ms) / 1e3), "final_rmse": traj[-1],
                      "rmse_trajectory_after_D2": [round(t[1], 7) for t in traj],
                      "status_per_iteration": st,
@@ -752,8 +812,13 @@ def study_ortho(args):
     ctx.profile(True)
     ctx.ortho_iterate(Yg, D1w, D2w, s, out=codes, rmse_out=rmse)
     ctx.profile(False)
-    split = {k: round(v[0], 4) for k, v in ctx.profile_collect().items() if v[1] > 0}
+    prof = {k: v for k, v in ctx.profile_collect().items() if v[1] > 0}
+    split = {k: round(v[0], 4) for k, v in prof.items()}
     ctx.check()
+    peak, _ = sdl.fp32_fma_peak(packed=True)
+    roof = alu_roofline("ortho_code (thresholded coding, 12x12, both sides)",
+                        N * flops_ortho_pass(p, p, s), prof["ortho_code"][0] / prof["ortho_code"][1],
+                        peak, PEAK_BASIS)
     # general variant, same patches, same number of iterations (context)
     D1a, D2a = _device_dict(D1g_init, dev), _device_dict(D2g_init, dev)
     gen = []
@@ -766,7 +831,7 @@ def study_ortho(args):
     print(json.dumps({"study": "ortho", "workload": "200000 12x12 patches, orthonormal D 12x12, "
                       "s=6, 20 iterations", "ms_per_iteration": med,
                       "signals_per_s": N / (med / 1e3), "rmse_trajectory": traj,
-                      "kernel_ms_one_iteration": split,
+                      "kernel_ms_one_iteration": split, "roofline": roof,
                       "general_variant_rmse_trajectory_D12x24": gen}), flush=True)
     return 0
 
@@ -907,11 +972,23 @@ def study_tmod3(args):
         ms.append(a.elapsed_time(b))
         traj.append([round(v, 6) for v in rmse.tolist()])
     ctx.check()
+    ctx.profile_collect()
+    ctx.profile(True)
+    ctx.iterate3(Yg, *Dw, s, out=codes, rmse_out=rmse)
+    ctx.profile(False)
+    prof = {k: v for k, v in ctx.profile_collect().items() if v[1] > 0}
+    ctx.check()
+    peak, _ = sdl.fp32_fma_peak(packed=True)
+    roof = alu_roofline("code (three-mode pursuit, 4x4x16 cubes, 8x8x16 triples, s=8; three passes)",
+                        N * flops_pass3((4, 4, 16), (8, 8, 16), s), prof["code"][0] / prof["code"][1],
+                        peak, PEAK_BASIS)
     ctx.close()
     med = statistics.median(ms)
     print(json.dumps({"study": "tmod3", "workload": "50000 hyperspectral-shaped 4x4x16 cubes, "
                       "D 4x8, 4x8, 16x16, s=8, 10 iterations", "ms_per_iteration": med,
-                      "signals_per_s": N / (med / 1e3), "rmse_after_each_update": traj}),
+                      "signals_per_s": N / (med / 1e3), "rmse_after_each_update": traj,
+                      "kernel_ms_one_iteration": {k: round(v[0], 4) for k, v in prof.items()},
+                      "roofline": roof}),
           flush=True)
     return 0
 
@@ -951,6 +1028,13 @@ def study_denoise(args):
         phases.append(r["ms_phases"])
     ctx.check()
     n_patches = sum((512 - p + 1) ** 2 for p, _, _ in dn.DEFAULT_GROUPS)
+    # the final coding pass of all patches (one launch of the multi-problem
+    # coder, code only): its algorithmic FLOPs from the code sizes it produced
+    peak, _ = sdl.fp32_fma_peak(packed=True)
+    fl = sum(flops_pass_hist(p, p, n, n, sc, 0, h.tolist())
+             for (p, n, sc), h in zip(dn.DEFAULT_GROUPS, r["nnz_hist"]))
+    roof = alu_roofline("final coding pass (multi-problem coder, three patch sizes, error-driven)",
+                        fl, statistics.median(p["final_code"] for p in phases), peak, PEAK_BASIS)
     res = {"psnr_noisy": sdl.psnr(ng, cg).item(), "psnr_denoised": [x.item() for x in r["psnr"]],
            "nnz_mean": [x.item() for x in r["nnz_mean"]], "rmse_final": r["rmse"][-1].tolist(),
            "ms_pipeline": statistics.median(ms), "patches": n_patches,
@@ -958,7 +1042,7 @@ def study_denoise(args):
            "ms_phases": {k: statistics.median(p[k] for p in phases) for k in phases[0]},
            "ms_setup_first_pipeline": cold["ms_phases"]["setup"],
            "ms_per_learning_iteration": statistics.median(p["iterations"] for p in phases) / 10,
-           "tuning": r["tuning"],
+           "roofline": roof, "tuning": r["tuning"],
            "tuning_log": [dict(group=t["group"], shape_id=t["shape_id"], ctas_per_sm=t["ctas_per_sm"],
                                us=round(t["cost_us"], 1)) for t in r["tuning_log"]]}
     ctx.close()

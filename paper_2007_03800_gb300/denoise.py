@@ -52,13 +52,15 @@ def denoise(ctx: sdl.Context, noisy: torch.Tensor, sigma: float, groups=DEFAULT_
     mark()
     batch.sparse_code(stream=stream)
     mark()
-    out = dict(images=[], psnr=[], nnz_mean=[], tuning=batch.tuning(), tuning_log=batch.tuning_log(),
-               rmse=torch.stack(traj) if traj else None, dictionaries=[])
+    out = dict(images=[], psnr=[], nnz_mean=[], nnz_hist=[], tuning=batch.tuning(),
+               tuning_log=batch.tuning_log(), rmse=torch.stack(traj) if traj else None,
+               dictionaries=[])
     for spec, m in zip(batch.groups, meta):
         img = sdl.patch_average(ctx, spec["codes"], m["means"], spec["D1"], spec["D2"], m["p"],
                                 H, W, stream=stream)
         out["images"].append(img)
         out["nnz_mean"].append(spec["codes"].nnz.float().mean())
+        out["nnz_hist"].append(torch.bincount(spec["codes"].nnz.long(), minlength=m["s"] + 1))
         out["dictionaries"].append((spec["D1"], spec["D2"]))
         if clean is not None:
             out["psnr"].append(sdl.psnr(img, clean, stream=stream))
