@@ -393,13 +393,13 @@ int sdl_mlp_forward(sdl_mlp* mlp, const float* Y, int64_t N, float* scores, void
  * sdl_sparse_code_learned - 2D-OMP on learned shortlists, with the full coder
  * as the fallback:
  *   1. the network scores all pairs; the k best (1 <= k <= 32) form the
- *      shortlist, the next 2k the check set;
+ *      shortlist;
  *   2. 2D-OMP (same greedy rule, re-fit and stopping as sdl_sparse_code,
  *      fixed s_max) searches only the shortlist;
- *   3. a signal is flagged when some check-set pair correlates with the final
- *      residual more strongly than 0.7 x the weakest greedy score of its picks,
- *      or its data is not finite; flagged signals are coded again by the full
- *      coder;
+ *   3. a signal is flagged when it took s_max picks and some pair it did not
+ *      pick correlates with the final residual more strongly than 0.7 x the
+ *      weakest greedy score of its picks, or its data is not finite; flagged
+ *      signals are coded again by the full coder;
  *   4. the full coder also codes a strided sample of max(4096, N/16) signals
  *      (all of them when N is smaller) and judges the learned codes there: if
  *      their RMSE on the sample exceeds the full coder's by more than 1 %,
@@ -440,11 +440,12 @@ int sdl_learned_shortlists(sdl_ctx* ctx, const float* scores, int64_t N, int Q, 
  * |correlation| over unselected candidates, ties to the smallest q, with the
  * re-fit, energy identity and stopping rules of sdl_sparse_code (fixed
  * s_max).  flag[k] = 1 when the signal's data is not finite, or when it took
- * s_max picks and some check-set pair (cand[k][k1 .. k2-1]) correlates with
- * its final residual more strongly than 0.7 x the smallest best-score among
- * its picks (the learned coder's fallback test); else 0.  res_energy may be
- * NULL.  1 <= k1 <= 32, k1 <= k2 <= k1 + 64.  Compiled for (p1,p2,n1,n2,s_max)
- * = (12,12,24,24,6) and (8,8,16,16,4).
+ * s_max picks and some pair it did not pick (any of the n1 n2) correlates
+ * with its final residual more strongly than 0.7 x the smallest best-score
+ * among its picks (the learned coder's fallback test); else 0.  cand has k2
+ * entries per signal (only the first k1 are searched).  res_energy may be
+ * NULL.  1 <= k1 <= 32, k2 >= k1.  Compiled for (p1,p2,n1,n2,s_max) =
+ * (12,12,24,24,6) and (8,8,16,16,4).
  */
 int sdl_sparse_code_shortlist(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
                               const float* D1, int n1, const float* D2, int n2, int s_max,

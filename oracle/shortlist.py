@@ -17,10 +17,10 @@ rules define the extension's behaviour before its fallback to the full coder
                       (ties to the smallest q), the same full least-squares
                       re-fit, degenerate-pick and zero-score stops as omp2d.
   check_scores      : after the restricted pursuit, the largest |correlation|
-                      of a check-set pair with the final residual, and the
-                      weakest greedy score among the picks (the signal is sent
-                      to the full coder when the first exceeds 0.7 x the
-                      second, or when it has non-finite data).
+                      of an unselected pair with the final residual, and the
+                      weakest greedy score among the picks (a signal with s
+                      picks is sent to the full coder when the first exceeds
+                      0.7 x the second, or when it has non-finite data).
 """
 from __future__ import annotations
 
@@ -117,20 +117,20 @@ def omp2d_restricted(Y, D1, D2, s: int, cand, top_k: int = 4) -> OMPResult:
     return OMPResult(support, coef, nnz, res_energy, top_q, top_val)
 
 
-def check_scores(Y, D1, D2, res: OMPResult, check):
-    """For each signal: the largest |<R, d1_i d2_j^T>| over its check-set
-    pairs (R the final residual of `res`), and the weakest greedy score, i.e.
-    the smallest best-score among its picks (top_val[:, t, 0], inf when it
-    has none)."""
+def check_scores(Y, D1, D2, res: OMPResult):
+    """For each signal: the largest |<R, d1_i d2_j^T>| over the pairs it did
+    not pick (R the final residual of `res`), and the weakest greedy score,
+    i.e. the smallest best-score among its picks (top_val[:, t, 0], inf when
+    it has none)."""
     Y = np.asarray(Y, dtype=np.float64)
-    n1 = D1.shape[1]
     R = Y - reconstruct(D1, D2, res.support, res.coef)
     C = np.einsum("ai,kab,bj->kij", D1, R, D2, optimize=True)
-    score = np.abs(C).transpose(0, 2, 1).reshape(Y.shape[0], -1)
-    check = np.asarray(check, dtype=np.int64)
-    vals = np.where(check >= 0, np.take_along_axis(score, np.maximum(check, 0), axis=1), 0.0)
+    score = np.abs(C).transpose(0, 2, 1).reshape(Y.shape[0], -1)      # column q = i + n1*j
+    rows = np.repeat(np.arange(Y.shape[0])[:, None], res.support.shape[1], axis=1)
+    picked = res.support >= 0
+    score[rows[picked], res.support[picked]] = 0.0
     worst = np.full(Y.shape[0], np.inf)
     for t in range(res.support.shape[1]):
-        picked = res.support[:, t] >= 0
-        worst = np.where(picked, np.minimum(worst, res.top_val[:, t, 0]), worst)
-    return vals.max(axis=1, initial=0.0), worst
+        sel = res.support[:, t] >= 0
+        worst = np.where(sel, np.minimum(worst, res.top_val[:, t, 0]), worst)
+    return score.max(axis=1), worst

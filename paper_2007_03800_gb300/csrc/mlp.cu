@@ -220,10 +220,9 @@ __global__ void topk_kernel(const float* __restrict__ Z, int ldz, long long N, i
 }
 
 // ---------------------------------------------------------------- shortlist OMP
-// check set = the 2k pairs ranked after the shortlist (2 per lane at k = 32);
-// a check pair whose residual correlation exceeds this fraction of the
-// weakest greedy score flags the signal
-constexpr int kCheck = 2;
+// fallback test: a signal whose final residual correlates with some
+// unselected pair more strongly than this fraction of its weakest greedy
+// score is coded again by the full coder
 constexpr float kCheckMargin = 0.7f;
 template <int B, int E, class F>
 __device__ __forceinline__ void sfor(F&& f) {
@@ -235,10 +234,10 @@ __device__ __forceinline__ void sfor(F&& f) {
 
 // 2D-OMP restricted to the k1 shortlisted pairs (lane l owns candidate l),
 // the same greedy rule, Cholesky and energy identity as the full coder.
-// Fallback test: after the last pick, if any pair of the check set (the
-// next k2-k1 scores) correlates with the residual more strongly than the
-// weakest pick did when it was chosen, plain 2D-OMP might have taken it:
-// the signal is flagged for the full coder.
+// Fallback test: after the last pick, the residual's correlation with every
+// pair not picked, C0 - sum_l x_l G1[:, i_l] G2[j_l, :]; if one exceeds
+// kCheckMargin x the weakest pick's score at its step, plain 2D-OMP might
+// have taken a pair the shortlist missed: the signal is flagged.
 template <int P1, int P2, int N1, int N2, int S>
 __global__ void __launch_bounds__(256) shortlist_omp_kernel(
     const float* __restrict__ Y, long long N, const float* __restrict__ D1,
@@ -282,26 +281,12 @@ __global__ void __launch_bounds__(256) shortlist_omp_kernel(
             Zs[e] = z;
         }
         __syncwarp();
-        // lane's shortlist candidate and its kCheck check candidates
+        // lane's shortlist candidate
         const int q = lane < k1 ? cand[(size_t)k * k2 + lane] : -1;
         const int ci = q >= 0 ? q % N1 : 0, cj = q >= 0 ? q / N1 : 0;
-        int qe[kCheck], ei[kCheck], ej[kCheck];
-        float c0e[kCheck];
-#pragma unroll
-        for (int u = 0; u < kCheck; ++u) {
-            const int pos = k1 + u * 32 + lane;
-            qe[u] = pos < k2 ? cand[(size_t)k * k2 + pos] : -1;
-            ei[u] = qe[u] >= 0 ? qe[u] % N1 : 0;
-            ej[u] = qe[u] >= 0 ? qe[u] / N1 : 0;
-            c0e[u] = 0.f;
-        }
         float c0 = 0.f;
 #pragma unroll
-        for (int a = 0; a < P1; ++a) {
-            c0 = fmaf(D1c[ci * P1 + a], Zs[a * N2 + cj], c0);
-#pragma unroll
-            for (int u = 0; u < kCheck; ++u) c0e[u] = fmaf(D1c[ei[u] * P1 + a], Zs[a * N2 + ej[u]], c0e[u]);
-        }
+        for (int a = 0; a < P1; ++a) c0 = fmaf(D1c[ci * P1 + a], Zs[a * N2 + cj], c0);
         if (q < 0) c0 = __int_as_float(0x7fc00000);
         int si[S], sj[S];
         float xs[S], yv[S], Lrow[S], Lcol[S];
@@ -371,15 +356,22 @@ __global__ void __launch_bounds__(256) shortlist_omp_kernel(
 #pragma unroll
         for (int m = 0; m < S; ++m)
             if (lane == m) myx = xs[m];
-        // fallback test on the check set
+        // fallback test over every pair not picked (lane takes q = lane + 32 e)
         float ve = 0.f;
+        if (cnt == S) {
+            for (int qq = lane; qq < N1 * N2; qq += 32) {
+                const int i = qq % N1, j = qq / N1;
+                bool picked = false;
 #pragma unroll
-        for (int u = 0; u < kCheck; ++u) {
-            float sce = c0e[u];
+                for (int l = 0; l < S; ++l) picked |= (si[l] == i && sj[l] == j);
+                if (picked) continue;
+                float sce = 0.f;
 #pragma unroll
-            for (int l = 0; l < S; ++l)
-                if (l < cnt) sce = fmaf(-xs[l] * G1s[ei[u] * N1 + si[l]], G2s[sj[l] * N2 + ej[u]], sce);
-            if (qe[u] >= 0 && fabsf(sce) == fabsf(sce)) ve = fmaxf(ve, fabsf(sce));
+                for (int a = 0; a < P1; ++a) sce = fmaf(D1c[i * P1 + a], Zs[a * N2 + j], sce);
+#pragma unroll
+                for (int l = 0; l < S; ++l) sce = fmaf(-xs[l] * G1s[i * N1 + si[l]], G2s[sj[l] * N2 + j], sce);
+                ve = fmaxf(ve, fabsf(sce));
+            }
         }
         const float maxe = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(ve)));
         const bool fb = !isfinite(ss) || (cnt == S && maxe > kCheckMargin * weakest);
@@ -762,7 +754,7 @@ extern "C" int sdl_sparse_code_learned(sdl_ctx* c, sdl_mlp* m, const float* Y, i
     if (!shape_a && !shape_b) return SDL_ERR_UNSUPPORTED;
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const int k2 = k + 32 * kCheck < 3 * k ? k + 32 * kCheck : 3 * k, Q = m->Q;
+    const int k2 = k, Q = m->Q;     // the shortlist only: the fallback test scans every pair
     // workspace: scores of one chunk, candidates, Grams, scan buffers, index list
     const long long chunk = m->Bmax;
     const int nblk = (int)((N + kScanBlock - 1) / kScanBlock);
@@ -907,8 +899,7 @@ extern "C" int sdl_sparse_code_shortlist(sdl_ctx* c, const float* Y, int p1, int
                                          int s_max, const int32_t* cand, int k1, int k2,
                                          int32_t* support, float* coef, int32_t* nnz,
                                          float* res_energy, int32_t* flag, void* stream) {
-    if (!c || !D1 || !D2 || N < 0 || N > 0x7fffffffLL || k1 < 1 || k1 > 32 || k2 < k1 ||
-        k2 > k1 + 32 * kCheck)
+    if (!c || !D1 || !D2 || N < 0 || N > 0x7fffffffLL || k1 < 1 || k1 > 32 || k2 < k1)
         return SDL_ERR_ARG;
     const bool shape_a = p1 == 12 && p2 == 12 && n1 == 24 && n2 == 24 && s_max == 6;
     const bool shape_b = p1 == 8 && p2 == 8 && n1 == 16 && n2 == 16 && s_max == 4;

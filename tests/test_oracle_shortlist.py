@@ -114,14 +114,15 @@ def test_check_scores_pinned_by_explicit_residual():
     Y = rng.standard_normal((12, 4, 4))
     cand = np.stack([rng.permutation(36) for _ in range(12)])
     res = sl.omp2d_restricted(Y, D1, D2, 3, cand[:, :8])
-    maxe, worst = sl.check_scores(Y, D1, D2, res, cand[:, 8:20])
+    maxe, worst = sl.check_scores(Y, D1, D2, res)
     Dk = np.kron(D2, D1)
     for m in range(12):
         y = Y[m].flatten(order="F")
         S = list(res.support[m, :res.nnz[m]])
         x = np.linalg.lstsq(Dk[:, S], y, rcond=None)[0]
         r = y - Dk[:, S] @ x
-        assert np.isclose(maxe[m], np.abs(Dk[:, cand[m, 8:20]].T @ r).max(), rtol=1e-10)
+        others = [q for q in range(36) if q not in S]
+        assert np.isclose(maxe[m], np.abs(Dk[:, others].T @ r).max(), rtol=1e-10)
         # the weakest greedy score: replay the picks and take each step's best
         rr, w = y.copy(), np.inf
         for t, q in enumerate(S):
