@@ -274,12 +274,38 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
             unsigned exact = 0xffffffffu;      // bit r*RJ+c: c0 entry is an FP32 value
             const float bound = a.c0ext ? a.c0_err_rel * sqrtf(ss) : 0.f;
             if (!a.c0ext) {
-                // ---- Z = Y D2 (p1 x N2P, row-major)
-                for (int e = tau; e < p1 * N2P; e += T) {
-                    int r = e / N2P, j = e - r * N2P;
-                    float z = 0.f;
-                    for (int b = 0; b < p2; ++b) z = fmaf(Ys[r + p1 * b], D2r[b * N2P + j], z);
-                    Zs[e] = z;
+                // ---- Z = Y D2 (p1 x N2P, row-major).  When p1 is a multiple
+                // of 4, a thread forms 4 x 4 blocks: per b one float4 of Y's
+                // column b and one of D2's row b, 16 independent FMA chains
+                // (each entry still sums over b in order, as the scalar form)
+                if ((p1 & 3) == 0) {
+                    const int nbj = N2P / 4, nb = (p1 / 4) * nbj;
+                    for (int e = tau; e < nb; e += T) {
+                        const int a0 = (e / nbj) * 4, j0z = (e % nbj) * 4;
+                        float z[4][4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) z[r][c] = 0.f;
+                        for (int b = 0; b < p2; ++b) {
+                            const float4 y4 = *reinterpret_cast<const float4*>(Ys + a0 + p1 * b);
+                            const float4 d4 = *reinterpret_cast<const float4*>(D2r + b * N2P + j0z);
+                            const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+                            const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+                            rank1_rc<4, 4>(z, yv, dv);
+                        }
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            *reinterpret_cast<float4*>(Zs + (a0 + r) * N2P + j0z) =
+                                make_float4(z[r][0], z[r][1], z[r][2], z[r][3]);
+                    }
+                } else {
+                    for (int e = tau; e < p1 * N2P; e += T) {
+                        int r = e / N2P, j = e - r * N2P;
+                        float z = 0.f;
+                        for (int b = 0; b < p2; ++b) z = fmaf(Ys[r + p1 * b], D2r[b * N2P + j], z);
+                        Zs[e] = z;
+                    }
                 }
                 team_sync<TW>(team);
                 // ---- C0 = D1^T Z on this thread's (RI x RJ) block
@@ -382,12 +408,16 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                 if (Mu == 0u) break;  // every remaining score is exactly 0
                 const float Mf = __uint_as_float(Mu);
                 unsigned cand = 0xffffffffu;
+                // only a thread whose own maximum is the team's holds a
+                // candidate: the others (mostly whole warps) skip the search
+                if (m == Mf) {
 #pragma unroll
-                for (int r = 0; r < RI; ++r)
+                    for (int r = 0; r < RI; ++r)
 #pragma unroll
-                    for (int c = 0; c < RJ; ++c)
-                        if (fabsf(sc[r][c]) == Mf)
-                            cand = min(cand, (unsigned)(i0 + r + n1 * (j0 + c)));
+                        for (int c = 0; c < RJ; ++c)
+                            if (fabsf(sc[r][c]) == Mf)
+                                cand = min(cand, (unsigned)(i0 + r + n1 * (j0 + c)));
+                }
                 const unsigned q = team_min_u32<TW>(cand, misc + kMiscMin, wit, lane, team);
                 const int it = (int)(q % (unsigned)n1), jt = (int)(q / (unsigned)n1);
                 // owner of the picked entry hands out b_t = C0[q] and masks it
@@ -490,12 +520,36 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
         } else if constexpr (SIDE == kSideD2) {
             float* accM = acc;
             float* accB = acc + n2 * n2;
-            for (int e = tau; e < p2 * cnt; e += T) {
-                const int l = e / p2, bb = e - l * p2;
-                const int il = si[l];
-                float w = 0.f;
-                for (int r = 0; r < p1; ++r) w = fmaf(Ys[r + p1 * bb], D1r[r * N1P + il], w);
-                atomicAdd(&accB[bb * n2 + sj[l]], xv[l] * w);
+            // B2[b, j_l] += x_l (Y^T d1_{i_l})[b]
+            if ((p1 & 3) == 0 && p1 <= 16) {
+                // a thread keeps column b of Y in registers for every pick it takes
+                const int LG = T / p2 > 1 ? T / p2 : 1;
+                for (int e = tau; e < p2 * LG; e += T) {
+                    const int bb = e % p2, g = e / p2;
+                    float yc[16];
+#pragma unroll
+                    for (int r = 0; r < 16; r += 4) {
+                        const float4 v = r < p1 ? *reinterpret_cast<const float4*>(Ys + p1 * bb + r)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                        yc[r] = v.x; yc[r + 1] = v.y; yc[r + 2] = v.z; yc[r + 3] = v.w;
+                    }
+                    for (int l = g; l < cnt; l += LG) {
+                        const int il = si[l];
+                        float w = 0.f;
+#pragma unroll
+                        for (int r = 0; r < 16; ++r)
+                            if (r < p1) w = fmaf(yc[r], D1r[r * N1P + il], w);
+                        atomicAdd(&accB[bb * n2 + sj[l]], xv[l] * w);
+                    }
+                }
+            } else {
+                for (int e = tau; e < p2 * cnt; e += T) {
+                    const int l = e / p2, bb = e - l * p2;
+                    const int il = si[l];
+                    float w = 0.f;
+                    for (int r = 0; r < p1; ++r) w = fmaf(Ys[r + p1 * bb], D1r[r * N1P + il], w);
+                    atomicAdd(&accB[bb * n2 + sj[l]], xv[l] * w);
+                }
             }
             for (int e = tau; e < cnt * cnt; e += T) {
                 const int l = e / cnt, m2 = e - l * cnt;
