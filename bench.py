@@ -886,6 +886,115 @@ def study_gemm(args):
     return 0
 
 
+def study_densegram(args):
+    """The partial sums of a dictionary update formed densely on tensor cores
+    against the fused sparse epilogue of the coding pass, at c2 (200000 12x12
+    patches, D 12x24, s = 6; D1 side: P = sum T T^T, B1 = sum Y T^T with
+    T_k = X_k D2^T) and c3 (50000 16x64 signals, D1 16x32, D2 64x128, s = 10;
+    D2 side: M = sum Z^T Z, B2 = sum Y^T Z with Z_k = D1 X_k).  Fused: the
+    coding pass with partial sums minus the same pass without them (CUDA
+    events, per-kernel trace).  Dense: T (or Z) materialised in BF16 from the
+    codes, then the two products as BF16 GEMMs with FP32 accumulation
+    (cuBLAS through torch.matmul, which splits the long K = N p dimension);
+    times of both parts, and the HBM floor of writing and reading T once."""
+    import torch
+
+    from paper_2007_03800_gb300 import sdl, synth
+    dev = torch.device("cuda:0")
+    ctx = sdl.Context(0)
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+    out = {}
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        ms = []
+        for _ in range(reps):
+            a, b = _events()
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    for name in ("c2", "c3"):
+        if name == "c2":
+            Y, D1, D2 = make_inputs()
+            p1, p2, n1, n2, s, side = 12, 12, 24, 24, 6, 1
+        else:
+            Y = synth.hyperspectral(50_000, seed=31)
+            D1, D2 = synth.init_dictionaries(16, 64, 32, 128, seed=1)
+            p1, p2, n1, n2, s, side = 16, 64, 32, 128, 10, 2
+        N = Y.shape[0]
+        Yg = sdl.signals(torch.tensor(Y, dtype=torch.float32, device=dev))
+        D1g, D2g = _device_dict(D1, dev), _device_dict(D2, dev)
+        codes = ctx.sparse_code(Yg, D1g, D2g, s)
+        ctx.check()
+        # fused: per-kernel trace of one iteration (both passes) and of a code-only pass
+        kind = "code_D1" if side == 1 else "code_D2"
+        it_ms, co_ms = [], []
+        for _ in range(max(args.steps, 3)):
+            D1w, D2w = _device_dict(D1, dev), _device_dict(D2, dev)
+            ctx.profile_collect()
+            ctx.profile(True)
+            ctx.iterate(Yg, D1w, D2w, s)
+            ctx.sparse_code(Yg, D1g, D2g, s, out=codes)
+            ctx.profile(False)
+            pr = ctx.profile_collect()
+            it_ms.append(pr[kind][0] / pr[kind][1])
+            co_ms.append(pr["code"][0] / pr["code"][1])
+        ctx.status()
+        fused = statistics.median(it_ms) - statistics.median(co_ms)
+        # dense: materialise T_k = X_k D2^T (n1 x p2) or Z_k = D1 X_k (p1 x n2) in BF16
+        sup = codes.support.long()
+        valid = sup >= 0
+        q = torch.where(valid, sup, torch.zeros_like(sup))
+        x = torch.where(valid, codes.coef, torch.zeros_like(codes.coef))
+        ii, jj = q % n1, q // n1
+        Yf = Yg.float()
+
+        def materialise():
+            if side == 1:     # T[k, i, b] = sum_l [i_l = i] x_l D2[b, j_l]
+                T = torch.zeros(N, n1, p2, device=dev, dtype=torch.float32)
+                vals = x[:, :, None] * D2g.t()[jj]                     # (N, s, p2)
+                T.scatter_add_(1, ii[:, :, None].expand(N, s, p2), vals)
+            else:             # Z[k, a, j] = sum_l [j_l = j] x_l D1[a, i_l]
+                T = torch.zeros(N, n2, p1, device=dev, dtype=torch.float32)
+                vals = x[:, :, None] * D1g.t()[ii]                     # (N, s, p1)
+                T.scatter_add_(1, jj[:, :, None].expand(N, s, p1), vals)
+            return T.to(torch.bfloat16)
+
+        Tm = materialise()
+        if side == 1:
+            Tp = Tm.permute(1, 0, 2).reshape(n1, N * p2)            # T' = [T_1 ... T_N]
+            Yp = Yf.permute(1, 0, 2).reshape(p1, N * p2).to(torch.bfloat16)
+        else:
+            Tp = Tm.permute(1, 0, 2).reshape(n2, N * p1)            # Z'^T rows j, columns (k, a)
+            Yp = Yf.permute(2, 0, 1).reshape(p2, N * p1).to(torch.bfloat16)
+        Tp, Yp = Tp.contiguous(), Yp.contiguous()
+
+        def gemms():
+            Pm = Tp @ Tp.t()
+            Bm = Yp @ Tp.t()
+            return Pm, Bm
+
+        ms_mat = timed(materialise, max(args.steps, 3))
+        ms_gemm = timed(gemms, max(args.steps, 3))
+        t_bytes = Tp.numel() * 2
+        out[name] = {"fused_epilogue_ms_per_pass": fused, "pass_with_sums_ms": statistics.median(it_ms),
+                     "pass_code_only_ms": statistics.median(co_ms),
+                     "dense_materialise_ms": ms_mat, "dense_gemms_ms": ms_gemm,
+                     "dense_total_ms": ms_mat + ms_gemm,
+                     "dense_hbm_floor_ms": 2 * t_bytes / (hbm * 1e9) * 1e3,
+                     "dense_gemm_flops": 2.0 * Tp.shape[0] * Tp.shape[1] * (Tp.shape[0] + Yp.shape[0]),
+                     "T_bytes_bf16": t_bytes}
+        del Tm, Tp, Yp, Yg
+    ctx.close()
+    print(json.dumps({"study": "densegram", "unit": "ms", "cases": out}), flush=True)
+    return 0
+
+
 def study_table3(args):
     """The denoising protocol of Table III on synthetic stand-ins for its five
     512x512 test images: sigma in {5, 10, 20, 30, 50}, one noise realisation
@@ -1065,7 +1174,7 @@ def main():
                     help="timed region only: no e2e loop, CPU baseline or clock sampling "
                          "(for profiler runs; its numbers are not bench values)")
     ap.add_argument("--study", choices=["precision", "learned", "denoise", "ortho", "gemm", "table3",
-                                        "tmod3"],
+                                        "tmod3", "densegram"],
                     help="run one extra study on its own workload instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1075,7 +1184,7 @@ def main():
     if args.study:
         return {"precision": study_precision, "learned": study_learned,
                 "denoise": study_denoise, "ortho": study_ortho,
-                "gemm": study_gemm, "table3": study_table3,
+                "gemm": study_gemm, "table3": study_table3, "densegram": study_densegram,
                 "tmod3": study_tmod3}[args.study](args)
     return run_ours(args)
 

@@ -161,6 +161,29 @@ __device__ __forceinline__ void rank1_rc(float (&blk)[R][C], const float (&a)[R]
     }
 }
 
+// R consecutive floats from shared memory, as float4 / float2 loads when R
+// allows: every block a thread reads starts at a multiple of its own length
+// within rows whose lengths (N1P, N2P) and region offsets are multiples of 4
+template <int R>
+__device__ __forceinline__ void ldv(float (&v)[R], const float* p) {
+    if constexpr (R % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < R; k += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(p + k);
+            v[k] = t.x; v[k + 1] = t.y; v[k + 2] = t.z; v[k + 3] = t.w;
+        }
+    } else if constexpr (R % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < R; k += 2) {
+            const float2 t = *reinterpret_cast<const float2*>(p + k);
+            v[k] = t.x; v[k + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = p[k];
+    }
+}
+
 // FP32 re-scoring of one correlation: w_i . d2_j over p2 terms (w_i contiguous,
 // d2_j with stride ld), four interleaved partial sums so the loads and
 // multiply-adds overlap.  Kept out of line: it runs for a few flagged entries
@@ -315,10 +338,8 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                     for (int c = 0; c < RJ; ++c) c0[r][c] = 0.f;
                 for (int aa = 0; aa < p1; ++aa) {
                     float u[RI], v[RJ];
-#pragma unroll
-                    for (int r = 0; r < RI; ++r) u[r] = D1r[aa * N1P + i0 + r];
-#pragma unroll
-                    for (int c = 0; c < RJ; ++c) v[c] = Zs[aa * N2P + j0 + c];
+                    ldv<RI>(u, D1r + aa * N1P + i0);
+                    ldv<RJ>(v, Zs + aa * N2P + j0);
                     rank1_rc<RI, RJ>(c0, u, v);
                 }
             } else {
@@ -361,10 +382,10 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                     const int il = si[l], jl = sj[l];
                     const float xl = xv[l];
                     float u[RI], v[RJ];
+                    ldv<RI>(u, G1s + il * N1P + i0);
+                    ldv<RJ>(v, G2s + jl * N2P + j0);
 #pragma unroll
-                    for (int r = 0; r < RI; ++r) u[r] = G1s[il * N1P + i0 + r];
-#pragma unroll
-                    for (int c = 0; c < RJ; ++c) v[c] = -xl * G2s[jl * N2P + j0 + c];
+                    for (int c = 0; c < RJ; ++c) v[c] *= -xl;
                     rank1_rc<RI, RJ>(sc, u, v);
                 }
                 float m = 0.f;
