@@ -7,8 +7,11 @@
 // threads):
 //   warp 0  TMA producer: operand tiles by cp.async.bulk.tensor (128-byte
 //           swizzle) into a 4-stage shared-memory ring guarded by mbarriers;
-//   warp 1  MMA issuer: one thread issues tcgen05.mma (128 x 128 x 16) into
-//           one of two 128-column FP32 accumulators in tensor memory;
+//   warp 1  MMA issuer: one thread issues tcgen05.mma (128 x BN x 16, BN =
+//           256 when N is a multiple of 256, else 128) into one of two
+//           BN-column FP32 accumulators in tensor memory (all 512 columns at
+//           BN = 256: the wider tile halves the operand bytes each FLOP needs
+//           from L2);
 //           tcgen05.commit releases ring stages and hands a finished
 //           accumulator to the epilogue;
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
@@ -37,13 +40,12 @@ using namespace sdl;
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, UMMA_K = 16;
+constexpr int BM = 128, BK = 64, STAGES = 4, UMMA_K = 16;
 constexpr int kMaxTerms = 3;
 constexpr int kThreads = 192;
 constexpr int kEpiWarps = 4;
 constexpr int kStageLd = 33;                  // epilogue transpose row stride (floats)
 constexpr int TILE_A = BM * BK * 2;           // bytes
-constexpr int TILE_B = BN * BK * 2;
 constexpr long long kWaitCycles = 1ll << 31;  // about one second at 2 GHz
 
 struct Epi {
@@ -131,6 +133,7 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
     return a | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
 }
 // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major
+template <int BN>
 __host__ __device__ constexpr uint32_t instr_desc() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
            ((uint32_t)(BM >> 4) << 24);
@@ -150,9 +153,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ Maps maps, int terms, int M, int N, int K, Epi epi,
                    int* err) {
+    constexpr int TILE_B = BN * BK * 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~uintptr_t(1023));
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            const uint32_t idesc = instr_desc();
+            const uint32_t idesc = instr_desc<BN>();
             long long g = 0;
             int i = 0;   // local tile counter
             for (long long t = blockIdx.x; t < tiles && !*fail; t += gridDim.x, ++i) {
@@ -399,13 +404,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// rows x cols bf16 matrix, row stride ld (elements), box 128 rows x 64 cols
-int make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
+// rows x cols bf16 matrix, row stride ld (elements), box box_rows rows x 64 cols
+int make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return SDL_ERR_CUDA;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, 128u};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1u, 1u};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -414,8 +419,9 @@ int make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
     return r == CUDA_SUCCESS ? SDL_OK : SDL_ERR_ARG;
 }
 
-constexpr size_t kSmemBytes = 1024 + STAGES * (TILE_A + TILE_B) +
-                              sizeof(float) * kEpiWarps * 32 * kStageLd + 256;
+constexpr size_t smem_bytes(int BN) {
+    return 1024 + (size_t)STAGES * (TILE_A + BN * BK * 2) + sizeof(float) * kEpiWarps * 32 * kStageLd + 256;
+}
 
 int sm_count() {
     static int count[64] = {0};
@@ -440,6 +446,8 @@ int tc_gemm_terms(const void* const* A, int lda, const void* const* B, int ldb, 
     if (!A || !B || terms < 1 || terms > kMaxTerms || M < 1 || N < 1 || K < 1) return SDL_ERR_ARG;
     if (act == 2 && !gin) return SDL_ERR_ARG;
     if ((lda % 8) || (ldb % 8) || lda < K || ldb < K) return SDL_ERR_ARG;
+    // 128 x 256 tiles when N is a multiple of 256, else 128 x 128
+    const int bn = (N % 256 == 0) ? 256 : 128;
     Maps maps;
     std::memset(&maps, 0, sizeof(maps));
     int rc;
@@ -447,8 +455,8 @@ int tc_gemm_terms(const void* const* A, int lda, const void* const* B, int ldb, 
         if (!A[t] || !B[t] || (reinterpret_cast<uintptr_t>(A[t]) & 15u) ||
             (reinterpret_cast<uintptr_t>(B[t]) & 15u))
             return SDL_ERR_ARG;
-        if ((rc = make_map(&maps.a[t], A[t], M, K, lda)) != SDL_OK) return rc;
-        if ((rc = make_map(&maps.b[t], B[t], N, K, ldb)) != SDL_OK) return rc;
+        if ((rc = make_map(&maps.a[t], A[t], M, K, lda, BM)) != SDL_OK) return rc;
+        if ((rc = make_map(&maps.b[t], B[t], N, K, ldb, bn)) != SDL_OK) return rc;
     }
     Epi e;
     e.alpha = alpha;
@@ -465,13 +473,17 @@ int tc_gemm_terms(const void* const* A, int lda, const void* const* B, int ldb, 
     e.ldpre = ldpre;
     e.gin = gin;
     e.ldgin = ldgin;
-    if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes) != cudaSuccess)
-        return SDL_ERR_CUDA;
-    const long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-    const int grid = (int)std::min<long long>(tiles, sm_count());
-    tc_gemm_kernel<<<grid, kThreads, kSmemBytes, st>>>(maps, terms, M, N, K, e, err);
-    return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+    auto launch = [&](auto kern, int BN) -> int {
+        const size_t bytes = smem_bytes(BN);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+            cudaSuccess)
+            return SDL_ERR_CUDA;
+        const long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+        const int grid = (int)std::min<long long>(tiles, sm_count());
+        kern<<<grid, kThreads, bytes, st>>>(maps, terms, M, N, K, e, err);
+        return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
+    };
+    return bn == 256 ? launch(tc_gemm_kernel<256>, 256) : launch(tc_gemm_kernel<128>, 128);
 }
 
 int tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float alpha,
