@@ -6,7 +6,8 @@
 // Blackwell path, persistent and warp-specialised (one CTA per SM, 192
 // threads):
 //   warp 0  TMA producer: operand tiles by cp.async.bulk.tensor (128-byte
-//           swizzle) into a 4-stage shared-memory ring guarded by mbarriers;
+//           swizzle) into a shared-memory ring of 6 stages (4 at BN = 256)
+//           guarded by mbarriers;
 //   warp 1  MMA issuer: one thread issues tcgen05.mma (128 x BN x 16, BN =
 //           256 when N is a multiple of 256, else 128) into one of two
 //           BN-column FP32 accumulators in tensor memory (all 512 columns at
@@ -16,9 +17,14 @@
 //           accumulator to the epilogue;
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //           lanes 32 (w % 4) .. +31 = output rows), bias / GELU / GELU'
-//           and the outputs, row-major ones through a per-warp 32 x 33
-//           shared-memory transpose so that every global access is a
-//           coalesced 128-byte row segment.
+//           and the outputs.  The FP32 and BF16 row-major outputs leave by
+//           TMA: each warp writes its 32 x 32 block into one of two swizzled
+//           shared-memory slots and one lane issues cp.async.bulk.tensor (a
+//           tensor reduce-add when accumulating), so the stores neither cost
+//           the warp an instruction per row nor wait on it.  The other
+//           outputs (transposed BF16, pre-activation, the GELU' product) go
+//           through a per-warp 32 x 33 shared-memory transpose as coalesced
+//           128-byte row segments.
 // With two accumulators the epilogue of one tile overlaps the main loop of
 // the next.  Tiles are visited m-block-major, so CTAs running at the same
 // time share A rows and the whole of B in L2.
@@ -40,11 +46,16 @@ using namespace sdl;
 
 namespace {
 
-constexpr int BM = 128, BK = 64, STAGES = 4, UMMA_K = 16;
+constexpr int BM = 128, BK = 64, UMMA_K = 16;
+// shared-memory ring depth: as many stages as fit beside the epilogue's staging
+__host__ __device__ constexpr int stages_for(int BN) { return BN == 256 ? 4 : 6; }
 constexpr int kMaxTerms = 3;
 constexpr int kThreads = 192;
 constexpr int kEpiWarps = 4;
 constexpr int kStageLd = 33;                  // epilogue transpose row stride (floats)
+constexpr int kSlot = 4096;                   // one TMA output slot: 32 rows x 128 B
+constexpr int kEpiBytes = kEpiWarps * 2 * kSlot;   // both epilogue forms share this area
+static_assert(kEpiWarps * 32 * kStageLd * 4 <= kEpiBytes, "transpose staging must fit");
 constexpr int TILE_A = BM * BK * 2;           // bytes
 constexpr long long kWaitCycles = 1ll << 31;  // about one second at 2 GHz
 
@@ -59,6 +70,7 @@ struct Epi {
     int ldcb;
     __nv_bfloat16* Ct;   // BF16 transposed copy (Ct[n * ldct + m]) or null
     int ldct;
+    int tma;             // C and Cb leave through the tensor maps Maps::c / Maps::cb
     float* pre;          // FP32 pre-activation (alpha*acc + bias) or null
     int ldpre;
     const float* gin;    // act 2: multiply by GELU'(gin[m, n])
@@ -68,6 +80,8 @@ struct Epi {
 struct Maps {
     CUtensorMap a[kMaxTerms];
     CUtensorMap b[kMaxTerms];
+    CUtensorMap c;    // FP32 output, 32 x 32 boxes, 128-byte swizzle
+    CUtensorMap cb;   // BF16 output, 32 x 32 boxes, 64-byte swizzle
 };
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -121,6 +135,24 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
         : "memory");
 }
+// 32 x 32 output block from shared memory to global (clipped at the tensor's
+// edges); a reduce-add into global when `add`
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src,
+                                             bool add) {
+    if (add)
+        asm volatile(
+            "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                reinterpret_cast<uint64_t>(map)),
+            "r"(x), "r"(y), "r"(saddr(src))
+            : "memory");
+    else
+        asm volatile(
+            "cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                reinterpret_cast<uint64_t>(map)),
+            "r"(x), "r"(y), "r"(saddr(src))
+            : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -158,13 +190,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ Maps maps, int terms, int M, int N, int K, Epi epi,
                    int* err) {
     constexpr int TILE_B = BN * BK * 2;
+    constexpr int STAGES = stages_for(BN);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~uintptr_t(1023));
     uint8_t* sA = base;
     uint8_t* sB = base + STAGES * TILE_A;
-    float* stage_all = reinterpret_cast<float*>(sB + STAGES * TILE_B);
-    uint64_t* full = reinterpret_cast<uint64_t*>(stage_all + kEpiWarps * 32 * kStageLd);
+    // epilogue area (1024-byte aligned): two TMA slots per warp, or the
+    // transpose staging of the other outputs
+    uint8_t* epi_area = sB + STAGES * TILE_B;
+    float* stage_all = reinterpret_cast<float*>(epi_area);
+    uint64_t* full = reinterpret_cast<uint64_t*>(epi_area + kEpiBytes);
     uint64_t* empty = full + STAGES;
     uint64_t* acc_full = empty + STAGES;      // [2] MMA -> epilogue
     uint64_t* acc_empty = acc_full + 2;       // [2] epilogue -> MMA
@@ -271,6 +307,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---- epilogue warps
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         float* stage = stage_all + (warp - 2) * 32 * kStageLd;
+        uint8_t* slots = epi_area + (warp - 2) * 2 * kSlot;
+        int slot = 0;
         int i = 0;
         for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
             const int b = i & 1, use_b = i >> 1;
@@ -297,6 +335,57 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int n = n0 + c0 + j;
                     x[j] = epi.alpha * __uint_as_float(v[j]);
                     if (epi.bias && n < N) x[j] += epi.bias[n];
+                }
+                if (epi.tma) {
+                    // act is 0 or 1 here, no pre-activation or transposed copy
+                    if (epi.act == 1) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            x[j] = 0.5f * x[j] * (1.f + erff(x[j] * 0.70710678118654752f));
+                    }
+                    if (n0 + c0 >= N || row0 >= M) continue;   // block wholly outside C
+                    // a slot is rewritten only after the store issued from it two
+                    // stores ago has read it
+                    auto next_slot = [&]() {
+                        uint8_t* buf = slots + slot * kSlot;
+                        slot ^= 1;
+                        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                        __syncwarp();
+                        return buf;
+                    };
+                    auto issue = [&](const CUtensorMap* map, const uint8_t* buf, bool add) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) tma_store_2d(map, n0 + c0, row0, buf, add);
+                    };
+                    if (epi.C) {
+                        // row `lane` is 128 B; its 16-byte chunk k sits at k ^ (lane & 7)
+                        uint8_t* buf = next_slot();
+                        float4* row = reinterpret_cast<float4*>(buf + lane * 128);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            row[k ^ (lane & 7)] =
+                                make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+                        issue(&maps.c, buf, epi.accumulate != 0);
+                    }
+                    if (epi.Cb) {
+                        // row `lane` is 64 B; its 16-byte chunk k sits at k ^ ((lane >> 1) & 3)
+                        uint8_t* buf = next_slot();
+                        uint4* row = reinterpret_cast<uint4*>(buf + lane * 64);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const __nv_bfloat162 pr =
+                                    __floats2bfloat162_rn(x[8 * k + 2 * h], x[8 * k + 2 * h + 1]);
+                                w[h] = *reinterpret_cast<const uint32_t*>(&pr);
+                            }
+                            row[k ^ ((lane >> 1) & 3)] = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                        issue(&maps.cb, buf, false);
+                    }
+                    continue;
                 }
                 // row-major [m, n] block (32 rows of this warp x 32 columns),
                 // stored (or added) one coalesced row segment at a time
@@ -375,6 +464,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        // the output stores have left shared memory and are complete
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
     }
     __syncwarp();
     tc_fence_before();
@@ -420,7 +512,25 @@ int make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int 
 }
 
 constexpr size_t smem_bytes(int BN) {
-    return 1024 + (size_t)STAGES * (TILE_A + BN * BK * 2) + sizeof(float) * kEpiWarps * 32 * kStageLd + 256;
+    return 1024 + (size_t)stages_for(BN) * (TILE_A + BN * BK * 2) + kEpiBytes + 256;
+}
+static_assert(smem_bytes(256) <= 232448 && smem_bytes(128) <= 232448, "shared memory per CTA");
+
+// output map: rows x cols matrix of 4-byte (f32) or 2-byte (bf16) elements,
+// row stride ld elements, 32 x 32 boxes swizzled to match the epilogue's slots
+int make_out_map(CUtensorMap* map, void* ptr, int rows, int cols, int ld, bool bf16) {
+    auto fn = encode_fn();
+    if (!fn) return SDL_ERR_CUDA;
+    const size_t es = bf16 ? 2 : 4;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+    const cuuint32_t box[2] = {32u, 32u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                          2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SDL_OK : SDL_ERR_ARG;
 }
 
 int sm_count() {
@@ -473,6 +583,20 @@ int tc_gemm_terms(const void* const* A, int lda, const void* const* B, int ldb, 
     e.ldpre = ldpre;
     e.gin = gin;
     e.ldgin = ldgin;
+    // C and Cb leave by TMA when they are the only outputs and their rows
+    // start and end on 16-byte boundaries (a tensor store clips the row at
+    // 16-byte granularity: a row of 13 BF16 values would also get 3 values of
+    // its padding); otherwise every output takes the transpose path
+    bool tma = (C || Cb) && !pre && !Ct && act != 2;
+    if (C)
+        tma = tma && !(reinterpret_cast<uintptr_t>(C) & 15u) && ldc % 4 == 0 && N % 4 == 0 &&
+              ldc >= N;
+    if (Cb)
+        tma = tma && !(reinterpret_cast<uintptr_t>(Cb) & 15u) && ldcb % 8 == 0 && N % 8 == 0 &&
+              ldcb >= N;
+    if (tma && C) tma = make_out_map(&maps.c, C, M, N, ldc, false) == SDL_OK;
+    if (tma && Cb) tma = make_out_map(&maps.cb, Cb, M, N, ldcb, true) == SDL_OK;
+    e.tma = tma ? 1 : 0;
     auto launch = [&](auto kern, int BN) -> int {
         const size_t bytes = smem_bytes(BN);
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=

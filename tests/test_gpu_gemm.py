@@ -50,3 +50,48 @@ def test_gemm_epilogues(gpu_ctx):
     assert np.abs(C.cpu().numpy() - (g + 2.0)).max() < 1e-4 * np.abs(g).max()
     assert np.abs(Cb.float().cpu().numpy() - g).max() < 1e-2 * np.abs(g).max()
     assert np.abs(Ct[:, :M].float().cpu().numpy() - g.T).max() < 1e-2 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("M,N,K,ldc", [(300, 200, 192, 204), (1000, 512, 256, 512), (77, 13, 8, 13),
+                                       (77, 13, 8, 16), (64, 20, 8, 20), (4096, 576, 512, 576)])
+def test_gemm_tensor_map_outputs(gpu_ctx, M, N, K, ldc):
+    """FP32 and BF16 outputs alone (the tensor-map stores, a reduce-add when
+    accumulating; rows that are not whole 16-byte units, N = 13 and the BF16
+    output at N = 20, take the transpose path): every element of the M x N
+    block right, the padding of each row untouched."""
+    A, An = bf16_pair((M, K), 6)
+    B, Bn = bf16_pair((N, K), 7)
+    bias = torch.randn(N, generator=torch.Generator().manual_seed(8))
+    alpha = -1.25
+    Cfull = torch.full((M, ldc), 2.0, device="cuda:0")
+    C = Cfull[:, :N]
+    sdl.gemm_bf16(gpu_ctx, A, B, alpha=alpha, bias=bias.cuda(), act=1, C=C, accumulate=True)
+    Cbfull = torch.full((M, ldc + 8 - ldc % 8 if ldc % 8 else ldc), 7.0, dtype=torch.bfloat16,
+                        device="cuda:0")
+    Cb = Cbfull[:, :N]
+    sdl.gemm_bf16(gpu_ctx, A, B, alpha=alpha, bias=bias.cuda(), act=1, Cb=Cb)
+    C2 = sdl.gemm_bf16(gpu_ctx, A, B, alpha=alpha)
+    assert gpu_ctx.status() == 0
+    z = alpha * (An @ Bn.T) + bias.double().numpy()[None, :]
+    erf = np.vectorize(math.erf)
+    g = 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+    assert np.abs(C.cpu().numpy() - (g + 2.0)).max() < 1e-4 * (np.abs(g).max() + 2.0)
+    assert np.abs(Cb.float().cpu().numpy() - g).max() < 1e-2 * np.abs(g).max()
+    assert np.abs(C2.cpu().numpy() - alpha * (An @ Bn.T)).max() < 2e-5 * np.abs(z).max()
+    assert bool((Cfull[:, N:] == 2.0).all())
+    assert bool((Cbfull[:, N:].float() == 7.0).all())
+
+
+def test_gemm_ragged_k_ignores_row_padding(gpu_ctx):
+    """K = 13 inside rows of 16: the operand loads stop at column K, so huge
+    values in the padding columns change nothing."""
+    M, N, K, ld = 200, 136, 13, 16
+    g = torch.Generator().manual_seed(9)
+    A = torch.full((M, ld), 1e30).to(torch.bfloat16)
+    B = torch.full((N, ld), 1e30).to(torch.bfloat16)
+    A[:, :K] = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B[:, :K] = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    C = sdl.gemm_bf16(gpu_ctx, A.cuda()[:, :K], B.cuda()[:, :K])
+    assert gpu_ctx.status() == 0
+    ref = A[:, :K].double().numpy() @ B[:, :K].double().numpy().T
+    assert np.abs(C.cpu().numpy() - ref).max() < 2e-5 * np.abs(ref).max()
