@@ -298,9 +298,9 @@ int sdl_gemm_bf16(sdl_ctx* ctx, const void* A, int lda, const void* B, int ldb, 
  *    accumulator.  Every entry is within
  *    e(p1 p2) = (3 + 1/64) 2^-16 + 2^-24 + 3 Kp 2^-23 (Kp = p1 p2 rounded up
  *    to 8) times ||Y_k||_F of its exact value; at every greedy step each
- *    entry within 2 e ||Y_k||_F of the running maximum is re-scored in FP32
- *    ((d1_i^T Y_k) d2_j, from the rows of D1^T Y_k formed once per signal),
- *    so the picks are FP32 picks.  The Gram-domain updates, the Cholesky
+ *    entry within 3 e ||Y_k||_F of the approximate maximum is re-scored in
+ *    FP32 ((d1_i^T Y_k) d2_j, from the rows of D1^T Y_k formed once per
+ *    signal), so the maximum is an FP32 score and the picks are FP32 picks.  The Gram-domain updates, the Cholesky
  *    factor and the partial sums stay FP32.  Uses N x n1n2 FP32 and
  *    2 (N + n1n2) x Kp BF16 of workspace.
  *  SDL_PREC_NO_RESCORE: with BF16_CORR, skip the re-scoring (pure BF16 picks;

@@ -294,7 +294,8 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
         // a signal already within the error target takes no atom: skip its correlations
         if (finite && !(a.eps2 > 0.f && ss <= a.eps2)) {
             float c0[RI][RJ];
-            unsigned exact = 0xffffffffu;      // bit r*RJ+c: c0 entry is an FP32 value
+            unsigned long long exact = ~0ull;  // bit r*RJ+c: c0 entry is an FP32 value
+            static_assert(RI * RJ <= 64, "one flag bit per entry");
             const float bound = a.c0ext ? a.c0_err_rel * sqrtf(ss) : 0.f;
             if (!a.c0ext) {
                 // ---- Z = Y D2 (p1 x N2P, row-major).  When p1 is a multiple
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                     for (int c = 0; c < RJ; ++c)
                         c0[r][c] = (i0 + r < n1 && j0 + c < n2) ? cg[(i0 + r) + n1 * (j0 + c)] : 0.f;
                 if (bound > 0.f) {
-                    exact = 0u;
+                    exact = 0ull;
                     // W = D1^T Y (n1 x p2, row i contiguous) in the Z area:
                     // a re-scored entry is then w_i . d2_j, p2 FMAs
                     float* Ws = Zs;
@@ -395,36 +396,37 @@ __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
                     for (int c = 0; c < RJ; ++c) m = fmaxf(m, fabsf(sc[r][c]));
                 unsigned Mu = team_max_u32<TW>(__float_as_uint(m), misc + kMiscMax, wit, lane, team);
                 if (bound > 0.f) {
-                    // FP32 re-scoring: every approximate entry within 2*bound of
-                    // the running maximum gets its FP32 correlation
-                    // (d1_i^T Y) d2_j; repeat until the maximum and every entry
-                    // that could reach it are FP32 values
-                    for (;;) {
-                        const float thr = __uint_as_float(Mu) - 2.f * bound;
-                        unsigned did = 0;
+                    // FP32 re-scoring, one pass: every approximate entry within
+                    // 3*bound of the approximate maximum Mu gets its FP32
+                    // correlation (d1_i^T Y) d2_j.  The entry at Mu is among them
+                    // and its FP32 score is >= Mu - bound - e (e: FP32 rounding,
+                    // far below bound); an entry left approximate has |score| <
+                    // Mu - 3*bound, so its FP32 score is < Mu - 2*bound + e.  The
+                    // new maximum is therefore an FP32 value and the pick is the
+                    // pick over FP32 scores.
+                    const float thr = __uint_as_float(Mu) - 3.f * bound;
+                    unsigned did = 0;
 #pragma unroll
-                        for (int r = 0; r < RI; ++r)
+                    for (int r = 0; r < RI; ++r)
 #pragma unroll
-                            for (int c = 0; c < RJ; ++c) {
-                                const int e = r * RJ + c;
-                                if (!((exact >> e) & 1u) && fabsf(sc[r][c]) >= thr) {
-                                    const int i = i0 + r, j = j0 + c;
-                                    const float ex = rescore_dot(Zs + i * p2, D2r + j, N2P, p2);
-                                    sc[r][c] = ex - (c0[r][c] - sc[r][c]);
-                                    c0[r][c] = ex;
-                                    exact |= 1u << e;
-                                    ++did;
-                                }
+                        for (int c = 0; c < RJ; ++c) {
+                            const int e = r * RJ + c;
+                            if (!((exact >> e) & 1ull) && fabsf(sc[r][c]) >= thr) {
+                                const int i = i0 + r, j = j0 + c;
+                                const float ex = rescore_dot(Zs + i * p2, D2r + j, N2P, p2);
+                                sc[r][c] = ex - (c0[r][c] - sc[r][c]);
+                                c0[r][c] = ex;
+                                exact |= 1ull << e;
+                                ++did;
                             }
-                        if (a.rescored && did) atomicAdd(a.rescored, (unsigned long long)did);
-                        if (team_max_u32<TW>(did, misc + kMiscSum, wit, lane, team) == 0u) break;
-                        m = 0.f;
+                        }
+                    if (a.rescored && did) atomicAdd(a.rescored, (unsigned long long)did);
+                    m = 0.f;
 #pragma unroll
-                        for (int r = 0; r < RI; ++r)
+                    for (int r = 0; r < RI; ++r)
 #pragma unroll
-                            for (int c = 0; c < RJ; ++c) m = fmaxf(m, fabsf(sc[r][c]));
-                        Mu = team_max_u32<TW>(__float_as_uint(m), misc + kMiscMax, wit, lane, team);
-                    }
+                        for (int c = 0; c < RJ; ++c) m = fmaxf(m, fabsf(sc[r][c]));
+                    Mu = team_max_u32<TW>(__float_as_uint(m), misc + kMiscSum, wit, lane, team);
                 }
                 if (Mu == 0u) break;  // every remaining score is exactly 0
                 const float Mf = __uint_as_float(Mu);
@@ -843,7 +845,7 @@ int launch_acc_impl(const PassArgs& a0, cudaStream_t st, int num_sms) {
 using Tile16 = Tile<4, 8, 4, 2, 1>;      // n1, n2 <= 16
 using Tile24 = Tile<4, 8, 6, 3, 1>;      // n1, n2 <= 24
 using Tile32 = Tile<4, 8, 8, 4, 1>;      // n1, n2 <= 32
-using Tile32x128 = Tile<4, 32, 8, 4, 4>; // n1 <= 32, n2 <= 128
+using Tile32x128 = Tile<2, 32, 16, 4, 2>; // n1 <= 32, n2 <= 128: 4 two-warp teams per CTA
 using Tile128x32 = Tile<16, 8, 8, 4, 4>; // n1 <= 128, n2 <= 32
 using Tile64 = Tile<8, 16, 8, 4, 4>;     // n1, n2 <= 64
 

@@ -12,8 +12,8 @@
 // additions at most 3 p1p2 2^-23 of the sum of |terms|; with unit-norm
 // Kronecker atoms and Cauchy-Schwarz every entry is within
 //   c0_split_err_rel(p1 p2) * ||Y_k||_F
-// of its exact value.  The coding kernel re-scores in FP32 every entry that
-// close to the running maximum, so its picks are the FP32 picks.
+// of its exact value.  The coding kernel re-scores in FP32 every entry within
+// three times that of the approximate maximum, so its picks are the FP32 picks.
 #include <cuda_bf16.h>
 
 #include "ctx.cuh"
