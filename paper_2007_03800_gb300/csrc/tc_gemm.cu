@@ -9,7 +9,8 @@
 //           swizzle) into a shared-memory ring of 6 stages (4 at BN = 256)
 //           guarded by mbarriers;
 //   warp 1  MMA issuer: one thread issues tcgen05.mma (128 x BN x 16, BN =
-//           256 when N is a multiple of 256, else 128) into one of two
+//           256 when N is a multiple of 256 and the 256-wide tiles fill the
+//           SMs, else 128) into one of two
 //           BN-column FP32 accumulators in tensor memory (all 512 columns at
 //           BN = 256: the wider tile halves the operand bytes each FLOP needs
 //           from L2);
@@ -533,6 +534,43 @@ int make_out_map(CUtensorMap* map, void* ptr, int rows, int cols, int ld, bool b
     return r == CUDA_SUCCESS ? SDL_OK : SDL_ERR_ARG;
 }
 
+// Encoded tensor maps, remembered per host thread: a training loop calls the
+// same GEMMs on the same buffers thousands of times, and encoding two to four
+// maps per call is host time on a launch-bound path.  A map depends only on
+// the arguments of its encoding, which form the key.
+struct MapKey {
+    const void* ptr;
+    int rows, cols, ld, box_rows, kind;   // kind 0: operand, 1: FP32 out, 2: BF16 out
+    bool operator==(const MapKey& o) const {
+        return ptr == o.ptr && rows == o.rows && cols == o.cols && ld == o.ld &&
+               box_rows == o.box_rows && kind == o.kind;
+    }
+};
+constexpr int kMapCache = 32;
+struct MapCache {
+    MapKey key[kMapCache];
+    CUtensorMap map[kMapCache];
+    int used = 0, next = 0;
+};
+thread_local MapCache t_maps;
+
+template <class Encode>
+int cached_map(CUtensorMap* out, const MapKey& k, Encode encode) {
+    MapCache& c = t_maps;
+    for (int i = 0; i < c.used; ++i)
+        if (c.key[i] == k) {
+            *out = c.map[i];
+            return SDL_OK;
+        }
+    const int rc = encode(out);
+    if (rc != SDL_OK) return rc;
+    const int slot = c.used < kMapCache ? c.used++ : c.next;
+    c.next = (slot + 1) % kMapCache;
+    c.key[slot] = k;
+    c.map[slot] = *out;
+    return SDL_OK;
+}
+
 int sm_count() {
     static int count[64] = {0};
     int dev = 0;
@@ -556,8 +594,11 @@ int tc_gemm_terms(const void* const* A, int lda, const void* const* B, int ldb, 
     if (!A || !B || terms < 1 || terms > kMaxTerms || M < 1 || N < 1 || K < 1) return SDL_ERR_ARG;
     if (act == 2 && !gin) return SDL_ERR_ARG;
     if ((lda % 8) || (ldb % 8) || lda < K || ldb < K) return SDL_ERR_ARG;
-    // 128 x 256 tiles when N is a multiple of 256, else 128 x 128
-    const int bn = (N % 256 == 0) ? 256 : 128;
+    // 128 x 256 tiles when N is a multiple of 256 and there are enough of them
+    // to fill the SMs, else 128 x 128 (a small output with a long K, such as a
+    // weight gradient, keeps twice the CTAs busy)
+    const long long mb = (M + BM - 1) / BM;
+    const int bn = (N % 256 == 0 && mb * (N / 256) >= sm_count()) ? 256 : 128;
     Maps maps;
     std::memset(&maps, 0, sizeof(maps));
     int rc;
@@ -565,8 +606,14 @@ int tc_gemm_terms(const void* const* A, int lda, const void* const* B, int ldb, 
         if (!A[t] || !B[t] || (reinterpret_cast<uintptr_t>(A[t]) & 15u) ||
             (reinterpret_cast<uintptr_t>(B[t]) & 15u))
             return SDL_ERR_ARG;
-        if ((rc = make_map(&maps.a[t], A[t], M, K, lda, BM)) != SDL_OK) return rc;
-        if ((rc = make_map(&maps.b[t], B[t], N, K, ldb, bn)) != SDL_OK) return rc;
+        if ((rc = cached_map(&maps.a[t], MapKey{A[t], M, K, lda, BM, 0}, [&](CUtensorMap* m) {
+                 return make_map(m, A[t], M, K, lda, BM);
+             })) != SDL_OK)
+            return rc;
+        if ((rc = cached_map(&maps.b[t], MapKey{B[t], N, K, ldb, bn, 0}, [&](CUtensorMap* m) {
+                 return make_map(m, B[t], N, K, ldb, bn);
+             })) != SDL_OK)
+            return rc;
     }
     Epi e;
     e.alpha = alpha;
@@ -594,14 +641,28 @@ int tc_gemm_terms(const void* const* A, int lda, const void* const* B, int ldb, 
     if (Cb)
         tma = tma && !(reinterpret_cast<uintptr_t>(Cb) & 15u) && ldcb % 8 == 0 && N % 8 == 0 &&
               ldcb >= N;
-    if (tma && C) tma = make_out_map(&maps.c, C, M, N, ldc, false) == SDL_OK;
-    if (tma && Cb) tma = make_out_map(&maps.cb, Cb, M, N, ldcb, true) == SDL_OK;
+    if (tma && C)
+        tma = cached_map(&maps.c, MapKey{C, M, N, ldc, 32, 1}, [&](CUtensorMap* m) {
+                  return make_out_map(m, C, M, N, ldc, false);
+              }) == SDL_OK;
+    if (tma && Cb)
+        tma = cached_map(&maps.cb, MapKey{Cb, M, N, ldcb, 32, 2}, [&](CUtensorMap* m) {
+                  return make_out_map(m, Cb, M, N, ldcb, true);
+              }) == SDL_OK;
     e.tma = tma ? 1 : 0;
     auto launch = [&](auto kern, int BN) -> int {
         const size_t bytes = smem_bytes(BN);
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-            cudaSuccess)
-            return SDL_ERR_CUDA;
+        // the shared-memory opt-in is set once per device and tile width
+        static bool attr_set[2][64] = {};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return SDL_ERR_CUDA;
+        bool& done = attr_set[BN == 256][dev & 63];
+        if (!done || dev >= 64) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                cudaSuccess)
+                return SDL_ERR_CUDA;
+            done = dev < 64;
+        }
         const long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
         const int grid = (int)std::min<long long>(tiles, sm_count());
         kern<<<grid, kThreads, bytes, st>>>(maps, terms, M, N, K, e, err);
