@@ -752,6 +752,20 @@ def study_learned(args):
     for _ in range(args.warmup):
         learned.compare(ctx, net, Yt[:65536], D1g, D2g, s, k=k, reps=1)
     res = learned.compare(ctx, net, Yt, D1g, D2g, s, k=k, reps=max(args.steps, 1))
+    # shortlist recall on the fresh signals: the share of the plain coder's
+    # picks inside the k-pair shortlist, per pick and per signal (all picks)
+    plain = ctx.sparse_code(Yt, D1g, D2g, s)
+    hits, picks, whole = 0, 0, 0
+    for r0 in range(0, N, 131072):
+        sl = slice(r0, min(N, r0 + 131072))
+        cand = ctx.learned_shortlists(net.forward(Yt[sl]), k, k)
+        sup = plain.support[sl]
+        inside = (cand[:, :, None] == sup[:, None, :]).any(dim=1) | (sup < 0)
+        hits += int(((cand[:, :, None] == sup[:, None, :]).any(dim=1) & (sup >= 0)).sum())
+        picks += int((sup >= 0).sum())
+        whole += int(inside.all(dim=1).sum())
+    res.update({"shortlist_recall_per_pick": hits / max(picks, 1),
+                "shortlist_holds_every_pick": whole / N})
     ctx.profile_collect()
     ctx.profile(True)
     net.sparse_code(Yt, D1g, D2g, s, k=k)
@@ -833,6 +847,72 @@ def study_ortho(args):
                       "signals_per_s": N / (med / 1e3), "rmse_trajectory": traj,
                       "kernel_ms_one_iteration": split, "roofline": roof,
                       "general_variant_rmse_trajectory_D12x24": gen}), flush=True)
+    return 0
+
+
+def study_nsweep(args):
+    """Signals/s per Algorithm-1 iteration against N on the c2 shapes (12x12
+    patches of the 64 seeded images, D 12x24, s = 6): the batched path (graph
+    replay, autotuned) and per-call sdl_iterate (tuned tiling), L2 flushed
+    before every timed iteration, median of steps.  The patches of each N are
+    the first N of one seeded stream (chunks of 250 000)."""
+    import torch
+
+    from paper_2007_03800_gb300 import sdl, synth
+    dev = torch.device("cuda:0")
+    p1, p2, n1, n2, s = W["p1"], W["p2"], W["n1"], W["n2"], W["s"]
+    imgs = np.stack([synth.synthetic_image(W["image_seed"] + i) for i in range(W["n_images"])])
+    sizes = [4096, 16384, 65536, 200_000, 1_000_000, 2_000_000]
+    chunks, have = [], 0
+    while have < sizes[-1]:
+        n = min(250_000, sizes[-1] - have)
+        chunks.append(synth.random_patches(imgs, n, p1, seed=W["patch_seed"] + 1000 * len(chunks))
+                      .astype(np.float32))
+        have += n
+    Yall = np.concatenate(chunks)
+    D1, D2 = synth.init_dictionaries(p1, p2, n1, n2, seed=W["dict_seed"])
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = sdl.Context(0)
+    ctx.reserve(p1, p2, n1, n2, s)
+    rows = []
+    for N in sizes:
+        Yg = sdl.signals(torch.from_numpy(Yall[:N]).to(dev))
+        D1g = sdl.dictionary(torch.tensor(D1, dtype=torch.float32, device=dev))
+        D2g = sdl.dictionary(torch.tensor(D2, dtype=torch.float32, device=dev))
+        codes = sdl.Codes.empty(N, s, dev)
+        rmse = torch.zeros(2, dtype=torch.float64, device=dev)
+        tiling, _ = ctx.tune_tiling(Yg, D1g, D2g, s)
+
+        def timed(fn):
+            ms = []
+            for k in range(max(args.steps, 1)):
+                flush.fill_(float(k))
+                a, b = _events()
+                a.record()
+                fn()
+                b.record()
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            return statistics.median(ms)
+
+        for _ in range(args.warmup):
+            ctx.iterate(Yg, D1g, D2g, s, out=codes, rmse_out=rmse)
+        ms_plain = timed(lambda: ctx.iterate(Yg, D1g, D2g, s, out=codes, rmse_out=rmse))
+        batch = sdl.Batch(ctx, [dict(Y=Yg, D1=D1g, D2=D2g, s=s, codes=codes)], autotune=True,
+                          graph=True)
+        for _ in range(args.warmup):
+            batch.iterate(rmse_out=rmse)
+        ms_batch = timed(lambda: batch.iterate(rmse_out=rmse))
+        batch.close()
+        ctx.check()
+        rows.append({"N": N, "ms_batched": round(ms_batch, 4), "signals_per_s_batched": N / (ms_batch / 1e3),
+                     "ms_per_call": round(ms_plain, 4), "signals_per_s_per_call": N / (ms_plain / 1e3),
+                     "per_call_tiling": tiling})
+        del Yg, codes
+    ctx.close()
+    print(json.dumps({"study": "nsweep", "workload": "12x12 patches of the 64 seeded images, D 12x24, s=6, "
+                      "one Algorithm-1 iteration per step, L2 flushed before each", "unit": "signals/s",
+                      "rows": rows}), flush=True)
     return 0
 
 
@@ -1176,7 +1256,7 @@ def main():
                     help="timed region only: no e2e loop, CPU baseline or clock sampling "
                          "(for profiler runs; its numbers are not bench values)")
     ap.add_argument("--study", choices=["precision", "learned", "denoise", "ortho", "gemm", "table3",
-                                        "tmod3", "densegram"],
+                                        "tmod3", "densegram", "nsweep"],
                     help="run one extra study on its own workload instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1187,7 +1267,7 @@ def main():
         return {"precision": study_precision, "learned": study_learned,
                 "denoise": study_denoise, "ortho": study_ortho,
                 "gemm": study_gemm, "table3": study_table3, "densegram": study_densegram,
-                "tmod3": study_tmod3}[args.study](args)
+                "tmod3": study_tmod3, "nsweep": study_nsweep}[args.study](args)
     return run_ours(args)
 
 

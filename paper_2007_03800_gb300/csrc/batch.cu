@@ -28,6 +28,7 @@ struct sdl_batch {
     int total_ctas = 0;
     size_t smem[3] = {0, 0, 0};    // multi-kernel dynamic smem per side
     size_t solve_smem[2] = {0, 0};
+    bool solve_large[2] = {false, false};   // some group's n on this side is > 32
     int gram_blocks = 0, red_blocks[2] = {0, 0}, rescale_blocks = 0;
     // device memory: one allocation, carved up
     char* dmem = nullptr;
@@ -95,7 +96,8 @@ int enqueue_iteration(sdl_batch* b, cudaStream_t st, bool trace) {
         });
         if (rc) return rc;
         rc = run(kSolve, [&] {
-            return launch_multi_update_kernels(2, b->d_solve[si], G, G, b->solve_smem[si], c->err, st);
+            return launch_multi_update_kernels(b->solve_large[si] ? 4 : 2, b->d_solve[si], G, G,
+                                               b->solve_smem[si], c->err, st);
         });
         if (rc) return rc;
     }
@@ -417,6 +419,7 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
             rb += (nf + 31) / 32;
             int keep = 0;
             sm = std::max(sm, solve_smem_bytes(p, n, &keep));
+            if (n > 32) b->solve_large[si] = true;
             SolveDesc d;
             d.red_f = b->red_f[g];
             d.red_d = b->red_d[g];

@@ -155,7 +155,8 @@ struct RescaleDesc {
     int n1, n2, side;
     const float* norms;
 };
-// which: 0 gram, 1 reduce, 2 solve (one CTA per problem), 3 rescale.
+// which: 0 gram, 1 reduce, 2 solve (one CTA per problem; 4 when some problem
+// has n > 32), 3 rescale.
 int launch_multi_update_kernels(int which, const void* d_desc, int G, int blocks, size_t smem,
                                 int* err, cudaStream_t st);
 size_t solve_smem_bytes(int p, int n, int* keep_p);

@@ -2,6 +2,7 @@
 // small normal-equation solve with atom normalisation (Corollary 1 for D1,
 // Result 1 for D2), the W^{-1} rescale of the codes, and the Gram matrices.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 
 #include <cstdint>
@@ -152,23 +153,181 @@ __global__ void __launch_bounds__(kReduceWarps * 32)
 //   4. norms of the columns of D*, D <- D* diag(1/norm), optional G = D^T D.
 // Every step is a data-parallel sweep, one barrier per pivot.  On any
 // failure D is left untouched and the norms are set to 1.
-constexpr int kSolveThreads = 512;
+constexpr int kSolveThreads = 512;       // n > 32
+constexpr int kSolveThreadsSmall = 256;  // n <= 32
 
+// f(integral_constant<int, i>) for i = B .. E-1, unrolled at compile time
+template <int B, int E, class F>
+__device__ __forceinline__ void unrolled_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        unrolled_for<B + 1, E>(f);
+    }
+}
+
+// In-place Gauss-Jordan inverse of the nu x nu matrix A (stride lda) without
+// pivoting, the matrix held in registers: thread (ti, tj) of a TI x TJ grid
+// owns rows ti + TI r and columns tj + TJ c (r < RI, c < RJ), so a warp reads
+// consecutive columns.  Only the pivot row and column go through shared
+// memory (rc: two buffers of row | column, 4 nu floats), published by their
+// owners after each update: one barrier per pivot.  Every element takes the
+// same operations as the shared-memory form:
+//   a_rc - (a_rk / p) a_kc,  a_kc / p,  -a_rk / p,  1 / p.
+// Pivots run as k = t + TI r (r outer and unrolled, t inner), so pivot k sits
+// in register row r and, with TJ a multiple of TI, in register column
+// r / (TJ / TI): no register array is indexed at run time.
+// Returns false (everywhere) at the first pivot that fails the relative test.
+template <int TI, int TJ, int RI, int RJ>
+__device__ bool gj_inverse_regs(float* A, int lda, int nu, const float* d0, float* rc) {
+    static_assert(TJ % TI == 0, "pivot columns must follow the row blocks");
+    constexpr int M = TJ / TI;
+    const int tid = threadIdx.x, ti = tid / TJ, tj = tid % TJ;
+    float a[RI][RJ];
+#pragma unroll
+    for (int r = 0; r < RI; ++r)
+#pragma unroll
+        for (int c = 0; c < RJ; ++c) {
+            const int R = ti + TI * r, C = tj + TJ * c;
+            a[r][c] = (R < nu && C < nu) ? A[R * lda + C] : 0.f;
+        }
+    // buffer b: pivot row at rc + 2 nu b, pivot column at rc + 2 nu b + nu;
+    // the owners of row / column kn (register row rr, register column cc)
+    // write them there
+    auto publish = [&](int kn, auto rrc, auto ccc) {
+        constexpr int rr = decltype(rrc)::value, cc = decltype(ccc)::value;
+        float* rown = rc + 2 * nu * (kn & 1);
+        float* coln = rown + nu;
+        if (ti == kn % TI)
+#pragma unroll
+            for (int c = 0; c < RJ; ++c)
+                if (tj + TJ * c < nu) rown[tj + TJ * c] = a[rr][c];
+        if (tj == kn % TJ)
+#pragma unroll
+            for (int r = 0; r < RI; ++r)
+                if (ti + TI * r < nu) coln[ti + TI * r] = a[r][cc];
+    };
+    publish(0, std::integral_constant<int, 0>{}, std::integral_constant<int, 0>{});
+    __syncthreads();
+    bool ok = true, done = false;
+    unrolled_for<0, RI>([&](auto rcst) {
+        constexpr int r0 = decltype(rcst)::value;
+        if (done) return;
+        for (int t = 0; t < TI; ++t) {
+            const int k = t + TI * r0;
+            if (k >= nu) {
+                done = true;
+                break;
+            }
+            const float* rowk = rc + 2 * nu * (k & 1);
+            const float* colk = rowk + nu;
+            const float piv = colk[k];
+            if (!(piv > kSolvePivotRel * d0[k])) {
+                ok = false;
+                done = true;
+                break;
+            }
+            const float inv = 1.f / piv;
+            float cr[RI], rw[RJ];
+#pragma unroll
+            for (int r = 0; r < RI; ++r) cr[r] = colk[min(ti + TI * r, nu - 1)];
+#pragma unroll
+            for (int c = 0; c < RJ; ++c) rw[c] = rowk[min(tj + TJ * c, nu - 1)];
+#pragma unroll
+            for (int r = 0; r < RI; ++r) {
+                const int R = ti + TI * r;
+                const float f = cr[r] * inv;
+#pragma unroll
+                for (int c = 0; c < RJ; ++c) {
+                    const int C = tj + TJ * c;
+                    float v;
+                    if (R != k) v = (C != k) ? fmaf(-f, rw[c], a[r][c]) : cr[r] * -inv;
+                    else v = (C != k) ? rw[c] * inv : inv;
+                    a[r][c] = v;
+                }
+            }
+            const int kn = k + 1;
+            if (kn < nu) {
+                if (t + 1 < TI) {
+                    publish(kn, std::integral_constant<int, r0>{}, std::integral_constant<int, r0 / M>{});
+                } else if constexpr (r0 + 1 < RI) {
+                    publish(kn, std::integral_constant<int, r0 + 1>{},
+                            std::integral_constant<int, (r0 + 1) / M>{});
+                }
+            }
+            __syncthreads();
+        }
+    });
+    if (ok)
+#pragma unroll
+        for (int r = 0; r < RI; ++r)
+#pragma unroll
+            for (int c = 0; c < RJ; ++c) {
+                const int R = ti + TI * r, C = tj + TJ * c;
+                if (R < nu && C < nu) A[R * lda + C] = a[r][c];
+            }
+    return ok;
+}
+
+// out[a][c] = init(a, c) + sum_k Lf(a, k) Rf(k, c) for a < m, c < nu, k in
+// increasing order (each entry one FMA chain, as a plain loop), in 4 x 4
+// register blocks: thread (ta, tc) of a TA x TC grid takes rows ta + TA i and
+// columns tc + TC j, so a warp reads one row of L and consecutive columns of
+// R.  `emit` receives (a, c, value).
+template <int TA, int TC, class Lf, class Rf, class Init, class Emit>
+__device__ __forceinline__ void block_product(int m, int nu, int kn, Lf lf, Rf rf, Init init,
+                                              Emit emit) {
+    const int tid = threadIdx.x, ta = tid / TC, tc = tid % TC;
+    for (int ab = 0; ab < m; ab += 4 * TA)
+        for (int cb = 0; cb < nu; cb += 4 * TC) {
+            float acc[4][4];
+            int ai[4], ci[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ai[i] = min(ab + ta + TA * i, m - 1);
+                ci[i] = min(cb + tc + TC * i, nu - 1);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = init(ai[i], ci[j]);
+            for (int k = 0; k < kn; ++k) {
+                float l[4], r[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) l[i] = lf(ai[i], k);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) r[j] = rf(k, ci[j]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(l[i], r[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int a = ab + ta + TA * i, c = cb + tc + TC * j;
+                    if (a < m && c < nu) emit(a, c, acc[i][j]);
+                }
+        }
+}
+
+// kLarge: the n > 32 instantiation (the 8 x 4 register Gauss-Jordan and the
+// blocked products); the n <= 32 one stays small, since each solve runs once
+// from a cold instruction cache.
+template <bool kLarge>
 __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
                                            const double* __restrict__ red_d, float* D, int p,
                                            int n, float* __restrict__ norms, double inv_count,
                                            double* objective_out, double* rmse_out, int* err,
                                            float* G_out, int keep_p) {
     extern __shared__ __align__(16) float sm[];
-    // keep_p bit 0: a copy of P_u stays in shared memory; bit 1: the inverse
-    // alternates between two buffers (one barrier per pivot), else it is formed
-    // in place from saved copies of the pivot row and column (two barriers)
-    const bool pingpong = (keep_p & 2) != 0;
+    // keep_p: a copy of P_u stays in shared memory for the objective term
+    // (else P_u is read again into A once the inverse has been used)
     keep_p &= 1;
     const int lda = n | 1;                          // odd row strides: fewer bank conflicts
     float* A = sm;                                  // nu x nu (stride lda): P_u, then its inverse
-    float* A2 = A + n * lda;                        // second buffer, or pivot row | column (2n)
-    float* Bc = A2 + (pingpong ? n * lda : 2 * n);  // p x nu right-hand sides (stride lda)
+    float* A2 = A + n * lda;                        // pivot rows | columns, two buffers (4n)
+    float* Bc = A2 + 4 * n;                         // p x nu right-hand sides (stride lda)
     float* X = Bc + p * lda;                        // p x nu, D* rows (stride lda)
     float* Dn = X + p * lda;                        // p x n, old then new D (stride lda)
     float* P0 = Dn + p * lda;                       // nu x nu copy of P_u (stride lda), if kept
@@ -207,6 +366,7 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
     const int nu = s_nu;
     // every loop below maps rows to warps and columns to lanes (no index division)
     int bad = 0;
+#pragma unroll 4
     for (int r = warp; r < nu; r += nw)
         for (int c = lane; c < nu; c += 32) {
             const float v = P[idx[r] * n + idx[c]];
@@ -214,89 +374,127 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
             if (keep_p) P0[r * lda + c] = v;
             if (!isfinite(v)) bad = SDL_ERR_NONFINITE;
         }
+#pragma unroll 4
     for (int r = warp; r < p; r += nw)
         for (int c = lane; c < nu; c += 32) {
             const float v = B[r * n + idx[c]];
             Bc[r * lda + c] = v;
             if (!isfinite(v)) bad = SDL_ERR_NONFINITE;
         }
+#pragma unroll 4
     for (int c = warp; c < n; c += nw)
         for (int r = lane; r < p; r += 32) Dn[r * lda + c] = D[r + p * c];
     if (bad) s_fail = bad;
     __syncthreads();
 
-    // 1. Gauss-Jordan inverse of the used block: each pivot step reads one
-    //    buffer and writes the other (one barrier per pivot); every thread sees
-    //    the same pivot, so a failed pivot test ends the loop everywhere
-    float* Ain = A;
+    // 1. Gauss-Jordan inverse of the used block, held in registers (one
+    //    barrier per pivot); every thread sees the same pivot, so a failed
+    //    pivot test ends the loop everywhere
     if (s_fail == 0) {
-        float* Aout = A2;
-        float* rowk = A2;           // in-place form: saved pivot row and column
-        float* colk = A2 + n;
-        for (int k = 0; k < nu; ++k) {
-            const float piv = Ain[k * lda + k];
-            if (!(piv > kSolvePivotRel * d0[k])) {
-                if (tid == 0) s_fail = SDL_ERR_SINGULAR;
-                break;
+        bool ok;
+        bool regs = false;
+        if constexpr (kLarge) {
+            if (nth == kSolveThreads && nu <= 128) {
+                ok = gj_inverse_regs<16, 32, 8, 4>(A, lda, nu, d0, A2);
+                regs = true;
             }
-            const float inv = 1.f / piv;
-            const float* rk = Ain + k * lda;
-            if (!pingpong) {
-                for (int c = tid; c < nu; c += nth) {
-                    rowk[c] = rk[c];
-                    colk[c] = Ain[c * lda + k];
-                }
-                __syncthreads();
-                rk = rowk;
-            }
-            for (int r = warp; r < nu; r += nw) {
-                const float* ar = Ain + r * lda;
-                const float ark = pingpong ? ar[k] : colk[r];
-                const float f = ark * inv;
-                float* out = (pingpong ? Aout : Ain) + r * lda;
-                for (int c = lane; c < nu; c += 32) {
-                    float v;
-                    if (r != k) v = (c != k) ? fmaf(-f, rk[c], ar[c]) : ark * -inv;
-                    else v = (c != k) ? rk[c] * inv : inv;
-                    out[c] = v;
-                }
-            }
-            __syncthreads();
-            if (pingpong) {
-                float* t = Ain;
-                Ain = Aout;
-                Aout = t;
+        } else {
+            if (nth == kSolveThreadsSmall && nu <= 32) {
+                ok = gj_inverse_regs<16, 16, 2, 2>(A, lda, nu, d0, A2);
+                regs = true;
             }
         }
+        if (!regs) {
+            // any other size: in place through shared memory, the saved pivot
+            // row and column in A2 (two barriers per pivot)
+            ok = true;
+            float* rowk = A2;
+            float* colk = A2 + n;
+            for (int k = 0; k < nu; ++k) {
+                const float piv = A[k * lda + k];
+                if (!(piv > kSolvePivotRel * d0[k])) {
+                    ok = false;
+                    break;
+                }
+                const float inv = 1.f / piv;
+                for (int c = tid; c < nu; c += nth) {
+                    rowk[c] = A[k * lda + c];
+                    colk[c] = A[c * lda + k];
+                }
+                __syncthreads();
+                for (int r = warp; r < nu; r += nw) {
+                    float* ar = A + r * lda;
+                    const float ark = colk[r];
+                    const float f = ark * inv;
+                    for (int c = lane; c < nu; c += 32) {
+                        float v;
+                        if (r != k) v = (c != k) ? fmaf(-f, rowk[c], ar[c]) : ark * -inv;
+                        else v = (c != k) ? rowk[c] * inv : inv;
+                        ar[c] = v;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (!ok && tid == 0) s_fail = SDL_ERR_SINGULAR;
     }
     __syncthreads();
+    const float* Ain = A;
     const bool ok_inv = (s_fail == 0);
     double part = 0.0;
     if (ok_inv) {
-        // 2. D* rows
-        for (int a = warp; a < p; a += nw)
-            for (int c = lane; c < nu; c += 32) {
-                float x = 0.f;
+        // 2. D* rows: D*[a][c] = sum_k B[a][k] P_u^{-1}[k][c].  Few entries
+        //    (p nu <= 2 threads): one chain per thread; else 4 x 4 blocks
+        const bool blocked = kLarge && nth == kSolveThreads && p * nu > 2 * nth;
+        if constexpr (kLarge) {
+            if (blocked)
+            block_product<16, 32>(
+                p, nu, nu, [&](int a, int k) { return Bc[a * lda + k]; },
+                [&](int k, int c) { return Ain[k * lda + c]; }, [](int, int) { return 0.f; },
+                [&](int a, int c, float v) { X[a * lda + c] = v; });
+        }
+        if (!blocked) {
+            for (int a = warp; a < p; a += nw)
+                for (int c = lane; c < nu; c += 32) {
+                    float x = 0.f;
 #pragma unroll 4
-                for (int k = 0; k < nu; ++k) x = fmaf(Bc[a * lda + k], Ain[k * lda + c], x);
-                X[a * lda + c] = x;
-            }
+                    for (int k = 0; k < nu; ++k) x = fmaf(Bc[a * lda + k], Ain[k * lda + c], x);
+                    X[a * lda + c] = x;
+                }
+        }
         __syncthreads();
-        // 3. objective change, row a and used atom c at a time, P (used
-        //    block) from the kept copy or read back from red_f
-        for (int a = warp; a < p; a += nw)
-            for (int c = lane; c < nu; c += 32) {
-                float w = -2.f * Bc[a * lda + c];
-                if (keep_p) {
-                    const float* prow = P0 + c * lda;
+        // 3. objective change: for row a and used atom c,
+        //    w = -2 B[a][c] + sum_k P_u[c][k] (D_old[a][idx k] + D*[a][k]),
+        //    the sum in increasing k; P_u from the kept copy, or read again
+        //    into A (the inverse is no longer needed)
+        const float* Pu = P0;
+        if (!keep_p) {
+#pragma unroll 4
+            for (int r = warp; r < nu; r += nw)
+                for (int c = lane; c < nu; c += 32) A[r * lda + c] = P[idx[r] * n + idx[c]];
+            __syncthreads();
+            Pu = A;
+        }
+        if constexpr (kLarge) {
+            if (blocked)
+            block_product<16, 32>(
+                p, nu, nu, [&](int a, int k) { return Dn[a * lda + idx[k]] + X[a * lda + k]; },
+                [&](int k, int c) { return Pu[c * lda + k]; },
+                [&](int a, int c) { return -2.f * Bc[a * lda + c]; },
+                [&](int a, int c, float w) {
+                    part += (double)(X[a * lda + c] - Dn[a * lda + idx[c]]) * (double)w;
+                });
+        }
+        if (!blocked) {
+            for (int a = warp; a < p; a += nw)
+                for (int c = lane; c < nu; c += 32) {
+                    float w = -2.f * Bc[a * lda + c];
+                    const float* prow = Pu + c * lda;
 #pragma unroll 4
                     for (int k = 0; k < nu; ++k) w = fmaf(prow[k], Dn[a * lda + idx[k]] + X[a * lda + k], w);
-                } else {
-                    const float* prow = P + (size_t)idx[c] * n;
-                    for (int k = 0; k < nu; ++k) w = fmaf(prow[idx[k]], Dn[a * lda + idx[k]] + X[a * lda + k], w);
+                    part += (double)(X[a * lda + c] - Dn[a * lda + idx[c]]) * (double)w;
                 }
-                part += (double)(X[a * lda + c] - Dn[a * lda + idx[c]]) * (double)w;
-            }
+        }
         // 4. column norms of D*
         for (int c = tid; c < nu; c += nth) {
             float ss = 0.f;
@@ -345,19 +543,21 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ red_f,
     }
 }
 
+template <bool kLarge>
 __global__ void __launch_bounds__(kSolveThreads)
     solve_kernel(const float* __restrict__ red_f, const double* __restrict__ red_d, float* D, int p,
                  int n, float* __restrict__ norms, double inv_count, double* objective_out,
                  double* rmse_out, int* err, float* G_out, int keep_p) {
-    solve_body(red_f, red_d, D, p, n, norms, inv_count, objective_out, rmse_out, err, G_out,
-               keep_p);
+    solve_body<kLarge>(red_f, red_d, D, p, n, norms, inv_count, objective_out, rmse_out, err,
+                       G_out, keep_p);
 }
 
 // One CTA per problem.
+template <bool kLarge>
 __global__ void __launch_bounds__(kSolveThreads) solve_multi_kernel(const SolveDesc* __restrict__ d,
                                                                     int* err) {
     const SolveDesc q = d[blockIdx.x];
-    solve_body(q.red_f, q.red_d, q.D, q.p, q.n, q.norms, q.inv_count, q.objective_out, q.rmse_out,
+    solve_body<kLarge>(q.red_f, q.red_d, q.D, q.p, q.n, q.norms, q.inv_count, q.objective_out, q.rmse_out,
                err, q.G_out, q.keep_p);
 }
 
@@ -574,14 +774,13 @@ __global__ void rescale_multi_kernel(const RescaleDesc* __restrict__ d) {
 
 size_t solve_smem_bytes(int p, int n, int* keep_p) {
     const size_t lda = (size_t)(n | 1);
-    const size_t rest = 3 * (size_t)p * lda + 3 * (size_t)n;
+    // A, the two pivot row | column buffers, B, D*, D and the n-vectors
+    const size_t base = (size_t)n * lda + 4 * (size_t)n + 3 * (size_t)p * lda + 3 * (size_t)n;
     const size_t limit = 200 * 1024 / sizeof(float);
-    // prefer the kept copy of P, then the second inverse buffer
-    const int keep = (size_t)n * lda * 2 + 2 * (size_t)n + rest <= limit ? 1 : 0;
-    const size_t base = (size_t)n * lda * (1 + keep) + rest;
-    const int pp = base + (size_t)n * lda <= limit ? 2 : 0;
-    if (keep_p) *keep_p = keep | pp;
-    return sizeof(float) * (base + (pp ? (size_t)n * lda : 2 * (size_t)n));
+    // a kept copy of P for the objective term when it fits
+    const int keep = base + (size_t)n * lda <= limit ? 1 : 0;
+    if (keep_p) *keep_p = keep;
+    return sizeof(float) * (base + (keep ? (size_t)n * lda : 0));
 }
 
 int launch_multi_update_kernels(int which, const void* d_desc, int G, int blocks, size_t smem,
@@ -595,12 +794,16 @@ int launch_multi_update_kernels(int which, const void* d_desc, int G, int blocks
                 static_cast<const ReduceDesc*>(d_desc), G);
             break;
         case 2:
-            if (cudaFuncSetAttribute(solve_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
+        case 4: {
+            // 4: some problem has n > 32
+            auto kern = which == 4 ? solve_multi_kernel<true> : solve_multi_kernel<false>;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
                 return SDL_ERR_CUDA;
-            solve_multi_kernel<<<G, kSolveThreads, smem, st>>>(static_cast<const SolveDesc*>(d_desc),
-                                                               err);
+            kern<<<G, which == 4 ? kSolveThreads : kSolveThreadsSmall, smem, st>>>(
+                static_cast<const SolveDesc*>(d_desc), err);
             break;
+        }
         case 3:
             rescale_multi_kernel<<<dim3(std::max(1, blocks), G), 256, 0, st>>>(
                 static_cast<const RescaleDesc*>(d_desc));
@@ -651,11 +854,11 @@ int launch_solve(const float* red_f, const double* red_d, float* D, int p, int n
     // keep a copy of P in shared memory for the objective term when it fits
     int keep_p = 0;
     const size_t bytes = solve_smem_bytes(p, n, &keep_p);
-    if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes) != cudaSuccess)
+    auto kern = n > 32 ? solve_kernel<true> : solve_kernel<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
         return SDL_ERR_CUDA;
-    const int threads = n <= 32 ? 256 : kSolveThreads;
-    solve_kernel<<<1, threads, bytes, st>>>(red_f, red_d, D, p, n, norms, inv_count, objective_out,
+    kern<<<1, n > 32 ? kSolveThreads : kSolveThreadsSmall, bytes, st>>>(red_f, red_d, D, p, n, norms, inv_count, objective_out,
                                             rmse_out, err, G_out, keep_p);
     return cudaGetLastError() == cudaSuccess ? SDL_OK : SDL_ERR_CUDA;
 }
