@@ -207,13 +207,24 @@ __device__ __noinline__ float rescore_dot(const float* __restrict__ w, const flo
 // [16,24) sum scratch, 24 = broadcast b, 25 = accept flag.
 enum { kMiscMax = 0, kMiscMin = 8, kMiscSum = 16, kMiscB = 24, kMiscOk = 25 };
 
-template <class Tl, int SIDE>
+// Signal and dictionary sizes fixed at compile time (0: taken from the call),
+// so that the contraction, re-scoring and epilogue loops of a frequent shape
+// unroll with constant bounds and strides.
+template <int P1, int P2, int N1, int N2, int S>
+struct FixedSizes {
+    static constexpr int p1 = P1, p2 = P2, n1 = N1, n2 = N2, s = S;
+};
+using RuntimeSizes = FixedSizes<0, 0, 0, 0, 0>;
+
+template <class Tl, int SIDE, class FS = RuntimeSizes>
 __global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
     constexpr int T = Tl::T, TW = Tl::TW, RI = Tl::RI, RJ = Tl::RJ;
     constexpr int LI = Tl::LI, N1P = Tl::N1P, N2P = Tl::N2P;
     extern __shared__ __align__(16) float smem[];
 
-    const int p1 = a.p1, p2 = a.p2, n1 = a.n1, n2 = a.n2, s = a.s;
+    const int p1 = FS::p1 ? FS::p1 : a.p1, p2 = FS::p2 ? FS::p2 : a.p2;
+    const int n1 = FS::n1 ? FS::n1 : a.n1, n2 = FS::n2 ? FS::n2 : a.n2;
+    const int s = FS::s ? FS::s : a.s;
     const int p1p2 = p1 * p2;
     const int tpc = blockDim.x / T;
     const int team = threadIdx.x / T;
@@ -743,7 +754,7 @@ constexpr int kMaxSmem = 200 * 1024;
 constexpr int kCtaSlotsPerSm = 8;
 constexpr int kGlobalSlots = 64;
 
-template <class Tl, int SIDE>
+template <class Tl, int SIDE, class FS = RuntimeSizes>
 int launch_code_impl(const PassArgs& a0, cudaStream_t st, int num_sms) {
     PassArgs a = a0;
     const int nacc = (SIDE == kSideD1) ? a.n1 : a.n2;
@@ -764,7 +775,7 @@ int launch_code_impl(const PassArgs& a0, cudaStream_t st, int num_sms) {
             return SDL_ERR_UNSUPPORTED;
         }
     }
-    auto kern = code_pass_kernel<Tl, SIDE>;
+    auto kern = code_pass_kernel<Tl, SIDE, FS>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
         cudaSuccess)
         return SDL_ERR_CUDA;
@@ -855,7 +866,17 @@ int dispatch_code(const PassArgs& a, cudaStream_t st, int num_sms) {
     if (n1 <= 16 && n2 <= 16) return launch_code_impl<Tile16, SIDE>(a, st, num_sms);
     if (n1 <= 24 && n2 <= 24) return launch_code_impl<Tile24, SIDE>(a, st, num_sms);
     if (n1 <= 32 && n2 <= 32) return launch_code_impl<Tile32, SIDE>(a, st, num_sms);
-    if (n1 <= 32 && n2 <= 128) return launch_code_impl<Tile32x128, SIDE>(a, st, num_sms);
+    if (n1 <= 32 && n2 <= 128) {
+        // the hyperspectral-shaped problem (16 x 64 signals, 32 x 128 atoms,
+        // and s = 10) with its sizes fixed at compile time
+        if (a.p1 == 16 && a.p2 == 64 && n1 == 32 && n2 == 128) {
+            if (a.s == 10)
+                return launch_code_impl<Tile32x128, SIDE, FixedSizes<16, 64, 32, 128, 10>>(a, st,
+                                                                                          num_sms);
+            return launch_code_impl<Tile32x128, SIDE, FixedSizes<16, 64, 32, 128, 0>>(a, st, num_sms);
+        }
+        return launch_code_impl<Tile32x128, SIDE>(a, st, num_sms);
+    }
     if (n1 <= 128 && n2 <= 32) return launch_code_impl<Tile128x32, SIDE>(a, st, num_sms);
     if (n1 <= 64 && n2 <= 64) return launch_code_impl<Tile64, SIDE>(a, st, num_sms);
     return SDL_ERR_UNSUPPORTED;

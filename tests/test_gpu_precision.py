@@ -192,3 +192,20 @@ def test_hsi_precision_study(prec_ctx):
         assert e["D1_abs"] < 1e-3, (name, e)
         assert e["D2_abs"] < 1e-3, (name, e)
 
+
+
+@pytest.mark.parametrize("s,eps", [(10, None), (7, None), (10, 15.2)])
+def test_fp32_hsi_shape_codes_match_oracle(prec_ctx, s, eps):
+    """The FP32 coder at the 16x64 / 32x128 shapes (its compiled-size
+    instantiations: s = 10 fixed, any other s, and the error-driven stop)
+    against the FP64 oracle on 515 signals (several CTAs of four teams and a
+    ragged tail)."""
+    Y, D1, D2 = hsi_problem(515, seed=35)
+    ref = oracle.omp2d(Y, D1, D2, s, eps=eps)        # eps 15.2: about half stop early
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    out = prec_ctx.sparse_code(Yg, D1g, D2g, s, eps=eps or 0.0,
+                               out=sdl.Codes.empty(515, s, "cuda:0", with_energy=True))
+    assert prec_ctx.status() == 0
+    check_codes(Y, D1, D2, s, out.support.cpu().numpy(), out.nnz.cpu().numpy(),
+                out.coef.cpu().numpy(), energy=out.res_energy.cpu().numpy(), eps=eps,
+                ref=ref).assert_ok()
