@@ -172,9 +172,13 @@ int sdl_iterate(sdl_ctx* ctx, const float* Y, int p1, int p2, int64_t N,
  *
  * A group is described like the arguments of sdl_iterate (all device
  * pointers, owned by the caller, which must keep them valid and unmoved for
- * the batch's lifetime; Y 16-byte aligned).  Each group must have a compiled
- * specialised shape: (p1, p2, n1, n2, s_max) in {(8,8,16,16,4),
- * (12,12,24,24,6), (16,16,32,32,8)}, else SDL_ERR_UNSUPPORTED.  eps > 0 gives
+ * the batch's lifetime).  A group with a compiled specialised shape,
+ * (p1, p2, n1, n2, s_max) in {(8,8,16,16,4), (12,12,24,24,6), (16,16,32,32,8)},
+ * and Y 16-byte aligned joins the persistent multi-problem launch.  Any other
+ * group that sdl_sparse_code supports (n1 <= 32 and n2 <= 128, n1 <= 128 and
+ * n2 <= 32, or both <= 64) is coded by the generic kernel in a launch of its
+ * own within the same iteration (and graph); its update stages still share
+ * the one launch per stage.  Other shapes: SDL_ERR_UNSUPPORTED.  eps > 0 gives
  * the group an error-driven stop (Sec. IV), per group.
  */
 typedef struct sdl_group {
@@ -217,9 +221,11 @@ int sdl_batch_sparse_code(sdl_batch* batch, void* stream);
  * its D1 update (2g) and after its D2 update (2g + 1). */
 int sdl_batch_iterate(sdl_batch* batch, double* rmse_out, void* stream);
 
-/* Host arrays of n_groups (each may be NULL): chosen tiling id, CTAs given to
- * the group, and the measured (autotune) or modelled cost of one of its
- * coding passes in microseconds.  Returns n_groups. */
+/* Host arrays of n_groups (each may be NULL): chosen tiling id (-1 for a
+ * group coded by the generic kernel), CTAs given to the group in the
+ * multi-problem launch (0 for those), and the measured (autotune) or
+ * modelled cost of one of its coding passes in microseconds.  Returns
+ * n_groups. */
 int sdl_batch_tuning(const sdl_batch* batch, int* shape_id, int* ctas, float* cost_us);
 
 /* Every measurement the autotuner took (empty without SDL_BATCH_AUTOTUNE): for

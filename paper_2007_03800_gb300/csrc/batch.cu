@@ -4,6 +4,9 @@
 // groups, and the whole Algorithm-1 iteration captured once into a CUDA graph
 // that is replayed every iteration.  An autotuner times the compiled lane
 // tilings of every group and splits the CTAs between groups by measured cost.
+// A group whose shape has no compiled tiling (for instance 16 x 64 signals
+// with 32 x 128 atoms) is coded by the generic kernel in a launch of its own
+// inside the same iteration; its update stages join the others'.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -18,7 +21,10 @@ struct sdl_batch {
     sdl_ctx* ctx = nullptr;
     int G = 0;
     std::vector<sdl_group> groups;
-    std::vector<int> shape;        // compiled tiling per group
+    std::vector<int> shape;        // compiled tiling per group (-1: generic kernel)
+    std::vector<int> generic;      // groups coded by the generic kernel
+    std::vector<int> gslots[3];    // their partial-sum slots per pass side
+    int n_fast = 0;                // groups in the multi-problem kernel
     std::vector<int> cta_begin;    // G + 1 prefix of CTAs per group
     std::vector<float> cost_us;    // time of one fused pass of the group alone
     int single_cps = 0;            // one group: the CTAs per SM the autotuner chose
@@ -56,9 +62,19 @@ constexpr int kMultiWarps = 8;   // warps per CTA of the persistent multi-proble
 // single group its tiling's own kernel on the same CTAs (no other problem's
 // code shares its register allocation).
 int code_pass(const sdl_batch* b, int side, cudaStream_t st) {
-    if (b->G == 1) return launch_code_pass_grid(b->args[side][0], side, b->shape[0], b->total_ctas, st);
-    return launch_code_multi(b->d_args[side], b->d_cta_begin, b->d_shape, b->G, b->total_ctas,
-                             b->smem[side], side, st, b->ctx->num_sms);
+    int rc = SDL_OK;
+    if (b->n_fast > 0) {
+        rc = b->G == 1 ? launch_code_pass_grid(b->args[side][0], side, b->shape[0], b->total_ctas, st)
+                       : launch_code_multi(b->d_args[side], b->d_cta_begin, b->d_shape, b->G,
+                                           b->total_ctas, b->smem[side], side, st, b->ctx->num_sms);
+        if (rc != SDL_OK) return rc;
+    }
+    for (size_t i = 0; i < b->generic.size(); ++i) {
+        const int r = launch_code_pass_generic(b->args[side][b->generic[i]], side, st, b->ctx->num_sms);
+        if (r < 0) return r;
+        if (r != b->gslots[side][i]) return SDL_ERR_CUDA;   // the planned reduction would miss slots
+    }
+    return SDL_OK;
 }
 
 
@@ -106,15 +122,22 @@ int enqueue_iteration(sdl_batch* b, cudaStream_t st, bool trace) {
     });
 }
 
-bool valid_group(const sdl_group& g, int* shape_ids, int* n_ids) {
-    if (!g.Y || !g.D1 || !g.D2 || !g.support || !g.coef || !g.nnz || g.N < 1) return false;
-    if ((reinterpret_cast<uintptr_t>(g.Y) & 15u) != 0) return false;
-    int all[16];
-    const int n = fast_shape_variants(g.p1, g.p2, g.n1, g.n2, g.s_max, all, 16);
+// A group is valid with at least one compiled tiling the multi-problem kernel
+// can run (Y 16-byte aligned), or else a shape the generic kernel supports
+// (*generic set, *n_ids = 0).
+bool valid_group(const sdl_group& g, int* shape_ids, int* n_ids, bool* generic) {
     *n_ids = 0;
-    for (int v = 0; v < n && *n_ids < 8; ++v)
-        if (fast_variant_warps(all[v]) <= kMultiWarps) shape_ids[(*n_ids)++] = all[v];
-    return *n_ids > 0;
+    *generic = false;
+    if (!g.Y || !g.D1 || !g.D2 || !g.support || !g.coef || !g.nnz || g.N < 1) return false;
+    if ((reinterpret_cast<uintptr_t>(g.Y) & 15u) == 0) {
+        int all[16];
+        const int n = fast_shape_variants(g.p1, g.p2, g.n1, g.n2, g.s_max, all, 16);
+        for (int v = 0; v < n && *n_ids < 8; ++v)
+            if (fast_variant_warps(all[v]) <= kMultiWarps) shape_ids[(*n_ids)++] = all[v];
+    }
+    if (*n_ids > 0) return true;
+    *generic = code_shape_supported(g.p1, g.p2, g.n1, g.n2, g.s_max);
+    return *generic;
 }
 
 void destroy(sdl_batch* b) {
@@ -144,12 +167,15 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
     std::vector<std::vector<int>> variants(G);
     for (int g = 0; g < G; ++g) {
         int ids[8], n = 0;
-        if (!valid_group(groups[g], ids, &n)) {
+        bool gen = false;
+        if (!valid_group(groups[g], ids, &n, &gen)) {
             destroy(b);
             return SDL_ERR_UNSUPPORTED;
         }
         variants[g].assign(ids, ids + n);
+        if (gen) b->generic.push_back(g);
     }
+    b->n_fast = G - (int)b->generic.size();
 
     // ---- device memory
     const int max_slots = c->num_sms * kSlotsPerSm;
@@ -237,6 +263,16 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
         b->args[kCodeOnly][g] = a;               // sparse coding only
         b->args[kSideD2][g] = a;                 // pass 2: codes + partial sums
     }
+    // slots the generic groups' passes will write (their reductions are sized now)
+    for (int side = 0; side < 3; ++side)
+        for (int g : b->generic) {
+            const int r = launch_code_pass_generic(b->args[side][g], side, st, c->num_sms, true);
+            if (r < 0 || r > max_slots) {
+                destroy(b);
+                return r < 0 ? r : SDL_ERR_UNSUPPORTED;
+            }
+            b->gslots[side].push_back(r);
+        }
     // Gram matrices of the given dictionaries, needed by the autotuning passes
     std::vector<GramDesc> gram(2 * G);
     int blk = 0;
@@ -299,8 +335,12 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
         for (int g = 0; g < G; ++g) {
             float best = 1e30f;
             int best_cps = 2;
-            b->shape[g] = variants[g][0];
             b->cost_us[g] = (float)(model_cost(groups[g]) * 1e-6);
+            if (variants[g].empty()) {   // generic kernel: nothing to tune
+                b->shape[g] = -1;
+                continue;
+            }
+            b->shape[g] = variants[g][0];
             for (int v : variants[g]) {
                 const size_t sm_v = fast_smem_bytes(v, kSideD1);
                 int fit = G == 1 ? fast_variant_ctas_per_sm(v, kSideD1) : multi_ctas_per_sm(sm_v, kSideD1);
@@ -353,29 +393,37 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
         if (!replaced) c->batch_tunes.push_back(std::move(t));
     } else {
         for (int g = 0; g < G; ++g) {
-            b->shape[g] = variants[g][0];
+            b->shape[g] = variants[g].empty() ? -1 : variants[g][0];
             b->cost_us[g] = (float)(model_cost(groups[g]) * 1e-6);
         }
     }
+    // the multi-problem kernel's groups (generic ones take no CTAs in it)
+    std::vector<int> fast;
+    for (int g = 0; g < G; ++g)
+        if (!variants[g].empty()) fast.push_back(g);
+    const int F = (int)fast.size();
     for (int side = 0; side < 3; ++side) {
         size_t m = 0;
-        for (int g = 0; g < G; ++g) m = std::max(m, fast_smem_bytes(b->shape[g], side));
+        for (int g : fast) m = std::max(m, fast_smem_bytes(b->shape[g], side));
         b->smem[side] = m;
     }
     int cps = 2;
-    for (int side = 0; side < 3; ++side)
+    for (int side = 0; side < 3 && F > 0; ++side)
         cps = std::min(cps, std::max(1, G == 1 ? fast_variant_ctas_per_sm(b->shape[0], side)
                                                : multi_ctas_per_sm(b->smem[side], side)));
     if (G == 1 && b->single_cps > 0) cps = std::min(cps, b->single_cps);
-    int total = c->num_sms * cps;
-    std::vector<int> n_cta(G, 1);
-    {
-        std::vector<long long> cap(G);
-        for (int g = 0; g < G; ++g) cap[g] = std::max<long long>(1, (groups[g].N + 7) / 8);
-        const double csum = std::accumulate(b->cost_us.begin(), b->cost_us.end(), 0.0);
+    int total = F > 0 ? c->num_sms * cps : 0;
+    std::vector<int> n_cta(G, 0);
+    if (F > 0) {
+        std::vector<long long> cap(G, 0);
+        double csum = 0.0;
+        for (int g : fast) {
+            cap[g] = std::max<long long>(1, (groups[g].N + 7) / 8);
+            csum += b->cost_us[g];
+        }
         int used = 0;
-        std::vector<double> frac(G);
-        for (int g = 0; g < G; ++g) {
+        std::vector<double> frac(G, 0.0);
+        for (int g : fast) {
             const double want = std::max(1.0, total * b->cost_us[g] / std::max(csum, 1e-30));
             n_cta[g] = (int)std::min<long long>(cap[g], (long long)std::floor(want));
             n_cta[g] = std::max(1, n_cta[g]);
@@ -383,18 +431,17 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
             used += n_cta[g];
         }
         // hand out what is left by largest remainder (fixed order on ties)
-        std::vector<int> order(G);
-        std::iota(order.begin(), order.end(), 0);
+        std::vector<int> order = fast;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return frac[x] > frac[y]; });
-        for (int k = 0; used < total && k < 4 * G; ++k) {
-            const int g = order[k % G];
+        for (int k = 0; used < total && k < 4 * F; ++k) {
+            const int g = order[k % F];
             if (n_cta[g] < cap[g] && n_cta[g] < max_slots) {
                 ++n_cta[g];
                 ++used;
             }
         }
         total = 0;
-        for (int g = 0; g < G; ++g) {
+        for (int g : fast) {
             n_cta[g] = std::min(n_cta[g], max_slots);
             total += n_cta[g];
         }
@@ -414,7 +461,10 @@ int sdl_batch_create(sdl_ctx* c, const sdl_group* groups, int n_groups, int flag
             const sdl_group& q = groups[g];
             const int p = si == 0 ? q.p1 : q.p2, n = si == 0 ? q.n1 : q.n2;
             const int nf = n * n + p * n;
-            red[si * G + g] = ReduceDesc{b->part_f[g], b->part_d[g], n_cta[g], nf, b->red_f[g],
+            int slots = n_cta[g];
+            for (size_t i = 0; i < b->generic.size(); ++i)
+                if (b->generic[i] == g) slots = b->gslots[si + 1][i];
+            red[si * G + g] = ReduceDesc{b->part_f[g], b->part_d[g], slots, nf, b->red_f[g],
                                          b->red_d[g], rb};
             rb += (nf + 31) / 32;
             int keep = 0;
@@ -528,9 +578,10 @@ int sdl_batch_iterate(sdl_batch* b, double* rmse_out, void* stream) {
             Trace tr(c, kBatchGraph, st);
             if (cudaGraphLaunch(b->graph, st) != cudaSuccess) rc = SDL_ERR_CUDA;
         }
+        const int code_launches = (b->n_fast > 0 ? 1 : 0) + (int)b->generic.size();
         c->launches[kGram] += 1;
-        c->launches[kCodeD1] += 1;
-        c->launches[kCodeD2] += 1;
+        c->launches[kCodeD1] += code_launches;
+        c->launches[kCodeD2] += code_launches;
         c->launches[kReduce] += 2;
         c->launches[kSolve] += 2;
         c->launches[kRescale] += 1;

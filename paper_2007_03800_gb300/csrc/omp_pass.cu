@@ -754,8 +754,9 @@ constexpr int kMaxSmem = 200 * 1024;
 constexpr int kCtaSlotsPerSm = 8;
 constexpr int kGlobalSlots = 64;
 
+// plan_only: return the partial-sum slots the launch would write, launch nothing
 template <class Tl, int SIDE, class FS = RuntimeSizes>
-int launch_code_impl(const PassArgs& a0, cudaStream_t st, int num_sms) {
+int launch_code_impl(const PassArgs& a0, cudaStream_t st, int num_sms, bool plan_only = false) {
     PassArgs a = a0;
     const int nacc = (SIDE == kSideD1) ? a.n1 : a.n2;
     const int pacc = (SIDE == kSideD1) ? a.p1 : a.p2;
@@ -788,17 +789,16 @@ int launch_code_impl(const PassArgs& a0, cudaStream_t st, int num_sms) {
     const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms * bps));
     int slots = 0;
     if (SIDE != kCodeOnly) {
-        if (a.acc_in_smem) {
-            slots = grid;
-        } else {
-            slots = std::min(grid, kGlobalSlots);
+        slots = a.acc_in_smem ? grid : std::min(grid, kGlobalSlots);
+        if (plan_only) return slots;
+        if (!a.acc_in_smem) {
             a.n_slots = slots;
-            if (cudaMemsetAsync(a.part_f, 0, sizeof(float) * (size_t)slots * nf, st) != cudaSuccess)
+            if (cudaMemsetAsync(a.part_f, 0, sizeof(float) * (size_t)slots * nf, st) != cudaSuccess ||
+                cudaMemsetAsync(a.part_d, 0, sizeof(double) * 2 * (size_t)slots, st) != cudaSuccess)
                 return SDL_ERR_CUDA;
         }
-        if (!a.acc_in_smem &&
-            cudaMemsetAsync(a.part_d, 0, sizeof(double) * 2 * (size_t)slots, st) != cudaSuccess)
-            return SDL_ERR_CUDA;
+    } else if (plan_only) {
+        return 0;
     }
     kern<<<grid, threads, bytes, st>>>(a);
     if (cudaGetLastError() != cudaSuccess) return SDL_ERR_CUDA;
@@ -861,24 +861,25 @@ using Tile128x32 = Tile<16, 8, 8, 4, 4>; // n1 <= 128, n2 <= 32
 using Tile64 = Tile<8, 16, 8, 4, 4>;     // n1, n2 <= 64
 
 template <int SIDE>
-int dispatch_code(const PassArgs& a, cudaStream_t st, int num_sms) {
+int dispatch_code(const PassArgs& a, cudaStream_t st, int num_sms, bool plan_only = false) {
     const int n1 = a.n1, n2 = a.n2;
-    if (n1 <= 16 && n2 <= 16) return launch_code_impl<Tile16, SIDE>(a, st, num_sms);
-    if (n1 <= 24 && n2 <= 24) return launch_code_impl<Tile24, SIDE>(a, st, num_sms);
-    if (n1 <= 32 && n2 <= 32) return launch_code_impl<Tile32, SIDE>(a, st, num_sms);
+    if (n1 <= 16 && n2 <= 16) return launch_code_impl<Tile16, SIDE>(a, st, num_sms, plan_only);
+    if (n1 <= 24 && n2 <= 24) return launch_code_impl<Tile24, SIDE>(a, st, num_sms, plan_only);
+    if (n1 <= 32 && n2 <= 32) return launch_code_impl<Tile32, SIDE>(a, st, num_sms, plan_only);
     if (n1 <= 32 && n2 <= 128) {
         // the hyperspectral-shaped problem (16 x 64 signals, 32 x 128 atoms,
         // and s = 10) with its sizes fixed at compile time
         if (a.p1 == 16 && a.p2 == 64 && n1 == 32 && n2 == 128) {
             if (a.s == 10)
-                return launch_code_impl<Tile32x128, SIDE, FixedSizes<16, 64, 32, 128, 10>>(a, st,
-                                                                                          num_sms);
-            return launch_code_impl<Tile32x128, SIDE, FixedSizes<16, 64, 32, 128, 0>>(a, st, num_sms);
+                return launch_code_impl<Tile32x128, SIDE, FixedSizes<16, 64, 32, 128, 10>>(
+                    a, st, num_sms, plan_only);
+            return launch_code_impl<Tile32x128, SIDE, FixedSizes<16, 64, 32, 128, 0>>(a, st, num_sms,
+                                                                                     plan_only);
         }
-        return launch_code_impl<Tile32x128, SIDE>(a, st, num_sms);
+        return launch_code_impl<Tile32x128, SIDE>(a, st, num_sms, plan_only);
     }
-    if (n1 <= 128 && n2 <= 32) return launch_code_impl<Tile128x32, SIDE>(a, st, num_sms);
-    if (n1 <= 64 && n2 <= 64) return launch_code_impl<Tile64, SIDE>(a, st, num_sms);
+    if (n1 <= 128 && n2 <= 32) return launch_code_impl<Tile128x32, SIDE>(a, st, num_sms, plan_only);
+    if (n1 <= 64 && n2 <= 64) return launch_code_impl<Tile64, SIDE>(a, st, num_sms, plan_only);
     return SDL_ERR_UNSUPPORTED;
 }
 
@@ -905,6 +906,16 @@ int launch_code_pass(const PassArgs& a, int side, cudaStream_t st, int num_sms) 
         case kCodeOnly: return dispatch_code<kCodeOnly>(a, st, num_sms);
         case kSideD1: return dispatch_code<kSideD1>(a, st, num_sms);
         case kSideD2: return dispatch_code<kSideD2>(a, st, num_sms);
+        default: return SDL_ERR_ARG;
+    }
+}
+
+int launch_code_pass_generic(const PassArgs& a, int side, cudaStream_t st, int num_sms,
+                             bool plan_only) {
+    switch (side) {
+        case kCodeOnly: return dispatch_code<kCodeOnly>(a, st, num_sms, plan_only);
+        case kSideD1: return dispatch_code<kSideD1>(a, st, num_sms, plan_only);
+        case kSideD2: return dispatch_code<kSideD2>(a, st, num_sms, plan_only);
         default: return SDL_ERR_ARG;
     }
 }

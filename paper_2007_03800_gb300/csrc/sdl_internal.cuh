@@ -70,6 +70,11 @@ struct PassArgs {
 // Host launchers (omp_pass.cu).  They return the number of partial-sum
 // slots written (to be reduced), or a negative sdl_error.
 int launch_code_pass(const PassArgs& a, int side, cudaStream_t st, int num_sms);
+// The generic kernel alone (any supported shape, Y at any alignment); with
+// plan_only it returns the slot count the launch would write and launches
+// nothing (a batch sizes its reductions with it before capturing the graph).
+int launch_code_pass_generic(const PassArgs& a, int side, cudaStream_t st, int num_sms,
+                             bool plan_only = false);
 int launch_accumulate_pass(const PassArgs& a, int side, cudaStream_t st, int num_sms);
 // omp_fast.cu: compile-time-shape kernels; SDL_ERR_UNSUPPORTED when no
 // specialisation matches (the caller then uses the generic kernel).

@@ -110,11 +110,67 @@ def test_graph_replay_equals_direct_launches(gpu_ctx):
     assert torch.equal(results[0][-1], results[1][-1])
 
 
-def test_batch_rejects_shapes_without_specialisation(gpu_ctx):
-    Yg, D1g, D2g = to_gpu_problem(np.zeros((64, 16, 64)), *synth.init_dictionaries(16, 64, 32, 128))
+def test_batch_rejects_unsupported_shapes(gpu_ctx):
+    """n2 = 256 is beyond every coder (compiled tilings and the generic kernel)."""
+    Yg, D1g, D2g = to_gpu_problem(np.zeros((64, 16, 64)), *synth.init_dictionaries(16, 64, 32, 256))
     with pytest.raises(sdl.SDLError) as e:
         sdl.Batch(gpu_ctx, [dict(Y=Yg, D1=D1g, D2=D2g, s=10)])
     assert e.value.code == -7
+
+
+def hsi_group(N=700, seed=37):
+    """16 x 64 signals, D1 16 x 32, D2 64 x 128, s = 10: no compiled tiling.
+    Signals of the separable model at those shapes (30 dB): its normal matrices
+    are well conditioned, so the FP32 updates hold the 1e-4 dictionary bar (on
+    the hyperspectral-shaped data few D2 atoms are used and cond(M) ~ 6e4)."""
+    Y, *_ = synth.kron_model(N, 16, 64, 32, 128, 10, 30.0, seed=seed)
+    D1, D2 = synth.init_dictionaries(16, 64, 32, 128, seed=1)
+    return dict(Y=Y, D1=D1, D2=D2, s=10, eps=0.0)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_with_generic_shape_groups_matches_oracle(gpu_ctx, graph):
+    """A group whose shape has no compiled tiling is coded by the generic
+    kernel inside the batch iteration, beside compiled-tiling groups (and on
+    its own): in both runs every group's iteration matches the oracle and
+    the generic group's codes equal the per-call coder's; the compiled-tiling
+    groups replay bit for bit, the generic group (whose teams add their partial
+    sums with atomics, in no fixed order) to FP32 rounding."""
+    for groups in (make_groups(seed=6, N=(1200, 1000, 600)) + [hsi_group()], [hsi_group(seed=38)]):
+        G = len(groups)
+        results = []
+        for gr in (False, graph):
+            specs = to_specs(groups)
+            batch = sdl.Batch(gpu_ctx, specs, autotune=True, graph=gr)
+            assert batch.tuning()[-1]["shape_id"] == -1 and batch.tuning()[-1]["ctas"] == 0
+            rmse = torch.zeros(2 * G, dtype=torch.float64, device="cuda:0")
+            batch.iterate(rmse_out=rmse)
+            assert gpu_ctx.status() == 0
+            results.append([(sp["D1"].clone(), sp["D2"].clone(), sp["codes"].support.clone(),
+                             sp["codes"].coef.clone()) for sp in batch.groups] + [rmse.clone()])
+            r = rmse.cpu().numpy()
+            for g, (grp, sp) in enumerate(zip(groups, batch.groups)):
+                codes = sp["codes"]
+                check_iteration(grp["Y"], grp["D1"], grp["D2"], grp["s"],
+                                codes.support.cpu().numpy(), codes.nnz.cpu().numpy(),
+                                codes.coef.cpu().numpy(), sp["D1"].cpu().numpy(),
+                                sp["D2"].cpu().numpy(), r[2 * g:2 * g + 2],
+                                eps=grp["eps"] or None)
+            # coding only, with the updated dictionaries: the per-call coder's codes
+            batch.sparse_code()
+            assert gpu_ctx.status() == 0
+            sp = batch.groups[-1]
+            single = gpu_ctx.sparse_code(sp["Y"], sp["D1"], sp["D2"], sp["s"])
+            assert torch.equal(single.support, sp["codes"].support)
+            assert torch.equal(single.coef, sp["codes"].coef)
+            batch.close()
+        for a, b in zip(results[0][:G - 1], results[1][:G - 1]):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y)
+        assert torch.equal(results[0][-1][:2 * G - 2], results[1][-1][:2 * G - 2])
+        for x, y in zip(results[0][G - 1][:2], results[1][G - 1][:2]):    # generic group's D1, D2
+            assert (x - y).abs().max().item() < 1e-5
+        assert torch.allclose(results[0][-1][2 * G - 2:], results[1][-1][2 * G - 2:], rtol=1e-6, atol=0)
 
 
 @pytest.mark.parametrize("graph", [False, True])
