@@ -209,3 +209,33 @@ def test_fp32_hsi_shape_codes_match_oracle(prec_ctx, s, eps):
     check_codes(Y, D1, D2, s, out.support.cpu().numpy(), out.nnz.cpu().numpy(),
                 out.coef.cpu().numpy(), energy=out.res_energy.cpu().numpy(), eps=eps,
                 ref=ref).assert_ok()
+
+
+def test_hsi_full_size_properties(prec_ctx):
+    """The c3 workload at full size (50 000 hyperspectral-shaped 16x64 signals,
+    D1 16x32, D2 64x128, s = 10, the precision study's inputs and launch
+    configuration): sampled signals of the FP32 and the re-scored BF16 coder
+    match the oracle; after one FP32 iteration the dictionaries have unit
+    columns and the closed-form RMSE equals the explicit residual of the
+    returned (D1, D2, X)."""
+    Y, D1, D2 = hsi_problem(50_000, seed=31)
+    Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
+    rows = np.random.default_rng(7).choice(50_000, 250, replace=False)
+    ref = oracle.omp2d(Y[rows], D1, D2, 10)
+    for flags in (0, sdl.Context.PREC_BF16_CORR):
+        prec_ctx.set_precision(flags)
+        codes = prec_ctx.sparse_code(Yg, D1g, D2g, 10)
+        assert prec_ctx.status() == 0
+        check_codes(Y[rows], D1, D2, 10, codes.support.cpu().numpy()[rows],
+                    codes.nnz.cpu().numpy()[rows], codes.coef.cpu().numpy()[rows],
+                    codes.res_energy.cpu().numpy()[rows], ref=ref).assert_ok()
+    prec_ctx.set_precision(0)
+    rmse = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+    out = prec_ctx.iterate(Yg, D1g, D2g, 10, rmse_out=rmse)
+    assert prec_ctx.status() == 0
+    D1n, D2n = D1g.cpu().numpy().astype(np.float64), D2g.cpu().numpy().astype(np.float64)
+    assert np.allclose(np.linalg.norm(D1n, axis=0), 1.0, atol=1e-5)
+    assert np.allclose(np.linalg.norm(D2n, axis=0), 1.0, atol=1e-5)
+    explicit = oracle.rmse(Y, D1n, D2n, out.support.cpu().numpy().astype(np.int64),
+                           out.coef.cpu().numpy().astype(np.float64))
+    assert abs(rmse.cpu().numpy()[1] - explicit) / explicit < 2e-4
