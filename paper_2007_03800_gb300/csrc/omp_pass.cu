@@ -34,9 +34,11 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __host__ __device__ constexpr int align4(int x) { return (x + 3) & ~3; }
 
-template <int LI_, int LJ_, int RI_, int RJ_, int TW_>
+// Lane grid LI x LJ of a team of TW warps, each thread an RI x RJ block of the
+// n1 x n2 scores; CTA threads per block (the teams it holds: CTA / (32 TW)).
+template <int LI_, int LJ_, int RI_, int RJ_, int TW_, int CTA_ = 256>
 struct Tile {
-    static constexpr int LI = LI_, LJ = LJ_, RI = RI_, RJ = RJ_, TW = TW_;
+    static constexpr int LI = LI_, LJ = LJ_, RI = RI_, RJ = RJ_, TW = TW_, CTA = CTA_;
     static constexpr int T = 32 * TW;
     static constexpr int N1P = LI * RI, N2P = LJ * RJ;
     static_assert(LI * LJ == T, "the lane grid must cover the team");
@@ -217,7 +219,7 @@ struct FixedSizes {
 using RuntimeSizes = FixedSizes<0, 0, 0, 0, 0>;
 
 template <class Tl, int SIDE, class FS = RuntimeSizes>
-__global__ void __launch_bounds__(256) code_pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(Tl::CTA) code_pass_kernel(PassArgs a) {
     constexpr int T = Tl::T, TW = Tl::TW, RI = Tl::RI, RJ = Tl::RJ;
     constexpr int LI = Tl::LI, N1P = Tl::N1P, N2P = Tl::N2P;
     extern __shared__ __align__(16) float smem[];
@@ -761,7 +763,7 @@ int launch_code_impl(const PassArgs& a0, cudaStream_t st, int num_sms, bool plan
     const int nacc = (SIDE == kSideD1) ? a.n1 : a.n2;
     const int pacc = (SIDE == kSideD1) ? a.p1 : a.p2;
     const int nf = (SIDE == kCodeOnly) ? 0 : nacc * nacc + pacc * nacc;
-    int tpc = 256 / Tl::T;
+    int tpc = Tl::CTA / Tl::T;
     a.acc_in_smem = 1;
     size_t bytes = 0;
     for (;;) {
@@ -856,7 +858,8 @@ int launch_acc_impl(const PassArgs& a0, cudaStream_t st, int num_sms) {
 using Tile16 = Tile<4, 8, 4, 2, 1>;      // n1, n2 <= 16
 using Tile24 = Tile<4, 8, 6, 3, 1>;      // n1, n2 <= 24
 using Tile32 = Tile<4, 8, 8, 4, 1>;      // n1, n2 <= 32
-using Tile32x128 = Tile<2, 32, 16, 4, 2>; // n1 <= 32, n2 <= 128: 4 two-warp teams per CTA
+using Tile32x128 = Tile<4, 32, 8, 4, 4, 512>; // n1 <= 32, n2 <= 128: 4 four-warp teams per
+                                              // 512-thread CTA (16 warps per SM at 128 registers)
 using Tile128x32 = Tile<16, 8, 8, 4, 4>; // n1 <= 128, n2 <= 32
 using Tile64 = Tile<8, 16, 8, 4, 4>;     // n1, n2 <= 64
 
