@@ -858,7 +858,7 @@ int launch_acc_impl(const PassArgs& a0, cudaStream_t st, int num_sms) {
 using Tile16 = Tile<4, 8, 4, 2, 1>;      // n1, n2 <= 16
 using Tile24 = Tile<4, 8, 6, 3, 1>;      // n1, n2 <= 24
 using Tile32 = Tile<4, 8, 8, 4, 1>;      // n1, n2 <= 32
-using Tile32x128 = Tile<4, 32, 8, 4, 4, 512>; // n1 <= 32, n2 <= 128: 4 four-warp teams per
+using Tile32x128 = Tile<8, 16, 4, 8, 4, 512>; // n1 <= 32, n2 <= 128: 4 four-warp teams per
                                               // 512-thread CTA (16 warps per SM at 128 registers)
 using Tile128x32 = Tile<16, 8, 8, 4, 4>; // n1 <= 128, n2 <= 32
 using Tile64 = Tile<8, 16, 8, 4, 4>;     // n1, n2 <= 64
