@@ -121,6 +121,39 @@ __device__ __forceinline__ unsigned team_min_u32(unsigned v, unsigned* scratch, 
     }
 }
 
+// The team's smallest candidate pair index and the C0 value its owner holds:
+// each warp's minimum (candidates are distinct pair indices, so one lane
+// holds it) with its value, then the minimum over the warps.  Returns q
+// (0xffffffff when no thread has a candidate) and sets b.
+template <int TW>
+__device__ __forceinline__ unsigned team_min_pick(unsigned cand, float bc, float& b, unsigned* scratch,
+                                                  float* bscratch, int wit, int lane, int team) {
+    static_assert(TW <= 6, "one value slot per warp");
+    const unsigned wmin = __reduce_min_sync(kFull, cand);
+    const unsigned holder = __ballot_sync(kFull, cand == wmin && wmin != 0xffffffffu);
+    const float wb = __shfl_sync(kFull, bc, holder ? __ffs(holder) - 1 : 0);
+    if constexpr (TW == 1) {
+        b = wb;
+        return wmin;
+    } else {
+        if (lane == 0) {
+            scratch[wit] = wmin;
+            bscratch[wit] = wb;
+        }
+        team_sync<TW>(team);
+        unsigned r = scratch[0];
+        float rb = bscratch[0];
+#pragma unroll
+        for (int w = 1; w < TW; ++w)
+            if (scratch[w] < r) {
+                r = scratch[w];
+                rb = bscratch[w];
+            }
+        b = rb;
+        return r;
+    }
+}
+
 template <int TW>
 __device__ __forceinline__ float team_sum_f32(float v, float* scratch, int wit, int lane, int team) {
     v = warp_sum(v);
@@ -207,7 +240,8 @@ __device__ __noinline__ float rescore_dot(const float* __restrict__ w, const flo
 
 // misc area of the slab (32 words): [0,8) max scratch, [8,16) min scratch,
 // [16,24) sum scratch, 24 = broadcast b, 25 = accept flag.
-enum { kMiscMax = 0, kMiscMin = 8, kMiscSum = 16, kMiscB = 24, kMiscOk = 25 };
+// [26, 32) the C0 value of each warp's smallest candidate.
+enum { kMiscMax = 0, kMiscMin = 8, kMiscSum = 16, kMiscB = 24, kMiscOk = 25, kMiscPickB = 26 };
 
 // Signal and dictionary sizes fixed at compile time (0: taken from the call),
 // so that the contraction, re-scoring and epilogue loops of a frequent shape
@@ -444,38 +478,34 @@ __global__ void __launch_bounds__(Tl::CTA) code_pass_kernel(PassArgs a) {
                 if (Mu == 0u) break;  // every remaining score is exactly 0
                 const float Mf = __uint_as_float(Mu);
                 unsigned cand = 0xffffffffu;
+                float bc = 0.f;   // C0 at this thread's candidate
                 // only a thread whose own maximum is the team's holds a
                 // candidate: the others (mostly whole warps) skip the search
                 if (m == Mf) {
 #pragma unroll
                     for (int r = 0; r < RI; ++r)
 #pragma unroll
-                        for (int c = 0; c < RJ; ++c)
-                            if (fabsf(sc[r][c]) == Mf)
-                                cand = min(cand, (unsigned)(i0 + r + n1 * (j0 + c)));
+                        for (int c = 0; c < RJ; ++c) {
+                            const unsigned qe = (unsigned)(i0 + r + n1 * (j0 + c));
+                            if (fabsf(sc[r][c]) == Mf && qe < cand) {
+                                cand = qe;
+                                bc = c0[r][c];
+                            }
+                        }
                 }
-                const unsigned q = team_min_u32<TW>(cand, misc + kMiscMin, wit, lane, team);
+                // the pick and b_t = C0[q] arrive together; the owner masks it
+                float b;
+                const unsigned q = team_min_pick<TW>(cand, bc, b, misc + kMiscMin, miscf + kMiscPickB,
+                                                     wit, lane, team);
                 const int it = (int)(q % (unsigned)n1), jt = (int)(q / (unsigned)n1);
-                // owner of the picked entry hands out b_t = C0[q] and masks it
                 const int owner = it / RI + LI * (jt / RJ);
                 const int rt = it % RI, ct = jt % RJ;
-                float b = 0.f;
                 if (tau == owner) {
 #pragma unroll
                     for (int r = 0; r < RI; ++r)
 #pragma unroll
                         for (int c = 0; c < RJ; ++c)
-                            if (r == rt && c == ct) {
-                                b = c0[r][c];
-                                c0[r][c] = __int_as_float(0x7fc00000);
-                            }
-                }
-                if constexpr (TW == 1) {
-                    b = __shfl_sync(kFull, b, owner);
-                } else {
-                    if (tau == owner) miscf[kMiscB] = b;
-                    team_sync<TW>(team);
-                    b = miscf[kMiscB];
+                            if (r == rt && c == ct) c0[r][c] = __int_as_float(0x7fc00000);
                 }
                 // ---- Cholesky row + solves, warp 0 of the team
                 if (wit == 0) {
