@@ -200,7 +200,7 @@ __global__ void topk_kernel(const float* __restrict__ Z, int ldz, long long N, i
         return mask;
     };
     const unsigned m1 = select(k1);
-    const unsigned m2 = select(k2) & ~m1;
+    const unsigned m2 = k2 > k1 ? select(k2) & ~m1 : 0u;   // no check set: one bisection
     int base = 0;
     int32_t* o = out + (size_t)k * k2;
     for (int pass = 0; pass < 2; ++pass) {
