@@ -888,8 +888,12 @@ int launch_acc_impl(const PassArgs& a0, cudaStream_t st, int num_sms) {
 using Tile16 = Tile<4, 8, 4, 2, 1>;      // n1, n2 <= 16
 using Tile24 = Tile<4, 8, 6, 3, 1>;      // n1, n2 <= 24
 using Tile32 = Tile<4, 8, 8, 4, 1>;      // n1, n2 <= 32
-using Tile32x128 = Tile<8, 16, 4, 8, 4, 512>; // n1 <= 32, n2 <= 128: 4 four-warp teams per
-                                              // 512-thread CTA (16 warps per SM at 128 registers)
+// n1 <= 32, n2 <= 128: FP32 correlations on six four-warp teams per 768-thread
+// CTA (24 warps per SM at 80 registers, 8 x 4 blocks); correlations from the
+// tensor cores with FP32 re-scoring on four per 512-thread CTA (16 warps at
+// 128 registers, 4 x 8 blocks), where the re-scoring needs the registers
+using Tile32x128 = Tile<4, 32, 8, 4, 4, 768>;
+using Tile32x128R = Tile<8, 16, 4, 8, 4, 512>;
 using Tile128x32 = Tile<16, 8, 8, 4, 4>; // n1 <= 128, n2 <= 32
 using Tile64 = Tile<8, 16, 8, 4, 4>;     // n1, n2 <= 64
 
@@ -900,16 +904,20 @@ int dispatch_code(const PassArgs& a, cudaStream_t st, int num_sms, bool plan_onl
     if (n1 <= 24 && n2 <= 24) return launch_code_impl<Tile24, SIDE>(a, st, num_sms, plan_only);
     if (n1 <= 32 && n2 <= 32) return launch_code_impl<Tile32, SIDE>(a, st, num_sms, plan_only);
     if (n1 <= 32 && n2 <= 128) {
-        // the hyperspectral-shaped problem (16 x 64 signals, 32 x 128 atoms,
-        // and s = 10) with its sizes fixed at compile time
-        if (a.p1 == 16 && a.p2 == 64 && n1 == 32 && n2 == 128) {
-            if (a.s == 10)
-                return launch_code_impl<Tile32x128, SIDE, FixedSizes<16, 64, 32, 128, 10>>(
-                    a, st, num_sms, plan_only);
-            return launch_code_impl<Tile32x128, SIDE, FixedSizes<16, 64, 32, 128, 0>>(a, st, num_sms,
-                                                                                     plan_only);
-        }
-        return launch_code_impl<Tile32x128, SIDE>(a, st, num_sms, plan_only);
+        auto run = [&](auto tl) {
+            using Tl = decltype(tl);
+            // the hyperspectral-shaped problem (16 x 64 signals, 32 x 128
+            // atoms, and s = 10) with its sizes fixed at compile time
+            if (a.p1 == 16 && a.p2 == 64 && n1 == 32 && n2 == 128) {
+                if (a.s == 10)
+                    return launch_code_impl<Tl, SIDE, FixedSizes<16, 64, 32, 128, 10>>(a, st, num_sms,
+                                                                                      plan_only);
+                return launch_code_impl<Tl, SIDE, FixedSizes<16, 64, 32, 128, 0>>(a, st, num_sms,
+                                                                                 plan_only);
+            }
+            return launch_code_impl<Tl, SIDE>(a, st, num_sms, plan_only);
+        };
+        return a.c0ext ? run(Tile32x128R{}) : run(Tile32x128{});
     }
     if (n1 <= 128 && n2 <= 32) return launch_code_impl<Tile128x32, SIDE>(a, st, num_sms, plan_only);
     if (n1 <= 64 && n2 <= 64) return launch_code_impl<Tile64, SIDE>(a, st, num_sms, plan_only);
