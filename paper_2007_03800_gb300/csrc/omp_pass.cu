@@ -239,9 +239,9 @@ __device__ __noinline__ float rescore_dot(const float* __restrict__ w, const flo
 }
 
 // misc area of the slab (32 words): [0,8) max scratch, [8,16) min scratch,
-// [16,24) sum scratch, 24 = broadcast b, 25 = accept flag.
-// [26, 32) the C0 value of each warp's smallest candidate.
-enum { kMiscMax = 0, kMiscMin = 8, kMiscSum = 16, kMiscB = 24, kMiscOk = 25, kMiscPickB = 26 };
+// [16,24) sum scratch, 25 = accept flag, [26,32) the C0 value of each warp's
+// smallest candidate.
+enum { kMiscMax = 0, kMiscMin = 8, kMiscSum = 16, kMiscOk = 25, kMiscPickB = 26 };
 
 // Signal and dictionary sizes fixed at compile time (0: taken from the call),
 // so that the contraction, re-scoring and epilogue loops of a frequent shape
