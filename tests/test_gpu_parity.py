@@ -50,7 +50,8 @@ def iterate_and_check(ctx, Y, D1, D2, s, eps=None, ref=None, out=None, Ygpu=None
     (8, 8, 16, 16, 4, 4096),      # 8x8 Kronecker workload, 256 atom pairs
     (12, 12, 24, 24, 6, 3001),    # 12x12 patches, ragged count
     (16, 16, 32, 32, 8, 1003),
-    (16, 64, 32, 128, 10, 257),   # hyperspectral shape: 4-warp team
+    (16, 64, 32, 128, 10, 257),   # hyperspectral shape: compiled sizes, 768-thread CTAs
+    (8, 40, 16, 72, 6, 1111),     # the same tiling with run-time sizes, ragged 16 x 72 and count
     (6, 10, 12, 20, 5, 999),      # p1 != p2, n1 != n2
     (8, 8, 6, 6, 3, 500),         # undercomplete
     (8, 8, 16, 16, 1, 777),       # s = 1
@@ -112,6 +113,8 @@ def test_error_driven_mode(gpu_ctx):
     (12, 12, 24, 24, 6, 2000),
     (16, 64, 32, 128, 10, 600),
     (6, 10, 12, 20, 5, 999),
+    (8, 16, 20, 48, 5, 700),     # n2 > 32: the large solve, one output per thread
+    (8, 40, 16, 72, 6, 800),     # the large solve's 4 x 4 blocks over a ragged 40 x 72
 ])
 @pytest.mark.parametrize("side", [1, 2])
 def test_update_matches_oracle(gpu_ctx, p1, p2, n1, n2, s, N, side):
