@@ -69,16 +69,28 @@ def test_split_bf16_correlation_error_within_bound(prec_ctx):
     assert err.max() < 2.0 ** -7 * np.linalg.norm(Y, axis=(1, 2)).max() / 50
 
 
-def test_bf16_rescored_picks_match_oracle(prec_ctx):
-    Y, D1, D2 = hsi_problem(257)
-    ref = oracle.omp2d(Y, D1, D2, 10)
+@pytest.mark.parametrize("shape", ["hsi", "runtime"])
+def test_bf16_rescored_picks_match_oracle(prec_ctx, shape):
+    """Split-BF16 correlations with FP32 re-scoring give FP32 picks: at the
+    16x64 / 32x128 shape (compiled sizes) and at 8x40 / 16x72 (the same
+    tiling with run-time sizes, ragged pairs)."""
+    if shape == "hsi":
+        Y, D1, D2 = hsi_problem(257)
+        s = 10
+    else:
+        Y = np.random.default_rng(77).standard_normal((333, 8, 40))
+        D1, D2 = synth.init_dictionaries(8, 40, 16, 72, seed=1)
+        s = 6
+    ref = oracle.omp2d(Y, D1, D2, s)
     Yg, D1g, D2g = to_gpu_problem(Y, D1, D2)
     prec_ctx.set_precision(sdl.Context.PREC_BF16_CORR)
-    out = prec_ctx.sparse_code(Yg, D1g, D2g, 10)
+    out = prec_ctx.sparse_code(Yg, D1g, D2g, s)
     assert prec_ctx.status() == 0
     assert prec_ctx.precision_stats() > 0
-    check_codes(Y, D1, D2, 10, out.support.cpu().numpy(), out.nnz.cpu().numpy(),
+    check_codes(Y, D1, D2, s, out.support.cpu().numpy(), out.nnz.cpu().numpy(),
                 out.coef.cpu().numpy(), ref=ref).assert_ok()
+    if shape != "hsi":
+        return
     # without re-scoring (a diagnostic mode) the split-BF16 picks carry no
     # guarantee, but the split keeps C0 within ~1e-4 ||Y||: nearly all agree
     prec_ctx.set_precision(sdl.Context.PREC_BF16_CORR | sdl.Context.PREC_NO_RESCORE)
