@@ -921,7 +921,9 @@ def study_nsweep(args):
 def study_gemm(args):
     """The tcgen05 BF16 GEMM on the shapes the library runs it at: the split
     correlations of the 50k hyperspectral-shaped signals (three operand pairs,
-    M = 50000, N = n1 n2 = 4096, K = p1 p2 = 1024), the same with one pair,
+    M = 50000, N = n1 n2 = 4096, K = p1 p2 = 1024, summed in one accumulator
+    by one launch as the coding pass runs it, and as three accumulating
+    launches), the same with one pair,
     and the support network's forward GEMMs at a 65536-signal chunk; first a
     16384-row correlation GEMM (C = 268 MB, > L2), the case the kernel's
     profile is captured on.  Device time (CUDA events, median of steps) and
@@ -934,16 +936,21 @@ def study_gemm(args):
     peak = float(measured_peaks().get("bf16_tflops", 1900.0))
     out = {}
     g = torch.Generator(device=dev).manual_seed(0)
-    for name, (M, N, K, terms) in {"corr_16384x4096x1024": (16384, 4096, 1024, 1),
-                                   "corr_split_50000x4096x1024x3": (50000, 4096, 1024, 3),
-                                   "corr_50000x4096x1024": (50000, 4096, 1024, 1),
-                                   "mlp_fwd1_65536x512x144": (65536, 512, 144, 1),
-                                   "mlp_fwd2_65536x576x512": (65536, 576, 512, 1)}.items():
+    for name, (M, N, K, terms, fused) in {
+            "corr_16384x4096x1024": (16384, 4096, 1024, 1, False),
+            "corr_split_50000x4096x1024x3_one_launch": (50000, 4096, 1024, 3, True),
+            "corr_split_50000x4096x1024x3": (50000, 4096, 1024, 3, False),
+            "corr_50000x4096x1024": (50000, 4096, 1024, 1, False),
+            "mlp_fwd1_65536x512x144": (65536, 512, 144, 1, False),
+            "mlp_fwd2_65536x576x512": (65536, 576, 512, 1, False)}.items():
         A = [torch.randn(M, K, device=dev, generator=g).to(torch.bfloat16) for _ in range(terms)]
         B = [torch.randn(N, K, device=dev, generator=g).to(torch.bfloat16) for _ in range(terms)]
         C = torch.empty(M, N, device=dev)
 
         def run():
+            if fused:
+                sdl.gemm_bf16_terms(ctx, A, B, C=C)
+                return
             sdl.gemm_bf16(ctx, A[0], B[0], C=C)
             for t in range(1, terms):
                 sdl.gemm_bf16(ctx, A[t], B[t], C=C, accumulate=True)
@@ -961,7 +968,7 @@ def study_gemm(args):
         med = statistics.median(ms)
         tf = 2.0 * M * N * K * terms / (med / 1e3) / 1e12
         out[name] = {"ms": med, "tflops": tf, "frac_of_measured_bf16": tf / peak,
-                     "launches": terms}
+                     "launches": 1 if fused else terms}
         del A, B, C
     ctx.check()
     ctx.close()

@@ -296,6 +296,21 @@ int sdl_gemm_bf16(sdl_ctx* ctx, const void* A, int lda, const void* B, int ldb, 
                   int ldpre, void* stream);
 
 /*
+ * sdl_gemm_bf16_terms - the same GEMM over the sum of `terms` (1 to 3)
+ *   operand pairs in one FP32 accumulator:
+ *   out = act(alpha * sum_t A[t] B[t]^T + bias).
+ * A and B are HOST arrays of `terms` device pointers; every A[t] is M x K
+ * with leading dimension lda and every B[t] is N x K with ldb (the rules of
+ * sdl_gemm_bf16 apply to each).  This is the split-BF16 correlation product
+ * hi*hi + hi*lo + lo*hi of the BF16 precision mode.  SDL_ERR_ARG for terms
+ * outside 1..3 or a null or misaligned pointer.
+ */
+int sdl_gemm_bf16_terms(sdl_ctx* ctx, const void* const* A, int lda, const void* const* B,
+                        int ldb, int terms, int M, int N, int K, float alpha, const float* bias,
+                        int act, float* C, int ldc, int accumulate, void* Cb, int ldcb, void* Ct,
+                        int ldct, float* pre, int ldpre, void* stream);
+
+/*
  * Precision modes (an extension beyond the paper; default SDL_PREC_FP32).
  *  SDL_PREC_BF16_CORR: the correlations C0 = D1^T Y_k D2 of a coding pass come
  *    from ONE tensor-core GEMM of the vectorised signals with the Kronecker

@@ -172,16 +172,28 @@ __host__ __device__ constexpr uint32_t instr_desc() {
            ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32]) {
+// 64 consecutive accumulator columns of this thread's TMEM lane (one load
+// per 64 columns: the load's latency is paid half as often as with 32); the
+// wait follows at once, so v is complete when the call returns
+__device__ __forceinline__ void tmem_ld64(uint32_t ta, uint32_t (&v)[64]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-        "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
-        "%26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {"
+        "%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, "
+        "%19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, "
+        "%36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, "
+        "%53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63 "
+        "}, [%64];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
           "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
           "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+          "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]),
+          "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]),
+          "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]),
+          "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+          "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]),
+          "=r"(v[62]), "=r"(v[63])
         : "r"(ta));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -321,20 +333,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int m0 = (int)(t / nt) * BM, n0 = (int)(t % nt) * BN;
             const int row0 = m0 + quarter * 32;    // first output row of this warp
             const int m = row0 + lane;
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), v);
-                if (c0 + 32 == BN) {
+            for (int c64 = 0; c64 < BN; c64 += 64) {
+                uint32_t v[64];
+                tmem_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c64), v);
+                if (c64 + 64 == BN) {
                     // the whole accumulator has been read: hand it back
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acc_empty[b]);
                 }
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int c0 = c64 + 32 * h;   // this 32-column block
                 float x[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int n = n0 + c0 + j;
-                    x[j] = epi.alpha * __uint_as_float(v[j]);
+                    x[j] = epi.alpha * __uint_as_float(v[32 * h + j]);
                     if (epi.bias && n < N) x[j] += epi.bias[n];
                 }
                 if (epi.tma) {
@@ -463,6 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (n < N) epi.Ct[(size_t)n * epi.ldct + m] = __float2bfloat16_rn(x[j]);
                     }
                 }
+              }
             }
         }
         // the output stores have left shared memory and are complete
@@ -691,4 +707,17 @@ extern "C" int sdl_gemm_bf16(sdl_ctx* c, const void* A, int lda, const void* B, 
     if (act == 2) return SDL_ERR_ARG;   // the GELU-derivative mode is internal
     return tc_gemm(A, lda, B, ldb, M, N, K, alpha, bias, act, C, ldc, accumulate, Cb, ldcb, Ct,
                    ldct, pre, ldpre, c->err, (cudaStream_t)stream, nullptr, 0);
+}
+
+extern "C" int sdl_gemm_bf16_terms(sdl_ctx* c, const void* const* A, int lda,
+                                   const void* const* B, int ldb, int terms, int M, int N, int K,
+                                   float alpha, const float* bias, int act, float* C, int ldc,
+                                   int accumulate, void* Cb, int ldcb, void* Ct, int ldct,
+                                   float* pre, int ldpre, void* stream) {
+    if (!c) return SDL_ERR_ARG;
+    DeviceGuard guard(c->device);
+    if (act == 2) return SDL_ERR_ARG;
+    return sdl::tc_gemm_terms(A, lda, B, ldb, terms, M, N, K, alpha, bias, act, C, ldc,
+                              accumulate, Cb, ldcb, Ct, ldct, pre, ldpre, c->err,
+                              (cudaStream_t)stream, nullptr, 0);
 }

@@ -57,6 +57,8 @@ SIGNATURES = {
     "sdl_psnr": [_P, _P, _L, _F, _P, _P],
     "sdl_gemm_bf16": [_P, _P, _I, _P, _I, _I, _I, _I, _F, _P, _I, _P, _I, _I, _P, _I, _P, _I,
                       _P, _I, _P],
+    "sdl_gemm_bf16_terms": [_P, _P, _I, _P, _I, _I, _I, _I, _I, _F, _P, _I, _P, _I, _I, _P, _I,
+                            _P, _I, _P, _I, _P],
     "sdl_mlp_create": [_P, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_P)],
     "sdl_mlp_destroy": [_P],
     "sdl_mlp_set_weights": [_P, _P, _P, _P, _P],
@@ -616,6 +618,39 @@ def gemm_bf16(ctx: Context, A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0
         Cb.stride(0) if Cb is not None else 0, _ptr(Ct), Ct.stride(0) if Ct is not None else 0,
         _ptr(pre), pre.stride(0) if pre is not None else 0, _stream(stream))
     _check(rc, "sdl_gemm_bf16")
+    return C
+
+
+def gemm_bf16_terms(ctx: Context, A, B, alpha: float = 1.0, bias=None, act: int = 0, C=None,
+                    accumulate: bool = False, Cb=None, Ct=None, pre=None, stream=None):
+    """``sdl_gemm_bf16_terms``: act(alpha sum_t A[t] B[t]^T + bias) in one
+    accumulator, A and B sequences of 1 to 3 BF16 tensors of equal shapes and
+    row strides (the rules of :func:`gemm_bf16` for each)."""
+    A, B = list(A), list(B)
+    if not A or len(A) != len(B):
+        raise ValueError("A and B must hold the same number (1 to 3) of operands")
+    M, K = A[0].shape
+    N = B[0].shape[0]
+    for t in A + B:
+        if t.dtype != torch.bfloat16 or t.stride(1) != 1:
+            raise ValueError("operands must be BF16 with contiguous rows")
+    for t in A:
+        if tuple(t.shape) != (M, K) or t.stride(0) != A[0].stride(0):
+            raise ValueError("every A[t] must share shape and row stride")
+    for t in B:
+        if tuple(t.shape) != (N, K) or t.stride(0) != B[0].stride(0):
+            raise ValueError("every B[t] must share shape and row stride")
+    if C is None and Cb is None and Ct is None and pre is None:
+        C = torch.empty((M, N), dtype=torch.float32, device=A[0].device)
+    pa = (ctypes.c_void_p * len(A))(*[t.data_ptr() for t in A])
+    pb = (ctypes.c_void_p * len(B))(*[t.data_ptr() for t in B])
+    rc = ctx._lib.sdl_gemm_bf16_terms(
+        ctx._h, ctypes.cast(pa, ctypes.c_void_p), A[0].stride(0), ctypes.cast(pb, ctypes.c_void_p),
+        B[0].stride(0), len(A), M, N, K, float(alpha), _ptr(bias), int(act), _ptr(C),
+        C.stride(0) if C is not None else 0, int(bool(accumulate)), _ptr(Cb),
+        Cb.stride(0) if Cb is not None else 0, _ptr(Ct), Ct.stride(0) if Ct is not None else 0,
+        _ptr(pre), pre.stride(0) if pre is not None else 0, _stream(stream))
+    _check(rc, "sdl_gemm_bf16_terms")
     return C
 
 

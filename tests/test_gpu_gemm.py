@@ -95,3 +95,39 @@ def test_gemm_ragged_k_ignores_row_padding(gpu_ctx):
     assert gpu_ctx.status() == 0
     ref = A[:, :K].double().numpy() @ B[:, :K].double().numpy().T
     assert np.abs(C.cpu().numpy() - ref).max() < 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("M,N,K,terms", [(1000, 4096, 1024, 3), (300, 200, 192, 2), (77, 13, 8, 3),
+                                         (256, 384, 512, 1)])
+def test_gemm_terms_sum_in_one_accumulator(gpu_ctx, M, N, K, terms):
+    """sdl_gemm_bf16_terms: the sum of 1 to 3 products in one accumulator
+    (plain FP32 output, an accumulating one with bias and GELU, and the BF16
+    copy) against the FP64 sum of the same BF16-rounded operands."""
+    ops = [(bf16_pair((M, K), 20 + t), bf16_pair((N, K), 40 + t)) for t in range(terms)]
+    A = [a for (a, _), _ in ops]
+    B = [b for _, (b, _) in ops]
+    ref = sum(an @ bn.T for (_, an), (_, bn) in ops)
+    C = sdl.gemm_bf16_terms(gpu_ctx, A, B)
+    bias = torch.randn(N, generator=torch.Generator().manual_seed(11))
+    C2 = torch.full((M, N), -1.5, device="cuda:0")
+    Cb = torch.empty((M, N + (-N) % 8), dtype=torch.bfloat16, device="cuda:0")[:, :N]
+    sdl.gemm_bf16_terms(gpu_ctx, A, B, alpha=0.5, bias=bias.cuda(), act=1, C=C2,
+                        accumulate=True, Cb=Cb)
+    assert gpu_ctx.status() == 0
+    scale = np.abs(ref).max()
+    assert np.abs(C.cpu().numpy() - ref).max() < 2e-5 * scale
+    z = 0.5 * ref + bias.double().numpy()[None, :]
+    g = 0.5 * z * (1.0 + torch.special.erf(torch.from_numpy(z / math.sqrt(2.0))).numpy())
+    assert np.abs(C2.cpu().numpy() - (g - 1.5)).max() < 1e-4 * (np.abs(g).max() + 1.5)
+    assert np.abs(Cb.float().cpu().numpy() - g).max() < 1e-2 * np.abs(g).max()
+
+
+def test_gemm_terms_rejects_bad_counts(gpu_ctx):
+    """Four operand pairs, or lists of unequal length, are argument errors
+    checked on the host before any launch."""
+    A = [torch.zeros((128, 64), dtype=torch.bfloat16, device="cuda:0") for _ in range(4)]
+    with pytest.raises(sdl.SDLError):
+        sdl.gemm_bf16_terms(gpu_ctx, A, A)
+    with pytest.raises(ValueError):
+        sdl.gemm_bf16_terms(gpu_ctx, A[:2], A[:1])
+    assert gpu_ctx.status() == 0
