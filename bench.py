@@ -923,7 +923,9 @@ def study_gemm(args):
     correlations of the 50k hyperspectral-shaped signals (three operand pairs,
     M = 50000, N = n1 n2 = 4096, K = p1 p2 = 1024, summed in one accumulator
     by one launch as the coding pass runs it, and as three accumulating
-    launches), the same with one pair,
+    launches), the same with one pair (and at K = 512 and 3072: the time per
+    round of tiles against K shows whether the main loop or the per-tile
+    epilogue sets the pace),
     and the support network's forward GEMMs at a 65536-signal chunk; first a
     16384-row correlation GEMM (C = 268 MB, > L2), the case the kernel's
     profile is captured on.  Device time (CUDA events, median of steps) and
@@ -934,6 +936,7 @@ def study_gemm(args):
     dev = torch.device("cuda:0")
     ctx = sdl.Context(0)
     peak = float(measured_peaks().get("bf16_tflops", 1900.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     out = {}
     g = torch.Generator(device=dev).manual_seed(0)
     for name, (M, N, K, terms, fused) in {
@@ -941,6 +944,8 @@ def study_gemm(args):
             "corr_split_50000x4096x1024x3_one_launch": (50000, 4096, 1024, 3, True),
             "corr_split_50000x4096x1024x3": (50000, 4096, 1024, 3, False),
             "corr_50000x4096x1024": (50000, 4096, 1024, 1, False),
+            "corr_50000x4096x512": (50000, 4096, 512, 1, False),
+            "corr_50000x4096x3072": (50000, 4096, 3072, 1, False),
             "mlp_fwd1_65536x512x144": (65536, 512, 144, 1, False),
             "mlp_fwd2_65536x576x512": (65536, 576, 512, 1, False)}.items():
         A = [torch.randn(M, K, device=dev, generator=g).to(torch.bfloat16) for _ in range(terms)]
@@ -967,8 +972,14 @@ def study_gemm(args):
             ms.append(a.elapsed_time(b))
         med = statistics.median(ms)
         tf = 2.0 * M * N * K * terms / (med / 1e3) / 1e12
+        # time per round of output tiles (one tile per SM; the launcher's
+        # 128 x 256 tiles when N is a multiple of 256 and they fill the SMs)
+        mb = -(-M // 128)
+        bn = 256 if N % 256 == 0 and mb * (N // 256) >= sms else 128
+        rounds = -(-(mb * -(-N // bn)) // sms)
         out[name] = {"ms": med, "tflops": tf, "frac_of_measured_bf16": tf / peak,
-                     "launches": 1 if fused else terms}
+                     "launches": 1 if fused else terms,
+                     "us_per_tile_round": med * 1e3 / rounds / (1 if fused else terms)}
         del A, B, C
     ctx.check()
     ctx.close()
