@@ -77,6 +77,10 @@ def test_host_argument_errors_without_gpu(lib):
                                  None, None) == -1
     assert lib.sdl_ortho_sparse_code(None, None, 8, 8, 10, None, None, 4, 0.0, None, None, None,
                                      None, None) == -1
+    assert lib.sdl_gemm_bf16(None, None, 64, None, 64, 128, 128, 64, 1.0, None, 0, None, 0, 0,
+                             None, 0, None, 0, None, 0, None) == -1
+    assert lib.sdl_gemm_bf16_terms(None, None, 64, None, 64, 2, 128, 128, 64, 1.0, None, 0, None,
+                                   0, 0, None, 0, None, 0, None, 0, None) == -1
     assert lib.sdl_create(None, 0) == -1
     assert lib.sdl_destroy(None) == 0
     assert lib.sdl_strerror(-4) == b"normal matrix not positive definite"
@@ -106,3 +110,17 @@ def test_binding_constants_match_the_header():
     ctx_cls = sdl.Context
     for name in ("PREC_FP32", "PREC_BF16_CORR", "PREC_NO_RESCORE", "PREC_FP64_SOLVE"):
         assert getattr(ctx_cls, name) == defs["SDL_" + name], name
+
+
+def test_summed_gemm_binding_checks_operands_on_the_host():
+    """gemm_bf16_terms rejects operand lists of unequal length, empty lists,
+    non-BF16 operands and pairs of differing shapes before any library call."""
+    import torch
+
+    from paper_2007_03800_gb300 import sdl
+    a = torch.zeros((128, 64), dtype=torch.bfloat16)
+    b = torch.zeros((96, 64), dtype=torch.bfloat16)
+    for A, B in (([a, a], [b]), ([], []), ([a.float()], [b]), ([a, a[:, :32]], [b, b]),
+                 ([a, a], [b, b[:64]])):
+        with pytest.raises(ValueError):
+            sdl.gemm_bf16_terms(None, A, B)
